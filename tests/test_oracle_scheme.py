@@ -1,0 +1,316 @@
+"""Scheme-level pins of the CPU oracle: what the paper and the mathematics fix.
+
+  * lake at rest preserved to round-off (Prop. in Sec. 2.1 and Sec. 3; Tables 1-3 double rows)
+  * the limiter returns V^mod = 0 exactly at rest and changes smooth data by O(dx^4) (end of Sec. 2.2)
+  * fifth-order truncation of the semi-discrete operator and fifth-order convergence of full runs
+    (Ex. 4.1 and 4.6)
+  * mirror symmetry of the upwind reconstruction (Sec. 2.1: the f'(u) < 0 case is the mirror image)
+  * x <-> y transpose symmetry of the dimension-by-dimension 2D scheme (Sec. 3)
+  * 2D data invariant in y reproduce the 1D scheme
+  * mass conservation where the scheme conserves it exactly
+  * Ex. 4.8 contour ranges as a loose check
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2208_01260_gb300 import scenarios as S
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def grid_of(orc, s):
+    if s.dim == 1:
+        return orc.make_grid(s.nx, 1, s.x0, s.x1, bc_x=s.bc_x)
+    return orc.make_grid(s.nx, s.ny, s.x0, s.x1, s.y0, s.y1, s.bc_x, s.bc_y)
+
+
+def state_of(orc, s):
+    if s.dim == 1:
+        return orc.to_state1d(s.h, s.hu, s.b, s.deriv)
+    return orc.to_state2d(s.h, s.hu, s.hv, s.b, s.deriv)
+
+
+# ------------------------------------------------------------------------------------------------
+# well-balance
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("step,key", [(False, "table1_ex42_smooth_double"), (True, "table2_ex42_step_double")])
+def test_lake_at_rest_1d_ex42(orc, step, key):
+    s = S.ex42(200, step=step)
+    g, p = grid_of(orc, s), orc.make_params()
+    st, stat = state_of(orc, s)
+    out, t, n = orc.run1d(g, p, st, stat, 0.5)
+    assert abs(t - 0.5) < 1e-14
+    e_h = np.abs(out[0] - 10.0)
+    e_m = np.abs(out[1])
+    ref = GOLD[key]
+    # round-off level: within two decades of the paper's double-precision row, and below 1e-12
+    assert e_h.max() < max(100 * ref["h_Linf"], 1e-12)
+    assert e_m.max() < max(100 * ref["hu_Linf"], 1e-12)
+    assert e_h.mean() < 100 * ref["h_L1"] + 1e-13
+
+
+def test_lake_at_rest_2d_ex47(orc):
+    s = S.ex47(100)
+    g, p = grid_of(orc, s), orc.make_params()
+    st, stat = state_of(orc, s)
+    out, t, n = orc.run2d(g, p, st, stat, 0.1)
+    ref = GOLD["table3_ex47_double"]
+    assert np.abs(out[0] - 1.0).max() < max(100 * ref["h_Linf"], 1e-13)
+    assert np.abs(out[1]).max() < max(100 * ref["hu_Linf"], 1e-13)
+    assert np.abs(out[2]).max() < max(100 * ref["hv_Linf"], 1e-13)
+
+
+def test_lake_at_rest_2d_reflective_bumps(orc):
+    s = S.bumps2d(64, 48, strip=0.0)
+    g, p = grid_of(orc, s), orc.make_params()
+    st, stat = state_of(orc, s)
+    cur = st
+    for _ in range(10):
+        cur = orc.rk3_step2d(g, p, orc.cfl_dt2d(g, p, cur, stat), cur, stat)
+    assert max(np.abs(cur[0] - 1).max(), np.abs(cur[1]).max(), np.abs(cur[2]).max()) < 1e-12
+
+
+def test_limiter_exact_zero_at_rest(orc):
+    s = S.bumps2d(32, 24, strip=0.0)
+    g, p = grid_of(orc, s), orc.make_params()
+    st, stat = state_of(orc, s)
+    mod = orc.limiter2d(g, p, st, stat)
+    for m in mod:
+        assert np.all(m == 0.0)
+    s1 = S.perturbed1d(lake=True)
+    st1, stat1 = state_of(orc, s1)
+    for m in orc.limiter1d(grid_of(orc, s1), p, st1, stat1):
+        assert np.all(m == 0.0)
+
+
+# ------------------------------------------------------------------------------------------------
+# accuracy
+# ------------------------------------------------------------------------------------------------
+def _exact_rhs_1d(x, phase):
+    sp = pytest.importorskip("sympy")
+    X = sp.symbols("x")
+    tp = 2 * sp.pi
+    h = 5 + sp.exp(sp.cos(tp * (X - phase)))
+    m = sp.sin(sp.cos(tp * (X - phase)))
+    b = sp.sin(sp.pi * (X - phase)) ** 2
+    eta = h + b
+    g = sp.Float(9.812)
+    R0 = -sp.diff(m, X)
+    R1 = -sp.diff(m ** 2 / h + g / 2 * (eta ** 2 - 2 * eta * b), X) - g * eta * sp.diff(b, X)
+    out = []
+    for r in (R0, R1, sp.diff(R0, X), sp.diff(R1, X)):
+        out.append(sp.lambdify(X, r, "numpy")(x))
+    return out
+
+
+@pytest.mark.parametrize("linear", [1, 0])
+def test_rhs_truncation_order_1d(orc, linear):
+    # dU/dt = -F_x + S and dV/dt = (dU/dt)_x: the semi-discrete operator is fifth order (Sec. 2.1).
+    phase = 0.37
+    errs = []
+    ns = [50, 100, 200, 400]
+    for n in ns:
+        s = S.accuracy1d(n, phases=(phase,) * 3)
+        g, p = grid_of(orc, s), orc.make_params(linear_weights=linear)
+        st, stat = state_of(orc, s)
+        R, a = orc.rhs1d(g, p, st, stat)
+        E = _exact_rhs_1d(orc.node_coords(g), phase)
+        errs.append([np.abs(R[q] - E[q]).max() for q in range(4)])
+    errs = np.array(errs)
+    order = np.log2(errs[-2] / errs[-1])
+    assert np.all(order[:2] > 4.7), order
+    assert np.all(order[2:] > 4.5), order
+
+
+def test_convergence_order_1d_full_runs(orc):
+    # Config 2 style: Ex. 4.1 data, t = 0.1, dt ~ dx^(5/3) so RK3 error is O(dx^5); self-refinement.
+    def run(n, n0=50):
+        s = S.accuracy1d(n)
+        g, p = grid_of(orc, s), orc.make_params()
+        st, stat = state_of(orc, s)
+        dx = 1.0 / n
+        def dtf(cur):
+            return 0.6 * dx / orc.alpha1d(g, p, cur, stat) * (dx / (1.0 / n0)) ** (2.0 / 3.0)
+        return orc.run1d(g, p, st, stat, 0.1, dt_fn=dtf)[0]
+    res = {n: run(n) for n in (200, 400, 800)}
+    e200 = [np.abs(res[200][q] - res[400][q][::2]).mean() for q in range(2)]
+    e400 = [np.abs(res[400][q] - res[800][q][::2]).mean() for q in range(2)]
+    order = [math.log2(a / b) for a, b in zip(e200, e400)]
+    assert min(order) > 4.6, order
+
+
+def _exact_rhs_2d_ex46(X, Y):
+    sp = pytest.importorskip("sympy")
+    x, y = sp.symbols("x y")
+    tp = 2 * sp.pi
+    b = sp.sin(tp * x) + sp.sin(tp * y)
+    h = 10 + sp.exp(sp.sin(tp * x)) * sp.cos(tp * y)
+    m = sp.sin(sp.cos(tp * x)) * sp.sin(tp * y)
+    w = sp.cos(tp * x) * sp.cos(sp.sin(tp * y))
+    eta = h + b
+    g = sp.Float(9.812)
+    pres = g / 2 * (eta ** 2 - 2 * eta * b)
+    F1 = [m, m * m / h + pres, m * w / h]
+    F2 = [w, m * w / h, w * w / h + pres]
+    Sx = [0, -g * eta * sp.diff(b, x), -g * eta * sp.diff(b, y)]
+    R = [-sp.diff(F1[c], x) - sp.diff(F2[c], y) + Sx[c] for c in range(3)]
+    exprs = R + [sp.diff(r, x) for r in R] + [sp.diff(r, y) for r in R]
+    return [np.broadcast_to(sp.lambdify((x, y), e, "numpy")(X, Y), X.shape) for e in exprs]
+
+
+def test_rhs_truncation_order_2d_ex46(orc):
+    # Ex. 4.6 data: U equations fifth order; V, Q equations at least fourth (the mixed terms of
+    # eq. (mixed) are fourth-order interface values).
+    errs = []
+    for n in (40, 80):
+        s = S.ex46(n)
+        g, p = grid_of(orc, s), orc.make_params()
+        st, stat = state_of(orc, s)
+        R, a = orc.rhs2d(g, p, st, stat)
+        x, y = orc.node_coords(g)
+        X, Y = np.meshgrid(x, y)
+        E = _exact_rhs_2d_ex46(X, Y)
+        errs.append([np.abs(R[q] - E[q]).max() for q in range(9)])
+    errs = np.array(errs)
+    order = np.log2(errs[0] / errs[1])
+    assert np.all(order[:3] > 4.5), order
+    assert np.all(order[3:] > 3.7), order
+
+
+def test_limiter_changes_smooth_data_by_dx4(orc):
+    # End of Sec. 2.2: |V^mod - V| = O(dx^4) for smooth solutions.
+    errs = []
+    for n in (200, 400, 800):
+        s = S.accuracy1d(n)
+        g, p = grid_of(orc, s), orc.make_params()
+        st, stat = state_of(orc, s)
+        M = orc.limiter1d(g, p, st, stat)
+        errs.append(max(np.abs(M[0] - st[2]).max(), np.abs(M[1] - st[3]).max()))
+    assert math.log2(errs[1] / errs[2]) > 3.7, errs
+
+
+# ------------------------------------------------------------------------------------------------
+# symmetries and reductions
+# ------------------------------------------------------------------------------------------------
+def _mirror_runs(orc, s, steps):
+    g, p = grid_of(orc, s), orc.make_params()
+    st, stat = state_of(orc, s)
+    par = [1, -1, -1, 1]
+    mst = [par[q] * st[q][::-1].copy() for q in range(4)]
+    mstat = [stat[0][::-1].copy(), -stat[1][::-1].copy()]
+    a, b = st, mst
+    out = []
+    for k in range(steps):
+        dt = orc.cfl_dt1d(g, p, a, stat)
+        a = orc.rk3_step1d(g, p, dt, a, stat)
+        b = orc.rk3_step1d(g, p, dt, b, mstat)
+        out.append([np.abs(par[q] * b[q][::-1] - a[q]).max() / max(np.abs(a[q]).max(), 1e-300) for q in range(4)])
+    return np.array(out)
+
+
+def test_mirror_symmetry_1d(orc):
+    # Reflecting x -> x0 + x1 - x maps the scheme onto itself (eta, M, b even; m, H, b_x odd): the '-'
+    # reconstruction is the mirror image of the '+' one (Sec. 2.1). Smooth data: bitwise identical.
+    s = S.accuracy1d(200)
+    s.bc_x = S.REFLECTIVE
+    assert np.all(_mirror_runs(orc, s, 10) == 0.0)
+    # Across a jump the nonlinear weights amplify one-ulp differences of the summation order; they
+    # start at rounding level and stay far below any real asymmetry.
+    d = _mirror_runs(orc, S.perturbed1d(perturb=0.05), 15)
+    assert d[0].max() <= 1e-15
+    assert d[-1].max() <= 1e-11
+
+
+def test_transpose_symmetry_2d(orc):
+    # Swapping x <-> y together with m <-> w (and the derivative planes) on a square grid.
+    s = S.hump2d(24, 24, seed=5)
+    g, p = grid_of(orc, s), orc.make_params()
+    st, stat = state_of(orc, s)
+    T = lambda a: np.ascontiguousarray(a.T)
+    # (eta, m, w, H1, M1, W1, H2, M2, W2) -> (eta, w, m, H2, W2, M2, H1, W1, M1); (b, bx, by) -> (b, by, bx)
+    perm = [0, 2, 1, 6, 8, 7, 3, 5, 4]
+    tst = [T(st[perm[q]]) for q in range(9)]
+    tstat = [T(stat[0]), T(stat[2]), T(stat[1])]
+    a, b = st, tst
+    for _ in range(4):
+        dt = orc.cfl_dt2d(g, p, a, stat)
+        a = orc.rk3_step2d(g, p, dt, a, stat)
+        b = orc.rk3_step2d(g, p, dt, b, tstat)
+    for q in range(9):
+        scale = max(np.abs(a[q]).max(), 1.0)
+        assert np.abs(T(b[perm[q]]) - a[q]).max() <= 1e-13 * scale
+
+
+def _compare_2d_1d(orc, s1, steps):
+    g1, p = grid_of(orc, s1), orc.make_params(eps_w=1e-6)
+    st1, stat1 = state_of(orc, s1)
+    ny = 4
+    rep = lambda a: np.repeat(a[None, :], ny, axis=0)
+    z = np.zeros((ny, s1.nx))
+    st2 = [rep(st1[0]), rep(st1[1]), z, rep(st1[2]), rep(st1[3]), z, z, z, z]
+    stat2 = [rep(stat1[0]), rep(stat1[1]), z]
+    g2 = orc.make_grid(s1.nx, ny, s1.x0, s1.x1, 0.0, 0.04, s1.bc_x, orc.BC_REFLECTIVE)
+    a, b = st1, st2
+    for _ in range(steps):
+        dt = orc.cfl_dt1d(g1, p, a, stat1) * 0.5
+        a = orc.rk3_step1d(g1, p, dt, a, stat1)
+        b = orc.rk3_step2d(g2, p, dt, b, stat2)
+    for q2 in (2, 5, 6, 7, 8):
+        assert np.abs(b[q2]).max() == 0.0
+    return max(np.abs(b[q2][j] - a[q1]).max() / max(1.0, np.abs(a[q1]).max())
+               for q1, q2 in [(0, 0), (1, 1), (2, 3), (3, 4)] for j in range(ny))
+
+
+def test_2d_reduces_to_1d(orc):
+    # Data invariant in y with w = 0 reproduce the 1D scheme of Sec. 2 (the y-sweep contributes exact
+    # zeros and the x-sweep's middle characteristic field carries w = 0). The two codes order one
+    # product differently in the source term, so agreement is to rounding, not bitwise.
+    smooth = S.accuracy1d(160)
+    smooth.bc_x = S.REFLECTIVE
+    assert _compare_2d_1d(orc, smooth, 10) <= 1e-12
+    assert _compare_2d_1d(orc, S.perturbed1d(perturb=0.05), 1) <= 1e-14
+
+
+def test_mass_conservation(orc):
+    # Flat bottom: the source vanishes and the flux form conserves sum(h) to round-off (periodic and
+    # reflective). Without characteristic decomposition the projected source has no first component,
+    # so sum(h) is conserved over any bottom.
+    for bc, cd, flat in [(S.PERIODIC, 1, True), (S.REFLECTIVE, 1, True), (S.REFLECTIVE, 0, False)]:
+        s = S.hump2d(32, 24, seed=11, bc=bc)
+        if flat:
+            s.b[:] = 0.0
+            s.deriv[6][:] = 0.0
+            s.deriv[7][:] = 0.0
+        g, p = grid_of(orc, s), orc.make_params(char_decomp=cd)
+        st, stat = state_of(orc, s)
+        m0 = np.sum(st[0] - stat[0])
+        cur = st
+        for _ in range(5):
+            cur = orc.rk3_step2d(g, p, orc.cfl_dt2d(g, p, cur, stat), cur, stat)
+        assert abs(np.sum(cur[0] - stat[0]) - m0) <= 1e-12 * abs(m0)
+
+
+def test_ex48_contour_range_loose(orc):
+    # Ex. 4.8 at 200x100, t = 0.12: the surface stays within the printed contour range (taken from the
+    # WENO-XS paper) to 3e-4. Only a loose check: the boundary condition is unstated.
+    s = S.ex48(200, 100)
+    g, p = grid_of(orc, s), orc.make_params()
+    st, stat = state_of(orc, s)
+    out, t, n = orc.run2d(g, p, st, stat, 0.12)
+    ref = GOLD["ex48_contour_ranges"]
+    lo, hi = ref["lo"][0], ref["hi"][0]
+    eta = out[0]
+    assert abs(eta.min() - lo) < 3e-4 and abs(eta.max() - hi) < 3e-4
+
+
+def test_operation_tally_positive(orc):
+    s = S.hump2d(8, 8, seed=3)
+    g, p = grid_of(orc, s), orc.make_params()
+    st, stat = state_of(orc, s)
+    c = orc.count_stage2d(g, p, st, stat)
+    per = (c["add"] + c["mul"] + c["div"] + c["sqrt"]) / 64
+    assert 1500 < per < 20000, c
