@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the 2D well-balanced fifth-order FD HWENO scheme on GB300.
+
+Workload: 2048 x 2048 nodes on [0,2] x [0,1], reflective walls, seeded bottom of 8 Gaussian bumps,
+still water eta = 1 plus a 0.01 strip on x in [0.05, 0.15], state = 3 conserved variables and their
+x and y derivatives, SSP-RK3 at CFL 0.6 with the time step computed on the device.
+A step is one SSP-RK3 step (3 stages) over the whole grid. Metric: FP64 point-updates/s
+(grid points x RK stages per second), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the CPU oracle (the plain FP64 restatement of the paper's scheme used by the
+tests) on this machine's host cores on the same workload. Multi-GPU runs are independent replicas
+of the workload (one per rank, no data exchange), so `value` scales weakly.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = 2048
+STAGES = 3
+WORKLOAD = ("2D plain scheme, 2048x2048 on [0,2]x[0,1], reflective walls, 8 Gaussian bumps (seeded), "
+            "eta=1 + 0.01 strip on x in [0.05,0.15], SSP-RK3 CFL 0.6, dt on device")
+METRIC = "FP64 point-updates/s (grid pts x RK stages) at 2048^2"
+UNIT = "point-updates/s"
+
+# Algorithmic FP64 work per unit of each kernel, counted from the formulas the kernels evaluate
+# (add/sub = 1 flop, mul = 1, fma = 2; a reciprocal or reciprocal square root is its three-fma or
+# five-op refinement; see the design notes for the per-term tally).
+FLOPS_PER_UNIT = {
+    "sweep_x": 687.0,   # per x-interface, including its share of the node records
+    "sweep_y": 687.0,   # per y-interface
+    "node": 518.0,      # per node (RHS assembly, limiter in x and y, RK combination)
+    "alpha": 21.0,      # per node
+}
+UNITS_PER_LAUNCH = {
+    "sweep_x": (NX + 1) * NY,
+    "sweep_y": NX * (NY + 1),
+    "node": NX * NY,
+    "alpha": NX * NY,
+}
+STATE_BYTES = 9 * NX * NY * 8
+
+
+def peaks():
+    p = {"hbm_gbs": 6783.5, "fp64_tflops": None, "src": "fallback"}
+    try:
+        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        p["hbm_gbs"] = m.get("hbm_gbs", p["hbm_gbs"])
+        p["src"] = "measured"
+        p["fp64_tflops"] = m.get("fp64_tflops")
+    except Exception:
+        pass
+    if p["fp64_tflops"] is None:
+        # DFMA throughput measured on this machine's GB300 (1.6 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flops)
+        p["fp64_tflops"] = 1.0086
+        p["fp64_src"] = "measured DFMA microbenchmark (0.505e12 DFMA/s)"
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if n > 0 else "gloo")
+    return ws, rank, local
+
+
+def allreduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_rate(seconds_budget=60.0):
+    """Oracle (CPU, all host cores) on the same workload: one RK3 step of the full 2048^2 grid if it fits
+    the budget, else the first stage only. Returns (point-updates/s, sample description, threads)."""
+    import oracle
+    from paper_2208_01260_gb300 import scenarios as S
+    sc = S.bumps2d(NX, NY, strip=0.01)
+    g = oracle.make_grid(sc.nx, sc.ny, sc.x0, sc.x1, sc.y0, sc.y1, sc.bc_x, sc.bc_y)
+    p = oracle.make_params()
+    st, stat = oracle.to_state2d(sc.h, sc.hu, sc.hv, sc.b, sc.deriv)
+    dt = oracle.cfl_dt2d(g, p, st, stat)
+    t0 = time.perf_counter()
+    out, base, _ = oracle.stage2d(g, p, 1, dt, st, stat)
+    t1 = time.perf_counter()
+    stages, elapsed = 1, t1 - t0
+    if 3 * elapsed < seconds_budget:
+        out2, _, _ = oracle.stage2d(g, p, 2, dt, out, stat, base)
+        oracle.stage2d(g, p, 3, dt, out2, stat, base)
+        stages, elapsed = 3, time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = "%d RK stage(s) of the full 2048x2048 workload" % stages
+    return NX * NY * stages / elapsed, desc, threads, elapsed
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2208_01260_gb300 import scenarios as S
+    sc = S.bumps2d(NX, NY, strip=0.01)
+    g = oracle.make_grid(sc.nx, sc.ny, sc.x0, sc.x1, sc.y0, sc.y1, sc.bc_x, sc.bc_y)
+    p = oracle.make_params()
+    st, stat = oracle.to_state2d(sc.h, sc.hu, sc.hv, sc.b, sc.deriv)
+    # a reference step is one RK stage of the full grid (a bounded sample of one RK3 step)
+    dt = oracle.cfl_dt2d(g, p, st, stat)
+    cur, base = st, None
+    k = 0
+    for _ in range(args.warmup):
+        cur, base, _ = oracle.stage2d(g, p, k % 3 + 1, dt, cur, stat, base)
+        k += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cur, base, _ = oracle.stage2d(g, p, k % 3 + 1, dt, cur, stat, base if k % 3 else None)
+        k += 1
+    el = time.perf_counter() - t0
+    value = NX * NY * args.steps / el
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "step": "one RK stage of the full grid (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "each step = one SSP-RK3 stage over the full 2048x2048 grid"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--nx", type=int, default=2048, help="smaller grids for profiling captures only")
+    ap.add_argument("--ny", type=int, default=2048)
+    args = ap.parse_args()
+    global NX, NY, STATE_BYTES
+    NX, NY = args.nx, args.ny
+    STATE_BYTES = 9 * NX * NY * 8
+    UNITS_PER_LAUNCH.update(sweep_x=(NX + 1) * NY, sweep_y=NX * (NY + 1), node=NX * NY, alpha=NX * NY)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    import paper_2208_01260_gb300 as hw
+    from paper_2208_01260_gb300 import scenarios as S
+
+    sc = S.bumps2d(NX, NY, strip=0.01)
+    solver = hw.Solver.from_scenario(sc, hw.make_params())
+    if (NX, NY) != (2048, 2048):
+        args.no_cpu_baseline = True
+    stream = torch.cuda.current_stream()
+
+    # warm-up (CUDA graph of two steps)
+    solver.advance(args.warmup, use_graph=True)
+    torch.cuda.synchronize()
+
+    # timed region 1: K steps from the captured graph (production path)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        solver.advance(args.steps, use_graph=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    ms = ev0.elapsed_time(ev1)
+    ms = allreduce_max(ms, ws)
+    value = ws * NX * NY * STAGES * args.steps / (ms * 1e-3)
+
+    # timed region 2: the same K steps with every kernel bracketed by events (per-kernel roofline)
+    hw.hw_set_profiling(solver.h, True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.advance(args.steps, use_graph=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = e0.elapsed_time(e1)
+    prof = hw.hw_get_profile(solver.h)
+    hw.hw_set_profiling(solver.h, False)
+    launches_per_step = sum(n for _, n in prof.values()) / args.steps
+
+    pk = peaks()
+    kernels = {}
+    for k in ("sweep_x", "sweep_y", "node", "alpha"):
+        tot, n = prof[k]
+        if n == 0:
+            continue
+        nl = n if k != "alpha" else n // 2  # the alpha class counts reduction + finish launches
+        avg_ms = tot / nl
+        fl = FLOPS_PER_UNIT[k] * UNITS_PER_LAUNCH[k]
+        kernels[k] = {"ms_avg": avg_ms, "launches": n, "share": tot / ms_prof,
+                      "tflops": fl / (avg_ms * 1e-3) / 1e12}
+    dom = max(kernels, key=lambda k: kernels[k]["share"])
+    ach = kernels[dom]["tflops"]
+    roofline = {"bound": "alu", "achieved": ach, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                "frac": ach / pk["fp64_tflops"], "traffic": None, "kernel": "k_" + dom,
+                "peak_src": "FP64 DFMA throughput measured on this GB300 pool (no FP64 entry in the peaks file)",
+                "hbm_frac_of_measured": None}
+
+    # e2e through the public API with pinned host buffers: each step uploads the state (physical
+    # layout, 9 planes), advances one RK3 step and downloads the state.
+    host_in = [torch.empty(NY, NX, dtype=torch.float64).pin_memory() for _ in range(9)]
+    host_out = [torch.empty(NY, NX, dtype=torch.float64).pin_memory() for _ in range(9)]
+    hin = [t.numpy() for t in host_in]
+    hout = [t.numpy() for t in host_out]
+    hw.hw_get_state(solver.h, hout, hw.HW_LAYOUT_PHYSICAL)
+    for a, b in zip(hin, hout):
+        a[...] = b
+    ke = max(1, min(args.e2e_steps, args.steps))
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        hw.hw_set_state(solver.h, hin, hw.HW_LAYOUT_PHYSICAL)
+        solver.advance(1, use_graph=False)
+        hw.hw_get_state(solver.h, hout, hw.HW_LAYOUT_PHYSICAL)
+    torch.cuda.synchronize()
+    e2e_s = allreduce_max(time.perf_counter() - t0, ws)
+    e2e = {"value": ws * NX * NY * STAGES * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": STATE_BYTES,
+           "d2h_bytes_per_step": STATE_BYTES, "steps": ke}
+
+    solver.sync()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "stages_per_step": STAGES,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (state 302 MB + interface planes 806 MB per grid)",
+                       "timed_path": "hw_advance with a captured CUDA graph (2 steps per graph)"},
+            "roofline": roofline, "kernels": kernels, "ms_per_step_profiled": ms_prof / args.steps,
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clk.summary(), "e2e": e2e}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, desc, threads, el = oracle_rate()
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+                                "seconds": el}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

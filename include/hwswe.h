@@ -1,0 +1,149 @@
+/*
+ * hwswe.h — C ABI of the GB300 (sm_103a) implementation of the well-balanced fifth-order
+ * finite-difference Hermite WENO scheme for the shallow water equations in pre-balanced form
+ * (Zhao & Zhang, arXiv:2208.01260).
+ *
+ * The problem statement the calls follow: the pre-balanced system in the equilibrium variables
+ * U = (eta = h + b, m = hu[, w = hv]) with the bottom b and its derivatives (Sec. 2 eq. swe-form-1d-e,
+ * Sec. 3 eq. swe-form-2d-e), evolved together with the first derivatives V = U_x (and Q = U_y in 2D)
+ * (eqs. swe-form-1d-h, swe-form-2d-h), gravity g, a CFL number (Sec. 4: 0.6, g = 9.812), and
+ * boundary conditions per direction.
+ *
+ * Conventions for every call:
+ *   - Return value: HW_OK (0) or a negative HW_ERR_* code; hw_last_error() gives a message for the
+ *     calling thread. No exception crosses the ABI.
+ *   - Arrays are FP64, row-major [ny][nx] with x fastest (1D: [nx]).
+ *   - ptr_kind HW_HOST: pageable or pinned host memory; the call copies synchronously on the solver's
+ *     stream. HW_DEVICE: device memory of the solver's GPU; the call is stream-ordered.
+ *   - The library owns every device buffer it allocates (hw_create) and frees them (hw_destroy).
+ *     Caller arrays are only read (inputs) or written (outputs) during the call, never retained.
+ *   - One solver is bound to one CUDA stream; a solver is not thread-safe.
+ *   - Node layout: periodic directions place nodes at x0 + i dx, reflective directions at cell
+ *     centres x0 + (i + 1/2) dx with walls at x0 and x1; dx = (x1 - x0) / nx.
+ */
+#ifndef HWSWE_H
+#define HWSWE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HW_OK 0
+#define HW_ERR_ARG (-1)       /* invalid argument, size or pointer kind                          */
+#define HW_ERR_DEPTH (-2)     /* h <= 0 or non-finite state (the scheme has no wet/dry treatment) */
+#define HW_ERR_NONFINITE (-3) /* non-finite input                                                 */
+#define HW_ERR_CUDA (-4)      /* a CUDA runtime call failed (message in hw_last_error)            */
+#define HW_ERR_TIMEOUT (-5)   /* a bounded device wait gave up                                    */
+#define HW_ERR_STATE (-6)     /* call out of order (e.g. rk3_step before init)                    */
+#define HW_ERR_NOMEM (-7)     /* device allocation failed                                         */
+
+#define HW_BC_PERIODIC 0
+#define HW_BC_REFLECTIVE 1
+
+#define HW_HOST 0
+#define HW_DEVICE 1
+
+#define HW_LAYOUT_PHYSICAL 0    /* h, hu[, hv], h_x, hu_x[, hv_x][, h_y, hu_y, hv_y]                  */
+#define HW_LAYOUT_EQUILIBRIUM 1 /* eta, m[, w], eta_x, m_x[, w_x][, eta_y, m_y, w_y] (the scheme's U, V, Q) */
+
+/* Grid: dim 1 (ny must be 1) or 2; nx, ny >= 2 (2D) or nx >= 2 (1D); bc_* are HW_BC_*. */
+typedef struct {
+  int dim;
+  int nx, ny;
+  double x0, x1, y0, y1;
+  int bc_x, bc_y;
+} hw_grid;
+
+/* Parameters (Sec. 2.1 eq. GHYZZ: eps = 1e-6, 1e-10 for tiny perturbations per Ex. 4.3; Sec. 4: CFL
+ * 0.6, g = 9.812). eps_lim is the epsilon of the limiter weights (Sec. 2.2). char_decomp = 1 projects
+ * on characteristic fields (Sec. 2.1); limiter = 1 applies the HWENO limiter (Sec. 2.2);
+ * linear_weights = 1 replaces the nonlinear weights by the linear ones (accuracy tests only). */
+typedef struct {
+  double g, cfl, eps_w, eps_lim;
+  int char_decomp, limiter, linear_weights;
+} hw_params;
+
+typedef struct hw_solver hw_solver;
+
+/* Create a solver on the current CUDA device, bound to cuda_stream (a cudaStream_t; NULL = legacy
+ * default stream). Allocates all device buffers. *out is set on success. */
+int hw_create(const hw_grid* grid, const hw_params* params, void* cuda_stream, hw_solver** out);
+
+/* Free all device buffers of the solver and the solver itself. Safe on NULL. */
+int hw_destroy(hw_solver* s);
+
+/* Load the initial state from physical variables (Sec. 2: eta = h + b; V = (h_x + b_x, hu_x)).
+ *   2D: h, hu, hv, b: nx*ny each; deriv[8] = h_x, hu_x, hv_x, h_y, hu_y, hv_y, b_x, b_y.
+ *   1D: h, hu, b: nx each (hv ignored, may be NULL); deriv[3] = h_x, hu_x, b_x.
+ * Precomputes the parts of the source terms that depend on b only. Returns HW_ERR_DEPTH if any
+ * h <= 0 or is not finite (the state is still loaded). Synchronises the stream. */
+int hw_init(hw_solver* s, const double* h, const double* hu, const double* hv, const double* b,
+            const double* const* deriv, int ptr_kind);
+
+/* Right-hand side of the semi-discrete scheme at the current state, without limiter (Sec. 2.1
+ * eq. swe-form-1d-semi; Sec. 3 eq. swe-form-2d-dis with the source terms read with '-'), using
+ * alpha = max(|u|+c) per direction over the current state (Sec. 2.1 Step 1).
+ * out: 2D 9 planes d/dt (eta, m, w, eta_x, m_x, w_x, eta_y, m_y, w_y); 1D 4 planes d/dt (eta, m, eta_x,
+ * m_x). Stream-ordered for HW_DEVICE, synchronous for HW_HOST. */
+int hw_rhs(hw_solver* s, double* const* out, int ptr_kind);
+
+/* Lax-Friedrichs constants of the current state: alpha[0] = max(|u|+c), alpha[1] = max(|v|+c) (2D;
+ * 0 in 1D). Synchronises the stream. HW_ERR_DEPTH if the state has h <= 0 or non-finite values. */
+int hw_alpha(hw_solver* s, double* alpha);
+
+/* CFL time step of the current state (Sec. 4, CFL from params): 2D dt = cfl / (alpha_x/dx +
+ * alpha_y/dy), 1D dt = cfl dx / alpha. Synchronises the stream. */
+int hw_cfl_dt(hw_solver* s, double* dt_out);
+
+/* One SSP-RK3 step (Sec. 2.2 eq. RK, applied to eq. swe-form-2d-dis in 2D): the right-hand side is
+ * evaluated on the unmodified stage states, the combination uses the limited derivatives, alpha is
+ * recomputed at every stage, and the new derivatives are stored unlimited. Asynchronous on the
+ * stream; errors from the device are reported by the next synchronising call. */
+int hw_rk3_step(hw_solver* s, double dt);
+
+/* One stage k = 1, 2, 3 of the step above (per-stage testing). Stage 1 stores the step's base U^n and
+ * the limited V^{n,mod}, Q^{n,mod}; stages 2, 3 use them. */
+int hw_rk3_stage(hw_solver* s, int k, double dt);
+
+/* nsteps RK3 steps with dt = CFL step computed on the device at the start of each step, clipped so
+ * that the last step ends at t_end if t_end > 0 (stops early once t_end is reached). The steps run
+ * from a captured CUDA graph when use_graph != 0. On return *t_out (may be NULL) holds the simulated
+ * time advanced and *steps_out (may be NULL) the steps taken; synchronises the stream. */
+int hw_advance(hw_solver* s, int nsteps, double t_end, int use_graph, double* t_out, int* steps_out);
+
+/* Read / write the state. layout is HW_LAYOUT_*; out/in hold 9 (2D) or 4 (1D) planes. */
+int hw_get_state(hw_solver* s, double* const* out, int layout, int ptr_kind);
+int hw_set_state(hw_solver* s, const double* const* in, int layout, int ptr_kind);
+
+/* Read the base of the current step stored by stage 1 (U^n, V^{n,mod}, Q^{n,mod}) in the
+ * equilibrium layout; out holds 9 (2D) or 4 (1D) planes. */
+int hw_get_base(hw_solver* s, double* const* out, int ptr_kind);
+
+/* Per-kernel timing of the hot path. While profiling is on, every kernel the solver launches is
+ * bracketed by CUDA events on the solver's stream and hw_advance runs without a CUDA graph.
+ * hw_get_profile waits for the stream, returns per kernel class the accumulated device time in ms and
+ * the launch count, then clears them. Classes (HW_PROF_*): alpha reduction, x-sweep, y-sweep, node
+ * (assembly + limiter + RK), other (scalars, conversions). ms and launches hold HW_PROF_N entries. */
+#define HW_PROF_ALPHA 0
+#define HW_PROF_SWEEP_X 1
+#define HW_PROF_SWEEP_Y 2
+#define HW_PROF_NODE 3
+#define HW_PROF_OTHER 4
+#define HW_PROF_N 5
+int hw_set_profiling(hw_solver* s, int on);
+int hw_get_profile(hw_solver* s, double* ms, int* launches);
+
+/* Wait for the stream and return the device status as an HW_ERR_* code (HW_OK if clean). */
+int hw_sync(hw_solver* s);
+
+/* Message of the last error on the calling thread ("" if none). Valid until the next call. */
+const char* hw_last_error(void);
+
+/* Library version string. */
+const char* hw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HWSWE_H */

@@ -294,15 +294,17 @@ def count_stage2d(grid, params, st, stat):
 
 
 def run2d(grid, params, st, stat, t_end, max_steps=10**9, dt_fn=None):
-    """Advance with the CFL step clipped so the last step lands on t_end. Returns (state, t, steps)."""
+    """Advance with the CFL step; the step that reaches t_end (within a relative 1e-12) is shortened to
+    end exactly on it (the paper does not say how the last step ends). Returns (state, t, steps)."""
     cur = [np.array(p, dtype=np.float64, copy=True) for p in st]
     t, n = 0.0, 0
     while t < t_end and n < max_steps:
         dt = cfl_dt2d(grid, params, cur, stat) if dt_fn is None else dt_fn(cur)
-        if t + dt > t_end:
+        last = dt >= (t_end - t) - 1e-12 * t_end
+        if last:
             dt = t_end - t
         cur = rk3_step2d(grid, params, dt, cur, stat)
-        t += dt
+        t = t_end if last else t + dt
         n += 1
     return cur, t, n
 
@@ -366,9 +368,10 @@ def run1d(grid, params, st, stat, t_end, max_steps=10**9, dt_fn=None):
     t, n = 0.0, 0
     while t < t_end and n < max_steps:
         dt = cfl_dt1d(grid, params, cur, stat) if dt_fn is None else dt_fn(cur)
-        if t + dt > t_end:
+        last = dt >= (t_end - t) - 1e-12 * t_end
+        if last:
             dt = t_end - t
         cur = rk3_step1d(grid, params, dt, cur, stat)
-        t += dt
+        t = t_end if last else t + dt
         n += 1
     return cur, t, n

@@ -1,0 +1,341 @@
+"""GB300 (sm_103a) well-balanced fifth-order FD HWENO solver for the shallow water equations.
+
+Python binding of the C ABI in ``include/hwswe.h``: the functions below have the C names and do
+argument marshalling only (numpy arrays go as host pointers, torch CUDA tensors as device
+pointers, the stream is torch's current stream). Every step of the scheme runs in the CUDA
+library ``libhwswe.so`` built from ``csrc/``; there is no CPU fallback: if the library is missing
+the first call raises.
+
+Scheme: Zhao & Zhang, arXiv:2208.01260 (Sec. 2 one-dimensional, Sec. 3 two-dimensional).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+__all__ = [
+    "HW_OK", "HW_BC_PERIODIC", "HW_BC_REFLECTIVE", "HW_HOST", "HW_DEVICE", "HW_LAYOUT_PHYSICAL",
+    "HW_LAYOUT_EQUILIBRIUM", "HwError", "hw_grid", "hw_params", "lib", "make_grid", "make_params",
+    "hw_create", "hw_destroy", "hw_init", "hw_rhs", "hw_alpha", "hw_cfl_dt", "hw_rk3_step", "hw_rk3_stage",
+    "hw_advance", "hw_get_state", "hw_set_state", "hw_get_base", "hw_sync", "hw_version", "Solver",
+    "hw_set_profiling", "hw_get_profile",
+]
+
+HW_OK = 0
+HW_ERR = {-1: "HW_ERR_ARG", -2: "HW_ERR_DEPTH", -3: "HW_ERR_NONFINITE", -4: "HW_ERR_CUDA", -5: "HW_ERR_TIMEOUT",
+          -6: "HW_ERR_STATE", -7: "HW_ERR_NOMEM"}
+HW_BC_PERIODIC = 0
+HW_BC_REFLECTIVE = 1
+HW_HOST = 0
+HW_DEVICE = 1
+HW_LAYOUT_PHYSICAL = 0
+HW_LAYOUT_EQUILIBRIUM = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhwswe.so")
+_lib = None
+
+
+class HwError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__("%s failed: %s (%s)" % (where, HW_ERR.get(code, str(code)), msg))
+        self.code = code
+
+
+class hw_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+                ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+                ("bc_x", C.c_int), ("bc_y", C.c_int)]
+
+
+class hw_params(C.Structure):
+    _fields_ = [("g", C.c_double), ("cfl", C.c_double), ("eps_w", C.c_double), ("eps_lim", C.c_double),
+                ("char_decomp", C.c_int), ("limiter", C.c_int), ("linear_weights", C.c_int)]
+
+
+def lib():
+    """Load libhwswe.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhwswe.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        vp, dp, i = C.c_void_p, C.POINTER(C.c_double), C.c_int
+        pp = C.POINTER(C.c_void_p)
+        sigs = {
+            "hw_create": ([C.POINTER(hw_grid), C.POINTER(hw_params), vp, C.POINTER(vp)], i),
+            "hw_destroy": ([vp], i),
+            "hw_init": ([vp, vp, vp, vp, vp, pp, i], i),
+            "hw_rhs": ([vp, pp, i], i),
+            "hw_alpha": ([vp, dp], i),
+            "hw_cfl_dt": ([vp, dp], i),
+            "hw_rk3_step": ([vp, C.c_double], i),
+            "hw_rk3_stage": ([vp, i, C.c_double], i),
+            "hw_advance": ([vp, i, C.c_double, i, dp, C.POINTER(C.c_int)], i),
+            "hw_get_state": ([vp, pp, i, i], i),
+            "hw_set_state": ([vp, pp, i, i], i),
+            "hw_get_base": ([vp, pp, i], i),
+            "hw_sync": ([vp], i),
+            "hw_set_profiling": ([vp, i], i),
+            "hw_get_profile": ([vp, dp, C.POINTER(C.c_int)], i),
+            "hw_last_error": ([], C.c_char_p),
+            "hw_version": ([], C.c_char_p),
+        }
+        for name, (args, res) in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != HW_OK:
+        raise HwError(rc, where, lib().hw_last_error().decode())
+
+
+def make_grid(nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=HW_BC_PERIODIC, bc_y=HW_BC_PERIODIC, dim=None):
+    if dim is None:
+        dim = 1 if ny == 1 else 2
+    return hw_grid(dim, nx, ny, x0, x1, y0, y1, bc_x, bc_y)
+
+
+def make_params(g=9.812, cfl=0.6, eps_w=1e-6, eps_lim=None, char_decomp=1, limiter=1, linear_weights=0):
+    return hw_params(g, cfl, eps_w, eps_w if eps_lim is None else eps_lim, char_decomp, limiter, linear_weights)
+
+
+# ------------------------------------------------------------------------------------------------
+# marshalling helpers
+# ------------------------------------------------------------------------------------------------
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _kind(arrays) -> int:
+    kinds = set()
+    for a in arrays:
+        if a is None:
+            continue
+        if _is_torch(a):
+            if not a.is_cuda:
+                raise ValueError("torch tensors must live on the GPU")
+            kinds.add(HW_DEVICE)
+        else:
+            kinds.add(HW_HOST)
+    if len(kinds) != 1:
+        raise ValueError("pass either all numpy arrays (host) or all CUDA tensors (device)")
+    return kinds.pop()
+
+
+def _ptr(a, n: int, writable: bool = False):
+    if a is None:
+        return None
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != n:
+            raise ValueError("device planes must be contiguous float64 tensors of %d elements" % n)
+        return C.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != n:
+        raise ValueError("host planes must be C-contiguous float64 numpy arrays of %d elements" % n)
+    if writable and not a.flags["WRITEABLE"]:
+        raise ValueError("output array is read-only")
+    return C.c_void_p(a.ctypes.data)
+
+
+def _pp(ptrs):
+    return (C.c_void_p * len(ptrs))(*[p.value if p is not None else None for p in ptrs])
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------------------------------------
+# C names
+# ------------------------------------------------------------------------------------------------
+class _Handle:
+    def __init__(self, ptr, grid, params, n, nstate):
+        self.ptr, self.grid, self.params, self.n, self.nstate = ptr, grid, params, n, nstate
+
+
+def hw_create(grid: hw_grid, params: hw_params, stream=None) -> _Handle:
+    out = C.c_void_p()
+    _check(lib().hw_create(C.byref(grid), C.byref(params), _stream_handle(stream), C.byref(out)), "hw_create")
+    n = grid.nx * (grid.ny if grid.dim == 2 else 1)
+    return _Handle(out, grid, params, n, 9 if grid.dim == 2 else 4)
+
+
+def hw_destroy(h: _Handle):
+    if h is not None and h.ptr:
+        lib().hw_destroy(h.ptr)
+        h.ptr = None
+
+
+def hw_init(h: _Handle, hh, hu, hv, b, deriv: Sequence):
+    arrays = [hh, hu, hv, b, *deriv]
+    kind = _kind(arrays)
+    nd = 8 if h.grid.dim == 2 else 3
+    if len(deriv) != nd:
+        raise ValueError("deriv needs %d planes" % nd)
+    P = _pp([_ptr(a, h.n) for a in deriv])
+    _check(lib().hw_init(h.ptr, _ptr(hh, h.n), _ptr(hu, h.n), _ptr(hv, h.n) if hv is not None else None,
+                         _ptr(b, h.n), P, kind), "hw_init")
+
+
+def hw_rhs(h: _Handle, out: Sequence):
+    kind = _kind(out)
+    _check(lib().hw_rhs(h.ptr, _pp([_ptr(a, h.n, True) for a in out]), kind), "hw_rhs")
+
+
+def hw_alpha(h: _Handle):
+    a = (C.c_double * 2)()
+    _check(lib().hw_alpha(h.ptr, a), "hw_alpha")
+    return a[0], a[1]
+
+
+def hw_cfl_dt(h: _Handle) -> float:
+    dt = C.c_double()
+    _check(lib().hw_cfl_dt(h.ptr, C.byref(dt)), "hw_cfl_dt")
+    return dt.value
+
+
+def hw_rk3_step(h: _Handle, dt: float):
+    _check(lib().hw_rk3_step(h.ptr, float(dt)), "hw_rk3_step")
+
+
+def hw_rk3_stage(h: _Handle, k: int, dt: float):
+    _check(lib().hw_rk3_stage(h.ptr, int(k), float(dt)), "hw_rk3_stage")
+
+
+def hw_advance(h: _Handle, nsteps: int, t_end: float = -1.0, use_graph: bool = True):
+    t = C.c_double()
+    n = C.c_int()
+    _check(lib().hw_advance(h.ptr, int(nsteps), float(t_end), int(bool(use_graph)), C.byref(t), C.byref(n)),
+           "hw_advance")
+    return t.value, n.value
+
+
+def hw_get_state(h: _Handle, out: Sequence, layout: int = HW_LAYOUT_PHYSICAL):
+    kind = _kind(out)
+    _check(lib().hw_get_state(h.ptr, _pp([_ptr(a, h.n, True) for a in out]), int(layout), kind), "hw_get_state")
+
+
+def hw_set_state(h: _Handle, planes: Sequence, layout: int = HW_LAYOUT_PHYSICAL):
+    kind = _kind(planes)
+    _check(lib().hw_set_state(h.ptr, _pp([_ptr(a, h.n) for a in planes]), int(layout), kind), "hw_set_state")
+
+
+def hw_get_base(h: _Handle, out: Sequence):
+    kind = _kind(out)
+    _check(lib().hw_get_base(h.ptr, _pp([_ptr(a, h.n, True) for a in out]), kind), "hw_get_base")
+
+
+def hw_sync(h: _Handle):
+    _check(lib().hw_sync(h.ptr), "hw_sync")
+
+
+HW_PROF_NAMES = ["alpha", "sweep_x", "sweep_y", "node", "other"]
+
+
+def hw_set_profiling(h: _Handle, on: bool):
+    _check(lib().hw_set_profiling(h.ptr, int(bool(on))), "hw_set_profiling")
+
+
+def hw_get_profile(h: _Handle):
+    """{class: (ms, launches)} accumulated since the last call."""
+    ms = (C.c_double * 5)()
+    n = (C.c_int * 5)()
+    _check(lib().hw_get_profile(h.ptr, ms, n), "hw_get_profile")
+    return {k: (ms[i], n[i]) for i, k in enumerate(HW_PROF_NAMES)}
+
+
+def hw_version() -> str:
+    return lib().hw_version().decode()
+
+
+# ------------------------------------------------------------------------------------------------
+# convenience object over the C names
+# ------------------------------------------------------------------------------------------------
+class Solver:
+    """One grid on the current CUDA device, bound to torch's current stream (or `stream`)."""
+
+    def __init__(self, grid: hw_grid, params: hw_params, stream=None):
+        self.h = hw_create(grid, params, stream)
+        self.grid, self.params = grid, params
+        self.shape = (grid.ny, grid.nx) if grid.dim == 2 else (grid.nx,)
+
+    def close(self):
+        hw_destroy(self.h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @classmethod
+    def from_scenario(cls, sc, params: Optional[hw_params] = None, stream=None, device: bool = False):
+        """Create and initialise from a ``scenarios.Scenario`` (host arrays, or copied to the GPU)."""
+        grid = make_grid(sc.nx, sc.ny, sc.x0, sc.x1, sc.y0, sc.y1, sc.bc_x, sc.bc_y, dim=sc.dim)
+        if params is None:
+            params = make_params(eps_w=sc.eps_w)
+        s = cls(grid, params, stream)
+        arrs = [sc.h, sc.hu, sc.hv if sc.dim == 2 else None, sc.b] + list(sc.deriv)
+        if device:
+            import torch
+            arrs = [None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+                    for a in arrs]
+        else:
+            arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+        hw_init(s.h, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4:])
+        return s
+
+    def _planes(self, count):
+        return [np.empty(self.shape) for _ in range(count)]
+
+    def rhs(self):
+        out = self._planes(self.h.nstate)
+        hw_rhs(self.h, out)
+        return out
+
+    def alpha(self):
+        return hw_alpha(self.h)
+
+    def cfl_dt(self):
+        return hw_cfl_dt(self.h)
+
+    def rk3_step(self, dt):
+        hw_rk3_step(self.h, dt)
+
+    def rk3_stage(self, k, dt):
+        hw_rk3_stage(self.h, k, dt)
+
+    def advance(self, nsteps, t_end=-1.0, use_graph=True):
+        return hw_advance(self.h, nsteps, t_end, use_graph)
+
+    def state(self, layout=HW_LAYOUT_EQUILIBRIUM):
+        out = self._planes(self.h.nstate)
+        hw_get_state(self.h, out, layout)
+        return out
+
+    def set_state(self, planes, layout=HW_LAYOUT_EQUILIBRIUM):
+        hw_set_state(self.h, [np.ascontiguousarray(p, dtype=np.float64) for p in planes], layout)
+
+    def base(self):
+        out = self._planes(self.h.nstate)
+        hw_get_base(self.h, out)
+        return out
+
+    def sync(self):
+        hw_sync(self.h)

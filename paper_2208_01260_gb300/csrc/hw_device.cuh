@@ -1,0 +1,176 @@
+// Device-side building blocks of the well-balanced fifth-order FD HWENO scheme (Zhao & Zhang,
+// arXiv:2208.01260) for sm_103a, written for an FP64-pipe-bound kernel: every FP64 add, mul and
+// fma counts, memory traffic is cheap.
+//
+// Conventions shared by all kernels (each one mathematically identical to the paper's formulas):
+//   * Derivative planes are stored multiplied by the grid spacing of their direction: the state holds
+//     V' = dx V and Q' = dy Q, and the static planes hold b, dx b_x, dy b_y. Every Hermite formula of
+//     Sec. 2.1-2.2 uses the derivative only as dx*phi, so the scaling removes those multiplications.
+//   * The Lax-Friedrichs split F^+- = (F +- alpha U)/2 (Sec. 2.1 Step 1) is used without the 1/2, and
+//     the characteristic projection uses the rows of L = R^{-1} without their 1/(2c) factor. Both are
+//     per-interface scalings s_k of a characteristic field (s = (4c, 2, 4c) in a sweep, (2c, 1, 2c) in the
+//     limiter). The smoothness indicators are quadratic in the data, so the nonlinear weights of
+//     eq. (GHYZZ) are unchanged when epsilon is replaced by s_k^2 epsilon; the scaling is undone at the
+//     back-projection.
+//   * The weights are normalised with one reciprocal: omega_l = gamma_l p_l / sum(gamma_m p_m) with
+//     p_1 = s_2 s_3, p_2 = s_1 s_3, p_3 = s_1 s_2, s_l = (beta_l + eps)^2, equal to eq. (GHYZZ).
+//   * Reciprocals and square roots use the hardware approximation plus one cubically convergent
+//     Newton step (Householder order 3 for 1/x and for 1/sqrt(x)), accurate to a few ulp.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hw {
+
+enum { BC_PERIODIC = 0, BC_REFLECTIVE = 1 };
+
+// State planes: 0 eta, 1 m, 2 w, 3 H1', 4 M1', 5 W1', 6 H2', 7 M2', 8 W2' (2D);
+//               0 eta, 1 m, 2 H', 3 M' (1D).
+// Static planes: 0 b, 1 dx b_x, 2 dy b_y (2D); 0 b, 1 dx b_x (1D).
+// Reflective parity of the 12 planes (state then static) across an x-wall and a y-wall
+// (mirror image of the SWE: u odd across x-walls, v odd across y-walls).
+__host__ __device__ constexpr double par_x2d(int q) {
+  return (q == 1 || q == 3 || q == 5 || q == 7 || q == 10) ? -1.0 : 1.0;
+}
+__host__ __device__ constexpr double par_y2d(int q) {
+  return (q == 2 || q == 5 || q == 6 || q == 7 || q == 11) ? -1.0 : 1.0;
+}
+// 1D: eta +, m -, H' -, M' +, b +, dx b_x -.
+__host__ __device__ constexpr double par_1d(int q) { return (q == 1 || q == 2 || q == 5) ? -1.0 : 1.0; }
+
+// Map a node index that may lie up to n outside [0, n) onto the grid. flip = reflected.
+__device__ __forceinline__ int map_index(int i, int n, int bc, bool& flip) {
+  flip = false;
+  if (i < 0) {
+    if (bc == BC_PERIODIC) return i + n;
+    flip = true;
+    return -1 - i;
+  }
+  if (i >= n) {
+    if (bc == BC_PERIODIC) return i - n;
+    flip = true;
+    return 2 * n - 1 - i;
+  }
+  return i;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Reciprocal and reciprocal square root: hardware seed (about 20 bits) refined by one cubically
+// convergent step, so the relative error is below 2^-52 plus rounding.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ double rcp_seed(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ double rsqrt_seed(double x) {
+  double r;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+// 1/x: e = 1 - x r, r' = r (1 + e + e^2) (Householder iteration of order 3 for f(r) = 1/r - x).
+__device__ __forceinline__ double fast_rcp(double x) {
+  double r = rcp_seed(x);
+  double e = fma(-x, r, 1.0);
+  double t = fma(e, e, e);
+  return fma(r, t, r);
+}
+// 1/sqrt(x): e = 1 - x r^2, r' = r (1 + e/2 + 3 e^2 / 8) (third-order Householder step).
+__device__ __forceinline__ double fast_rsqrt(double x) {
+  double r = rsqrt_seed(x);
+  double r2 = r * r;
+  double e = fma(-x, r2, 1.0);
+  double t = fma(0.375, e, 0.5);
+  double u = e * t;
+  return fma(r, u, r);
+}
+
+// Non-negative double -> ordered 64-bit key (for an exact, order-independent atomicMax).
+__device__ __forceinline__ unsigned long long dkey(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+__device__ __forceinline__ double dabs(double x) {
+  return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+}
+
+// ---------------------------------------------------------------------------------------------
+// One characteristic field, one upwind side, scaled data (Sec. 2.1 Step 1).
+//   f0, f1, f2 = scaled f_{i-1}, f_i, f_{i+1};  p0, p1, p2 = scaled dx*phi (mirrored for the '-' side).
+// Returns the weighted value sum(w_l q_l) and the unnormalised weight numerators p (times 1/den)
+// for the source reconstruction with the same weights (Step 2).
+//
+// Algebra (exact rearrangement of the printed q_l and beta_l):
+//   d1 = f0 - f1, d2 = f1 - f2, B1 = 2 d1 + p0 + p1, A1 = B1 + d1 + p1, B2 = 2 d2 + p1 + p2,
+//   A2 = B2 + d2 + p1, e = f0 - 2 f1 + f2, g3 = f0 - f2 + 2 p1, P = f1 + p1/2;
+//   q1 = P + A1/6, q2 = P - A2/6, q3 = P + e/12;
+//   beta1 = p1^2 + 13/3 A1^2 + 781/20 B1^2, beta2 = p1^2 + 13/3 A2^2 + 781/20 B2^2,
+//   beta3 = p1^2 + 13/12 e^2 + 781/80 g3^2.
+// ---------------------------------------------------------------------------------------------
+struct Weights {
+  // omega_l = n_l * r (n_3 already carries gamma_3 / gamma_1 = 4/3)
+  double n1, n2, n3, r;
+};
+
+template <bool LINEAR>
+__device__ __forceinline__ double hweno_side(double f0, double f1, double f2, double p0, double p1, double p2,
+                                             double eps, Weights& W) {
+  const double d1 = f0 - f1, d2 = f1 - f2;
+  const double B1 = fma(2.0, d1, p0 + p1);
+  const double A1 = B1 + (d1 + p1);
+  const double B2 = fma(2.0, d2, p1 + p2);
+  const double A2 = B2 + (d2 + p1);
+  const double P = fma(0.5, p1, f1);
+  const double e = fma(-2.0, f1, f0 + f2);
+  const double q1 = fma(1.0 / 6.0, A1, P);
+  const double q2 = fma(-1.0 / 6.0, A2, P);
+  const double q3 = fma(1.0 / 12.0, e, P);
+  if (LINEAR) {
+    W.n1 = 0.3; W.n2 = 0.3; W.n3 = 0.4; W.r = 1.0;
+    return fma(0.3, q1, fma(0.3, q2, 0.4 * q3));
+  }
+  const double g3 = fma(2.0, p1, f0 - f2);
+  const double pp = p1 * p1;
+  const double b1 = fma((781.0 / 20.0) * B1, B1, fma((13.0 / 3.0) * A1, A1, pp));
+  const double b2 = fma((781.0 / 20.0) * B2, B2, fma((13.0 / 3.0) * A2, A2, pp));
+  const double b3 = fma((781.0 / 80.0) * g3, g3, fma((13.0 / 12.0) * e, e, pp));
+  const double t1 = b1 + eps, t2 = b2 + eps, t3 = b3 + eps;
+  const double s1 = t1 * t1, s2 = t2 * t2, s3 = t3 * t3;
+  // gamma = (3, 3, 4)/10 -> proportional to (1, 1, 4/3)
+  W.n1 = s2 * s3;
+  W.n2 = s1 * s3;
+  W.n3 = (4.0 / 3.0) * (s1 * s2);
+  W.r = fast_rcp(W.n1 + W.n2 + W.n3);
+  return fma(W.n1, q1, fma(W.n2, q2, W.n3 * q3)) * W.r;
+}
+
+// The source reconstructed with the same weights (Sec. 2.1 Step 2) from precomputed candidates.
+__device__ __forceinline__ double weighted(const Weights& W, double c1, double c2, double c3) {
+  return fma(W.n1, c1, fma(W.n2, c2, W.n3 * c3)) * W.r;
+}
+
+// Limiter for one characteristic field (eqs. step1-dxi, limiter-1d), scaled data:
+//   m0, m1, m2 = scaled mu_{i-1}, mu_i, mu_{i+1};  nl, nr = scaled dx*nu_{i-1}, dx*nu_{i+1}.
+// Returns the scaled dx*nu^mod. p'_1 = 2(m1-m0) - nl, p'_2 = 2(m2-m1) - nr, p'_3 = (m2-m0)/2,
+// beta^L_1 = p'_1^2 + 13/3 (m1-m0-nl)^2, beta^L_2 = p'_2^2 + 13/3 (m2-m1-nr)^2,
+// beta^L_3 = p'_3^2 + 13/12 (m2 - 2 m1 + m0)^2, d = (1,1,2)/4.
+template <bool LINEAR>
+__device__ __forceinline__ double limiter_field(double m0, double m1, double m2, double nl, double nr, double eps) {
+  const double dl = m1 - m0, dr = m2 - m1;
+  const double pl = fma(2.0, dl, -nl);
+  const double pr = fma(2.0, dr, -nr);
+  const double pc2 = dl + dr;  // 2 p'_3
+  if (LINEAR) return fma(0.25, pl + pr, 0.25 * pc2);
+  const double al = dl - nl, ar = dr - nr, ac = dr - dl;
+  const double b1 = fma((13.0 / 3.0) * al, al, pl * pl);
+  const double b2 = fma((13.0 / 3.0) * ar, ar, pr * pr);
+  const double b3 = fma((13.0 / 12.0) * ac, ac, (0.25 * pc2) * pc2);
+  const double t1 = b1 + eps, t2 = b2 + eps, t3 = b3 + eps;
+  const double s1 = t1 * t1, s2 = t2 * t2, s3 = t3 * t3;
+  // d = (1, 1, 2)/4 -> proportional to (1, 1, 2); p'_3 = pc2 / 2 so its term is s1 s2 pc2
+  const double n1 = s2 * s3, n2 = s1 * s3, n3 = s1 * s2;
+  const double den = fma(2.0, n3, n1 + n2);
+  const double num = fma(n1, pl, fma(n2, pr, n3 * pc2));
+  return num * fast_rcp(den);
+}
+
+}  // namespace hw

@@ -1,0 +1,92 @@
+// Internal structures shared by the kernels and the C-ABI layer (not part of the public header).
+#pragma once
+#include <algorithm>
+#include <cstddef>
+#include <cuda_runtime.h>
+
+namespace hw {
+
+enum { MODE_STAGE = 0, MODE_RHS = 1 };
+enum { HW_STATUS_DEPTH = 1, HW_STATUS_NONFINITE = 2, HW_STATUS_TIMEOUT = 4, HW_STATUS_BOUNDS = 8 };
+
+// Everything a 2D kernel needs, passed by value.
+struct Dev2D {
+  int nx, ny, bc_x, bc_y;
+  double dx, dy, inv_dx, inv_dy, g, eps_w, eps_lim;
+  // assembly constants: 1/(2dx), 1/(2dy), 1/(24dx), 1/(24dy), 1/(12dx), 1/(12dy)
+  double c_bx, c_by, c_gx, c_gy, c_mx, c_my;
+  double* S[9];      // current state (eta, m, w, dx V, dy Q)
+  double* stat[3];   // b, dx b_x, dy b_y
+  double* bxy[2];    // b_x, b_y (physical, for conversions and static terms)
+  double* X[12];     // x-interface values, pitch nx+1
+  double* Y[12];     // y-interface values, pitch nx, ny+1 rows
+  double* qbx[6];    // source candidates at x-interfaces ('+' q1..q3, '-' q1..q3)
+  double* qby[6];
+  double* sv[2];     // static derivative-source terms of the V equations (m, w components)
+  double* sq[2];     // ... of the Q equations
+};
+
+struct StageArgs {
+  int k;             // RK stage 1..3
+  int limiter;
+  const double* dt;  // device scalar
+  double* out[9];
+  double* base[9];
+  double* rhs_out[9];
+};
+
+struct Ptr9 {
+  double* p[9];
+};
+
+struct PhysIn {
+  const double* p[12];  // h, hu, hv, b, h_x, hu_x, hv_x, h_y, hu_y, hv_y, b_x, b_y
+};
+
+// 1D
+struct Dev1D {
+  int nx, bc;
+  double dx, inv_dx, g, eps_w, eps_lim;
+  double c_b, c_g;   // 1/(2dx), 1/(24dx)
+  double* S[4];      // eta, m, dx H, dx M
+  double* stat[2];   // b, dx b_x
+  double* bx;        // b_x
+  double* X[9];      // interface values: 2Fhat (2), 2bhat (2), 24dx Ghat (2), + 3 spare
+  double* qb[6];
+  double* sv;        // dx [B^]_x / dx (m component)
+};
+
+struct StageArgs1D {
+  int k, limiter;
+  const double* dt;
+  double* out[4];
+  double* base[4];
+  double* rhs_out[4];
+};
+
+struct PhysIn1D {
+  const double* p[6];  // h, hu, b, h_x, hu_x, b_x
+};
+
+// launchers (hw_kernels2d.cu)
+int set_kernel_attributes2d();
+void launch_alpha2d(const Dev2D& d, unsigned long long* amax, int* status, cudaStream_t st);
+void launch_finish_alpha2d(const Dev2D& d, const unsigned long long* amax, double* alpha, double* dt_out,
+                           double cfl, const double* t_now, double t_end, cudaStream_t st);
+void launch_sweep_x2d(const Dev2D& d, const double* alpha, bool linear, bool chr, cudaStream_t st);
+void launch_sweep_y2d(const Dev2D& d, const double* alpha, bool linear, bool chr, cudaStream_t st);
+void launch_node2d(const Dev2D& d, const StageArgs& sa, int mode, bool linear, bool chr, cudaStream_t st);
+void launch_init2d(const Dev2D& d, const PhysIn& in, int* status, cudaStream_t st);
+void launch_convert2d(const Dev2D& d, const Ptr9& src, const Ptr9& dst, int layout, int dir, cudaStream_t st);
+
+// launchers (hw_kernels1d.cu)
+void launch_alpha1d(const Dev1D& d, unsigned long long* amax, int* status, cudaStream_t st);
+void launch_finish_alpha1d(const Dev1D& d, const unsigned long long* amax, double* alpha, double* dt_out,
+                           double cfl, const double* t_now, double t_end, cudaStream_t st);
+void launch_sweep1d(const Dev1D& d, const double* alpha, bool linear, bool chr, cudaStream_t st);
+void launch_node1d(const Dev1D& d, const StageArgs1D& sa, int mode, bool linear, bool chr, cudaStream_t st);
+void launch_init1d(const Dev1D& d, const PhysIn1D& in, int* status, cudaStream_t st);
+void launch_convert1d(const Dev1D& d, const Ptr9& src, const Ptr9& dst, int layout, int dir, cudaStream_t st);
+
+
+}  // namespace hw

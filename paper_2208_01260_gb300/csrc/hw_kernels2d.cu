@@ -1,0 +1,700 @@
+// 2D kernels of the well-balanced fifth-order FD HWENO scheme (Zhao & Zhang, arXiv:2208.01260,
+// Sec. 3) for sm_103a. One RK stage is four launches on the solver's stream:
+//   k_alpha2d   global Lax-Friedrichs constants alpha_x = max(|u|+c), alpha_y = max(|v|+c)
+//   k_sweep_x   x-interfaces: Sec. 2.1 Steps 1-2 along x for (F1, Phi1, tilde-b, tilde-B1) and the
+//               mixed term Psi1 of eq. (mixed)
+//   k_sweep_y   y-interfaces: Steps 1-2 along y for (F2, Psi2, bar-b, bar-B2) and the mixed Phi2
+//   k_node2d    eq. (swe-form-2d-dis) (source signs read as '-'), the HWENO limiter of Sec. 2.2
+//               applied dimension by dimension, and the SSP-RK3 combination of eq. (RK)
+// Interface values go through global memory: the FP64 pipe, not memory, bounds this scheme on
+// GB300, so each interface is computed exactly once.
+#include "hw_device.cuh"
+#include "hw_internal.h"
+
+namespace hw {
+
+// ---------------------------------------------------------------------------------------------
+// Loading a node with boundary mapping
+// ---------------------------------------------------------------------------------------------
+struct Node12 {
+  double v[12];  // eta m w H1' M1' W1' H2' M2' W2' b bxs bys
+};
+
+__device__ __forceinline__ void load_node(const Dev2D& d, int i, int j, Node12& n) {
+  bool fx, fy;
+  const int ii = map_index(i, d.nx, d.bc_x, fx);
+  const int jj = map_index(j, d.ny, d.bc_y, fy);
+  const size_t o = (size_t)jj * d.nx + ii;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    double x = __ldg(d.S[q] + o);
+    if (fx) x *= par_x2d(q);
+    if (fy) x *= par_y2d(q);
+    n.v[q] = x;
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    double x = __ldg(d.stat[q] + o);
+    if (fx) x *= par_x2d(9 + q);
+    if (fy) x *= par_y2d(9 + q);
+    n.v[9 + q] = x;
+  }
+}
+
+// Per-node record a sweep keeps for its stencil (18 doubles).
+enum { R_FP = 0, R_FM = 3, R_GP = 6, R_GM = 9, R_MIX = 12, R_H = 15, R_M = 16, R_W = 17, NREC = 18 };
+
+// Pointwise fluxes of eq. (swe-form-2d-e) and their chain-rule derivatives of eq. (swe-form-2d-h),
+// split with the global alpha (Sec. 2.1 Step 1, without the factor 1/2). DIR = 0: x-sweep record
+// (F1, d_x F1 for the split, d_y F1 for the mixed term); DIR = 1: y-sweep record (F2, d_y F2, d_x F2).
+template <int DIR>
+__device__ __forceinline__ void node_record(const Node12& n, double g, double alpha, double rec[NREC]) {
+  const double eta = n.v[0], m = n.v[1], w = n.v[2], b = n.v[9];
+  const double h = eta - b;
+  const double rh = fast_rcp(h);
+  const double u = m * rh, v = w * rh;
+  const double gh = g * h, ge = g * eta;
+  const double pres = ge * fma(0.5, eta, -b);  // g/2 (eta^2 - 2 eta b)
+  const double uv = u * v;
+  // derivative data along the sweep (split) and across it (mixed)
+  const int qs = DIR == 0 ? 3 : 6, qm = DIR == 0 ? 6 : 3;
+  const double Hs = n.v[qs], Ms = n.v[qs + 1], Ws = n.v[qs + 2], Bs = n.v[DIR == 0 ? 10 : 11];
+  const double Hm = n.v[qm], Mm = n.v[qm + 1], Wm = n.v[qm + 2], Bm = n.v[DIR == 0 ? 11 : 10];
+  double F[3], Gs[3], Gm[3];
+  const double mv = m * v;
+  if (DIR == 0) {
+    const double uu = u * u, a1 = gh - uu, a2 = uu - ge, u2 = u + u;
+    F[0] = m; F[1] = fma(m, u, pres); F[2] = mv;
+    Gs[0] = Ms;
+    Gs[1] = fma(u2, Ms, fma(a1, Hs, a2 * Bs));
+    Gs[2] = fma(uv, Bs - Hs, fma(v, Ms, u * Ws));
+    Gm[0] = Mm;
+    Gm[1] = fma(u2, Mm, fma(a1, Hm, a2 * Bm));
+    Gm[2] = fma(uv, Bm - Hm, fma(v, Mm, u * Wm));
+  } else {
+    const double vv = v * v, a1 = gh - vv, a2 = vv - ge, v2 = v + v;
+    F[0] = w; F[1] = mv; F[2] = fma(w, v, pres);
+    Gs[0] = Ws;
+    Gs[1] = fma(uv, Bs - Hs, fma(v, Ms, u * Ws));
+    Gs[2] = fma(v2, Ws, fma(a1, Hs, a2 * Bs));
+    Gm[0] = Wm;
+    Gm[1] = fma(uv, Bm - Hm, fma(v, Mm, u * Wm));
+    Gm[2] = fma(v2, Wm, fma(a1, Hm, a2 * Bm));
+  }
+  const double U[3] = {eta, m, w}, D[3] = {Hs, Ms, Ws};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    rec[R_FP + c] = fma(alpha, U[c], F[c]);
+    rec[R_FM + c] = fma(-alpha, U[c], F[c]);
+    rec[R_GP + c] = fma(alpha, D[c], Gs[c]);
+    rec[R_GM + c] = fma(-alpha, D[c], Gs[c]);
+    rec[R_MIX + c] = Gm[c];
+  }
+  rec[R_H] = h;
+  rec[R_M] = m;
+  rec[R_W] = w;
+}
+
+// ---------------------------------------------------------------------------------------------
+// One interface from the four stencil records (nodes i-1, i, i+1, i+2 along the sweep).
+// Outputs (12): 2 Fhat, 2 bhat, 24 dS Ghat (derivative-equation flux), 12 dT Mhat (mixed term),
+// where dS is the spacing along the sweep and dT the spacing across it.
+// qb[6] = source candidates q_1..q_3 of (b, dS b_s) for the '+' side then the mirrored '-' side.
+// ---------------------------------------------------------------------------------------------
+template <int DIR, bool LINEAR, bool CHAR>
+__device__ __forceinline__ void interface_values(const double* r0, const double* r1, const double* r2,
+                                                 const double* r3, int stride, const double qb[6], double g,
+                                                 double eps_w, double out[12]) {
+#define RV(r, f) (r)[(f) * stride]
+  // interface state: h = (h_i + h_{i+1})/2, u = (m_i + m_{i+1})/(h_i + h_{i+1}), v likewise
+  const double hs = RV(r1, R_H) + RV(r2, R_H);
+  const double rhs = fast_rcp(hs);
+  const double ub = (RV(r1, R_M) + RV(r2, R_M)) * rhs;
+  const double vb = (RV(r1, R_W) + RV(r2, R_W)) * rhs;
+  const double gh = (0.5 * g) * hs;
+  const double rs = fast_rsqrt(gh);
+  const double cb = gh * rs;
+  const double ic2 = 0.5 * rs;  // 1/(2c)
+  // normal / tangential velocity of this sweep
+  const double un = DIR == 0 ? ub : vb, ut = DIR == 0 ? vb : ub;
+  const double upc = un + cb, umc = un - cb;
+  // component indices: normal momentum and tangential momentum
+  const int cn = DIR == 0 ? 1 : 2, ct = DIR == 0 ? 2 : 1;
+  // scaled epsilon: fields 1, 3 carry s = 4c, field 2 carries s = 2 (both 2 without projection)
+  const double eps13 = CHAR ? (8.0 * g * eps_w) * hs : 4.0 * eps_w;
+  const double eps2 = 4.0 * eps_w;
+
+  double G[3], GB1 = 0.0, GB3 = 0.0;  // per-field sums over both sides; source fields 1 and 3
+  const double* rp[4] = {r0, r1, r2, r3};
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    // '+' uses nodes 0,1,2 of (F+, G+); '-' uses nodes 3,2,1 of (F-, G-) with the derivative negated.
+    const int o0 = side == 0 ? 0 : 3, o1 = side == 0 ? 1 : 2, o2 = side == 0 ? 2 : 1;
+    const int fo = side == 0 ? R_FP : R_FM, go = side == 0 ? R_GP : R_GM;
+    const double sg = side == 0 ? 1.0 : -1.0;
+    double f[3][3], p[3][3];  // [field][stencil point]
+    const int os[3] = {o0, o1, o2};
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const double* r = rp[os[t]];
+      const double F0 = RV(r, fo), Fn = RV(r, fo + cn), Ft = RV(r, fo + ct);
+      const double G0 = sg * RV(r, go), Gn = sg * RV(r, go + cn), Gt = sg * RV(r, go + ct);
+      if (CHAR) {
+        // rows of L without 1/(2c): (un+c, -1, 0), (-ut, 0, 1), (-(un-c), 1, 0) on (rho, normal, tangential)
+        f[0][t] = fma(upc, F0, -Fn);
+        f[1][t] = fma(-ut, F0, Ft);
+        f[2][t] = fma(-umc, F0, Fn);
+        p[0][t] = fma(upc, G0, -Gn);
+        p[1][t] = fma(-ut, G0, Gt);
+        p[2][t] = fma(-umc, G0, Gn);
+      } else {
+        f[0][t] = F0; f[1][t] = Fn; f[2][t] = Ft;
+        p[0][t] = G0; p[1][t] = Gn; p[2][t] = Gt;
+      }
+    }
+    const double* qbs = qb + 3 * side;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      Weights W;
+      const double e = (k == 1) ? eps2 : eps13;
+      const double v = hweno_side<LINEAR>(f[k][0], f[k][1], f[k][2], p[k][0], p[k][1], p[k][2], e, W);
+      G[k] = side == 0 ? v : G[k] + v;
+      if (CHAR) {
+        // source data per field: (-b, 0, +b) (row entries of the normal-momentum column)
+        if (k == 0) GB1 -= weighted(W, qbs[0], qbs[1], qbs[2]);
+        if (k == 2) GB3 += weighted(W, qbs[0], qbs[1], qbs[2]);
+      } else {
+        if (k == 1) GB1 += weighted(W, qbs[0], qbs[1], qbs[2]);  // the normal-momentum component itself
+      }
+    }
+  }
+  // back to physical components: 2 Fhat = R diag(1/s) G * 2
+  double F2[3], B2[3];
+  if (CHAR) {
+    const double A = (G[0] + G[2]) * ic2;
+    F2[0] = A;
+    F2[cn] = fma(un, A, 0.5 * (G[2] - G[0]));
+    F2[ct] = fma(ut, A, G[1]);
+    const double Bs = (GB1 + GB3) * ic2;
+    B2[0] = Bs;
+    B2[cn] = fma(un, Bs, 0.5 * (GB3 - GB1));
+    B2[ct] = ut * Bs;
+  } else {
+    F2[0] = G[0]; F2[cn] = G[1]; F2[ct] = G[2];
+    B2[0] = 0.0; B2[cn] = GB1; B2[ct] = 0.0;
+  }
+  // derivative-equation flux (eq. Rec-phi, component-wise): 24 dS Ghat = 3 fpart + gpart
+  // mixed term (eq. mixed): 12 dT Mhat = 7 (X_i + X_{i+1}) - (X_{i-1} + X_{i+2})
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double fpart =
+        fma(7.0, RV(r2, R_FP + c) - RV(r1, R_FM + c),
+            fma(8.0, RV(r2, R_FM + c) - RV(r1, R_FP + c), RV(r0, R_FP + c) - RV(r3, R_FM + c)));
+    const double gpart = fma(-5.0, RV(r2, R_GP + c) + RV(r1, R_GM + c),
+                             fma(-2.0, RV(r1, R_GP + c) + RV(r2, R_GM + c), RV(r0, R_GP + c) + RV(r3, R_GM + c)));
+    out[c] = F2[c];
+    out[3 + c] = B2[c];
+    out[6 + c] = fma(3.0, fpart, gpart);
+    out[9 + c] = fma(7.0, RV(r1, R_MIX + c) + RV(r2, R_MIX + c), -(RV(r0, R_MIX + c) + RV(r3, R_MIX + c)));
+  }
+#undef RV
+}
+
+// ---------------------------------------------------------------------------------------------
+// x-sweep: one block = XS_T consecutive x-interfaces k (between nodes k-1 and k) of one row.
+// ---------------------------------------------------------------------------------------------
+constexpr int XS_T = 128;
+constexpr int XS_N = XS_T + 3;
+
+template <bool LINEAR, bool CHAR>
+__global__ void __launch_bounds__(XS_T) k_sweep_x(Dev2D d, const double* __restrict__ alpha) {
+  __shared__ double sm[NREC * XS_N];
+  const int j = blockIdx.y;
+  const int k0 = blockIdx.x * XS_T;
+  const double ax = alpha[0];
+  for (int t = threadIdx.x; t < XS_N; t += XS_T) {
+    const int i = k0 - 2 + t;
+    if (i > d.nx + 1) break;
+    Node12 n;
+    load_node(d, i, j, n);
+    double rec[NREC];
+    node_record<0>(n, d.g, ax, rec);
+#pragma unroll
+    for (int f = 0; f < NREC; ++f) sm[f * XS_N + t] = rec[f];
+  }
+  __syncthreads();
+  const int k = k0 + threadIdx.x;
+  if (k > d.nx) return;
+  const int t = threadIdx.x;
+  const size_t o = (size_t)j * (d.nx + 1) + k;
+  double qb[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qbx[q] + o);
+  double out[12];
+  interface_values<0, LINEAR, CHAR>(sm + t, sm + t + 1, sm + t + 2, sm + t + 3, XS_N, qb, d.g, d.eps_w, out);
+#pragma unroll
+  for (int q = 0; q < 12; ++q) d.X[q][o] = out[q];
+}
+
+// ---------------------------------------------------------------------------------------------
+// y-sweep: each thread owns one column and marches down YS_T interfaces keeping the last four node
+// records in a private shared-memory ring (no block barrier, no recomputed halo across threads).
+// ---------------------------------------------------------------------------------------------
+constexpr int YS_W = 64;
+constexpr int YS_T = 64;
+
+template <bool LINEAR, bool CHAR>
+__global__ void __launch_bounds__(YS_W) k_sweep_y(Dev2D d, const double* __restrict__ alpha) {
+  extern __shared__ double ring[];  // [4 slots][NREC][YS_W]
+  const int i = blockIdx.x * YS_W + threadIdx.x;
+  if (i >= d.nx) return;
+  const int k0 = blockIdx.y * YS_T;
+  const double ay = alpha[1];
+  const int rend = min(k0 + YS_T, d.ny + 1);
+  const int stride = YS_W;  // field stride inside one slot
+  for (int r = k0 - 2; r <= rend; ++r) {
+    Node12 n;
+    load_node(d, i, r, n);
+    double rec[NREC];
+    node_record<1>(n, d.g, ay, rec);
+    double* slot = ring + (size_t)(r & 3) * NREC * YS_W + threadIdx.x;
+#pragma unroll
+    for (int f = 0; f < NREC; ++f) slot[f * stride] = rec[f];
+    const int k = r - 1;
+    if (k >= k0 && k < k0 + YS_T && k <= d.ny) {
+      const double* s0 = ring + (size_t)((k - 2) & 3) * NREC * YS_W + threadIdx.x;
+      const double* s1 = ring + (size_t)((k - 1) & 3) * NREC * YS_W + threadIdx.x;
+      const double* s2 = ring + (size_t)((k) & 3) * NREC * YS_W + threadIdx.x;
+      const double* s3 = ring + (size_t)((k + 1) & 3) * NREC * YS_W + threadIdx.x;
+      const size_t o = (size_t)k * d.nx + i;
+      double qb[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qby[q] + o);
+      double out[12];
+      interface_values<1, LINEAR, CHAR>(s0, s1, s2, s3, stride, qb, d.g, d.eps_w, out);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) d.Y[q][o] = out[q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Node kernel: RHS assembly, limiter, RK combination (or the bare RHS).
+// ---------------------------------------------------------------------------------------------
+struct NodeLim {
+  double U[3], D[3];
+};
+
+// Limiter along one direction at one node (Sec. 2.2), scaled data. L-rows without 1/(2c):
+// x: (u+c, -1, 0), (-v, 0, 1), (-(u-c), 1, 0); y: (v+c, 0, -1), (-u, 1, 0), (-(v-c), 0, 1).
+template <int DIR, bool LINEAR, bool CHAR>
+__device__ __forceinline__ void limit_dir(const double Um[3], const double U0[3], const double Up[3],
+                                          const double Dm[3], const double Dp[3], double u, double v, double c,
+                                          double ic2, double gh, double eps, double out[3]) {
+  const int cn = DIR == 0 ? 1 : 2, ct = DIR == 0 ? 2 : 1;
+  const double un = DIR == 0 ? u : v, ut = DIR == 0 ? v : u;
+  const double upc = un + c, umc = un - c;
+  auto proj = [&](const double* a, double o[3]) {
+    if (CHAR) {
+      o[0] = fma(upc, a[0], -a[cn]);
+      o[1] = fma(-ut, a[0], a[ct]);
+      o[2] = fma(-umc, a[0], a[cn]);
+    } else {
+      o[0] = a[0]; o[1] = a[cn]; o[2] = a[ct];
+    }
+  };
+  double m0[3], m1[3], m2[3], nl[3], nr[3];
+  proj(Um, m0); proj(U0, m1); proj(Up, m2); proj(Dm, nl); proj(Dp, nr);
+  const double e13 = CHAR ? (4.0 * eps) * gh : eps;
+  double nu[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) nu[k] = limiter_field<LINEAR>(m0[k], m1[k], m2[k], nl[k], nr[k], k == 1 ? eps : e13);
+  if (CHAR) {
+    const double A = (nu[0] + nu[2]) * ic2;
+    out[0] = A;
+    out[cn] = fma(un, A, 0.5 * (nu[2] - nu[0]));
+    out[ct] = fma(ut, A, nu[1]);
+  } else {
+    out[0] = nu[0]; out[cn] = nu[1]; out[ct] = nu[2];
+  }
+}
+
+template <int MODE, bool LINEAR, bool CHAR>
+__global__ void __launch_bounds__(256) k_node2d(Dev2D d, StageArgs sa) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y;
+  if (i >= d.nx || j >= d.ny) return;
+  const size_t o = (size_t)j * d.nx + i;
+  const size_t ox = (size_t)j * (d.nx + 1) + i;  // left x-interface; right is ox + 1
+  const size_t oy = (size_t)j * d.nx + i;        // lower y-interface; upper is oy + nx
+  double cur[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) cur[q] = __ldg(d.S[q] + o);
+  if (MODE == MODE_STAGE && !(*sa.dt > 0.0)) {
+    // a step of size 0 (e.g. clipped at the end time) leaves the state unchanged
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sa.out[q][o] = cur[q];
+    return;
+  }
+  const double eta = cur[0], H1 = cur[3], H2 = cur[6];
+  const double g = d.g;
+  const double ge = g * eta;
+  // ---- RHS (eq. swe-form-2d-dis) in scaled units: R_U, dx R_V, dy R_Q ----
+  double R[9];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double dFx = __ldg(d.X[c] + ox + 1) - __ldg(d.X[c] + ox);
+    const double dFy = __ldg(d.Y[c] + oy + d.nx) - __ldg(d.Y[c] + oy);
+    const double dbx = __ldg(d.X[3 + c] + ox + 1) - __ldg(d.X[3 + c] + ox);
+    const double dby = __ldg(d.Y[3 + c] + oy + d.nx) - __ldg(d.Y[3 + c] + oy);
+    const double dGx = __ldg(d.X[6 + c] + ox + 1) - __ldg(d.X[6 + c] + ox);
+    const double dGy = __ldg(d.Y[6 + c] + oy + d.nx) - __ldg(d.Y[6 + c] + oy);
+    const double dMx = __ldg(d.X[9 + c] + ox + 1) - __ldg(d.X[9 + c] + ox);
+    const double dMy = __ldg(d.Y[9 + c] + oy + d.nx) - __ldg(d.Y[9 + c] + oy);
+    const double db = fma(d.c_bx, dbx, d.c_by * dby);  // [b~]_x/dx + [b-]_y/dy
+    R[c] = fma(-ge, db, fma(-d.c_bx, dFx, -d.c_by * dFy));
+    double rv = fma(-d.c_gx, dGx, -d.c_my * dMy);
+    double rq = fma(-d.c_mx, dMx, -d.c_gy * dGy);
+    if (c > 0) {
+      rv = fma(-ge, __ldg(d.sv[c - 1] + o), rv);
+      rq = fma(-ge, __ldg(d.sq[c - 1] + o), rq);
+    }
+    R[3 + c] = fma(-g * H1, db, rv);
+    R[6 + c] = fma(-g * H2, db, rq);
+  }
+  if (MODE == MODE_RHS) {
+    // physical units: R_V = (dx R_V)/dx, R_Q = (dy R_Q)/dy
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const double s = q < 3 ? 1.0 : (q < 6 ? d.inv_dx : d.inv_dy);
+      sa.rhs_out[q][o] = R[q] * s;
+    }
+    return;
+  }
+  // ---- limiter (Sec. 2.2, dimension by dimension) ----
+  double mod[6];
+  if (sa.limiter) {
+    const double b0 = __ldg(d.stat[0] + o);
+    const double h = eta - b0;
+    const double gh = g * h;
+    const double rh = fast_rcp(h);
+    const double u = cur[1] * rh, v = cur[2] * rh;
+    const double rs = fast_rsqrt(gh);
+    const double c = gh * rs, ic2 = 0.5 * rs;
+    Node12 nm, np;
+    // x neighbours
+    load_node(d, i - 1, j, nm);
+    load_node(d, i + 1, j, np);
+    limit_dir<0, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 3, np.v + 3, u, v, c, ic2, gh, d.eps_lim, mod);
+    load_node(d, i, j - 1, nm);
+    load_node(d, i, j + 1, np);
+    limit_dir<1, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 6, np.v + 6, u, v, c, ic2, gh, d.eps_lim, mod + 3);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) mod[q] = cur[3 + q];
+  }
+  // ---- SSP-RK3 combination (eq. RK) ----
+  const double dt = *sa.dt;
+  if (sa.k == 1) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const double cq = q < 3 ? cur[q] : mod[q - 3];
+      if (sa.base) sa.base[q][o] = cq;
+      sa.out[q][o] = fma(dt, R[q], cq);
+    }
+  } else {
+    const double a = sa.k == 2 ? 0.75 : 1.0 / 3.0;
+    const double b = sa.k == 2 ? 0.25 : 2.0 / 3.0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const double cq = q < 3 ? cur[q] : mod[q - 3];
+      sa.out[q][o] = fma(a, __ldg(sa.base[q] + o), b * fma(dt, R[q], cq));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// alpha_x, alpha_y = max over nodes of |u| + c, |v| + c (exact max via ordered 64-bit keys),
+// plus a status flag for non-finite or non-positive depth.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_alpha2d(Dev2D d, unsigned long long* amax, int* status) {
+  unsigned long long kx = 0, ky = 0;
+  int bad = 0;
+  const size_t n = (size_t)d.nx * d.ny;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const double h = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
+    if (!(h > 0.0) || !(h < 1e300)) { bad = 1; continue; }
+    const double rh = fast_rcp(h);
+    const double gh = d.g * h;
+    const double c = gh * fast_rsqrt(gh);
+    const double u = __ldg(d.S[1] + o) * rh, v = __ldg(d.S[2] + o) * rh;
+    const double ax = dabs(u) + c, ay = dabs(v) + c;
+    if (!(ax < 1e300) || !(ay < 1e300)) { bad = 1; continue; }
+    kx = max(kx, dkey(ax));
+    ky = max(ky, dkey(ay));
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    kx = max(kx, __shfl_xor_sync(0xffffffffu, kx, s));
+    ky = max(ky, __shfl_xor_sync(0xffffffffu, ky, s));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(amax, kx);
+    atomicMax(amax + 1, ky);
+  }
+  if (bad) atomicOr(status, HW_STATUS_DEPTH);
+}
+
+// alpha keys -> doubles; dt = cfl / (alpha_x/dx + alpha_y/dy), optionally clipped to t_end - t.
+__global__ void k_finish_alpha2d(const unsigned long long* amax, double* alpha, double* dt_out, double cfl,
+                                 double inv_dx, double inv_dy, const double* t_now, double t_end) {
+  const double ax = __longlong_as_double((long long)amax[0]);
+  const double ay = __longlong_as_double((long long)amax[1]);
+  alpha[0] = ax;
+  alpha[1] = ay;
+  if (dt_out) {
+    double dt = cfl / fma(ax, inv_dx, ay * inv_dy);
+    double t_next = t_now ? *t_now + dt : 0.0;
+    if (t_now && t_end > 0.0) {
+      // the step that reaches t_end (within a relative 1e-12) ends exactly on it
+      const double rem = t_end - *t_now;
+      if (dt >= rem - 1e-12 * t_end) {
+        dt = rem > 0.0 ? rem : 0.0;
+        t_next = rem > 0.0 ? t_end : *t_now;
+      }
+    }
+    *dt_out = dt;
+    if (t_now) dt_out[1] = t_next;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Initialisation and conversion kernels
+// ---------------------------------------------------------------------------------------------
+// physical (h, hu, hv, b, h_x, hu_x, hv_x, h_y, hu_y, hv_y, b_x, b_y) -> equilibrium state with
+// scaled derivatives (eta = h + b, H = h_x + b_x; Sec. 3) and static (b, dx b_x, dy b_y).
+__global__ void k_init2d(Dev2D d, PhysIn in, int* status) {
+  const size_t n = (size_t)d.nx * d.ny;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const double h = in.p[0][o], b = in.p[3][o], bx = in.p[10][o], by = in.p[11][o];
+    if (!(h > 0.0) || !(h < 1e300)) atomicOr(status, HW_STATUS_DEPTH);
+    d.S[0][o] = h + b;
+    d.S[1][o] = in.p[1][o];
+    d.S[2][o] = in.p[2][o];
+    d.S[3][o] = d.dx * (in.p[4][o] + bx);
+    d.S[4][o] = d.dx * in.p[5][o];
+    d.S[5][o] = d.dx * in.p[6][o];
+    d.S[6][o] = d.dy * (in.p[7][o] + by);
+    d.S[7][o] = d.dy * in.p[8][o];
+    d.S[8][o] = d.dy * in.p[9][o];
+    d.stat[0][o] = b;
+    d.stat[1][o] = d.dx * bx;
+    d.stat[2][o] = d.dy * by;
+    d.bxy[0][o] = bx;
+    d.bxy[1][o] = by;
+  }
+}
+
+// state <-> user planes. layout 0: physical (h, hu, hv, h_x, hu_x, hv_x, h_y, hu_y, hv_y);
+// layout 1: equilibrium (eta, m, w, eta_x, m_x, w_x, eta_y, m_y, w_y). dir 0: export, 1: import.
+__global__ void k_convert2d(Dev2D d, Ptr9 src9, Ptr9 dst9, int layout, int dir) {
+  double* const* S = d.S;
+  const size_t n = (size_t)d.nx * d.ny;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const double b = d.stat[0][o], bx = d.bxy[0][o], by = d.bxy[1][o];
+    if (dir == 0) {
+      double x[9];
+      for (int q = 0; q < 9; ++q) x[q] = S[q][o];
+      dst9.p[0][o] = layout == 0 ? x[0] - b : x[0];
+      dst9.p[1][o] = x[1];
+      dst9.p[2][o] = x[2];
+      dst9.p[3][o] = layout == 0 ? x[3] * d.inv_dx - bx : x[3] * d.inv_dx;
+      dst9.p[4][o] = x[4] * d.inv_dx;
+      dst9.p[5][o] = x[5] * d.inv_dx;
+      dst9.p[6][o] = layout == 0 ? x[6] * d.inv_dy - by : x[6] * d.inv_dy;
+      dst9.p[7][o] = x[7] * d.inv_dy;
+      dst9.p[8][o] = x[8] * d.inv_dy;
+    } else {
+      double x[9];
+      for (int q = 0; q < 9; ++q) x[q] = src9.p[q][o];
+      S[0][o] = layout == 0 ? x[0] + b : x[0];
+      S[1][o] = x[1];
+      S[2][o] = x[2];
+      S[3][o] = d.dx * (layout == 0 ? x[3] + bx : x[3]);
+      S[4][o] = d.dx * x[4];
+      S[5][o] = d.dx * x[5];
+      S[6][o] = d.dy * (layout == 0 ? x[6] + by : x[6]);
+      S[7][o] = d.dy * x[7];
+      S[8][o] = d.dy * x[8];
+    }
+  }
+}
+
+// Static parts of the source terms that depend on b only (Sec. 2.1 Step 2 and eq. mixed):
+//   qbx/qby: Hermite candidates q_1..q_3 of (b, dS b_s) per interface and side (the nonlinear
+//            weights are applied per stage),
+//   sv, sq : dx [tilde-B1^]_x/dx + dx [bar-B1^]_y/dy and dy [tilde-B2^]_x/dx + dy [bar-B2^]_y/dy
+//            (normal-momentum and tangential-momentum components; the first component is zero).
+__device__ __forceinline__ double bval(const Dev2D& d, int q, int i, int j) {
+  // q: 0 b, 1 b_x, 2 b_y (physical); parities: b even; b_x odd across x-walls; b_y odd across y-walls
+  bool fx, fy;
+  const int ii = map_index(i, d.nx, d.bc_x, fx);
+  const int jj = map_index(j, d.ny, d.bc_y, fy);
+  const size_t o = (size_t)jj * d.nx + ii;
+  double x = q == 0 ? d.stat[0][o] : d.bxy[q - 1][o];
+  if (fx && q == 1) x = -x;
+  if (fy && q == 2) x = -x;
+  return x;
+}
+
+__device__ __forceinline__ void cands(double f0, double f1, double f2, double p0, double p1, double p2, double q[3]) {
+  q[0] = 0.5 * (f0 + f1) + (p0 + 5.0 * p1) / 6.0;
+  q[1] = 0.5 * (f1 + f2) + (p1 - p2) / 6.0;
+  q[2] = (f0 + 10.0 * f1 + f2) / 12.0 + 0.5 * p1;
+}
+
+// Derivative of the quintic at the interface, both sides summed, on (b/2, b_s/2) (eq. Rec-phi).
+__device__ __forceinline__ double qprime_sum(double b0, double b1, double b2, double b3, double s0, double s1,
+                                             double s2, double s3, double del) {
+  const double qp = (b0 - 8.0 * b1 + 7.0 * b2) / (4.0 * del) + (s0 - 2.0 * s1 - 5.0 * s2) / 12.0;
+  const double qm = (-7.0 * b1 + 8.0 * b2 - b3) / (4.0 * del) + (-5.0 * s1 - 2.0 * s2 + s3) / 12.0;
+  return 0.5 * (qp + qm);
+}
+
+__device__ __forceinline__ double mixed4(double a, double b, double c, double e) {
+  return (-a + 7.0 * b + 7.0 * c - e) / 12.0;
+}
+
+__global__ void k_static2d(Dev2D d) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y;
+  // x-interfaces k = i (0..nx) of row j; y-interfaces k = j (0..ny) of column i
+  if (j < d.ny && i <= d.nx) {
+    double b[4], s[4];
+    for (int t = 0; t < 4; ++t) {
+      b[t] = bval(d, 0, i - 2 + t, j);
+      s[t] = d.dx * bval(d, 1, i - 2 + t, j);
+    }
+    double qp[3], qm[3];
+    cands(b[0], b[1], b[2], s[0], s[1], s[2], qp);
+    cands(b[3], b[2], b[1], -s[3], -s[2], -s[1], qm);
+    const size_t o = (size_t)j * (d.nx + 1) + i;
+    for (int q = 0; q < 3; ++q) { d.qbx[q][o] = qp[q]; d.qbx[3 + q][o] = qm[q]; }
+  }
+  if (i < d.nx && j <= d.ny) {
+    double b[4], s[4];
+    for (int t = 0; t < 4; ++t) {
+      b[t] = bval(d, 0, i, j - 2 + t);
+      s[t] = d.dy * bval(d, 2, i, j - 2 + t);
+    }
+    double qp[3], qm[3];
+    cands(b[0], b[1], b[2], s[0], s[1], s[2], qp);
+    cands(b[3], b[2], b[1], -s[3], -s[2], -s[1], qm);
+    const size_t o = (size_t)j * d.nx + i;
+    for (int q = 0; q < 3; ++q) { d.qby[q][o] = qp[q]; d.qby[3 + q][o] = qm[q]; }
+  }
+  if (i < d.nx && j < d.ny) {
+    // x-interfaces i-1/2 (left, stencil i-2..i+1) and i+1/2 (right, i-1..i+2)
+    auto B1x = [&](int k) {  // tilde-B1 hat (normal-momentum component) at x-interface k-1/2
+      return qprime_sum(bval(d, 0, k - 2, j), bval(d, 0, k - 1, j), bval(d, 0, k, j), bval(d, 0, k + 1, j),
+                        bval(d, 1, k - 2, j), bval(d, 1, k - 1, j), bval(d, 1, k, j), bval(d, 1, k + 1, j), d.dx);
+    };
+    auto B2x = [&](int k) {  // tilde-B2 hat = mixed(b_y) at x-interface k-1/2
+      return mixed4(bval(d, 2, k - 2, j), bval(d, 2, k - 1, j), bval(d, 2, k, j), bval(d, 2, k + 1, j));
+    };
+    auto B1y = [&](int k) {  // bar-B1 hat = mixed(b_x) at y-interface k-1/2
+      return mixed4(bval(d, 1, i, k - 2), bval(d, 1, i, k - 1), bval(d, 1, i, k), bval(d, 1, i, k + 1));
+    };
+    auto B2y = [&](int k) {  // bar-B2 hat (tangential = y-momentum component) at y-interface k-1/2
+      return qprime_sum(bval(d, 0, i, k - 2), bval(d, 0, i, k - 1), bval(d, 0, i, k), bval(d, 0, i, k + 1),
+                        bval(d, 2, i, k - 2), bval(d, 2, i, k - 1), bval(d, 2, i, k), bval(d, 2, i, k + 1), d.dy);
+    };
+    const size_t o = (size_t)j * d.nx + i;
+    // dx * (tilde-B1 hat)_x / dx = difference; dx * (bar-B1 hat)_y / dy
+    d.sv[0][o] = B1x(i + 1) - B1x(i);
+    d.sv[1][o] = d.dx * (B1y(j + 1) - B1y(j)) * d.inv_dy;
+    // dy * (tilde-B2 hat)_x / dx; dy * (bar-B2 hat)_y / dy = difference
+    d.sq[0][o] = d.dy * (B2x(i + 1) - B2x(i)) * d.inv_dx;
+    d.sq[1][o] = B2y(j + 1) - B2y(j);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------------------------
+template <bool L, bool C>
+static void launch_sx(const Dev2D& d, const double* alpha, cudaStream_t st) {
+  dim3 gx((d.nx + 1 + XS_T - 1) / XS_T, d.ny);
+  k_sweep_x<L, C><<<gx, XS_T, 0, st>>>(d, alpha);
+}
+
+template <bool L, bool C>
+static void launch_sy(const Dev2D& d, const double* alpha, cudaStream_t st) {
+  dim3 gy((d.nx + YS_W - 1) / YS_W, (d.ny + 1 + YS_T - 1) / YS_T);
+  const size_t smem = (size_t)4 * NREC * YS_W * sizeof(double);
+  k_sweep_y<L, C><<<gy, YS_W, smem, st>>>(d, alpha);
+}
+
+template <int MODE, bool L, bool C>
+static void launch_node(const Dev2D& d, const StageArgs& sa, cudaStream_t st) {
+  dim3 g((d.nx + 31) / 32, (d.ny + 7) / 8);
+  k_node2d<MODE, L, C><<<g, dim3(32, 8), 0, st>>>(d, sa);
+}
+
+int set_kernel_attributes2d() {
+  const int smem = 4 * NREC * YS_W * (int)sizeof(double);
+  cudaError_t e = cudaSuccess;
+  e = cudaFuncSetAttribute(k_sweep_y<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_y<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_y<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_y<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e == cudaSuccess ? 0 : -1;
+}
+
+void launch_alpha2d(const Dev2D& d, unsigned long long* amax, int* status, cudaStream_t st) {
+  cudaMemsetAsync(amax, 0, 2 * sizeof(unsigned long long), st);
+  const size_t n = (size_t)d.nx * d.ny;
+  int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 8);
+  k_alpha2d<<<blocks, 256, 0, st>>>(d, amax, status);
+}
+
+void launch_finish_alpha2d(const Dev2D& d, const unsigned long long* amax, double* alpha, double* dt_out,
+                           double cfl, const double* t_now, double t_end, cudaStream_t st) {
+  k_finish_alpha2d<<<1, 1, 0, st>>>(amax, alpha, dt_out, cfl, d.inv_dx, d.inv_dy, t_now, t_end);
+}
+
+void launch_sweep_x2d(const Dev2D& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
+  if (linear) { if (chr) launch_sx<true, true>(d, alpha, st); else launch_sx<true, false>(d, alpha, st); }
+  else        { if (chr) launch_sx<false, true>(d, alpha, st); else launch_sx<false, false>(d, alpha, st); }
+}
+
+void launch_sweep_y2d(const Dev2D& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
+  if (linear) { if (chr) launch_sy<true, true>(d, alpha, st); else launch_sy<true, false>(d, alpha, st); }
+  else        { if (chr) launch_sy<false, true>(d, alpha, st); else launch_sy<false, false>(d, alpha, st); }
+}
+
+void launch_node2d(const Dev2D& d, const StageArgs& sa, int mode, bool linear, bool chr, cudaStream_t st) {
+  if (mode == MODE_RHS) {
+    if (linear) { if (chr) launch_node<MODE_RHS, true, true>(d, sa, st); else launch_node<MODE_RHS, true, false>(d, sa, st); }
+    else        { if (chr) launch_node<MODE_RHS, false, true>(d, sa, st); else launch_node<MODE_RHS, false, false>(d, sa, st); }
+  } else {
+    if (linear) { if (chr) launch_node<MODE_STAGE, true, true>(d, sa, st); else launch_node<MODE_STAGE, true, false>(d, sa, st); }
+    else        { if (chr) launch_node<MODE_STAGE, false, true>(d, sa, st); else launch_node<MODE_STAGE, false, false>(d, sa, st); }
+  }
+}
+
+void launch_init2d(const Dev2D& d, const PhysIn& in, int* status, cudaStream_t st) {
+  const size_t n = (size_t)d.nx * d.ny;
+  int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 16);
+  k_init2d<<<blocks, 256, 0, st>>>(d, in, status);
+  dim3 g((d.nx + 1 + 31) / 32, (d.ny + 1 + 7) / 8);
+  k_static2d<<<g, dim3(32, 8), 0, st>>>(d);
+}
+
+void launch_convert2d(const Dev2D& d, const Ptr9& src, const Ptr9& dst, int layout, int dir, cudaStream_t st) {
+  const size_t n = (size_t)d.nx * d.ny;
+  int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 16);
+  k_convert2d<<<blocks, 256, 0, st>>>(d, src, dst, layout, dir);
+}
+
+}  // namespace hw
