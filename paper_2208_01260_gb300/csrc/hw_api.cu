@@ -26,8 +26,12 @@ int fail(int code, const std::string& msg) {
   } while (0)
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
-// t <- t + dt, or the end time recorded next to dt by the CFL kernel (dt[1]) when dt came from it.
-__global__ void k_add_time(double* t, const double* dt, int snapped) { *t = snapped ? dt[1] : *t + *dt; }
+// t <- t + dt, or the end time recorded next to dt by the CFL kernel (dt[1]) when dt came from it;
+// counts the steps that advanced (dt > 0).
+__global__ void k_add_time(double* t, const double* dt, int snapped, unsigned long long* nsteps) {
+  *t = snapped ? dt[1] : *t + *dt;
+  if (*dt > 0.0) ++*nsteps;
+}
 
 }  // namespace
 
@@ -52,6 +56,7 @@ struct hw_solver {
   double* dt = nullptr;      // device dt
   double* t = nullptr;       // device simulated time
   int* status = nullptr;
+  unsigned long long* nsteps = nullptr;  // steps that advanced (dt > 0)
   hw::Dev2D d2{};
   hw::Dev1D d1{};
   cudaGraphExec_t graph = nullptr;
@@ -140,6 +145,7 @@ int hw_create(const hw_grid* grid, const hw_params* params, void* cuda_stream, h
   s->dt = misc + 4;  // dt[0] = step, dt[1] = time after the step (written by the CFL kernel)
   s->t = misc + 6;
   s->status = (int*)(misc + 7);
+  s->nsteps = (unsigned long long*)(misc + 8);
 
   const double dx = (grid->x1 - grid->x0) / nx;
   if (grid->dim == 2) {
@@ -307,7 +313,7 @@ int hw_rk3_step(hw_solver* s, double dt) {
     enqueue_alpha(s, false, -1.0);
     enqueue_stage(s, k);
   }
-  timed(s, HW_PROF_OTHER, [&] { k_add_time<<<1, 1, 0, s->stream>>>(s->t, s->dt, 0); });
+  timed(s, HW_PROF_OTHER, [&] { k_add_time<<<1, 1, 0, s->stream>>>(s->t, s->dt, 0, s->nsteps); });
   CUDA_OK(cudaGetLastError());
   return HW_OK;
 }
@@ -320,7 +326,7 @@ static void enqueue_cfl_step(hw_solver* s, double t_end) {
     enqueue_alpha(s, false, -1.0);
     enqueue_stage(s, k);
   }
-  timed(s, HW_PROF_OTHER, [&] { k_add_time<<<1, 1, 0, s->stream>>>(s->t, s->dt, 1); });
+  timed(s, HW_PROF_OTHER, [&] { k_add_time<<<1, 1, 0, s->stream>>>(s->t, s->dt, 1, s->nsteps); });
 }
 
 int hw_advance(hw_solver* s, int nsteps, double t_end, int use_graph, double* t_out, int* steps_out) {
@@ -328,7 +334,9 @@ int hw_advance(hw_solver* s, int nsteps, double t_end, int use_graph, double* t_
   if (!s->inited) return fail(HW_ERR_STATE, "hw_advance: call hw_init first");
   if (nsteps < 0) return fail(HW_ERR_ARG, "hw_advance: nsteps < 0");
   double t0 = 0.0;
+  unsigned long long n0 = 0, n1 = 0;
   CUDA_OK(cudaMemcpyAsync(&t0, s->t, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_OK(cudaMemcpyAsync(&n0, s->nsteps, sizeof(n0), cudaMemcpyDeviceToHost, s->stream));
   CUDA_OK(cudaStreamSynchronize(s->stream));
   int done = 0;
   const bool has_end = t_end > 0.0;
@@ -380,9 +388,10 @@ int hw_advance(hw_solver* s, int nsteps, double t_end, int use_graph, double* t_
     }
   }
   CUDA_OK(cudaMemcpyAsync(&t, s->t, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_OK(cudaMemcpyAsync(&n1, s->nsteps, sizeof(n1), cudaMemcpyDeviceToHost, s->stream));
   int rc = read_status(s);
   if (t_out) *t_out = t - t0;
-  if (steps_out) *steps_out = done;
+  if (steps_out) *steps_out = (int)(n1 - n0);  // steps of size 0 after t_end (inside a graph) do not count
   return rc;
 }
 

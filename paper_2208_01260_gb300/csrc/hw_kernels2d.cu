@@ -237,20 +237,19 @@ __global__ void __launch_bounds__(XS_T) k_sweep_x(Dev2D d, const double* __restr
 }
 
 // ---------------------------------------------------------------------------------------------
-// y-sweep: each thread owns one column and marches down YS_T interfaces keeping the last four node
+// y-sweep: each thread owns one column and marches down `seg` interfaces keeping the last four node
 // records in a private shared-memory ring (no block barrier, no recomputed halo across threads).
 // ---------------------------------------------------------------------------------------------
-constexpr int YS_W = 64;
-constexpr int YS_T = 64;
+constexpr int YS_W = 32;
 
 template <bool LINEAR, bool CHAR>
-__global__ void __launch_bounds__(YS_W) k_sweep_y(Dev2D d, const double* __restrict__ alpha) {
+__global__ void __launch_bounds__(YS_W) k_sweep_y(Dev2D d, const double* __restrict__ alpha, int seg) {
   extern __shared__ double ring[];  // [4 slots][NREC][YS_W]
   const int i = blockIdx.x * YS_W + threadIdx.x;
   if (i >= d.nx) return;
-  const int k0 = blockIdx.y * YS_T;
+  const int k0 = blockIdx.y * seg;
   const double ay = alpha[1];
-  const int rend = min(k0 + YS_T, d.ny + 1);
+  const int rend = min(k0 + seg, d.ny + 1);
   const int stride = YS_W;  // field stride inside one slot
   for (int r = k0 - 2; r <= rend; ++r) {
     Node12 n;
@@ -261,7 +260,7 @@ __global__ void __launch_bounds__(YS_W) k_sweep_y(Dev2D d, const double* __restr
 #pragma unroll
     for (int f = 0; f < NREC; ++f) slot[f * stride] = rec[f];
     const int k = r - 1;
-    if (k >= k0 && k < k0 + YS_T && k <= d.ny) {
+    if (k >= k0 && k < k0 + seg && k <= d.ny) {
       const double* s0 = ring + (size_t)((k - 2) & 3) * NREC * YS_W + threadIdx.x;
       const double* s1 = ring + (size_t)((k - 1) & 3) * NREC * YS_W + threadIdx.x;
       const double* s2 = ring + (size_t)((k) & 3) * NREC * YS_W + threadIdx.x;
@@ -628,11 +627,33 @@ static void launch_sx(const Dev2D& d, const double* alpha, cudaStream_t st) {
   k_sweep_x<L, C><<<gx, XS_T, 0, st>>>(d, alpha);
 }
 
+// Segment length of the y-sweep: one balanced wave of resident blocks when the grid allows it
+// (the blocks of a column segment all do the same work), at least 8 interfaces per segment.
+static int sweep_y_segment(int nx, int ny, int blocks_per_sm) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int cols = (nx + YS_W - 1) / YS_W;
+  const long resident = (long)sms * std::max(blocks_per_sm, 1);
+  long segs = std::max(1L, resident / cols);
+  int seg = (int)((ny + 1 + segs - 1) / segs);
+  return std::max(seg, std::min(8, ny + 1));
+}
+
 template <bool L, bool C>
 static void launch_sy(const Dev2D& d, const double* alpha, cudaStream_t st) {
-  dim3 gy((d.nx + YS_W - 1) / YS_W, (d.ny + 1 + YS_T - 1) / YS_T);
   const size_t smem = (size_t)4 * NREC * YS_W * sizeof(double);
-  k_sweep_y<L, C><<<gy, YS_W, smem, st>>>(d, alpha);
+  static int bps = -1;
+  if (bps < 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_sweep_y<L, C>, YS_W, smem) != cudaSuccess) bps = 1;
+  }
+  const int seg = sweep_y_segment(d.nx, d.ny, bps);
+  dim3 gy((d.nx + YS_W - 1) / YS_W, (d.ny + 1 + seg - 1) / seg);
+  k_sweep_y<L, C><<<gy, YS_W, smem, st>>>(d, alpha, seg);
 }
 
 template <int MODE, bool L, bool C>
