@@ -133,6 +133,25 @@ int hw_get_base(hw_solver* s, double* const* out, int ptr_kind);
 int hw_set_profiling(hw_solver* s, int on);
 int hw_get_profile(hw_solver* s, double* ms, int* launches);
 
+/* Allocation-free variant of the 1D right-hand side: the same numbers as hw_create + hw_init + hw_rhs on
+ * a 1D grid (out: 4 planes d/dt (eta, m, eta_x, m_x)), with every array pointer on the device. The paper
+ * has no counterpart; this call exists for callers that must not allocate device memory, such as code
+ * inside a framework whose memory pool owns the GPU's memory (a separate cudaMalloc could fail or escape
+ * the pool's accounting) and time-critical loops that cannot pay for cudaMalloc's implicit
+ * synchronisation and unpredictable latency. The caller passes inputs (h, hu, b: nx each; deriv[3] =
+ * h_x, hu_x, b_x) and outputs; the working memory (state, b-only source terms, interface values, the
+ * alpha accumulator) is a file-scope device array sized for HW_NOALLOC_MAX_NX nodes, which every GPU
+ * that loads the library holds until the process exits. Larger grids return HW_ERR_ARG.
+ *   - The call allocates nothing and is stream-ordered on cuda_stream (NULL = legacy default stream);
+ *     it does not check the depth (h must be > 0) and does not synchronise.
+ *   - Every call reuses the same array and leaves its contents behind (it clears what must start at
+ *     zero), so calls that may overlap on the GPU (other streams or unordered host threads) race.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ *     device current; make that first call before any stream capture. */
+#define HW_NOALLOC_MAX_NX 16384
+int hw_rhs1d_noalloc(const hw_grid* grid, const hw_params* params, const double* h, const double* hu,
+                     const double* b, const double* const* deriv, double* const* out, void* cuda_stream);
+
 /* Wait for the stream and return the device status as an HW_ERR_* code (HW_OK if clean). */
 int hw_sync(hw_solver* s);
 

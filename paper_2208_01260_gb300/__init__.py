@@ -21,7 +21,7 @@ __all__ = [
     "HW_LAYOUT_EQUILIBRIUM", "HwError", "hw_grid", "hw_params", "lib", "make_grid", "make_params",
     "hw_create", "hw_destroy", "hw_init", "hw_rhs", "hw_alpha", "hw_cfl_dt", "hw_rk3_step", "hw_rk3_stage",
     "hw_advance", "hw_get_state", "hw_set_state", "hw_get_base", "hw_sync", "hw_version", "Solver",
-    "hw_set_profiling", "hw_get_profile",
+    "hw_set_profiling", "hw_get_profile", "hw_rhs1d_noalloc",
 ]
 
 HW_OK = 0
@@ -258,6 +258,21 @@ def hw_get_profile(h: _Handle):
     n = (C.c_int * 5)()
     _check(lib().hw_get_profile(h.ptr, ms, n), "hw_get_profile")
     return {k: (ms[i], n[i]) for i, k in enumerate(HW_PROF_NAMES)}
+
+
+def hw_rhs1d_noalloc(grid: hw_grid, params: hw_params, hh, hu, b, deriv: Sequence, out: Sequence, stream=None):
+    """Allocation-free 1D right-hand side; every plane is a CUDA tensor of grid.nx float64 values."""
+    L = lib()
+    f = L.hw_rhs1d_noalloc
+    if f.argtypes is None:
+        f.argtypes = [C.POINTER(hw_grid), C.POINTER(hw_params), C.c_void_p, C.c_void_p, C.c_void_p,
+                      C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]
+        f.restype = C.c_int
+    if _kind([hh, hu, b, *deriv, *out]) != HW_DEVICE:
+        raise ValueError("hw_rhs1d_noalloc takes device tensors only")
+    n = grid.nx
+    _check(f(C.byref(grid), C.byref(params), _ptr(hh, n), _ptr(hu, n), _ptr(b, n), _pp([_ptr(a, n) for a in deriv]),
+             _pp([_ptr(a, n, True) for a in out]), _stream_handle(stream)), "hw_rhs1d_noalloc")
 
 
 def hw_version() -> str:

@@ -35,6 +35,10 @@ __global__ void k_add_time(double* t, const double* dt, int snapped, unsigned lo
 
 }  // namespace
 
+namespace hw {
+int set_last_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace hw
+
 struct hw_solver {
   int dev = 0;
   hw_grid grid{};

@@ -79,6 +79,9 @@ void launch_node2d(const Dev2D& d, const StageArgs& sa, int mode, bool linear, b
 void launch_init2d(const Dev2D& d, const PhysIn& in, int* status, cudaStream_t st);
 void launch_convert2d(const Dev2D& d, const Ptr9& src, const Ptr9& dst, int layout, int dir, cudaStream_t st);
 
+// record an error message for hw_last_error (hw_api.cu); returns code
+int set_last_error(int code, const char* msg);
+
 // launchers (hw_kernels1d.cu)
 void launch_alpha1d(const Dev1D& d, unsigned long long* amax, int* status, cudaStream_t st);
 void launch_finish_alpha1d(const Dev1D& d, const unsigned long long* amax, double* alpha, double* dt_out,
