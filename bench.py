@@ -34,14 +34,16 @@ WORKLOAD = ("2D plain scheme, 2048x2048 on [0,2]x[0,1], reflective walls, 8 Gaus
 METRIC = "FP64 point-updates/s (grid pts x RK stages) at 2048^2"
 UNIT = "point-updates/s"
 
-# Algorithmic FP64 work per unit of each kernel, counted from the formulas the kernels evaluate
-# (add/sub = 1 flop, mul = 1, fma = 2; a reciprocal or reciprocal square root is its three-fma or
-# five-op refinement; see the design notes for the per-term tally).
-FLOPS_PER_UNIT = {
-    "sweep_x": 687.0,   # per x-interface, including its share of the node records
-    "sweep_y": 687.0,   # per y-interface
-    "node": 518.0,      # per node (RHS assembly, limiter in x and y, RK combination)
-    "alpha": 21.0,      # per node
+# Algorithmic FP64 work per unit of each kernel, tallied from the formulas the kernels evaluate
+# (the design notes list every term): "ops" counts add, mul and fma as one FP64 operation each,
+# "flops" counts an fma as 2. A reciprocal is a hardware seed plus three fma, a reciprocal square
+# root a seed plus five operations. Sweeps: 432 operations per interface plus about 1.03 node
+# records of 42 operations; node kernel averaged over the three RK stages.
+ALGO = {
+    "sweep_x": {"ops": 475.0, "flops": 685.7},  # per x-interface
+    "sweep_y": {"ops": 475.7, "flops": 686.7},  # per y-interface
+    "node": {"ops": 365.0, "flops": 511.0},     # per node
+    "alpha": {"ops": 15.0, "flops": 27.0},      # per node
 }
 UNITS_PER_LAUNCH = {
     "sweep_x": (NX + 1) * NY,
@@ -49,23 +51,32 @@ UNITS_PER_LAUNCH = {
     "node": NX * NY,
     "alpha": NX * NY,
 }
+# FP64 peak from the unit counts and the clock: 152 SMs x 2 DFMA per SM per cycle (the sustained FP64
+# pipe peak ncu reports on GB300) x 2 flops x 2.07 GHz.
+SMS, DFMA_PER_SM_CLK, SM_GHZ = 152, 2, 2.07
+PEAK_FP64_TFLOPS = SMS * DFMA_PER_SM_CLK * 2 * SM_GHZ / 1e3
+PEAK_FP64_OPS = SMS * DFMA_PER_SM_CLK * SM_GHZ * 1e9
+# DRAM bytes per unit from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum), valid only
+# for the kernel sources they were taken on (sha256 of the CUDA sources).
+TRAFFIC = {}
 STATE_BYTES = 9 * NX * NY * 8
 
 
-def peaks():
-    p = {"hbm_gbs": 6783.5, "fp64_tflops": None, "src": "fallback"}
+def hbm_peak():
     try:
-        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        p["hbm_gbs"] = m.get("hbm_gbs", p["hbm_gbs"])
-        p["src"] = "measured"
-        p["fp64_tflops"] = m.get("fp64_tflops")
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"], "measured"
     except Exception:
-        pass
-    if p["fp64_tflops"] is None:
-        # DFMA throughput measured on this machine's GB300 (1.6 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flops)
-        p["fp64_tflops"] = 1.0086
-        p["fp64_src"] = "measured DFMA microbenchmark (0.505e12 DFMA/s)"
-    return p
+        return 6800.0, "fallback"
+
+
+def sources_sha():
+    import hashlib
+    d = os.path.join(ROOT, "paper_2208_01260_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
@@ -271,23 +282,37 @@ def main():
     hw.hw_set_profiling(solver.h, False)
     launches_per_step = sum(n for _, n in prof.values()) / args.steps
 
-    pk = peaks()
+    sha = sources_sha()
+    hbm, hbm_src = hbm_peak()
     kernels = {}
     for k in ("sweep_x", "sweep_y", "node", "alpha"):
         tot, n = prof[k]
         if n == 0:
             continue
         nl = n if k != "alpha" else n // 2  # the alpha class counts reduction + finish launches
-        avg_ms = tot / nl
-        fl = FLOPS_PER_UNIT[k] * UNITS_PER_LAUNCH[k]
-        kernels[k] = {"ms_avg": avg_ms, "launches": n, "share": tot / ms_prof,
-                      "tflops": fl / (avg_ms * 1e-3) / 1e12}
+        avg_s = tot / nl * 1e-3
+        units = UNITS_PER_LAUNCH[k]
+        tf = ALGO[k]["flops"] * units / avg_s / 1e12
+        tr = TRAFFIC.get(k)
+        traffic = tr["bytes_per_unit"] * units if tr and tr["sha"] == sha else None
+        kernels[k] = {"ms_avg": avg_s * 1e3, "launches": n, "share": tot / ms_prof, "tflops": tf,
+                      "frac": tf / PEAK_FP64_TFLOPS,
+                      "fp64_issue_frac": ALGO[k]["ops"] * units / avg_s / PEAK_FP64_OPS,
+                      "traffic_bytes": traffic,
+                      "hbm_frac": (traffic / avg_s / 1e9 / hbm) if traffic else None}
     dom = max(kernels, key=lambda k: kernels[k]["share"])
-    ach = kernels[dom]["tflops"]
-    roofline = {"bound": "alu", "achieved": ach, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
-                "frac": ach / pk["fp64_tflops"], "traffic": None, "kernel": "k_" + dom,
-                "peak_src": "FP64 DFMA throughput measured on this GB300 pool (no FP64 entry in the peaks file)",
-                "hbm_frac_of_measured": None}
+    kd = kernels[dom]
+    roofline = {"bound": "alu", "achieved": kd["tflops"], "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": kd["frac"], "traffic": kd["traffic_bytes"], "kernel": "k_" + dom,
+                "peak_src": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (recipe unit counts and clock; "
+                            "ncu sustained-peak 2 DFMA/clk/SM)",
+                "fp64_issue_frac": kd["fp64_issue_frac"], "hbm_peak_gbs": hbm, "hbm_peak_src": hbm_src,
+                "sources_sha": sha}
+    step_ops = sum(ALGO[k]["ops"] * UNITS_PER_LAUNCH[k] for k in ALGO) * STAGES
+    step_flops = sum(ALGO[k]["flops"] * UNITS_PER_LAUNCH[k] for k in ALGO) * STAGES
+    roofline["whole_step"] = {"tflops": step_flops / (ms / args.steps * 1e-3) / 1e12,
+                              "frac": step_flops / (ms / args.steps * 1e-3) / 1e12 / PEAK_FP64_TFLOPS,
+                              "fp64_issue_frac": step_ops / (ms / args.steps * 1e-3) / PEAK_FP64_OPS}
 
     # e2e through the public API with pinned host buffers: each step uploads the state (physical
     # layout, 9 planes), advances one RK3 step and downloads the state.
