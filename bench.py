@@ -182,6 +182,50 @@ def oracle_rate(seconds_budget=60.0):
     return NX * NY * stages / elapsed, desc, threads, elapsed
 
 
+def batched_compare(steps, n_inst=512):
+    """Config 4: n_inst grids with nx, ny log-uniform in [64, 1024] on [0,1]^2, reflective, seeded
+    bathymetry and surface hump, each at its own CFL dt. Aggregate point-updates/s of the batched form
+    (one launch per phase over all grids, CUDA graph) and of the plain loop (one single-grid solver per
+    instance advanced one step at a time)."""
+    import torch
+    import paper_2208_01260_gb300 as hw
+    from paper_2208_01260_gb300 import scenarios as S
+    nxs, nys = S.batch_sizes(n_inst)
+    scs = [S.batch_scenario(i, int(nxs[i]), int(nys[i])) for i in range(n_inst)]
+    pts = float(sum(int(a) * int(b) for a, b in zip(nxs, nys)))
+    stream = torch.cuda.current_stream()
+    b = hw.BatchedSolver(scs)
+    tune = b.autotune()
+    b.run(3, use_graph=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run(steps, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    b.close()
+    solvers = [hw.Solver.from_scenario(sc, hw.make_params()) for sc in scs]
+    for s in solvers:
+        s.advance(1, use_graph=False)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        for s in solvers:
+            s.advance(1, use_graph=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1)
+    for s in solvers:
+        s.close()
+    vb = pts * STAGES * steps / (ms_b * 1e-3)
+    vp = pts * STAGES * steps / (ms_p * 1e-3)
+    return {"instances": n_inst, "total_points": int(pts), "steps": steps, "value_batched": vb, "value_plain": vp,
+            "ratio": vb / vp, "ms_per_step_batched": ms_b / steps, "ms_per_step_plain": ms_p / steps,
+            "unit": UNIT, "plain": "hw_advance(1 step) per instance per step, eager",
+            "tiles": "autotuned per size class"}
+
+
 def run_reference(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -226,6 +270,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--batched-steps", type=int, default=6, help="steps of the batched comparison (0 = skip)")
     ap.add_argument("--nx", type=int, default=2048, help="smaller grids for profiling captures only")
     ap.add_argument("--ny", type=int, default=2048)
     args = ap.parse_args()
@@ -347,6 +392,9 @@ def main():
             "roofline": roofline, "kernels": kernels, "ms_per_step_profiled": ms_prof / args.steps,
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clk.summary(), "e2e": e2e}
+    if args.batched_steps > 0 and (NX, NY) == (2048, 2048):
+        solver.close()
+        line["batched"] = batched_compare(args.batched_steps)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, desc, threads, el = oracle_rate()
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,

@@ -133,6 +133,37 @@ int hw_get_base(hw_solver* s, double* const* out, int ptr_kind);
 int hw_set_profiling(hw_solver* s, int on);
 int hw_get_profile(hw_solver* s, double* ms, int* launches);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched form: n independent 2D grids of uneven sizes (all HW_BC_* allowed, shared parameters) that
+ * advance together, each with its own CFL time step computed on the device (Sec. 4: dt from the CFL
+ * number and alpha of that grid). Each phase of an RK stage is one launch over the tiles of all grids,
+ * and two steps run from one CUDA graph. Every grid's result equals a single-grid solver's
+ * (hw_create + hw_advance) to rounding; tile shapes do not change it at all.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct hw_batch hw_batch;
+
+/* grids[n]: 2D grids (nx, ny >= 2). Allocates pooled device buffers. */
+int hw_batch_create(int n, const hw_grid* grids, const hw_params* params, void* cuda_stream, hw_batch** out);
+int hw_batch_destroy(hw_batch* b);
+/* Initial state of grid i, as hw_init (2D): h, hu, hv, b and deriv[8]. Synchronises the stream. */
+int hw_batch_init(hw_batch* b, int i, const double* h, const double* hu, const double* hv, const double* bb,
+                  const double* const* deriv, int ptr_kind);
+/* nsteps SSP-RK3 steps of every grid at its own CFL dt; synchronises and reports HW_ERR_DEPTH if any
+ * grid produced a non-positive or non-finite depth. */
+int hw_batch_run(hw_batch* b, int nsteps, int use_graph);
+/* State of grid i (9 planes, layout HW_LAYOUT_*). */
+int hw_batch_get_state(hw_batch* b, int i, double* const* out, int layout, int ptr_kind);
+/* Simulated time and step count of every grid (t[n], steps[n]; either may be NULL). */
+int hw_batch_get_time(hw_batch* b, double* t, int* steps);
+/* Tile shapes of grid i: tx = interfaces per x-tile (32, 64 or 128; 128/tx rows per tile), seg =
+ * interfaces per y-segment (>= 1). Chosen by the autotuner; arithmetic is unaffected. */
+int hw_batch_set_tiles(hw_batch* b, int i, int tx, int seg);
+int hw_batch_get_tiles(hw_batch* b, int i, int* tx, int* seg);
+/* Autotuner measurement: average ms of the batched x-sweep and y-sweep over the grids ids[nids] with
+ * trial tile shapes (tx, seg), over reps repetitions. Changes no state (interface planes are scratch). */
+int hw_batch_time_tiles(hw_batch* b, int nids, const int* ids, int tx, int seg, int reps, double* ms_x,
+                        double* ms_y);
+
 /* Allocation-free variant of the 1D right-hand side: the same numbers as hw_create + hw_init + hw_rhs on
  * a 1D grid (out: 4 planes d/dt (eta, m, eta_x, m_x)), with every array pointer on the device. The paper
  * has no counterpart; this call exists for callers that must not allocate device memory, such as code

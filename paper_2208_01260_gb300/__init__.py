@@ -21,7 +21,9 @@ __all__ = [
     "HW_LAYOUT_EQUILIBRIUM", "HwError", "hw_grid", "hw_params", "lib", "make_grid", "make_params",
     "hw_create", "hw_destroy", "hw_init", "hw_rhs", "hw_alpha", "hw_cfl_dt", "hw_rk3_step", "hw_rk3_stage",
     "hw_advance", "hw_get_state", "hw_set_state", "hw_get_base", "hw_sync", "hw_version", "Solver",
-    "hw_set_profiling", "hw_get_profile", "hw_rhs1d_noalloc",
+    "hw_set_profiling", "hw_get_profile", "hw_rhs1d_noalloc", "BatchedSolver", "hw_batch_create",
+    "hw_batch_destroy", "hw_batch_init", "hw_batch_run", "hw_batch_get_state", "hw_batch_get_time",
+    "hw_batch_set_tiles", "hw_batch_get_tiles", "hw_batch_time_tiles",
 ]
 
 HW_OK = 0
@@ -273,6 +275,135 @@ def hw_rhs1d_noalloc(grid: hw_grid, params: hw_params, hh, hu, b, deriv: Sequenc
     n = grid.nx
     _check(f(C.byref(grid), C.byref(params), _ptr(hh, n), _ptr(hu, n), _ptr(b, n), _pp([_ptr(a, n) for a in deriv]),
              _pp([_ptr(a, n, True) for a in out]), _stream_handle(stream)), "hw_rhs1d_noalloc")
+
+
+# ------------------------------------------------------------------------------------------------
+# batched form
+# ------------------------------------------------------------------------------------------------
+def _batch_sigs():
+    L = lib()
+    if getattr(L, "_batch_ready", False):
+        return L
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    pp = C.POINTER(C.c_void_p)
+    for name, args in {
+        "hw_batch_create": [i, C.POINTER(hw_grid), C.POINTER(hw_params), vp, C.POINTER(vp)],
+        "hw_batch_destroy": [vp],
+        "hw_batch_init": [vp, i, vp, vp, vp, vp, pp, i],
+        "hw_batch_run": [vp, i, i],
+        "hw_batch_get_state": [vp, i, pp, i, i],
+        "hw_batch_get_time": [vp, C.POINTER(d), C.POINTER(i)],
+        "hw_batch_set_tiles": [vp, i, i, i],
+        "hw_batch_get_tiles": [vp, i, C.POINTER(i), C.POINTER(i)],
+        "hw_batch_time_tiles": [vp, i, C.POINTER(i), i, i, i, C.POINTER(d), C.POINTER(d)],
+    }.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = i
+    L._batch_ready = True
+    return L
+
+
+class _BHandle:
+    def __init__(self, ptr, grids):
+        self.ptr, self.grids = ptr, grids
+
+
+def hw_batch_create(grids: Sequence[hw_grid], params: hw_params, stream=None) -> _BHandle:
+    L = _batch_sigs()
+    arr = (hw_grid * len(grids))(*grids)
+    out = C.c_void_p()
+    _check(L.hw_batch_create(len(grids), arr, C.byref(params), _stream_handle(stream), C.byref(out)), "hw_batch_create")
+    return _BHandle(out, list(grids))
+
+
+def hw_batch_destroy(b: _BHandle):
+    if b is not None and b.ptr:
+        _batch_sigs().hw_batch_destroy(b.ptr)
+        b.ptr = None
+
+
+def hw_batch_init(b: _BHandle, i: int, hh, hu, hv, bb, deriv: Sequence):
+    g = b.grids[i]
+    n = g.nx * g.ny
+    kind = _kind([hh, hu, hv, bb, *deriv])
+    _check(_batch_sigs().hw_batch_init(b.ptr, i, _ptr(hh, n), _ptr(hu, n), _ptr(hv, n), _ptr(bb, n),
+                                       _pp([_ptr(a, n) for a in deriv]), kind), "hw_batch_init")
+
+
+def hw_batch_run(b: _BHandle, nsteps: int, use_graph: bool = True):
+    _check(_batch_sigs().hw_batch_run(b.ptr, int(nsteps), int(bool(use_graph))), "hw_batch_run")
+
+
+def hw_batch_get_state(b: _BHandle, i: int, out: Sequence, layout: int = HW_LAYOUT_EQUILIBRIUM):
+    g = b.grids[i]
+    n = g.nx * g.ny
+    _check(_batch_sigs().hw_batch_get_state(b.ptr, i, _pp([_ptr(a, n, True) for a in out]), int(layout), _kind(out)),
+           "hw_batch_get_state")
+
+
+def hw_batch_get_time(b: _BHandle):
+    n = len(b.grids)
+    t = (C.c_double * n)()
+    k = (C.c_int * n)()
+    _check(_batch_sigs().hw_batch_get_time(b.ptr, t, k), "hw_batch_get_time")
+    return np.array(t[:]), np.array(k[:])
+
+
+def hw_batch_set_tiles(b: _BHandle, i: int, tx: int, seg: int):
+    _check(_batch_sigs().hw_batch_set_tiles(b.ptr, int(i), int(tx), int(seg)), "hw_batch_set_tiles")
+
+
+def hw_batch_get_tiles(b: _BHandle, i: int):
+    tx, seg = C.c_int(), C.c_int()
+    _check(_batch_sigs().hw_batch_get_tiles(b.ptr, int(i), C.byref(tx), C.byref(seg)), "hw_batch_get_tiles")
+    return tx.value, seg.value
+
+
+def hw_batch_time_tiles(b: _BHandle, ids: Sequence[int], tx: int, seg: int, reps: int = 3):
+    arr = (C.c_int * len(ids))(*[int(i) for i in ids])
+    mx, my = C.c_double(), C.c_double()
+    _check(_batch_sigs().hw_batch_time_tiles(b.ptr, len(ids), arr, int(tx), int(seg), int(reps), C.byref(mx),
+                                             C.byref(my)), "hw_batch_time_tiles")
+    return mx.value, my.value
+
+
+class BatchedSolver:
+    """Many 2D grids advancing together (one launch per phase over all grids, CUDA graph)."""
+
+    def __init__(self, scenarios, params: Optional[hw_params] = None, stream=None):
+        grids = [make_grid(s.nx, s.ny, s.x0, s.x1, s.y0, s.y1, s.bc_x, s.bc_y, dim=2) for s in scenarios]
+        self.params = params or make_params()
+        self.h = hw_batch_create(grids, self.params, stream)
+        self.grids = grids
+        for i, s in enumerate(scenarios):
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in [s.h, s.hu, s.hv, s.b] + list(s.deriv)]
+            hw_batch_init(self.h, i, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4:])
+
+    def close(self):
+        hw_batch_destroy(self.h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, nsteps, use_graph=True):
+        hw_batch_run(self.h, nsteps, use_graph)
+
+    def state(self, i, layout=HW_LAYOUT_EQUILIBRIUM):
+        g = self.grids[i]
+        out = [np.empty((g.ny, g.nx)) for _ in range(9)]
+        hw_batch_get_state(self.h, i, out, layout)
+        return out
+
+    def times(self):
+        return hw_batch_get_time(self.h)
+
+    def autotune(self, cache_path: Optional[str] = None, reps: int = 3):
+        from . import autotune
+        return autotune.tune(self, cache_path=cache_path, reps=reps)
 
 
 def hw_version() -> str:

@@ -1,0 +1,86 @@
+"""The batched form against single-grid solvers (same formulas, only the launch organisation
+differs; the two kernels may contract multiply-adds differently, so agreement is to rounding) and
+the autotuner (tile shapes never change the numbers: bitwise)."""
+import numpy as np
+import pytest
+
+from paper_2208_01260_gb300 import scenarios as S
+from _parity import normwise, stage_scales
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hw():
+    import paper_2208_01260_gb300 as hw
+    import torch
+    assert torch.cuda.is_available()
+    hw.lib()
+    return hw
+
+
+def _mixed_batch():
+    sizes = [(64, 64), (100, 37), (257, 130), (33, 301), (150, 150), (2, 5), (513, 70)]
+    out = []
+    for k, (nx, ny) in enumerate(sizes):
+        sc = S.hump2d(nx, ny, seed=100 + k, bc=S.PERIODIC if k % 3 == 2 else S.REFLECTIVE)
+        out.append(sc)
+    return out
+
+
+def test_batched_equals_single_grid_solvers(hw):
+    scs = _mixed_batch()
+    b = hw.BatchedSolver(scs)
+    b.run(5, use_graph=True)
+    t, steps = b.times()
+    assert list(steps) == [5] * len(scs)
+    for i, sc in enumerate(scs):
+        s = hw.Solver.from_scenario(sc, hw.make_params())
+        ts, n = s.advance(5, use_graph=False)
+        assert n == 5 and abs(ts - t[i]) <= 1e-14 * t[i]
+        ref = s.state()
+        stat = [sc.b, sc.deriv[6], sc.deriv[7]]
+        assert max(normwise(b.state(i), ref, stage_scales(ref, stat))) <= 1e-12
+
+
+def test_tile_shapes_do_not_change_results(hw):
+    scs = _mixed_batch()
+    a = hw.BatchedSolver(scs)
+    c = hw.BatchedSolver(scs)
+    for i, sc in enumerate(scs):
+        hw.hw_batch_set_tiles(c.h, i, [32, 64, 128][i % 3], [5, 16, 64, 300][i % 4])
+    a.run(3, use_graph=False)
+    c.run(3, use_graph=True)
+    for i in range(len(scs)):
+        for x, y in zip(a.state(i), c.state(i)):
+            assert np.array_equal(x, y)
+
+
+def test_autotuner_picks_valid_tiles(hw, tmp_path):
+    from paper_2208_01260_gb300 import autotune
+    scs = [S.hump2d(nx, ny, seed=200 + k) for k, (nx, ny) in enumerate([(64, 300), (300, 64), (130, 130)])]
+    b = hw.BatchedSolver(scs)
+    ref = hw.BatchedSolver(scs)
+    res = b.autotune(cache_path=str(tmp_path / "tune.json"))
+    assert (tmp_path / "tune.json").exists()
+    for i, sc in enumerate(scs):
+        tx, seg = hw.hw_batch_get_tiles(b.h, i)
+        assert tx in autotune.TX_CANDIDATES and 1 <= seg <= sc.ny + 1
+    b.run(2)
+    ref.run(2)
+    for i in range(len(scs)):
+        for x, y in zip(b.state(i), ref.state(i)):
+            assert np.array_equal(x, y)
+
+
+def test_batch_rejects_bad_grids_and_depth(hw):
+    with pytest.raises(hw.HwError):
+        hw.hw_batch_create([hw.make_grid(64, 1, dim=1)], hw.make_params())
+    sc = S.hump2d(16, 16, seed=3)
+    b = hw.hw_batch_create([hw.make_grid(16, 16, 0, 1, 0, 1, 1, 1)], hw.make_params())
+    bad = sc.h.copy()
+    bad[2, 2] = 0.0
+    with pytest.raises(hw.HwError) as e:
+        hw.hw_batch_init(b, 0, bad, sc.hu, sc.hv, sc.b, sc.deriv)
+    assert e.value.code == -2
+    hw.hw_batch_destroy(b)
