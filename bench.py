@@ -226,6 +226,58 @@ def batched_compare(steps, n_inst=512):
             "tiles": "autotuned per size class"}
 
 
+def adjoint_cost(n=512, nsteps=400, snapshots=20):
+    """Config 5: gauge misfit over 32 gauges and `nsteps` steps at n x n (bottom of the benchmark plus
+    a surface hump, reflective; observations from a run with another hump; the unperturbed CFL step
+    sequence passed explicitly). Times the forward loss and the adjoint run with binomial
+    checkpointing (`snapshots` states)."""
+    import torch
+    import paper_2208_01260_gb300 as hw
+    from paper_2208_01260_gb300 import adjoint as A
+    from paper_2208_01260_gb300 import scenarios as S
+
+    def eq(sc):
+        st = [sc.h + sc.b, sc.hu, sc.hv, sc.deriv[0] + sc.deriv[6], sc.deriv[1], sc.deriv[2],
+              sc.deriv[3] + sc.deriv[7], sc.deriv[4], sc.deriv[5]]
+        T = lambda a: torch.tensor(np.stack(a), dtype=torch.float64, device="cuda").contiguous()
+        return T(st), T([sc.b, sc.deriv[6], sc.deriv[7]])
+    sc, osc = S.adjoint_case(n), S.adjoint_case(n, hump_seed=1)
+    gidx = S.gauges(n, n)
+    solver = hw.Solver.from_scenario(sc, hw.make_params())
+    state, static = eq(sc)
+    dts = []
+    for _ in range(nsteps):
+        dt = solver.cfl_dt()
+        dts.append(dt)
+        solver.rk3_step(dt)
+    osolver = hw.Solver.from_scenario(osc, hw.make_params())
+    ostate, ostatic = eq(osc)
+    A.load_problem(osolver, ostate, ostatic)
+    _, gv = A.hw_gauge_loss(osolver.h, dts, gidx, np.zeros(nsteps * len(gidx)))
+    obs = gv.ravel()
+    osolver.close()
+    A.load_problem(solver, state, static)
+    A.hw_gauge_loss(solver.h, dts[:4], gidx, obs[:4 * len(gidx)])  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss_f, _ = A.hw_gauge_loss(solver.h, dts, gidx, obs)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    gs = torch.empty_like(state)
+    gb = torch.empty_like(static)
+    t0 = time.perf_counter()
+    loss_a, nf = A.hw_adjoint_run(solver.h, dts, gidx, obs, snapshots, [gs[q] for q in range(9)],
+                                  [gb[q] for q in range(3)])
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    step_f = t_fwd / nsteps
+    return {"grid": [n, n], "steps": nsteps, "gauges": int(len(gidx)), "snapshots": snapshots, "loss": loss_a,
+            "loss_forward_only": loss_f, "forward_s": t_fwd, "adjoint_run_s": t_adj,
+            "adjoint_run_over_forward": t_adj / t_fwd, "forward_steps_in_adjoint_run": int(nf),
+            "reverse_step_over_forward_step": (t_adj - nf * step_f) / nsteps / step_f,
+            "grad_norm_state": float(gs.norm()), "grad_norm_static": float(gb.norm())}
+
+
 def run_reference(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -271,6 +323,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--batched-steps", type=int, default=6, help="steps of the batched comparison (0 = skip)")
+    ap.add_argument("--adjoint-steps", type=int, default=400, help="steps of the adjoint cost measurement (0 = skip)")
     ap.add_argument("--nx", type=int, default=2048, help="smaller grids for profiling captures only")
     ap.add_argument("--ny", type=int, default=2048)
     args = ap.parse_args()
@@ -395,6 +448,8 @@ def main():
     if args.batched_steps > 0 and (NX, NY) == (2048, 2048):
         solver.close()
         line["batched"] = batched_compare(args.batched_steps)
+    if args.adjoint_steps > 0 and (NX, NY) == (2048, 2048):
+        line["adjoint"] = adjoint_cost(nsteps=args.adjoint_steps)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, desc, threads, el = oracle_rate()
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,

@@ -164,6 +164,35 @@ int hw_batch_get_tiles(hw_batch* b, int i, int* tx, int* seg);
 int hw_batch_time_tiles(hw_batch* b, int nids, const int* ids, int tx, int seg, int reps, double* ms_x,
                         double* ms_y);
 
+/* ---------------------------------------------------------------------------------------------
+ * Discrete adjoint (2D, nonlinear weights and characteristic projection; limiter on or off).
+ * Gradients are with respect to the equilibrium state planes (eta, m, w, eta_x, m_x, w_x, eta_y, m_y,
+ * w_y) and the static planes (b, b_x, b_y) taken as independent arrays (eta held fixed when b moves).
+ * The time steps are given explicitly, so the adjoint differentiates the map the caller evaluates.
+ * alpha = max(|u|+c) is differentiated through the first node attaining the maximum, with d|x| = dx at
+ * x = 0.
+ * ------------------------------------------------------------------------------------------- */
+/* Reverse of one hw_rk3_step(dt) taken from the solver's current state: lam_state (9 device planes,
+ * equilibrium layout) holds the adjoint of the step's output on entry and of its input on return;
+ * lam_static (3 device planes: b, b_x, b_y) is incremented. The solver's state is unchanged. */
+int hw_adjoint_step(hw_solver* s, double dt, double* const* lam_state, double* const* lam_static);
+
+/* Gauge misfit L = sum_{n=1..nsteps} sum_g (eta^n[gauge_idx[g]] - eta_obs[(n-1)*ngauge + g])^2 of the run
+ * from the current state with time steps dts[nsteps] (host arrays; gauge_idx are node indices j*nx+i).
+ * eta_gauges (host, may be NULL) receives the model's gauge values. The solver returns to the initial
+ * state. */
+int hw_gauge_loss(hw_solver* s, int nsteps, const double* dts, const int* gauge_idx, int ngauge,
+                  const double* eta_obs, double* loss_out, double* eta_gauges);
+
+/* The same loss and its gradient (grad_state: 9 device planes, grad_static: 3 device planes, both
+ * overwritten) by the adjoint, with binomial checkpointing: at most `snapshots` intermediate states
+ * are held, and the schedule minimising the recomputed forward steps is found by dynamic
+ * programming over (steps left, snapshots left). *forward_steps_out (may be NULL) receives the
+ * forward steps taken (loss pass plus recomputation). The solver returns to the initial state. */
+int hw_adjoint_run(hw_solver* s, int nsteps, const double* dts, const int* gauge_idx, int ngauge,
+                   const double* eta_obs, int snapshots, double* loss_out, double* const* grad_state,
+                   double* const* grad_static, long long* forward_steps_out);
+
 /* Allocation-free variant of the 1D right-hand side: the same numbers as hw_create + hw_init + hw_rhs on
  * a 1D grid (out: 4 planes d/dt (eta, m, eta_x, m_x)), with every array pointer on the device. The paper
  * has no counterpart; this call exists for callers that must not allocate device memory, such as code

@@ -90,6 +90,7 @@ def lib():
             ("orc_stage1d", [gp, prp, C.c_int, C.c_double, pp, pp, pp, pp, dp], C.c_int),
             ("orc_rk3_step1d", [gp, prp, C.c_double, pp, pp], C.c_int),
             ("orc_cfl_dt1d", [gp, prp, pp, pp], C.c_double),
+            ("orc_gauge_loss_dual2d", [gp, prp, pp, pp, pp, pp, C.c_int, dp, ip, C.c_int, dp, dp], C.c_int),
         ]:
             f = getattr(L, name)
             f.argtypes = args
@@ -307,6 +308,23 @@ def run2d(grid, params, st, stat, t_end, max_steps=10**9, dt_fn=None):
         t = t_end if last else t + dt
         n += 1
     return cur, t, n
+
+
+def gauge_loss_dual2d(grid, params, st, stat, dst, dstat, dts, gauge_idx, obs):
+    """Gauge misfit sum_n sum_g (eta^n[g] - obs[n-1][g])^2 of the run with time steps dts, and its
+    derivative along the direction (dst: 9 state planes, dstat: b, b_x, b_y) by dual numbers."""
+    S, a = _ptrs(st)
+    T, b = _ptrs(stat)
+    DS, c = _ptrs(dst)
+    DT, d = _ptrs(dstat)
+    dts = _arr(dts)
+    gi = np.ascontiguousarray(gauge_idx, dtype=np.int32)
+    ob = _arr(obs)
+    out = np.zeros(2)
+    _check(lib().orc_gauge_loss_dual2d(C.byref(grid), C.byref(params), S, T, DS, DT, len(dts), _d(dts),
+                                       gi.ctypes.data_as(C.POINTER(C.c_int)), len(gi), _d(ob), _d(out)),
+           "orc_gauge_loss_dual2d")
+    return out[0], out[1]
 
 
 # ------------------------------------------------------------------------------------------------

@@ -1087,3 +1087,49 @@ double orc_cfl_dt1d(const Grid* g, const Params* p, const double* const* st, con
 }
 
 }  // extern "C"
+
+// =============================================================================================
+// Gauge-misfit loss of a 2D run and its directional derivative (forward-mode dual numbers): the
+// independent reference for the adjoint. L = sum_{n=1..N} sum_g (eta^n[g] - obs[n-1][g])^2.
+// =============================================================================================
+namespace orc {
+template <class T>
+void set_state2d(const Grid& gr, State2D<T>& S, std::vector<T>* planes) {
+  for (int q = 0; q < 9; ++q) {
+    for (int j = 0; j < gr.ny; ++j)
+      for (int i = 0; i < gr.nx; ++i) S.p[q].at(i, j) = planes[q][(size_t)j * gr.nx + i];
+    fill_ghosts(S.p[q], gr.bc_x, gr.bc_y, PAR2X[q], PAR2Y[q]);
+  }
+}
+
+template <class T>
+T gauge_loss2d(const Grid& gr, const Params& pr, State2D<T>& S, int nsteps, const double* dts, const int* gidx, int ng,
+               const double* obs) {
+  T L = T(0.0);
+  std::vector<T> B[9], O[9];
+  for (int n = 0; n < nsteps; ++n) {
+    for (int k = 1; k <= 3; ++k) {
+      stage2d(gr, pr, k, dts[n], S, B, O, (T*)nullptr);
+      set_state2d(gr, S, O);
+    }
+    for (int g = 0; g < ng; ++g) {
+      const int i = gidx[g] % gr.nx, j = gidx[g] / gr.nx;
+      T e = S.p[0].at(i, j) - obs[(size_t)n * ng + g];
+      L = L + e * e;
+    }
+  }
+  return L;
+}
+}  // namespace orc
+
+extern "C" int orc_gauge_loss_dual2d(const Grid* g, const Params* p, const double* const* st, const double* const* stat,
+                                     const double* const* dst, const double* const* dstat, int nsteps, const double* dts,
+                                     const int* gidx, int ng, const double* obs, double* out2) {
+  if (check_grid(g) || g->dim != 2 || nsteps < 1 || ng < 1) return -1;
+  orc::State2D<orc::Dual> S;
+  orc::load_state2d(*g, st, stat, S, dst, dstat);
+  orc::Dual L = orc::gauge_loss2d(*g, *p, S, nsteps, dts, gidx, ng, obs);
+  out2[0] = L.v;
+  out2[1] = L.d;
+  return 0;
+}

@@ -1,0 +1,1019 @@
+// Discrete adjoint of hw_rk3_step (2D, nonlinear weights, characteristic projection, limiter on or
+// off) and the gauge-misfit loss with binomial checkpointing over time steps.
+//
+// Reverse of one RK stage (eq. RK with the right-hand side of eq. swe-form-2d-dis):
+//   k_adj_node_pre   RK combination, node-local terms of the assembly (g eta, g H1, g H2 times the
+//                    source differences), the adjoint of the limited derivatives
+//   k_adj_sweep_x/y  adjoint of each interface's 12 values (from the two neighbouring nodes), reverse
+//                    of the reconstruction (Sec. 2.1 Steps 1-2, eq. mixed) into the four stencil records
+//   k_adj_records    reverse of the per-node records (fluxes, chain-rule derivatives, LF split), ghost
+//                    records mapped back to the mirrored or periodic node with the parity table
+//   k_adj_limiter    reverse of the HWENO limiter (Sec. 2.2) in x and y
+//   k_adj_alpha_*    alpha = max(|u| + c): its adjoint goes to the first node attaining the maximum
+// Scatters use FP64 atomics (sums in an unspecified order; the gradient tolerance is far above
+// rounding). The parts of the source balance that depend on b only (candidates, Q' and mixed terms
+// of b_x, b_y) are reversed by k_adj_static.
+#include <algorithm>
+#include <climits>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/hwswe.h"
+#include "hw_adjoint.cuh"
+#include "hw_internal.h"
+
+namespace hw {
+
+struct AdjDev {
+  Dev2D d;                // stage input state, static planes, grid constants
+  const double* alpha;    // alpha of this stage [2]
+  int k;
+  double dt, a, b;
+  int limiter;
+  const double* lout[9];  // adjoint of the stage output
+  double* lin[9];         // adjoint of the stage input (written)
+  double* lbase[9];       // adjoint of the step base (accumulated over stages 3, 2; consumed at stage 1)
+  double* lR[9];          // adjoint of the right-hand side (scratch)
+  double* lmod[6];        // adjoint of the limited derivatives (scratch)
+  double* lrecx[NREC];    // record adjoints, x: rows of nx + 4 (raw index -2 .. nx+1)
+  double* lrecy[NREC];    // record adjoints, y: ny + 4 rows of nx
+  double* lstat[3];       // adjoint of b, dx b_x, dy b_y (direct dependences), accumulated
+  double* lqbx[6];
+  double* lqby[6];
+  double* lsv[2];
+  double* lsq[2];
+  double* lalpha;         // [2], accumulated within the stage
+  const double* dbx[3];   // forward 2 bhat (x-interfaces) of this stage
+  const double* dby[3];   // forward 2 bhat (y-interfaces)
+  int* argmax;            // [2]
+};
+
+// atomically add parity-mapped adjoints of a (possibly ghost) node's 12 entries to the real node
+__device__ __forceinline__ void scatter_node(const AdjDev& A, int i, int j, const double ln[12], bool with_state,
+                                             bool with_stat) {
+  bool fx, fy;
+  const int ii = map_index(i, A.d.nx, A.d.bc_x, fx);
+  const int jj = map_index(j, A.d.ny, A.d.bc_y, fy);
+  const size_t o = (size_t)jj * A.d.nx + ii;
+  if (with_state)
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      double x = ln[q];
+      if (fx) x *= par_x2d(q);
+      if (fy) x *= par_y2d(q);
+      if (x != 0.0) atomicAdd(A.lin[q] + o, x);
+    }
+  if (with_stat)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      double x = ln[9 + q];
+      if (fx) x *= par_x2d(9 + q);
+      if (fy) x *= par_y2d(9 + q);
+      if (x != 0.0) atomicAdd(A.lstat[q] + o, x);
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+  return v;  // lane 0 of each warp holds the warp sum
+}
+
+// ---- 1. node pre-pass ----
+__global__ void __launch_bounds__(256) k_adj_node_pre(AdjDev A) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  const Dev2D& d = A.d;
+  if (i >= d.nx || j >= d.ny) return;
+  const size_t o = (size_t)j * d.nx + i;
+  double lc[9], lR[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const double lo = A.lout[q][o];
+    if (A.k == 1) {
+      lc[q] = lo + A.lbase[q][o];
+      lR[q] = A.dt * lo;
+    } else {
+      lc[q] = A.b * lo;
+      lR[q] = A.b * A.dt * lo;
+      A.lbase[q][o] += A.a * lo;
+    }
+  }
+  const double eta = d.S[0][o], g = d.g, ge = g * eta;
+  // source differences db_c = [b~^]_x/dx + [b-^]_y/dy from the forward interface values
+  double db[3];
+  const size_t ox = (size_t)j * (d.nx + 1) + i, oy = (size_t)j * d.nx + i;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    db[c] = fma(d.c_bx, A.dbx[c][ox + 1] - A.dbx[c][ox], d.c_by * (A.dby[c][oy + d.nx] - A.dby[c][oy]));
+  double leta = 0.0, lH1 = 0.0, lH2 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    leta -= g * db[c] * lR[c];
+    lH1 -= g * db[c] * lR[3 + c];
+    lH2 -= g * db[c] * lR[6 + c];
+  }
+#pragma unroll
+  for (int c = 1; c < 3; ++c) {
+    const double sv = d.sv[c - 1][o], sq = d.sq[c - 1][o];
+    leta -= g * (sv * lR[3 + c] + sq * lR[6 + c]);
+    A.lsv[c - 1][o] -= ge * lR[3 + c];
+    A.lsq[c - 1][o] -= ge * lR[6 + c];
+  }
+  A.lin[0][o] = lc[0] + leta;
+  A.lin[1][o] = lc[1];
+  A.lin[2][o] = lc[2];
+  if (A.limiter) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      A.lmod[q][o] = lc[3 + q];
+      A.lin[3 + q][o] = 0.0;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) A.lin[3 + q][o] = lc[3 + q];
+  }
+  A.lin[3][o] += lH1;
+  A.lin[6][o] += lH2;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) A.lR[q][o] = lR[q];
+}
+
+// adjoint of the 12 values of the x-interface k of row j (from nodes k-1 and k)
+__device__ __forceinline__ void interface_adjoint_x(const AdjDev& A, int k, int j, double lX[12]) {
+  const Dev2D& d = A.d;
+  for (int q = 0; q < 12; ++q) lX[q] = 0.0;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int p = side == 0 ? k - 1 : k;  // node seeing k as its right (side 0) or left (side 1) interface
+    if (p < 0 || p >= d.nx) continue;
+    const double sgn = side == 0 ? -1.0 : 1.0;
+    const size_t o = (size_t)j * d.nx + p;
+    const double g = d.g, ge = g * d.S[0][o], gH1 = g * d.S[3][o], gH2 = g * d.S[6][o];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double lu = A.lR[c][o], lv = A.lR[3 + c][o], lq = A.lR[6 + c][o];
+      lX[c] += sgn * d.c_bx * lu;
+      lX[3 + c] += sgn * d.c_bx * (ge * lu + gH1 * lv + gH2 * lq);
+      lX[6 + c] += sgn * d.c_gx * lv;
+      lX[9 + c] += sgn * d.c_mx * lq;
+    }
+  }
+}
+
+__device__ __forceinline__ void interface_adjoint_y(const AdjDev& A, int i, int k, double lY[12]) {
+  const Dev2D& d = A.d;
+  for (int q = 0; q < 12; ++q) lY[q] = 0.0;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int p = side == 0 ? k - 1 : k;
+    if (p < 0 || p >= d.ny) continue;
+    const double sgn = side == 0 ? -1.0 : 1.0;
+    const size_t o = (size_t)p * d.nx + i;
+    const double g = d.g, ge = g * d.S[0][o], gH1 = g * d.S[3][o], gH2 = g * d.S[6][o];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double lu = A.lR[c][o], lv = A.lR[3 + c][o], lq = A.lR[6 + c][o];
+      lY[c] += sgn * d.c_by * lu;
+      lY[3 + c] += sgn * d.c_by * (ge * lu + gH1 * lv + gH2 * lq);
+      lY[6 + c] += sgn * d.c_gy * lq;  // Psi2 hat feeds the Q equations
+      lY[9 + c] += sgn * d.c_my * lv;  // mixed Phi2 hat feeds the V equations
+    }
+  }
+}
+
+// ---- 2. x-interfaces ----
+constexpr int AX_T = 64;
+constexpr int AX_N = AX_T + 3;
+
+__global__ void __launch_bounds__(AX_T) k_adj_sweep_x(AdjDev A) {
+  __shared__ double sm[NREC * AX_N];
+  const Dev2D& d = A.d;
+  const int j = blockIdx.y, k0 = blockIdx.x * AX_T;
+  const double ax = A.alpha[0];
+  for (int t = threadIdx.x; t < AX_N; t += AX_T) {
+    const int i = k0 - 2 + t;
+    if (i > d.nx + 1) break;
+    Node12 n;
+    load_node(d, i, j, n);
+    double rec[NREC];
+    node_record<0>(n, d.g, ax, rec);
+#pragma unroll
+    for (int f = 0; f < NREC; ++f) sm[f * AX_N + t] = rec[f];
+  }
+  __syncthreads();
+  const int k = k0 + threadIdx.x;
+  if (k > d.nx) return;
+  const int t = threadIdx.x;
+  const size_t o = (size_t)j * (d.nx + 1) + k;
+  double qb[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) qb[q] = d.qbx[q][o];
+  double lX[12];
+  interface_adjoint_x(A, k, j, lX);
+  double lr[4][NREC] = {};
+  double lqb[6] = {0, 0, 0, 0, 0, 0};
+  interface_values_rev<0>(sm + t, sm + t + 1, sm + t + 2, sm + t + 3, AX_N, qb, d.g, d.eps_w, lX, lr, lqb);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) A.lqbx[q][o] += lqb[q];
+  const size_t row = (size_t)j * (d.nx + 4);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const size_t col = row + (k - 2 + s) + 2;
+#pragma unroll
+    for (int f = 0; f < NREC; ++f)
+      if (lr[s][f] != 0.0) atomicAdd(A.lrecx[f] + col, lr[s][f]);
+  }
+}
+
+// ---- 2'. y-interfaces (one thread per interface; records recomputed from the four nodes) ----
+__global__ void __launch_bounds__(128) k_adj_sweep_y(AdjDev A) {
+  const Dev2D& d = A.d;
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int k = blockIdx.y * 4 + (threadIdx.x >> 5);
+  if (i >= d.nx || k > d.ny) return;
+  const double ay = A.alpha[1];
+  double rec[4][NREC];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    Node12 n;
+    load_node(d, i, k - 2 + s, n);
+    node_record<1>(n, d.g, ay, rec[s]);
+  }
+  const size_t o = (size_t)k * d.nx + i;
+  double qb[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) qb[q] = d.qby[q][o];
+  double lY[12];
+  interface_adjoint_y(A, i, k, lY);
+  double lr[4][NREC] = {};
+  double lqb[6] = {0, 0, 0, 0, 0, 0};
+  interface_values_rev<1>(rec[0], rec[1], rec[2], rec[3], 1, qb, d.g, d.eps_w, lY, lr, lqb);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) A.lqby[q][o] += lqb[q];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const size_t pos = (size_t)(k - 2 + s + 2) * d.nx + i;
+#pragma unroll
+    for (int f = 0; f < NREC; ++f)
+      if (lr[s][f] != 0.0) atomicAdd(A.lrecy[f] + pos, lr[s][f]);
+  }
+}
+
+// ---- 3. records: raw x-records (r = -2..nx+1, row j) and raw y-records (column i, r = -2..ny+1) ----
+__global__ void __launch_bounds__(256) k_adj_records(AdjDev A) {
+  const Dev2D& d = A.d;
+  const int nxr = (d.nx + 4) * d.ny, nyr = d.nx * (d.ny + 4);
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  double la = 0.0;
+  int dir = -1;
+  if (tid < nxr) {
+    dir = 0;
+    const int j = tid / (d.nx + 4), r = tid - j * (d.nx + 4) - 2;
+    double lrec[NREC];
+    bool any = false;
+#pragma unroll
+    for (int f = 0; f < NREC; ++f) {
+      lrec[f] = A.lrecx[f][tid];
+      any |= lrec[f] != 0.0;
+    }
+    if (any) {
+      Node12 n;
+      load_node(d, r, j, n);
+      double ln[12] = {};
+      la = node_record_rev<0>(n, d.g, A.alpha[0], lrec, ln);
+      scatter_node(A, r, j, ln, true, true);
+    }
+  } else if (tid < nxr + nyr) {
+    dir = 1;
+    const int u = tid - nxr;
+    const int rr = u / d.nx, i = u - rr * d.nx, r = rr - 2;
+    double lrec[NREC];
+    bool any = false;
+#pragma unroll
+    for (int f = 0; f < NREC; ++f) {
+      lrec[f] = A.lrecy[f][u];
+      any |= lrec[f] != 0.0;
+    }
+    if (any) {
+      Node12 n;
+      load_node(d, i, r, n);
+      double ln[12] = {};
+      la = node_record_rev<1>(n, d.g, A.alpha[1], lrec, ln);
+      scatter_node(A, i, r, ln, true, true);
+    }
+  }
+  // alpha adjoints: warps may straddle the x/y boundary, so reduce per direction
+  const double lx = block_sum(dir == 0 ? la : 0.0), ly = block_sum(dir == 1 ? la : 0.0);
+  if ((threadIdx.x & 31) == 0) {
+    if (lx != 0.0) atomicAdd(A.lalpha, lx);
+    if (ly != 0.0) atomicAdd(A.lalpha + 1, ly);
+  }
+}
+
+// ---- 4. limiter ----
+__global__ void __launch_bounds__(256) k_adj_limiter(AdjDev A) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  const Dev2D& d = A.d;
+  if (i >= d.nx || j >= d.ny) return;
+  const size_t o = (size_t)j * d.nx + i;
+  double cur[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) cur[q] = d.S[q][o];
+  const double g = d.g;
+  const double b0 = d.stat[0][o];
+  const double h = cur[0] - b0, gh = g * h, rh = fast_rcp(h);
+  const double u = cur[1] * rh, v = cur[2] * rh;
+  const double rs = fast_rsqrt(gh), c = gh * rs, ic2 = 0.5 * rs;
+  double lu = 0.0, lv = 0.0, lc = 0.0, lic2 = 0.0, lgh = 0.0;
+  double l0[12] = {};
+  for (int dir = 0; dir < 2; ++dir) {
+    double lo[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) lo[q] = A.lmod[3 * dir + q][o];
+    if (lo[0] == 0.0 && lo[1] == 0.0 && lo[2] == 0.0) continue;
+    Node12 nm, np;
+    const int im = dir == 0 ? i - 1 : i, jm = dir == 0 ? j : j - 1;
+    const int ip = dir == 0 ? i + 1 : i, jp = dir == 0 ? j : j + 1;
+    load_node(d, im, jm, nm);
+    load_node(d, ip, jp, np);
+    const int qd = dir == 0 ? 3 : 6;
+    double lUm[3] = {}, lU0[3] = {}, lUp[3] = {}, lDm[3] = {}, lDp[3] = {};
+    if (dir == 0)
+      limit_dir_rev<0>(nm.v, cur, np.v, nm.v + qd, np.v + qd, u, v, c, ic2, gh, d.eps_lim, lo, lUm, lU0, lUp, lDm, lDp,
+                       lu, lv, lc, lic2, lgh);
+    else
+      limit_dir_rev<1>(nm.v, cur, np.v, nm.v + qd, np.v + qd, u, v, c, ic2, gh, d.eps_lim, lo, lUm, lU0, lUp, lDm, lDp,
+                       lu, lv, lc, lic2, lgh);
+    double lm12[12] = {}, lp12[12] = {};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      lm12[q] = lUm[q];
+      lm12[qd + q] = lDm[q];
+      lp12[q] = lUp[q];
+      lp12[qd + q] = lDp[q];
+      l0[q] += lU0[q];
+    }
+    scatter_node(A, im, jm, lm12, true, false);
+    scatter_node(A, ip, jp, lp12, true, false);
+  }
+  // node eigen quantities: u = m/h, v = w/h, c = gh rs, ic2 = rs/2, rs = gh^-1/2, gh = g h, h = eta - b
+  const double lrs = 0.5 * lic2 + gh * lc;
+  const double lght = lgh + rs * lc - 0.5 * rs * rs * rs * lrs;
+  const double lh = g * lght - rh * rh * (cur[1] * lu + cur[2] * lv);
+  l0[0] += lh;
+  l0[1] += rh * lu;
+  l0[2] += rh * lv;
+  l0[9] = -lh;
+  scatter_node(A, i, j, l0, true, true);
+}
+
+// ---- 5. alpha: the first node attaining the maximum receives the adjoint ----
+__global__ void __launch_bounds__(256) k_adj_alpha_find(AdjDev A) {
+  const Dev2D& d = A.d;
+  const int n = d.nx * d.ny;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+    const double h = d.S[0][o] - d.stat[0][o];
+    const double rh = fast_rcp(h), gh = d.g * h, c = gh * fast_rsqrt(gh);
+    const double ax = dabs(d.S[1][o] * rh) + c, ay = dabs(d.S[2][o] * rh) + c;
+    // the forward reduction may round the last bit differently (FMA contraction): 4e-16 relative window
+    if (fabs(ax - A.alpha[0]) <= 4e-16 * A.alpha[0]) atomicMin(A.argmax, o);
+    if (fabs(ay - A.alpha[1]) <= 4e-16 * A.alpha[1]) atomicMin(A.argmax + 1, o);
+  }
+}
+
+__global__ void k_adj_alpha_apply(AdjDev A) {
+  const Dev2D& d = A.d;
+  for (int dir = 0; dir < 2; ++dir) {
+    const int o = A.argmax[dir];
+    const double la = A.lalpha[dir];
+    if (o == INT_MAX || la == 0.0) continue;
+    const double h = d.S[0][o] - d.stat[0][o];
+    const double rh = fast_rcp(h), gh = d.g * h, rs = fast_rsqrt(gh), c = gh * rs;
+    const double mom = d.S[1 + dir][o];
+    const double un = mom * rh;
+    const double sg = un < 0.0 ? -1.0 : 1.0;  // d|x| = dx at x = 0 (same convention as the oracle)
+    // alpha = |mom/h| + sqrt(g h)
+    const double lmom = la * sg * rh;
+    const double lh = la * (-sg * un * rh + 0.5 * d.g * rs);
+    (void)c;
+    atomicAdd(A.lin[0] + o, lh);
+    atomicAdd(A.lin[1 + dir] + o, lmom);
+    atomicAdd(A.lstat[0] + o, -lh);
+  }
+}
+
+// ---- static terms (once per call): candidates, Q' of (b, b_x) and (b, b_y), mixed terms ----
+struct StatAdj {
+  Dev2D d;
+  const double* lqbx[6];
+  const double* lqby[6];
+  const double* lsv[2];
+  const double* lsq[2];
+  double* lb;   // adjoint of b (physical)
+  double* lbx;  // of b_x
+  double* lby;  // of b_y
+};
+
+__device__ __forceinline__ void add_b(const StatAdj& S, int q, int i, int j, double x) {
+  if (x == 0.0) return;
+  bool fx, fy;
+  const int ii = map_index(i, S.d.nx, S.d.bc_x, fx);
+  const int jj = map_index(j, S.d.ny, S.d.bc_y, fy);
+  if (fx && q == 1) x = -x;
+  if (fy && q == 2) x = -x;
+  double* dst = q == 0 ? S.lb : (q == 1 ? S.lbx : S.lby);
+  atomicAdd(dst + (size_t)jj * S.d.nx + ii, x);
+}
+
+// candidates q_1..q_3 of (b, s) with s = spacing * b_s, '+' side from nodes 0,1,2 and mirrored '-' side
+__device__ __forceinline__ void cands_rev(const double lq[6], double lb[4], double ls[4]) {
+  // + : q1 = (b0+b1)/2 + (s0 + 5 s1)/6, q2 = (b1+b2)/2 + (s1 - s2)/6, q3 = (b0 + 10 b1 + b2)/12 + s1/2
+  lb[0] += 0.5 * lq[0] + lq[2] / 12.0;
+  lb[1] += 0.5 * lq[0] + 0.5 * lq[1] + 10.0 * lq[2] / 12.0;
+  lb[2] += 0.5 * lq[1] + lq[2] / 12.0;
+  ls[0] += lq[0] / 6.0;
+  ls[1] += 5.0 * lq[0] / 6.0 + lq[1] / 6.0 + 0.5 * lq[2];
+  ls[2] += -lq[1] / 6.0;
+  // - : nodes (3, 2, 1) with s negated
+  lb[3] += 0.5 * lq[3] + lq[5] / 12.0;
+  lb[2] += 0.5 * lq[3] + 0.5 * lq[4] + 10.0 * lq[5] / 12.0;
+  lb[1] += 0.5 * lq[4] + lq[5] / 12.0;
+  ls[3] -= lq[3] / 6.0;
+  ls[2] -= 5.0 * lq[3] / 6.0 + lq[4] / 6.0 + 0.5 * lq[5];
+  ls[1] -= -lq[4] / 6.0;
+}
+
+// adjoint of qprime_sum(b0..b3, s0..s3, del) = ((b0-8b1+7b2) + (-7b1+8b2-b3))/(8 del) + ((s0-2s1-5s2) + (-5s1-2s2+s3))/24
+__device__ __forceinline__ void qps_rev(double l, double del, double lb[4], double ls[4]) {
+  const double cb = l / (8.0 * del), cs = l / 24.0;
+  lb[0] += cb; lb[1] -= 15.0 * cb; lb[2] += 15.0 * cb; lb[3] -= cb;
+  ls[0] += cs; ls[1] -= 7.0 * cs; ls[2] -= 7.0 * cs; ls[3] += cs;
+}
+
+__global__ void k_adj_static(StatAdj S) {
+  const Dev2D& d = S.d;
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  // x-interface k = i of row j: candidates (b, dx b_x); Q' of (b, b_x) from sv[0]; mixed b_y from sq[0]
+  if (j < d.ny && i <= d.nx) {
+    const int k = i;
+    const size_t o = (size_t)j * (d.nx + 1) + k;
+    double lq[6];
+    for (int q = 0; q < 6; ++q) lq[q] = S.lqbx[q][o];
+    double lb[4] = {}, ls[4] = {}, lby[4] = {};
+    cands_rev(lq, lb, ls);
+    for (int t = 0; t < 4; ++t) ls[t] *= d.dx;  // s = dx b_x
+    // B1x(k) enters sv[0] of node k-1 with + and of node k with -
+    double lB1 = 0.0, lB2 = 0.0;
+    if (k - 1 >= 0 && k - 1 < d.nx) {
+      lB1 += S.lsv[0][(size_t)j * d.nx + k - 1];
+      lB2 += S.lsq[0][(size_t)j * d.nx + k - 1] * d.dy * d.inv_dx;
+    }
+    if (k < d.nx) {
+      lB1 -= S.lsv[0][(size_t)j * d.nx + k];
+      lB2 -= S.lsq[0][(size_t)j * d.nx + k] * d.dy * d.inv_dx;
+    }
+    qps_rev(lB1, d.dx, lb, ls);
+    // mixed (-x0 + 7 x1 + 7 x2 - x3)/12 of b_y
+    lby[0] -= lB2 / 12.0; lby[1] += 7.0 * lB2 / 12.0; lby[2] += 7.0 * lB2 / 12.0; lby[3] -= lB2 / 12.0;
+    for (int t = 0; t < 4; ++t) {
+      add_b(S, 0, k - 2 + t, j, lb[t]);
+      add_b(S, 1, k - 2 + t, j, ls[t]);
+      add_b(S, 2, k - 2 + t, j, lby[t]);
+    }
+  }
+  // y-interface k = j of column i: candidates (b, dy b_y); Q' of (b, b_y) from sq[1]; mixed b_x from sv[1]
+  if (i < d.nx && j <= d.ny) {
+    const int k = j;
+    const size_t o = (size_t)k * d.nx + i;
+    double lq[6];
+    for (int q = 0; q < 6; ++q) lq[q] = S.lqby[q][o];
+    double lb[4] = {}, ls[4] = {}, lbx[4] = {};
+    cands_rev(lq, lb, ls);
+    for (int t = 0; t < 4; ++t) ls[t] *= d.dy;
+    double lB2 = 0.0, lB1 = 0.0;
+    if (k - 1 >= 0 && k - 1 < d.ny) {
+      lB2 += S.lsq[1][(size_t)(k - 1) * d.nx + i];
+      lB1 += S.lsv[1][(size_t)(k - 1) * d.nx + i] * d.dx * d.inv_dy;
+    }
+    if (k < d.ny) {
+      lB2 -= S.lsq[1][(size_t)k * d.nx + i];
+      lB1 -= S.lsv[1][(size_t)k * d.nx + i] * d.dx * d.inv_dy;
+    }
+    qps_rev(lB2, d.dy, lb, ls);
+    lbx[0] -= lB1 / 12.0; lbx[1] += 7.0 * lB1 / 12.0; lbx[2] += 7.0 * lB1 / 12.0; lbx[3] -= lB1 / 12.0;
+    for (int t = 0; t < 4; ++t) {
+      add_b(S, 0, i, k - 2 + t, lb[t]);
+      add_b(S, 2, i, k - 2 + t, ls[t]);
+      add_b(S, 1, i, k - 2 + t, lbx[t]);
+    }
+  }
+}
+
+// user gradient (equilibrium layout, physical derivatives) <-> internal adjoint (scaled derivatives)
+__global__ void k_adj_convert(int n, double dx, double dy, Ptr9 src, Ptr9 dst, int to_internal) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const double sc = q < 3 ? 1.0 : (q < 6 ? dx : dy);
+      // eta_x = H1'/dx: dL/dH1' = dL/deta_x / dx, and back
+      dst.p[q][o] = to_internal ? src.p[q][o] / sc : src.p[q][o] * sc;
+    }
+  }
+}
+
+// lb, lbx, lby (physical) += direct static adjoints (b, dx b_x, dy b_y)
+__global__ void k_adj_static_direct(int n, double dx, double dy, const double* l0, const double* l1, const double* l2,
+                                    double* lb, double* lbx, double* lby) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+    lb[o] += l0[o];
+    lbx[o] += dx * l1[o];
+    lby[o] += dy * l2[o];
+  }
+}
+
+__global__ void k_gather_eta(const double* eta, const int* idx, int ng, double* out) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < ng) out[g] = eta[idx[g]];
+}
+
+__global__ void k_loss_seed(const double* gval, const double* obs, const int* idx, int ng, double* leta) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < ng) atomicAdd(leta + idx[g], 2.0 * (gval[g] - obs[g]));
+}
+
+}  // namespace hw
+
+// =============================================================================================
+// Host side: one step's reverse, the loss, checkpointing
+// =============================================================================================
+namespace {
+
+int afail(int code, const std::string& m) { return hw::set_last_error(code, m.c_str()); }
+#define ACUDA(call)                                                                            \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return afail(HW_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct AdjBuffers {
+  hw_solver* owner = nullptr;
+  size_t n = 0;
+  int nx = 0, ny = 0;
+  std::vector<void*> allocs;
+  double* stage_in[3][9] = {};
+  double* stage_out[9] = {};
+  double* alpha_st = nullptr;  // [3][2]
+  double* dbx[3][3] = {};
+  double* dby[3][3] = {};
+  double* lam[2][9] = {};
+  double* lbase[9] = {};
+  double* lR[9] = {};
+  double* lmod[6] = {};
+  double* lrecx[hw::NREC] = {};
+  double* lrecy[hw::NREC] = {};
+  double* lstat[3] = {};
+  double* lqbx[6] = {};
+  double* lqby[6] = {};
+  double* lsv[2] = {};
+  double* lsq[2] = {};
+  double* lalpha = nullptr;
+  int* argmax = nullptr;
+  double* lstatic_phys[3] = {};
+};
+
+std::mutex g_adj_mu;
+std::vector<AdjBuffers*> g_adj;  // one per live solver that used the adjoint (released by hw_destroy)
+
+int adj_alloc(AdjBuffers* B, double** p, size_t cnt) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, cnt * sizeof(double));
+  if (e != cudaSuccess) return afail(HW_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  B->allocs.push_back(q);
+  *p = (double*)q;
+  return HW_OK;
+}
+
+int get_buffers(hw_solver* s, const hw::SolverView& v, AdjBuffers** out) {
+  std::lock_guard<std::mutex> lk(g_adj_mu);
+  for (AdjBuffers* B : g_adj)
+    if (B->owner == s) {
+      if (B->n != v.n || B->nx != v.d2->nx || B->ny != v.d2->ny)
+        return afail(HW_ERR_STATE, "adjoint: working buffers do not match the solver's grid");
+      *out = B;
+      return HW_OK;
+    }
+  AdjBuffers* B = new AdjBuffers();
+  B->owner = s;
+  B->n = v.n;
+  B->nx = v.d2->nx;
+  B->ny = v.d2->ny;
+  const size_t n = v.n, nxi = (size_t)(B->nx + 1) * B->ny, nyi = (size_t)B->nx * (B->ny + 1);
+  int rc = HW_OK;
+  auto A = [&](double** p, size_t c) { if (rc == HW_OK) rc = adj_alloc(B, p, c); };
+  for (int k = 0; k < 3; ++k)
+    for (int q = 0; q < 9; ++q) A(&B->stage_in[k][q], n);
+  for (int q = 0; q < 9; ++q) { A(&B->stage_out[q], n); A(&B->lam[0][q], n); A(&B->lam[1][q], n); A(&B->lbase[q], n); A(&B->lR[q], n); }
+  A(&B->alpha_st, 8);
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 3; ++c) { A(&B->dbx[k][c], nxi); A(&B->dby[k][c], nyi); }
+  for (int q = 0; q < 6; ++q) { A(&B->lmod[q], n); A(&B->lqbx[q], nxi); A(&B->lqby[q], nyi); }
+  for (int f = 0; f < hw::NREC; ++f) { A(&B->lrecx[f], (size_t)(B->nx + 4) * B->ny); A(&B->lrecy[f], (size_t)B->nx * (B->ny + 4)); }
+  for (int q = 0; q < 3; ++q) { A(&B->lstat[q], n); A(&B->lstatic_phys[q], n); }
+  for (int q = 0; q < 2; ++q) { A(&B->lsv[q], n); A(&B->lsq[q], n); }
+  double* misc = nullptr;
+  A(&misc, 8);
+  if (rc != HW_OK) {
+    for (void* p : B->allocs) cudaFree(p);
+    delete B;
+    return rc;
+  }
+  B->lalpha = misc;
+  B->argmax = (int*)(misc + 4);
+  g_adj.push_back(B);
+  *out = B;
+  return HW_OK;
+}
+
+}  // namespace
+
+void hw::adjoint_release(hw_solver* s) {
+  std::lock_guard<std::mutex> lk(g_adj_mu);
+  for (size_t k = 0; k < g_adj.size(); ++k)
+    if (g_adj[k]->owner == s) {
+      for (void* p : g_adj[k]->allocs) cudaFree(p);
+      delete g_adj[k];
+      g_adj.erase(g_adj.begin() + k);
+      return;
+    }
+}
+
+namespace {
+
+int zero_planes(double* const* p, int count, size_t n, cudaStream_t st) {
+  for (int q = 0; q < count; ++q) ACUDA(cudaMemsetAsync(p[q], 0, n * sizeof(double), st));
+  return HW_OK;
+}
+
+// Forward recompute of one step from the current state keeping every stage's input, alpha and source
+// interface values; the solver's state is left unchanged.
+int forward_record(hw_solver* s, const hw::SolverView& v, AdjBuffers* B, double dt) {
+  cudaStream_t st = v.stream;
+  const size_t bytes = v.n * sizeof(double);
+  for (int q = 0; q < 9; ++q) ACUDA(cudaMemcpyAsync(B->stage_in[0][q], v.state[q], bytes, cudaMemcpyDeviceToDevice, st));
+  ACUDA(cudaMemcpyAsync(v.dt, &dt, sizeof(double), cudaMemcpyHostToDevice, st));
+  hw::Dev2D d = *v.d2;
+  const bool lin = false, chr = true;
+  for (int k = 1; k <= 3; ++k) {
+    for (int q = 0; q < 9; ++q) d.S[q] = B->stage_in[k - 1][q];
+    double* amax = B->lalpha;  // scratch for the keys (reset below)
+    hw::launch_alpha2d(d, (unsigned long long*)amax, (int*)(B->lalpha + 2), st);
+    hw::launch_finish_alpha2d(d, (const unsigned long long*)amax, B->alpha_st + 2 * (k - 1), nullptr, v.params->cfl,
+                              nullptr, -1.0, st);
+    hw::launch_sweep_x2d(d, B->alpha_st + 2 * (k - 1), lin, chr, st);
+    hw::launch_sweep_y2d(d, B->alpha_st + 2 * (k - 1), lin, chr, st);
+    for (int c = 0; c < 3; ++c) {
+      ACUDA(cudaMemcpyAsync(B->dbx[k - 1][c], d.X[3 + c], (size_t)(d.nx + 1) * d.ny * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st));
+      ACUDA(cudaMemcpyAsync(B->dby[k - 1][c], d.Y[3 + c], (size_t)d.nx * (d.ny + 1) * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st));
+    }
+    hw::StageArgs sa{};
+    sa.k = k;
+    sa.limiter = v.params->limiter;
+    sa.dt = v.dt;
+    for (int q = 0; q < 9; ++q) {
+      sa.out[q] = k < 3 ? B->stage_in[k][q] : B->stage_out[q];
+      sa.base[q] = v.base[q];
+    }
+    hw::launch_node2d(d, sa, hw::MODE_STAGE, lin, chr, st);
+  }
+  ACUDA(cudaGetLastError());
+  return HW_OK;
+}
+
+// Reverse of one step: lam[cur] holds the adjoint of the step's output on entry and of its input on
+// return (in lam[*cur]); static adjoints accumulate.
+int reverse_step(hw_solver* s, const hw::SolverView& v, AdjBuffers* B, double dt, int* cur) {
+  int rc = forward_record(s, v, B, dt);
+  if (rc) return rc;
+  cudaStream_t st = v.stream;
+  const size_t n = v.n;
+  if ((rc = zero_planes(B->lbase, 9, n, st))) return rc;
+  hw::Dev2D d = *v.d2;
+  const double ak[4] = {0.0, 0.0, 0.75, 1.0 / 3.0}, bk[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
+  for (int k = 3; k >= 1; --k) {
+    for (int q = 0; q < 9; ++q) d.S[q] = B->stage_in[k - 1][q];
+    hw::AdjDev A{};
+    A.d = d;
+    A.alpha = B->alpha_st + 2 * (k - 1);
+    A.k = k;
+    A.dt = dt;
+    A.a = ak[k];
+    A.b = bk[k];
+    A.limiter = v.params->limiter;
+    for (int q = 0; q < 9; ++q) {
+      A.lout[q] = B->lam[*cur][q];
+      A.lin[q] = B->lam[*cur ^ 1][q];
+      A.lbase[q] = B->lbase[q];
+      A.lR[q] = B->lR[q];
+    }
+    for (int q = 0; q < 6; ++q) { A.lmod[q] = B->lmod[q]; A.lqbx[q] = B->lqbx[q]; A.lqby[q] = B->lqby[q]; }
+    for (int f = 0; f < hw::NREC; ++f) { A.lrecx[f] = B->lrecx[f]; A.lrecy[f] = B->lrecy[f]; }
+    for (int q = 0; q < 3; ++q) { A.lstat[q] = B->lstat[q]; A.dbx[q] = B->dbx[k - 1][q]; A.dby[q] = B->dby[k - 1][q]; }
+    for (int q = 0; q < 2; ++q) { A.lsv[q] = B->lsv[q]; A.lsq[q] = B->lsq[q]; }
+    A.lalpha = B->lalpha;
+    A.argmax = B->argmax;
+    if ((rc = zero_planes(B->lrecx, hw::NREC, (size_t)(d.nx + 4) * d.ny, st))) return rc;
+    if ((rc = zero_planes(B->lrecy, hw::NREC, (size_t)d.nx * (d.ny + 4), st))) return rc;
+    ACUDA(cudaMemsetAsync(B->lalpha, 0, 2 * sizeof(double), st));
+    ACUDA(cudaMemsetAsync(B->argmax, 0x7f, 2 * sizeof(int), st));
+    const dim3 gn((d.nx + 31) / 32, (d.ny + 7) / 8), bn(32, 8);
+    hw::k_adj_node_pre<<<gn, bn, 0, st>>>(A);
+    hw::k_adj_sweep_x<<<dim3((d.nx + 1 + hw::AX_T - 1) / hw::AX_T, d.ny), hw::AX_T, 0, st>>>(A);
+    hw::k_adj_sweep_y<<<dim3((d.nx + 31) / 32, (d.ny + 1 + 3) / 4), 128, 0, st>>>(A);
+    const int nrec = (d.nx + 4) * d.ny + d.nx * (d.ny + 4);
+    hw::k_adj_records<<<(nrec + 255) / 256, 256, 0, st>>>(A);
+    if (A.limiter) hw::k_adj_limiter<<<gn, bn, 0, st>>>(A);
+    hw::k_adj_alpha_find<<<std::min((int)((n + 255) / 256), 152 * 8), 256, 0, st>>>(A);
+    hw::k_adj_alpha_apply<<<1, 1, 0, st>>>(A);
+    ACUDA(cudaGetLastError());
+    *cur ^= 1;
+  }
+  return HW_OK;
+}
+
+// static adjoints -> (b, b_x, b_y) and clear the accumulators
+int finish_static(const hw::SolverView& v, AdjBuffers* B, double* const* out) {
+  int rc = HW_OK;
+  cudaStream_t st = v.stream;
+  const hw::Dev2D& d = *v.d2;
+  hw::StatAdj S{};
+  S.d = d;
+  for (int q = 0; q < 6; ++q) { S.lqbx[q] = B->lqbx[q]; S.lqby[q] = B->lqby[q]; }
+  for (int q = 0; q < 2; ++q) { S.lsv[q] = B->lsv[q]; S.lsq[q] = B->lsq[q]; }
+  S.lb = out[0];
+  S.lbx = out[1];
+  S.lby = out[2];
+  hw::k_adj_static<<<dim3((d.nx + 1 + 31) / 32, (d.ny + 1 + 7) / 8), dim3(32, 8), 0, st>>>(S);
+  const int blocks = std::min((int)((v.n + 255) / 256), 152 * 8);
+  hw::k_adj_static_direct<<<blocks, 256, 0, st>>>((int)v.n, d.dx, d.dy, B->lstat[0], B->lstat[1], B->lstat[2],
+                                                  out[0], out[1], out[2]);
+  ACUDA(cudaGetLastError());
+  if ((rc = zero_planes(B->lqbx, 6, (size_t)(d.nx + 1) * d.ny, st))) return rc;
+  if ((rc = zero_planes(B->lqby, 6, (size_t)d.nx * (d.ny + 1), st))) return rc;
+  if ((rc = zero_planes(B->lsv, 2, v.n, st))) return rc;
+  if ((rc = zero_planes(B->lsq, 2, v.n, st))) return rc;
+  if ((rc = zero_planes(B->lstat, 3, v.n, st))) return rc;
+  return HW_OK;
+}
+
+int check_adjoint_solver(hw_solver* s, hw::SolverView* v) {
+  if (!s) return afail(HW_ERR_ARG, "adjoint: null solver");
+  int rc = hw::solver_view(s, v);
+  if (rc) return rc;
+  if (!v->d2) return afail(HW_ERR_ARG, "adjoint: 2D solvers only");
+  if (v->params->linear_weights || !v->params->char_decomp)
+    return afail(HW_ERR_ARG, "adjoint: needs nonlinear weights and characteristic projection");
+  return HW_OK;
+}
+
+// DP table of binomial checkpointing: cost[n][s] = extra forward steps to reverse n steps holding s
+// free snapshots (besides the one at the start), split[n][s] = steps to advance before the next
+// snapshot.
+struct Schedule {
+  int N, S;
+  std::vector<long long> cost;
+  std::vector<int> split;
+  long long& c(int n, int s) { return cost[(size_t)n * (S + 1) + s]; }
+  int& m(int n, int s) { return split[(size_t)n * (S + 1) + s]; }
+  Schedule(int N_, int S_) : N(N_), S(S_), cost((size_t)(N_ + 1) * (S_ + 1), 0), split((size_t)(N_ + 1) * (S_ + 1), 0) {
+    for (int s = 0; s <= S; ++s) c(1, s) = 0;
+    for (int n = 2; n <= N; ++n) {
+      c(n, 0) = (long long)n * (n - 1) / 2;
+      for (int s = 1; s <= S; ++s) {
+        long long best = -1;
+        int bm = 1;
+        for (int mm = 1; mm < n; ++mm) {
+          const long long v = mm + c(n - mm, s - 1) + c(mm, s);
+          if (best < 0 || v < best) { best = v; bm = mm; }
+        }
+        c(n, s) = best;
+        m(n, s) = bm;
+      }
+    }
+  }
+};
+
+struct RunCtx {
+  hw_solver* s;
+  hw::SolverView v;
+  AdjBuffers* B;
+  const double* dts;
+  double* d_gvals;     // [N][ng]
+  const double* d_obs; // [N][ng]
+  const int* d_idx;
+  int ng;
+  std::vector<double*> slots;  // snapshots: 9 planes each
+  int cur;
+  long long fwd_steps;
+};
+
+int load_slot(RunCtx& R, int slot) {
+  double* src[9];
+  for (int q = 0; q < 9; ++q) src[q] = R.slots[slot] + (size_t)q * R.v.n;
+  return hw::solver_set_state_planes(R.s, src);
+}
+
+int save_slot(RunCtx& R, int slot) {
+  for (int q = 0; q < 9; ++q)
+    ACUDA(cudaMemcpyAsync(R.slots[slot] + (size_t)q * R.v.n, R.v.state[q], R.v.n * sizeof(double),
+                          cudaMemcpyDeviceToDevice, R.v.stream));
+  return HW_OK;
+}
+
+int advance(RunCtx& R, int from, int steps) {
+  for (int j = 0; j < steps; ++j) {
+    int rc = hw_rk3_step(R.s, R.dts[from + j]);
+    if (rc) return rc;
+    hw::solver_view(R.s, &R.v);
+    ++R.fwd_steps;
+  }
+  return HW_OK;
+}
+
+int reverse_one(RunCtx& R, int j) {
+  // adjoint of the loss at S^{j+1}, then the reverse of step j (state S^j is loaded)
+  hw::k_loss_seed<<<(R.ng + 127) / 128, 128, 0, R.v.stream>>>(R.d_gvals + (size_t)j * R.ng, R.d_obs + (size_t)j * R.ng,
+                                                             R.d_idx, R.ng, R.B->lam[R.cur][0]);
+  hw::solver_view(R.s, &R.v);
+  return reverse_step(R.s, R.v, R.B, R.dts[j], &R.cur);
+}
+
+int reverse_range(RunCtx& R, Schedule& P, int a, int n, int s, int slot_a) {
+  int rc;
+  if (n == 1) {
+    if ((rc = load_slot(R, slot_a))) return rc;
+    return reverse_one(R, a);
+  }
+  if (s == 0) {
+    for (int j = a + n - 1; j >= a; --j) {
+      if ((rc = load_slot(R, slot_a))) return rc;
+      if ((rc = advance(R, a, j - a))) return rc;
+      if ((rc = reverse_one(R, j))) return rc;
+    }
+    return HW_OK;
+  }
+  const int m = P.m(n, s);
+  const int slot_b = slot_a + 1;
+  if ((rc = load_slot(R, slot_a))) return rc;
+  if ((rc = advance(R, a, m))) return rc;
+  if ((rc = save_slot(R, slot_b))) return rc;
+  if ((rc = reverse_range(R, P, a + m, n - m, s - 1, slot_b))) return rc;
+  return reverse_range(R, P, a, m, s, slot_a);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hw_adjoint_step(hw_solver* s, double dt, double* const* lam_state, double* const* lam_static) {
+  hw::SolverView v;
+  int rc = check_adjoint_solver(s, &v);
+  if (rc) return rc;
+  if (!lam_state || !lam_static) return afail(HW_ERR_ARG, "hw_adjoint_step: null adjoint planes");
+  for (int q = 0; q < 9; ++q)
+    if (!lam_state[q]) return afail(HW_ERR_ARG, "hw_adjoint_step: null state adjoint plane");
+  for (int q = 0; q < 3; ++q)
+    if (!lam_static[q]) return afail(HW_ERR_ARG, "hw_adjoint_step: null static adjoint plane");
+  if (!(dt >= 0) || !(dt < 1e300)) return afail(HW_ERR_ARG, "hw_adjoint_step: bad dt");
+  AdjBuffers* B = nullptr;
+  if ((rc = get_buffers(s, v, &B))) return rc;
+  const int blocks = std::min((int)((v.n + 255) / 256), 152 * 8);
+  hw::Ptr9 src{}, dst{};
+  for (int q = 0; q < 9; ++q) { src.p[q] = lam_state[q]; dst.p[q] = B->lam[0][q]; }
+  hw::k_adj_convert<<<blocks, 256, 0, v.stream>>>((int)v.n, v.d2->dx, v.d2->dy, src, dst, 1);
+  int cur = 0;
+  if ((rc = reverse_step(s, v, B, dt, &cur))) return rc;
+  for (int q = 0; q < 9; ++q) { src.p[q] = B->lam[cur][q]; dst.p[q] = lam_state[q]; }
+  hw::k_adj_convert<<<blocks, 256, 0, v.stream>>>((int)v.n, v.d2->dx, v.d2->dy, src, dst, 0);
+  if ((rc = finish_static(v, B, lam_static))) return rc;
+  ACUDA(cudaGetLastError());
+  return HW_OK;
+}
+
+int hw_gauge_loss(hw_solver* s, int nsteps, const double* dts, const int* gauge_idx, int ngauge,
+                  const double* eta_obs, double* loss_out, double* eta_gauges) {
+  hw::SolverView v;
+  int rc = check_adjoint_solver(s, &v);
+  if (rc) return rc;
+  if (nsteps < 1 || !dts || !gauge_idx || ngauge < 1 || !eta_obs || !loss_out)
+    return afail(HW_ERR_ARG, "hw_gauge_loss: bad argument");
+  for (int g = 0; g < ngauge; ++g)
+    if (gauge_idx[g] < 0 || (size_t)gauge_idx[g] >= v.n) return afail(HW_ERR_ARG, "hw_gauge_loss: gauge out of range");
+  cudaStream_t st = v.stream;
+  std::vector<double> start(9 * v.n);
+  double *d_save = nullptr, *d_g = nullptr;
+  int* d_idx = nullptr;
+  ACUDA(cudaMalloc(&d_save, 9 * v.n * sizeof(double)));
+  ACUDA(cudaMalloc(&d_g, (size_t)nsteps * ngauge * sizeof(double)));
+  ACUDA(cudaMalloc(&d_idx, ngauge * sizeof(int)));
+  ACUDA(cudaMemcpyAsync(d_idx, gauge_idx, ngauge * sizeof(int), cudaMemcpyHostToDevice, st));
+  for (int q = 0; q < 9; ++q)
+    ACUDA(cudaMemcpyAsync(d_save + (size_t)q * v.n, v.state[q], v.n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  for (int j = 0; j < nsteps && rc == HW_OK; ++j) {
+    rc = hw_rk3_step(s, dts[j]);
+    hw::solver_view(s, &v);
+    hw::k_gather_eta<<<(ngauge + 127) / 128, 128, 0, st>>>(v.state[0], d_idx, ngauge, d_g + (size_t)j * ngauge);
+  }
+  std::vector<double> g((size_t)nsteps * ngauge);
+  if (rc == HW_OK) {
+    ACUDA(cudaMemcpyAsync(g.data(), d_g, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ACUDA(cudaStreamSynchronize(st));
+    double L = 0.0;
+    for (size_t q = 0; q < g.size(); ++q) L += (g[q] - eta_obs[q]) * (g[q] - eta_obs[q]);
+    *loss_out = L;
+    if (eta_gauges) std::copy(g.begin(), g.end(), eta_gauges);
+    double* src[9];
+    for (int q = 0; q < 9; ++q) src[q] = d_save + (size_t)q * v.n;
+    rc = hw::solver_set_state_planes(s, src);
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(d_save);
+  cudaFree(d_g);
+  cudaFree(d_idx);
+  return rc;
+}
+
+int hw_adjoint_run(hw_solver* s, int nsteps, const double* dts, const int* gauge_idx, int ngauge,
+                   const double* eta_obs, int snapshots, double* loss_out, double* const* grad_state,
+                   double* const* grad_static, long long* forward_steps_out) {
+  hw::SolverView v;
+  int rc = check_adjoint_solver(s, &v);
+  if (rc) return rc;
+  if (nsteps < 1 || !dts || !gauge_idx || ngauge < 1 || !eta_obs || snapshots < 0 || !grad_state || !grad_static)
+    return afail(HW_ERR_ARG, "hw_adjoint_run: bad argument");
+  for (int g = 0; g < ngauge; ++g)
+    if (gauge_idx[g] < 0 || (size_t)gauge_idx[g] >= v.n) return afail(HW_ERR_ARG, "hw_adjoint_run: gauge out of range");
+  AdjBuffers* B = nullptr;
+  if ((rc = get_buffers(s, v, &B))) return rc;
+  cudaStream_t st = v.stream;
+  const int S = std::min(snapshots, std::max(nsteps - 1, 0));
+  RunCtx R;
+  R.s = s; R.v = v; R.B = B; R.dts = dts; R.ng = ngauge; R.cur = 0; R.fwd_steps = 0;
+  double* d_obs = nullptr;
+  int* d_idx = nullptr;
+  ACUDA(cudaMalloc(&R.d_gvals, (size_t)nsteps * ngauge * sizeof(double)));
+  ACUDA(cudaMalloc(&d_obs, (size_t)nsteps * ngauge * sizeof(double)));
+  ACUDA(cudaMalloc(&d_idx, ngauge * sizeof(int)));
+  R.d_obs = d_obs;
+  R.d_idx = d_idx;
+  ACUDA(cudaMemcpyAsync(d_obs, eta_obs, (size_t)nsteps * ngauge * sizeof(double), cudaMemcpyHostToDevice, st));
+  ACUDA(cudaMemcpyAsync(d_idx, gauge_idx, ngauge * sizeof(int), cudaMemcpyHostToDevice, st));
+  R.slots.resize(S + 1, nullptr);
+  for (int k = 0; k <= S && rc == HW_OK; ++k) {
+    cudaError_t e = cudaMalloc(&R.slots[k], 9 * v.n * sizeof(double));
+    if (e != cudaSuccess) rc = afail(HW_ERR_NOMEM, "hw_adjoint_run: snapshot allocation failed");
+  }
+  if (rc == HW_OK) rc = save_slot(R, 0);
+  // forward pass: loss and gauge values
+  for (int j = 0; j < nsteps && rc == HW_OK; ++j) {
+    rc = hw_rk3_step(s, dts[j]);
+    hw::solver_view(s, &R.v);
+    ++R.fwd_steps;
+    hw::k_gather_eta<<<(ngauge + 127) / 128, 128, 0, st>>>(R.v.state[0], d_idx, ngauge, R.d_gvals + (size_t)j * ngauge);
+  }
+  if (rc == HW_OK && loss_out) {
+    std::vector<double> g((size_t)nsteps * ngauge);
+    cudaMemcpyAsync(g.data(), R.d_gvals, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    double L = 0.0;
+    for (size_t q = 0; q < g.size(); ++q) L += (g[q] - eta_obs[q]) * (g[q] - eta_obs[q]);
+    *loss_out = L;
+  }
+  // reverse pass
+  if (rc == HW_OK) {
+    rc = zero_planes(B->lam[0], 9, v.n, st);
+    Schedule P(nsteps, S);
+    if (rc == HW_OK) rc = reverse_range(R, P, 0, nsteps, S, 0);
+  }
+  if (rc == HW_OK) {
+    hw::solver_view(s, &R.v);
+    const int blocks = std::min((int)((v.n + 255) / 256), 152 * 8);
+    hw::Ptr9 src{}, dst{};
+    for (int q = 0; q < 9; ++q) { src.p[q] = B->lam[R.cur][q]; dst.p[q] = grad_state[q]; }
+    hw::k_adj_convert<<<blocks, 256, 0, st>>>((int)v.n, v.d2->dx, v.d2->dy, src, dst, 0);
+    rc = zero_planes(grad_static, 3, v.n, st);
+    if (rc == HW_OK) rc = finish_static(R.v, B, grad_static);
+  }
+  if (rc == HW_OK) rc = load_slot(R, 0);  // leave the solver at the initial state
+  cudaStreamSynchronize(st);
+  for (double* p : R.slots) if (p) cudaFree(p);
+  cudaFree(R.d_gvals);
+  cudaFree(d_obs);
+  cudaFree(d_idx);
+  if (forward_steps_out) *forward_steps_out = R.fwd_steps;
+  return rc;
+}
+
+}  // extern "C"

@@ -194,6 +194,7 @@ int hw_destroy(hw_solver* s) {
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   if (s->stream) cudaStreamSynchronize(s->stream);
   else cudaDeviceSynchronize();
+  hw::adjoint_release(s);
   for (void* p : s->allocs) cudaFree(p);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   delete s;
@@ -497,6 +498,34 @@ int hw_set_state(hw_solver* s, const double* const* in, int layout, int ptr_kind
   if (ptr_kind == HW_HOST) CUDA_OK(cudaStreamSynchronize(s->stream));
   return HW_OK;
 }
+
+}  // extern "C"
+
+namespace hw {
+int solver_view(hw_solver* s, SolverView* v) {
+  if (!s) return fail(HW_ERR_ARG, "null solver");
+  if (!s->inited) return fail(HW_ERR_STATE, "call hw_init first");
+  v->stream = s->stream;
+  v->d2 = s->is2d() ? &s->d2 : nullptr;
+  v->state = s->state();
+  for (int q = 0; q < 9; ++q) v->base[q] = q < s->nstate ? s->base[q] : nullptr;
+  v->alpha = s->alpha;
+  v->dt = s->dt;
+  v->params = &s->params;
+  v->n = s->n;
+  bind_state(s, s->state());
+  return HW_OK;
+}
+
+int solver_set_state_planes(hw_solver* s, double* const* src) {
+  double** S = s->state();
+  for (int q = 0; q < s->nstate; ++q)
+    CUDA_OK(cudaMemcpyAsync(S[q], src[q], s->n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  return HW_OK;
+}
+}  // namespace hw
+
+extern "C" {
 
 int hw_set_profiling(hw_solver* s, int on) {
   if (!s) return fail(HW_ERR_ARG, "hw_set_profiling: null solver");

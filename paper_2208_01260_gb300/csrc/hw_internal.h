@@ -4,6 +4,8 @@
 #include <cstddef>
 #include <cuda_runtime.h>
 
+#include "../../include/hwswe.h"
+
 namespace hw {
 
 enum { MODE_STAGE = 0, MODE_RHS = 1 };
@@ -91,5 +93,21 @@ void launch_node1d(const Dev1D& d, const StageArgs1D& sa, int mode, bool linear,
 void launch_init1d(const Dev1D& d, const PhysIn1D& in, int* status, cudaStream_t st);
 void launch_convert1d(const Dev1D& d, const Ptr9& src, const Ptr9& dst, int layout, int dir, cudaStream_t st);
 
+
+
+// Solver internals used by the adjoint (hw_adjoint.cu); defined in hw_api.cu.
+struct SolverView {
+  cudaStream_t stream;
+  Dev2D* d2;            // null for 1D solvers
+  double** state;       // current state planes (9)
+  double* base[9];
+  double* alpha;
+  double* dt;
+  const hw_params* params;
+  size_t n;
+};
+int solver_view(hw_solver* s, SolverView* v);
+int solver_set_state_planes(hw_solver* s, double* const* src);  // device copy into the current state
+void adjoint_release(hw_solver* s);  // frees a solver's adjoint working buffers; hw_destroy calls it
 
 }  // namespace hw

@@ -284,6 +284,34 @@ def ex48(nx: int = 200, ny: int = 100, bc=REFLECTIVE) -> Scenario:
     return _still2d(X, Y, b, bx, by, eta, z, z, bc, bc, (0.0, 2.0, 0.0, 1.0), "ex48")
 
 
+def adjoint_case(n: int = 512, seed: int = SEED_BASE + 5, hump_seed: int = 0) -> Scenario:
+    """Adjoint workload: the benchmark's bottom (8 Gaussian bumps on [0,2]x[0,1], reflective) at n x n
+    without the strip, plus a Gaussian hump of the surface (amplitude U(0.02, 0.05), width U(0.05, 0.1),
+    centre in the interior) drawn from ``hump_seed`` (0 for the model, others for observation runs)."""
+    sc = bumps2d(n, n, seed=seed, strip=0.0)
+    r = _rng(seed * 7 + 1000 + hump_seed)
+    A = r.uniform(0.02, 0.05)
+    s_ = r.uniform(0.05, 0.1)
+    xc = r.uniform(0.4, 1.6)
+    yc = r.uniform(0.3, 0.7)
+    x = axis(sc.nx, sc.x0, sc.x1, sc.bc_x)
+    y = axis(sc.ny, sc.y0, sc.y1, sc.bc_y)
+    X, Y = np.meshgrid(x, y)
+    g = A * np.exp(-((X - xc) ** 2 + (Y - yc) ** 2) / s_ ** 2)
+    sc.h = sc.h + g
+    sc.deriv[0] = sc.deriv[0] - 2.0 * (X - xc) / s_ ** 2 * g
+    sc.deriv[3] = sc.deriv[3] - 2.0 * (Y - yc) / s_ ** 2 * g
+    sc.name = "adjoint%d" % hump_seed
+    sc.meta = dict(hump=(A, s_, xc, yc))
+    return sc
+
+
+def gauges(nx: int, ny: int, count: int = 32, seed: int = SEED_BASE + 6):
+    """Seeded gauge nodes (linear indices j*nx + i), distinct."""
+    r = _rng(seed)
+    return np.sort(r.choice(nx * ny, count, replace=False)).astype(np.int32)
+
+
 def batch_sizes(n: int = 512, seed: int = SEED_BASE + 4, lo: int = 64, hi: int = 1024):
     """Grid sizes nx, ny independently log-uniform integers on [lo, hi]."""
     r = _rng(seed)
