@@ -229,8 +229,8 @@ def batched_compare(steps, n_inst=512):
 def adjoint_cost(n=512, nsteps=400, snapshots=20):
     """Config 5: gauge misfit over 32 gauges and `nsteps` steps at n x n (bottom of the benchmark plus
     a surface hump, reflective; observations from a run with another hump; the unperturbed CFL step
-    sequence passed explicitly). Times the forward loss and the adjoint run with binomial
-    checkpointing (`snapshots` states)."""
+    sequence passed explicitly). Times the forward loss and the adjoint run, once on a whole-run tape
+    and once with binomial checkpointing (`snapshots` states)."""
     import torch
     import paper_2208_01260_gb300 as hw
     from paper_2208_01260_gb300 import adjoint as A
@@ -265,17 +265,23 @@ def adjoint_cost(n=512, nsteps=400, snapshots=20):
     t_fwd = time.perf_counter() - t0
     gs = torch.empty_like(state)
     gb = torch.empty_like(static)
-    t0 = time.perf_counter()
-    loss_a, nf = A.hw_adjoint_run(solver.h, dts, gidx, obs, snapshots, [gs[q] for q in range(9)],
-                                  [gb[q] for q in range(3)])
-    torch.cuda.synchronize()
-    t_adj = time.perf_counter() - t0
+    out = {"grid": [n, n], "steps": nsteps, "gauges": int(len(gidx)), "forward_s": t_fwd,
+           "loss_forward_only": loss_f, "unit": "adjoint run time / forward loss time"}
     step_f = t_fwd / nsteps
-    return {"grid": [n, n], "steps": nsteps, "gauges": int(len(gidx)), "snapshots": snapshots, "loss": loss_a,
-            "loss_forward_only": loss_f, "forward_s": t_fwd, "adjoint_run_s": t_adj,
-            "adjoint_run_over_forward": t_adj / t_fwd, "forward_steps_in_adjoint_run": int(nf),
-            "reverse_step_over_forward_step": (t_adj - nf * step_f) / nsteps / step_f,
-            "grad_norm_state": float(gs.norm()), "grad_norm_static": float(gb.norm())}
+    for name, snaps in (("tape", A.HW_ADJ_TAPE), ("checkpointed", snapshots)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss_a, nf = A.hw_adjoint_run(solver.h, dts, gidx, obs, snaps, [gs[q] for q in range(9)],
+                                      [gb[q] for q in range(3)])
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        out[name] = {"snapshots": "every stage of every step" if snaps < 0 else snaps, "loss": loss_a,
+                     "adjoint_run_s": t_adj, "adjoint_run_over_forward": t_adj / t_fwd,
+                     "forward_steps_in_adjoint_run": int(nf),
+                     "reverse_step_over_forward_step": (t_adj - nf * step_f) / nsteps / step_f,
+                     "grad_norm_state": float(gs.norm()), "grad_norm_static": float(gb.norm())}
+    solver.close()
+    return out
 
 
 def run_reference(args):

@@ -185,10 +185,18 @@ int hw_gauge_loss(hw_solver* s, int nsteps, const double* dts, const int* gauge_
                   const double* eta_obs, double* loss_out, double* eta_gauges);
 
 /* The same loss and its gradient (grad_state: 9 device planes, grad_static: 3 device planes, both
- * overwritten) by the adjoint, with binomial checkpointing: at most `snapshots` intermediate states
- * are held, and the schedule minimising the recomputed forward steps is found by dynamic
- * programming over (steps left, snapshots left). *forward_steps_out (may be NULL) receives the
- * forward steps taken (loss pass plus recomputation). The solver returns to the initial state. */
+ * overwritten) by the adjoint. `snapshots` selects the storage of the forward run:
+ *   >= 0          binomial checkpointing: at most `snapshots` intermediate states are held and the
+ *                 schedule minimising the recomputed forward steps is found by dynamic programming over
+ *                 (steps left, snapshots left); each reversed step is first recomputed from its state;
+ *   HW_ADJ_TAPE   every stage input, stage alpha and source interface value of every step is kept in
+ *                 device memory (about 51 planes of nx*ny doubles per step), so nothing is recomputed;
+ *                 HW_ERR_NOMEM when that exceeds 90% of the free device memory;
+ *   HW_ADJ_AUTO   HW_ADJ_TAPE when it fits, else checkpointing with as many snapshots as fit.
+ * *forward_steps_out (may be NULL) receives the forward steps taken (loss pass plus recomputation). The
+ * solver returns to the initial state. */
+#define HW_ADJ_TAPE (-1)
+#define HW_ADJ_AUTO (-2)
 int hw_adjoint_run(hw_solver* s, int nsteps, const double* dts, const int* gauge_idx, int ngauge,
                    const double* eta_obs, int snapshots, double* loss_out, double* const* grad_state,
                    double* const* grad_static, long long* forward_steps_out);

@@ -4,7 +4,8 @@
 ``include/hwswe.h`` (argument marshalling only). ``GaugeMisfit`` is a ``torch.autograd.Function``:
 its forward evaluates L = sum_n sum_g (eta^n[g] - eta_obs[n-1][g])^2 of a run with given time steps
 from an initial equilibrium state (9 planes) and bottom (b, b_x, b_y), and its backward calls the
-adjoint with binomial checkpointing.
+adjoint (by default on a whole-run tape when it fits in device memory, else with binomial
+checkpointing).
 """
 from __future__ import annotations
 
@@ -14,6 +15,10 @@ from typing import Sequence
 import numpy as np
 
 from . import HW_DEVICE, HW_LAYOUT_EQUILIBRIUM, _check, _pp, _ptr, hw_init, hw_set_state, lib
+
+# storage modes of hw_adjoint_run besides a snapshot count (include/hwswe.h)
+HW_ADJ_TAPE = -1  # keep every stage of every step: no recomputation
+HW_ADJ_AUTO = -2  # the tape when it fits in device memory, else checkpointing with the snapshots that fit
 
 
 def _sigs():
@@ -90,7 +95,7 @@ class GaugeMisfit:
     """torch.autograd.Function computing the gauge misfit of a run and its gradient by the adjoint."""
 
     @staticmethod
-    def apply(state, static, solver, dts, gauge_idx, eta_obs, snapshots=16):
+    def apply(state, static, solver, dts, gauge_idx, eta_obs, snapshots=HW_ADJ_AUTO):
         return _GaugeMisfitFn.apply(state, static, solver, dts, gauge_idx, eta_obs, snapshots)
 
 

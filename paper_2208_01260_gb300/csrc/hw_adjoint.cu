@@ -15,6 +15,7 @@
 // of b_x, b_y) are reversed by k_adj_static.
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -46,6 +47,8 @@ struct AdjDev {
   double* lalpha;         // [2], accumulated within the stage
   const double* dbx[3];   // forward 2 bhat (x-interfaces) of this stage
   const double* dby[3];   // forward 2 bhat (y-interfaces)
+  const double* fax;      // forward first component of 2 Fhat (x-interfaces) of this stage
+  const double* fay;      // forward first component of 2 Fhat (y-interfaces)
   int* argmax;            // [2]
 };
 
@@ -182,81 +185,134 @@ __device__ __forceinline__ void interface_adjoint_y(const AdjDev& A, int i, int 
   }
 }
 
-// ---- 2. x-interfaces ----
+// ---- 2. x-interfaces (a block: AX_T consecutive interfaces of one row) ----
+// The four record adjoints of each interface collect in a shared-memory slab; after the block has
+// finished, each record sums its (up to) four contributions, so only the three records a block shares
+// with each neighbour are added atomically.
 constexpr int AX_T = 64;
 constexpr int AX_N = AX_T + 3;
 
 __global__ void __launch_bounds__(AX_T) k_adj_sweep_x(AdjDev A) {
   __shared__ double sm[NREC * AX_N];
+  __shared__ double slab[4 * NREC * AX_T];
   const Dev2D& d = A.d;
   const int j = blockIdx.y, k0 = blockIdx.x * AX_T;
   const double ax = A.alpha[0];
-  for (int t = threadIdx.x; t < AX_N; t += AX_T) {
-    const int i = k0 - 2 + t;
+  const int t = threadIdx.x;
+  for (int u = t; u < AX_N; u += AX_T) {
+    const int i = k0 - 2 + u;
     if (i > d.nx + 1) break;
     Node12 n;
     load_node(d, i, j, n);
     double rec[NREC];
     node_record<0>(n, d.g, ax, rec);
 #pragma unroll
-    for (int f = 0; f < NREC; ++f) sm[f * AX_N + t] = rec[f];
+    for (int f = 0; f < NREC; ++f) sm[f * AX_N + u] = rec[f];
   }
   __syncthreads();
-  const int k = k0 + threadIdx.x;
-  if (k > d.nx) return;
-  const int t = threadIdx.x;
-  const size_t o = (size_t)j * (d.nx + 1) + k;
-  double qb[6];
+  const int k = k0 + t;
+  if (k <= d.nx) {
+    const size_t o = (size_t)j * (d.nx + 1) + k;
+    double qb[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) qb[q] = d.qbx[q][o];
-  double lX[12];
-  interface_adjoint_x(A, k, j, lX);
-  double lr[4][NREC] = {};
-  double lqb[6] = {0, 0, 0, 0, 0, 0};
-  interface_values_rev<0>(sm + t, sm + t + 1, sm + t + 2, sm + t + 3, AX_N, qb, d.g, d.eps_w, lX, lr, lqb);
+    for (int q = 0; q < 6; ++q) qb[q] = d.qbx[q][o];
+    double lX[12];
+    interface_adjoint_x(A, k, j, lX);
+    double lqb[6] = {0, 0, 0, 0, 0, 0};
+    interface_values_rev<0>(sm + t, 1, AX_N, qb, A.fax[o], A.dbx[0][o], d.g, d.eps_w, lX,
+                            SlabAcc{slab + t, AX_T}, lqb);
 #pragma unroll
-  for (int q = 0; q < 6; ++q) A.lqbx[q][o] += lqb[q];
+    for (int q = 0; q < 6; ++q) A.lqbx[q][o] += lqb[q];
+  } else {
+    for (int e = 0; e < 4 * NREC; ++e) slab[e * AX_T + t] = 0.0;  // interfaces past the row's end
+  }
+  __syncthreads();
   const size_t row = (size_t)j * (d.nx + 4);
+  for (int u = t; u < AX_N; u += AX_T) {
+    const int r = k0 - 2 + u;  // raw record index, -2 .. nx+1
+    if (r > d.nx + 1) break;
+    const bool shared_slot = u < 3 || u >= AX_T;
+    for (int f = 0; f < NREC; ++f) {
+      double acc = 0.0;
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const size_t col = row + (k - 2 + s) + 2;
-#pragma unroll
-    for (int f = 0; f < NREC; ++f)
-      if (lr[s][f] != 0.0) atomicAdd(A.lrecx[f] + col, lr[s][f]);
+      for (int s = 0; s < 4; ++s) {
+        const int tt = u - s;
+        if (tt >= 0 && tt < AX_T) acc += slab[(s * NREC + f) * AX_T + tt];
+      }
+      double* dst = A.lrecx[f] + row + (r + 2);
+      if (shared_slot) {
+        if (acc != 0.0) atomicAdd(dst, acc);
+      } else {
+        *dst = acc;
+      }
+    }
   }
 }
 
-// ---- 2'. y-interfaces (one thread per interface; records recomputed from the four nodes) ----
-__global__ void __launch_bounds__(128) k_adj_sweep_y(AdjDev A) {
+// ---- 2'. y-interfaces (a block: AY_R interface rows of 32 columns; records of AY_R + 3 node rows) ----
+constexpr int AY_R = 8;
+constexpr int AY_NR = AY_R + 3;
+constexpr int AY_T = 32 * AY_R;
+constexpr size_t AY_SMEM = (size_t)(NREC * AY_NR * 32 + 4 * NREC * AY_T) * sizeof(double);
+
+__global__ void __launch_bounds__(AY_T) k_adj_sweep_y(AdjDev A) {
+  extern __shared__ double ysm[];
+  double* recs = ysm;                      // [NREC][AY_NR][32]
+  double* slab = ysm + NREC * AY_NR * 32;  // [4][NREC][AY_T]
   const Dev2D& d = A.d;
-  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int k = blockIdx.y * 4 + (threadIdx.x >> 5);
-  if (i >= d.nx || k > d.ny) return;
+  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * AY_R;
+  const int tid = threadIdx.x, c = tid & 31, ty = tid >> 5;
   const double ay = A.alpha[1];
-  double rec[4][NREC];
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
+  for (int idx = tid; idx < AY_NR * 32; idx += AY_T) {
+    const int u = idx >> 5, cc = idx & 31;
+    const int i = i0 + cc, r = k0 - 2 + u;
+    if (i >= d.nx || r > d.ny + 1) continue;
     Node12 n;
-    load_node(d, i, k - 2 + s, n);
-    node_record<1>(n, d.g, ay, rec[s]);
+    load_node(d, i, r, n);
+    double rec[NREC];
+    node_record<1>(n, d.g, ay, rec);
+#pragma unroll
+    for (int f = 0; f < NREC; ++f) recs[(f * AY_NR + u) * 32 + cc] = rec[f];
   }
-  const size_t o = (size_t)k * d.nx + i;
-  double qb[6];
+  __syncthreads();
+  const int i = i0 + c, k = k0 + ty;
+  if (i < d.nx && k <= d.ny) {
+    const size_t o = (size_t)k * d.nx + i;
+    double qb[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) qb[q] = d.qby[q][o];
-  double lY[12];
-  interface_adjoint_y(A, i, k, lY);
-  double lr[4][NREC] = {};
-  double lqb[6] = {0, 0, 0, 0, 0, 0};
-  interface_values_rev<1>(rec[0], rec[1], rec[2], rec[3], 1, qb, d.g, d.eps_w, lY, lr, lqb);
+    for (int q = 0; q < 6; ++q) qb[q] = d.qby[q][o];
+    double lY[12];
+    interface_adjoint_y(A, i, k, lY);
+    double lqb[6] = {0, 0, 0, 0, 0, 0};
+    const double* r0 = recs + ty * 32 + c;
+    interface_values_rev<1>(r0, 32, AY_NR * 32, qb, A.fay[o], A.dby[0][o], d.g, d.eps_w, lY,
+                            SlabAcc{slab + tid, AY_T}, lqb);
 #pragma unroll
-  for (int q = 0; q < 6; ++q) A.lqby[q][o] += lqb[q];
+    for (int q = 0; q < 6; ++q) A.lqby[q][o] += lqb[q];
+  } else {
+    for (int e = 0; e < 4 * NREC; ++e) slab[e * AY_T + tid] = 0.0;  // past the grid's edge
+  }
+  __syncthreads();
+  for (int idx = tid; idx < AY_NR * 32; idx += AY_T) {
+    const int u = idx >> 5, cc = idx & 31;
+    const int ii = i0 + cc, r = k0 - 2 + u;  // raw record row, -2 .. ny+1
+    if (ii >= d.nx || r > d.ny + 1) continue;
+    const bool shared_row = u < 3 || u >= AY_R;
+    const size_t pos = (size_t)(r + 2) * d.nx + ii;
+    for (int f = 0; f < NREC; ++f) {
+      double acc = 0.0;
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const size_t pos = (size_t)(k - 2 + s + 2) * d.nx + i;
-#pragma unroll
-    for (int f = 0; f < NREC; ++f)
-      if (lr[s][f] != 0.0) atomicAdd(A.lrecy[f] + pos, lr[s][f]);
+      for (int s = 0; s < 4; ++s) {
+        const int uu = u - s;
+        if (uu >= 0 && uu < AY_R) acc += slab[(s * NREC + f) * AY_T + uu * 32 + cc];
+      }
+      double* dst = A.lrecy[f] + pos;
+      if (shared_row) {
+        if (acc != 0.0) atomicAdd(dst, acc);
+      } else {
+        *dst = acc;
+      }
+    }
   }
 }
 
@@ -566,6 +622,8 @@ struct AdjBuffers {
   double* alpha_st = nullptr;  // [3][2]
   double* dbx[3][3] = {};
   double* dby[3][3] = {};
+  double* fx[3] = {};  // first component of 2 Fhat per stage, x- and y-interfaces
+  double* fy[3] = {};
   double* lam[2][9] = {};
   double* lbase[9] = {};
   double* lR[9] = {};
@@ -615,8 +673,11 @@ int get_buffers(hw_solver* s, const hw::SolverView& v, AdjBuffers** out) {
     for (int q = 0; q < 9; ++q) A(&B->stage_in[k][q], n);
   for (int q = 0; q < 9; ++q) { A(&B->stage_out[q], n); A(&B->lam[0][q], n); A(&B->lam[1][q], n); A(&B->lbase[q], n); A(&B->lR[q], n); }
   A(&B->alpha_st, 8);
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 3; ++k) {
     for (int c = 0; c < 3; ++c) { A(&B->dbx[k][c], nxi); A(&B->dby[k][c], nyi); }
+    A(&B->fx[k], nxi);
+    A(&B->fy[k], nyi);
+  }
   for (int q = 0; q < 6; ++q) { A(&B->lmod[q], n); A(&B->lqbx[q], nxi); A(&B->lqby[q], nyi); }
   for (int f = 0; f < hw::NREC; ++f) { A(&B->lrecx[f], (size_t)(B->nx + 4) * B->ny); A(&B->lrecy[f], (size_t)B->nx * (B->ny + 4)); }
   for (int q = 0; q < 3; ++q) { A(&B->lstat[q], n); A(&B->lstatic_phys[q], n); }
@@ -655,35 +716,57 @@ int zero_planes(double* const* p, int count, size_t n, cudaStream_t st) {
   return HW_OK;
 }
 
-// Forward recompute of one step from the current state keeping every stage's input, alpha and source
-// interface values; the solver's state is left unchanged.
-int forward_record(hw_solver* s, const hw::SolverView& v, AdjBuffers* B, double dt) {
+// What the reverse of one step reads: every stage's input, the step's output, the stage alphas, the
+// stages' source interface values 2 bhat and the first components of their fluxes 2 Fhat. Points into AdjBuffers (one step, recomputed from a
+// checkpoint) or into a whole-run tape.
+struct StepTape {
+  double* in[3][9];
+  double* out[9];
+  double* alpha;  // [3][2]
+  double* dbx[3][3];
+  double* dby[3][3];
+  double* fx[3];
+  double* fy[3];
+};
+
+StepTape buffer_tape(AdjBuffers* B) {
+  StepTape T{};
+  for (int k = 0; k < 3; ++k)
+    for (int q = 0; q < 9; ++q) T.in[k][q] = B->stage_in[k][q];
+  for (int q = 0; q < 9; ++q) T.out[q] = B->stage_out[q];
+  T.alpha = B->alpha_st;
+  for (int k = 0; k < 3; ++k) {
+    for (int c = 0; c < 3; ++c) { T.dbx[k][c] = B->dbx[k][c]; T.dby[k][c] = B->dby[k][c]; }
+    T.fx[k] = B->fx[k];
+    T.fy[k] = B->fy[k];
+  }
+  return T;
+}
+
+// One forward step from T.in[0] recording into T (the sweeps write the source interface values straight
+// into the tape); the solver's state is not touched.
+int forward_record(const hw::SolverView& v, AdjBuffers* B, const StepTape& T, double dt) {
   cudaStream_t st = v.stream;
-  const size_t bytes = v.n * sizeof(double);
-  for (int q = 0; q < 9; ++q) ACUDA(cudaMemcpyAsync(B->stage_in[0][q], v.state[q], bytes, cudaMemcpyDeviceToDevice, st));
   ACUDA(cudaMemcpyAsync(v.dt, &dt, sizeof(double), cudaMemcpyHostToDevice, st));
   hw::Dev2D d = *v.d2;
   const bool lin = false, chr = true;
   for (int k = 1; k <= 3; ++k) {
-    for (int q = 0; q < 9; ++q) d.S[q] = B->stage_in[k - 1][q];
+    for (int q = 0; q < 9; ++q) d.S[q] = T.in[k - 1][q];
+    for (int c = 0; c < 3; ++c) { d.X[3 + c] = T.dbx[k - 1][c]; d.Y[3 + c] = T.dby[k - 1][c]; }
+    d.X[0] = T.fx[k - 1];
+    d.Y[0] = T.fy[k - 1];
     double* amax = B->lalpha;  // scratch for the keys (reset below)
     hw::launch_alpha2d(d, (unsigned long long*)amax, (int*)(B->lalpha + 2), st);
-    hw::launch_finish_alpha2d(d, (const unsigned long long*)amax, B->alpha_st + 2 * (k - 1), nullptr, v.params->cfl,
+    hw::launch_finish_alpha2d(d, (const unsigned long long*)amax, T.alpha + 2 * (k - 1), nullptr, v.params->cfl,
                               nullptr, -1.0, st);
-    hw::launch_sweep_x2d(d, B->alpha_st + 2 * (k - 1), lin, chr, st);
-    hw::launch_sweep_y2d(d, B->alpha_st + 2 * (k - 1), lin, chr, st);
-    for (int c = 0; c < 3; ++c) {
-      ACUDA(cudaMemcpyAsync(B->dbx[k - 1][c], d.X[3 + c], (size_t)(d.nx + 1) * d.ny * sizeof(double),
-                            cudaMemcpyDeviceToDevice, st));
-      ACUDA(cudaMemcpyAsync(B->dby[k - 1][c], d.Y[3 + c], (size_t)d.nx * (d.ny + 1) * sizeof(double),
-                            cudaMemcpyDeviceToDevice, st));
-    }
+    hw::launch_sweep_x2d(d, T.alpha + 2 * (k - 1), lin, chr, st);
+    hw::launch_sweep_y2d(d, T.alpha + 2 * (k - 1), lin, chr, st);
     hw::StageArgs sa{};
     sa.k = k;
     sa.limiter = v.params->limiter;
     sa.dt = v.dt;
     for (int q = 0; q < 9; ++q) {
-      sa.out[q] = k < 3 ? B->stage_in[k][q] : B->stage_out[q];
+      sa.out[q] = k < 3 ? T.in[k][q] : T.out[q];
       sa.base[q] = v.base[q];
     }
     hw::launch_node2d(d, sa, hw::MODE_STAGE, lin, chr, st);
@@ -692,21 +775,21 @@ int forward_record(hw_solver* s, const hw::SolverView& v, AdjBuffers* B, double 
   return HW_OK;
 }
 
-// Reverse of one step: lam[cur] holds the adjoint of the step's output on entry and of its input on
-// return (in lam[*cur]); static adjoints accumulate.
-int reverse_step(hw_solver* s, const hw::SolverView& v, AdjBuffers* B, double dt, int* cur) {
-  int rc = forward_record(s, v, B, dt);
-  if (rc) return rc;
+// Reverse of one recorded step: lam[cur] holds the adjoint of the step's output on entry and of its input
+// on return (in lam[*cur]); static adjoints accumulate.
+int reverse_recorded(const hw::SolverView& v, AdjBuffers* B, const StepTape& T, double dt, int* cur) {
+  int rc = HW_OK;
+  ACUDA(cudaFuncSetAttribute(hw::k_adj_sweep_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hw::AY_SMEM));
   cudaStream_t st = v.stream;
   const size_t n = v.n;
   if ((rc = zero_planes(B->lbase, 9, n, st))) return rc;
   hw::Dev2D d = *v.d2;
   const double ak[4] = {0.0, 0.0, 0.75, 1.0 / 3.0}, bk[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
   for (int k = 3; k >= 1; --k) {
-    for (int q = 0; q < 9; ++q) d.S[q] = B->stage_in[k - 1][q];
+    for (int q = 0; q < 9; ++q) d.S[q] = T.in[k - 1][q];
     hw::AdjDev A{};
     A.d = d;
-    A.alpha = B->alpha_st + 2 * (k - 1);
+    A.alpha = T.alpha + 2 * (k - 1);
     A.k = k;
     A.dt = dt;
     A.a = ak[k];
@@ -720,7 +803,9 @@ int reverse_step(hw_solver* s, const hw::SolverView& v, AdjBuffers* B, double dt
     }
     for (int q = 0; q < 6; ++q) { A.lmod[q] = B->lmod[q]; A.lqbx[q] = B->lqbx[q]; A.lqby[q] = B->lqby[q]; }
     for (int f = 0; f < hw::NREC; ++f) { A.lrecx[f] = B->lrecx[f]; A.lrecy[f] = B->lrecy[f]; }
-    for (int q = 0; q < 3; ++q) { A.lstat[q] = B->lstat[q]; A.dbx[q] = B->dbx[k - 1][q]; A.dby[q] = B->dby[k - 1][q]; }
+    for (int q = 0; q < 3; ++q) { A.lstat[q] = B->lstat[q]; A.dbx[q] = T.dbx[k - 1][q]; A.dby[q] = T.dby[k - 1][q]; }
+    A.fax = T.fx[k - 1];
+    A.fay = T.fy[k - 1];
     for (int q = 0; q < 2; ++q) { A.lsv[q] = B->lsv[q]; A.lsq[q] = B->lsq[q]; }
     A.lalpha = B->lalpha;
     A.argmax = B->argmax;
@@ -731,7 +816,7 @@ int reverse_step(hw_solver* s, const hw::SolverView& v, AdjBuffers* B, double dt
     const dim3 gn((d.nx + 31) / 32, (d.ny + 7) / 8), bn(32, 8);
     hw::k_adj_node_pre<<<gn, bn, 0, st>>>(A);
     hw::k_adj_sweep_x<<<dim3((d.nx + 1 + hw::AX_T - 1) / hw::AX_T, d.ny), hw::AX_T, 0, st>>>(A);
-    hw::k_adj_sweep_y<<<dim3((d.nx + 31) / 32, (d.ny + 1 + 3) / 4), 128, 0, st>>>(A);
+    hw::k_adj_sweep_y<<<dim3((d.nx + 31) / 32, (d.ny + 1 + hw::AY_R - 1) / hw::AY_R), hw::AY_T, hw::AY_SMEM, st>>>(A);
     const int nrec = (d.nx + 4) * d.ny + d.nx * (d.ny + 4);
     hw::k_adj_records<<<(nrec + 255) / 256, 256, 0, st>>>(A);
     if (A.limiter) hw::k_adj_limiter<<<gn, bn, 0, st>>>(A);
@@ -741,6 +826,17 @@ int reverse_step(hw_solver* s, const hw::SolverView& v, AdjBuffers* B, double dt
     *cur ^= 1;
   }
   return HW_OK;
+}
+
+// Reverse of one step from the solver's current state (recomputed into the one-step buffers).
+int reverse_step(const hw::SolverView& v, AdjBuffers* B, double dt, int* cur) {
+  const StepTape T = buffer_tape(B);
+  const size_t bytes = v.n * sizeof(double);
+  for (int q = 0; q < 9; ++q)
+    ACUDA(cudaMemcpyAsync(T.in[0][q], v.state[q], bytes, cudaMemcpyDeviceToDevice, v.stream));
+  int rc = forward_record(v, B, T, dt);
+  if (rc) return rc;
+  return reverse_recorded(v, B, T, dt, cur);
 }
 
 // static adjoints -> (b, b_x, b_y) and clear the accumulators
@@ -805,6 +901,41 @@ struct Schedule {
   }
 };
 
+// Whole-run tape: for each step its three stage inputs, the stages' source interface values and first
+// flux components, and the stage alphas, then the final state; step j's output is step j+1's first stage input. Planes start on 256-byte
+// boundaries.
+struct RunTape {
+  size_t pn, pxi, pyi, step_d;
+  int nsteps;
+  static size_t up(size_t x) { return (x + 31) & ~(size_t)31; }
+  RunTape(const hw::SolverView& v, int N) : nsteps(N) {
+    pn = up(v.n);
+    pxi = up((size_t)(v.d2->nx + 1) * v.d2->ny);
+    pyi = up((size_t)v.d2->nx * (v.d2->ny + 1));
+    step_d = 27 * pn + 12 * pxi + 12 * pyi + 32;
+  }
+  size_t bytes() const { return ((size_t)nsteps * step_d + 9 * pn) * sizeof(double); }
+  StepTape step(double* base, int j) const {
+    StepTape T{};
+    double* p = base + (size_t)j * step_d;
+    for (int k = 0; k < 3; ++k)
+      for (int q = 0; q < 9; ++q) T.in[k][q] = p + (size_t)(9 * k + q) * pn;
+    double* next = base + (size_t)(j + 1) * step_d;  // the final state sits where step nsteps would begin
+    for (int q = 0; q < 9; ++q) T.out[q] = next + (size_t)q * pn;
+    double* x = p + 27 * pn;
+    for (int k = 0; k < 3; ++k) {
+      for (int c = 0; c < 3; ++c) {
+        T.dbx[k][c] = x + (size_t)(4 * k + c) * pxi;
+        T.dby[k][c] = x + 12 * pxi + (size_t)(4 * k + c) * pyi;
+      }
+      T.fx[k] = x + (size_t)(4 * k + 3) * pxi;
+      T.fy[k] = x + 12 * pxi + (size_t)(4 * k + 3) * pyi;
+    }
+    T.alpha = x + 12 * pxi + 12 * pyi;
+    return T;
+  }
+};
+
 struct RunCtx {
   hw_solver* s;
   hw::SolverView v;
@@ -847,7 +978,7 @@ int reverse_one(RunCtx& R, int j) {
   hw::k_loss_seed<<<(R.ng + 127) / 128, 128, 0, R.v.stream>>>(R.d_gvals + (size_t)j * R.ng, R.d_obs + (size_t)j * R.ng,
                                                              R.d_idx, R.ng, R.B->lam[R.cur][0]);
   hw::solver_view(R.s, &R.v);
-  return reverse_step(R.s, R.v, R.B, R.dts[j], &R.cur);
+  return reverse_step(R.v, R.B, R.dts[j], &R.cur);
 }
 
 int reverse_range(RunCtx& R, Schedule& P, int a, int n, int s, int slot_a) {
@@ -894,7 +1025,7 @@ int hw_adjoint_step(hw_solver* s, double dt, double* const* lam_state, double* c
   for (int q = 0; q < 9; ++q) { src.p[q] = lam_state[q]; dst.p[q] = B->lam[0][q]; }
   hw::k_adj_convert<<<blocks, 256, 0, v.stream>>>((int)v.n, v.d2->dx, v.d2->dy, src, dst, 1);
   int cur = 0;
-  if ((rc = reverse_step(s, v, B, dt, &cur))) return rc;
+  if ((rc = reverse_step(v, B, dt, &cur))) return rc;
   for (int q = 0; q < 9; ++q) { src.p[q] = B->lam[cur][q]; dst.p[q] = lam_state[q]; }
   hw::k_adj_convert<<<blocks, 256, 0, v.stream>>>((int)v.n, v.d2->dx, v.d2->dy, src, dst, 0);
   if ((rc = finish_static(v, B, lam_static))) return rc;
@@ -951,51 +1082,122 @@ int hw_adjoint_run(hw_solver* s, int nsteps, const double* dts, const int* gauge
   hw::SolverView v;
   int rc = check_adjoint_solver(s, &v);
   if (rc) return rc;
-  if (nsteps < 1 || !dts || !gauge_idx || ngauge < 1 || !eta_obs || snapshots < 0 || !grad_state || !grad_static)
+  if (nsteps < 1 || !dts || !gauge_idx || ngauge < 1 || !eta_obs || !grad_state || !grad_static ||
+      (snapshots < 0 && snapshots != HW_ADJ_TAPE && snapshots != HW_ADJ_AUTO))
     return afail(HW_ERR_ARG, "hw_adjoint_run: bad argument");
   for (int g = 0; g < ngauge; ++g)
     if (gauge_idx[g] < 0 || (size_t)gauge_idx[g] >= v.n) return afail(HW_ERR_ARG, "hw_adjoint_run: gauge out of range");
+  for (int q = 0; q < 9; ++q)
+    if (!grad_state[q]) return afail(HW_ERR_ARG, "hw_adjoint_run: null gradient plane");
+  for (int q = 0; q < 3; ++q)
+    if (!grad_static[q]) return afail(HW_ERR_ARG, "hw_adjoint_run: null gradient plane");
   AdjBuffers* B = nullptr;
   if ((rc = get_buffers(s, v, &B))) return rc;
   cudaStream_t st = v.stream;
-  const int S = std::min(snapshots, std::max(nsteps - 1, 0));
+
+  // storage mode: a whole-run tape, or binomial checkpointing with S snapshots besides the start
+  const RunTape layout(v, nsteps);
+  bool use_tape = false;
+  int S = 0;
+  if (snapshots == HW_ADJ_TAPE || snapshots == HW_ADJ_AUTO) {
+    size_t free_b = 0, total_b = 0;
+    ACUDA(cudaMemGetInfo(&free_b, &total_b));
+    const double budget = 0.9 * (double)free_b;
+    if ((double)layout.bytes() <= budget) {
+      use_tape = true;
+    } else if (snapshots == HW_ADJ_TAPE) {
+      return afail(HW_ERR_NOMEM, "hw_adjoint_run: the whole-run tape does not fit in free device memory");
+    } else {
+      const double per = 9.0 * (double)v.n * sizeof(double);
+      S = (int)std::max(0.0, std::min((double)(nsteps - 1), std::floor(budget / per) - 1.0));
+    }
+  } else {
+    S = std::min(snapshots, std::max(nsteps - 1, 0));
+  }
+
   RunCtx R;
   R.s = s; R.v = v; R.B = B; R.dts = dts; R.ng = ngauge; R.cur = 0; R.fwd_steps = 0;
+  R.d_gvals = nullptr;
   double* d_obs = nullptr;
   int* d_idx = nullptr;
-  ACUDA(cudaMalloc(&R.d_gvals, (size_t)nsteps * ngauge * sizeof(double)));
-  ACUDA(cudaMalloc(&d_obs, (size_t)nsteps * ngauge * sizeof(double)));
-  ACUDA(cudaMalloc(&d_idx, ngauge * sizeof(int)));
+  double* tape = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    for (double* p : R.slots) if (p) cudaFree(p);
+    cudaFree(tape);
+    cudaFree(R.d_gvals);
+    cudaFree(d_obs);
+    cudaFree(d_idx);
+    if (forward_steps_out) *forward_steps_out = R.fwd_steps;
+  };
+  auto alloc = [&](void** p, size_t bytes, const char* what) {
+    if (rc != HW_OK) return;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      rc = afail(HW_ERR_NOMEM, std::string("hw_adjoint_run: allocation failed: ") + what);
+    }
+  };
+  alloc((void**)&R.d_gvals, (size_t)nsteps * ngauge * sizeof(double), "gauge values");
+  alloc((void**)&d_obs, (size_t)nsteps * ngauge * sizeof(double), "observations");
+  alloc((void**)&d_idx, ngauge * sizeof(int), "gauge indices");
+  if (use_tape) alloc((void**)&tape, layout.bytes(), "tape");
+  R.slots.assign(use_tape ? 0 : S + 1, nullptr);
+  for (size_t k = 0; k < R.slots.size(); ++k) alloc((void**)&R.slots[k], 9 * v.n * sizeof(double), "snapshot");
   R.d_obs = d_obs;
   R.d_idx = d_idx;
-  ACUDA(cudaMemcpyAsync(d_obs, eta_obs, (size_t)nsteps * ngauge * sizeof(double), cudaMemcpyHostToDevice, st));
-  ACUDA(cudaMemcpyAsync(d_idx, gauge_idx, ngauge * sizeof(int), cudaMemcpyHostToDevice, st));
-  R.slots.resize(S + 1, nullptr);
-  for (int k = 0; k <= S && rc == HW_OK; ++k) {
-    cudaError_t e = cudaMalloc(&R.slots[k], 9 * v.n * sizeof(double));
-    if (e != cudaSuccess) rc = afail(HW_ERR_NOMEM, "hw_adjoint_run: snapshot allocation failed");
+  auto check = [&](cudaError_t e, const char* what) {
+    if (rc == HW_OK && e != cudaSuccess) rc = afail(HW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  if (rc == HW_OK) {
+    check(cudaMemcpyAsync(d_obs, eta_obs, (size_t)nsteps * ngauge * sizeof(double), cudaMemcpyHostToDevice, st),
+          "hw_adjoint_run: copy of observations");
+    check(cudaMemcpyAsync(d_idx, gauge_idx, ngauge * sizeof(int), cudaMemcpyHostToDevice, st),
+          "hw_adjoint_run: copy of gauge indices");
   }
-  if (rc == HW_OK) rc = save_slot(R, 0);
-  // forward pass: loss and gauge values
-  for (int j = 0; j < nsteps && rc == HW_OK; ++j) {
-    rc = hw_rk3_step(s, dts[j]);
-    hw::solver_view(s, &R.v);
-    ++R.fwd_steps;
-    hw::k_gather_eta<<<(ngauge + 127) / 128, 128, 0, st>>>(R.v.state[0], d_idx, ngauge, R.d_gvals + (size_t)j * ngauge);
+  // forward pass: loss and gauge values (recording the tape, or from the solver with a snapshot at 0)
+  if (rc == HW_OK && use_tape) {
+    const StepTape T0 = layout.step(tape, 0);
+    for (int q = 0; q < 9 && rc == HW_OK; ++q)
+      check(cudaMemcpyAsync(T0.in[0][q], v.state[q], v.n * sizeof(double), cudaMemcpyDeviceToDevice, st),
+            "hw_adjoint_run: copy of the initial state");
+    for (int j = 0; j < nsteps && rc == HW_OK; ++j) {
+      const StepTape T = layout.step(tape, j);
+      rc = forward_record(v, B, T, dts[j]);
+      ++R.fwd_steps;
+      hw::k_gather_eta<<<(ngauge + 127) / 128, 128, 0, st>>>(T.out[0], d_idx, ngauge, R.d_gvals + (size_t)j * ngauge);
+    }
+  } else if (rc == HW_OK) {
+    rc = save_slot(R, 0);
+    for (int j = 0; j < nsteps && rc == HW_OK; ++j) {
+      rc = hw_rk3_step(s, dts[j]);
+      hw::solver_view(s, &R.v);
+      ++R.fwd_steps;
+      hw::k_gather_eta<<<(ngauge + 127) / 128, 128, 0, st>>>(R.v.state[0], d_idx, ngauge,
+                                                             R.d_gvals + (size_t)j * ngauge);
+    }
   }
+  if (rc == HW_OK) check(cudaGetLastError(), "hw_adjoint_run: forward pass");
   if (rc == HW_OK && loss_out) {
     std::vector<double> g((size_t)nsteps * ngauge);
-    cudaMemcpyAsync(g.data(), R.d_gvals, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
+    check(cudaMemcpyAsync(g.data(), R.d_gvals, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+          "hw_adjoint_run: copy of gauge values");
+    check(cudaStreamSynchronize(st), "hw_adjoint_run: forward pass");
     double L = 0.0;
     for (size_t q = 0; q < g.size(); ++q) L += (g[q] - eta_obs[q]) * (g[q] - eta_obs[q]);
     *loss_out = L;
   }
   // reverse pass
-  if (rc == HW_OK) {
-    rc = zero_planes(B->lam[0], 9, v.n, st);
+  if (rc == HW_OK) rc = zero_planes(B->lam[0], 9, v.n, st);
+  if (rc == HW_OK && use_tape) {
+    for (int j = nsteps - 1; j >= 0 && rc == HW_OK; --j) {
+      hw::k_loss_seed<<<(ngauge + 127) / 128, 128, 0, st>>>(R.d_gvals + (size_t)j * ngauge,
+                                                           d_obs + (size_t)j * ngauge, d_idx, ngauge,
+                                                           B->lam[R.cur][0]);
+      rc = reverse_recorded(v, B, layout.step(tape, j), dts[j], &R.cur);
+    }
+  } else if (rc == HW_OK) {
     Schedule P(nsteps, S);
-    if (rc == HW_OK) rc = reverse_range(R, P, 0, nsteps, S, 0);
+    rc = reverse_range(R, P, 0, nsteps, S, 0);
   }
   if (rc == HW_OK) {
     hw::solver_view(s, &R.v);
@@ -1006,13 +1208,8 @@ int hw_adjoint_run(hw_solver* s, int nsteps, const double* dts, const int* gauge
     rc = zero_planes(grad_static, 3, v.n, st);
     if (rc == HW_OK) rc = finish_static(R.v, B, grad_static);
   }
-  if (rc == HW_OK) rc = load_slot(R, 0);  // leave the solver at the initial state
-  cudaStreamSynchronize(st);
-  for (double* p : R.slots) if (p) cudaFree(p);
-  cudaFree(R.d_gvals);
-  cudaFree(d_obs);
-  cudaFree(d_idx);
-  if (forward_steps_out) *forward_steps_out = R.fwd_steps;
+  if (rc == HW_OK && !use_tape) rc = load_slot(R, 0);  // leave the solver at the initial state
+  cleanup();
   return rc;
 }
 

@@ -9,11 +9,13 @@
 namespace hw {
 
 // Reverse of hweno_side<false> (Sec. 2.1 eqs. HWEp1, GHYZZ, Rec-f). Inputs: forward data f, p, eps;
-// adjoints lv (of the weighted value) and ln1, ln2, ln3, lr (of the weight numerators and the
-// normaliser, from the source reconstruction that shares them). Outputs: adjoints of f, p (added) and
-// returns the adjoint of eps.
+// the adjoint lv of the weighted value. With SRC, the same weights also reconstruct a source from the
+// candidates qbs[3] (Sec. 2.1 Step 2) whose value has adjoint lw: its adjoint reaches the weight
+// numerators and normaliser here and the candidates through lqbs (added). Outputs: adjoints of f, p
+// (added); returns the adjoint of eps.
+template <bool SRC>
 __device__ __forceinline__ double hweno_side_rev(const double f[3], const double p[3], double eps, double lv,
-                                                 double ln1, double ln2, double ln3, double lr, double lf[3],
+                                                 const double* qbs, double lw, double* lqbs, double lf[3],
                                                  double lp[3]) {
   // forward
   const double d1 = f[0] - f[1], d2 = f[1] - f[2];
@@ -36,7 +38,19 @@ __device__ __forceinline__ double hweno_side_rev(const double f[3], const double
   const double n1 = s2 * s3, n2 = s1 * s3, n3 = (4.0 / 3.0) * (s1 * s2);
   const double r = fast_rcp(n1 + n2 + n3);
   const double num = fma(n1, q1, fma(n2, q2, n3 * q3));
-  // reverse
+  // reverse: source value S r with S = n1 qb1 + n2 qb2 + n3 qb3
+  double ln1 = 0.0, ln2 = 0.0, ln3 = 0.0, lr = 0.0;
+  if (SRC) {
+    const double rw = r * lw;
+    ln1 = qbs[0] * rw;
+    ln2 = qbs[1] * rw;
+    ln3 = qbs[2] * rw;
+    lr = fma(n1, qbs[0], fma(n2, qbs[1], n3 * qbs[2])) * lw;
+    lqbs[0] += n1 * rw;
+    lqbs[1] += n2 * rw;
+    lqbs[2] += n3 * rw;
+  }
+  // reverse of the weighted value
   const double lnum = r * lv;
   const double lrt = fma(num, lv, lr);
   const double lden = -r * r * lrt;
@@ -88,11 +102,6 @@ __device__ __forceinline__ double hweno_side_rev(const double f[3], const double
   lf[0] += lf0; lf[1] += lf1; lf[2] += lf2;
   lp[0] += lp0; lp[1] += lp1; lp[2] += lp2;
   return leps;
-}
-
-// Forward weights of one side (needed by the source reverse).
-__device__ __forceinline__ void hweno_weights(const double f[3], const double p[3], double eps, Weights& W) {
-  (void)hweno_side<false>(f[0], f[1], f[2], p[0], p[1], p[2], eps, W);
 }
 
 // Reverse of limiter_field<false> (eqs. step1-dxi, limiter-1d). Returns adjoint of eps.
@@ -247,16 +256,28 @@ __device__ __forceinline__ double node_record_rev(const Node12& n, double g, dou
   return lalpha;
 }
 
-// Reverse of interface_values<DIR, false, true>. lout: adjoint of the 12 outputs. Adds to the record
-// adjoints lr0..lr3 (stride 1) and to lqb[6]; returns nothing (interface values do not depend on alpha
-// directly).
-template <int DIR>
-__device__ __forceinline__ void interface_values_rev(const double* r0, const double* r1, const double* r2,
-                                                     const double* r3, int stride, const double qb[6], double g,
-                                                     double eps_w, const double lout[12], double lr[4][NREC],
-                                                     double lqb[6]) {
+// Record adjoints of the four nodes of an interface, kept in shared memory: entry (s, f) of thread t at
+// p[(s * NREC + f) * stride] (stride = threads of the block, t already added to p).
+struct SlabAcc {
+  double* p;
+  int stride;
+  __device__ __forceinline__ double& operator()(int s, int f) const { return p[(s * NREC + f) * stride]; }
+};
+
+// Reverse of interface_values<DIR, false, true>. lout: adjoint of the 12 outputs. Writes the adjoints of
+// the four nodes' records to lr(s, f) (every entry exactly once) and adds those of the source
+// candidates to lqb[6]; the interface values do not depend on alpha directly. The forward weighted
+// values enter only through the outputs' first components A and Bsum (read back from the forward
+// sweep), so the reverse recomputes each side's projections and weights just once, inside the
+// reverse of each reconstruction, with one side's data live at a time.
+template <int DIR, class Acc>
+__device__ __forceinline__ void interface_values_rev(const double* r0, int sstep, int stride, const double qb[6],
+                                                     double A, double Bsum, double g, double eps_w,
+                                                     const double lout[12], const Acc& lr, double lqb[6]) {
+  // node s = 0..3 of the stencil: field f at r0[s * sstep + f * stride]
 #define RV(r, f) (r)[(f) * stride]
-  const double* rp[4] = {r0, r1, r2, r3};
+  const double* r1 = r0 + sstep;
+  const double* r2 = r0 + 2 * sstep;
   // ---- forward: interface state and eigenvectors ----
   const double hs = RV(r1, R_H) + RV(r2, R_H);
   const double rhs = fast_rcp(hs);
@@ -269,60 +290,27 @@ __device__ __forceinline__ void interface_values_rev(const double* r0, const dou
   const double upc = un + cb, umc = un - cb;
   const int cn = DIR == 0 ? 1 : 2, ct = DIR == 0 ? 2 : 1;
   const double eps13 = (8.0 * g * eps_w) * hs, eps2 = 4.0 * eps_w;
-  // projected data and weights per side and field
-  double f[2][3][3], p[2][3][3];
-  Weights W[2][3];
-  double G[3] = {0.0, 0.0, 0.0}, GB1 = 0.0, GB3 = 0.0;
-#pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    const int os[3] = {side == 0 ? 0 : 3, side == 0 ? 1 : 2, side == 0 ? 2 : 1};
+  // characteristic projections of one side's three nodes (rows of the left eigenvectors; side 1
+  // reads the nodes mirrored and its derivative records negated)
+  auto project = [&](int side, double f[3][3], double p[3][3]) {
     const int fo = side == 0 ? R_FP : R_FM, go = side == 0 ? R_GP : R_GM;
     const double sg = side == 0 ? 1.0 : -1.0;
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
-      const double* r = rp[os[t]];
+      const double* r = r0 + (side == 0 ? t : 3 - t) * sstep;
       const double F0 = RV(r, fo), Fn = RV(r, fo + cn), Ft = RV(r, fo + ct);
       const double G0 = sg * RV(r, go), Gn = sg * RV(r, go + cn), Gt = sg * RV(r, go + ct);
-      f[side][0][t] = fma(upc, F0, -Fn);
-      f[side][1][t] = fma(-ut, F0, Ft);
-      f[side][2][t] = fma(-umc, F0, Fn);
-      p[side][0][t] = fma(upc, G0, -Gn);
-      p[side][1][t] = fma(-ut, G0, Gt);
-      p[side][2][t] = fma(-umc, G0, Gn);
+      f[0][t] = fma(upc, F0, -Fn);
+      f[1][t] = fma(-ut, F0, Ft);
+      f[2][t] = fma(-umc, F0, Fn);
+      p[0][t] = fma(upc, G0, -Gn);
+      p[1][t] = fma(-ut, G0, Gt);
+      p[2][t] = fma(-umc, G0, Gn);
     }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const double v = hweno_side<false>(f[side][k][0], f[side][k][1], f[side][k][2], p[side][k][0], p[side][k][1],
-                                         p[side][k][2], k == 1 ? eps2 : eps13, W[side][k]);
-      G[k] += v;
-    }
-    GB1 -= weighted(W[side][0], qb[3 * side], qb[3 * side + 1], qb[3 * side + 2]);
-    GB3 += weighted(W[side][2], qb[3 * side], qb[3 * side + 1], qb[3 * side + 2]);
-  }
-  const double A = (G[0] + G[2]) * ic2;
-  const double Bsum = (GB1 + GB3) * ic2;
+  };
+  // A = (G_1 + G_3) ic2 and Bsum = (GB_1 + GB_3) ic2 are the first components of the forward outputs
+  // 2 Fhat and 2 bhat, passed in; 1 / ic2 = 2 c.
   // ---- reverse ----
-  // linear parts: derivative flux and mixed term
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const double l6 = lout[6 + c], l9 = lout[9 + c];
-    lr[0][R_FP + c] += 3.0 * l6;
-    lr[3][R_FM + c] -= 3.0 * l6;
-    lr[2][R_FM + c] += 24.0 * l6;
-    lr[1][R_FP + c] -= 24.0 * l6;
-    lr[2][R_FP + c] += 21.0 * l6;
-    lr[1][R_FM + c] -= 21.0 * l6;
-    lr[0][R_GP + c] += l6;
-    lr[3][R_GM + c] += l6;
-    lr[1][R_GP + c] -= 2.0 * l6;
-    lr[2][R_GM + c] -= 2.0 * l6;
-    lr[2][R_GP + c] -= 5.0 * l6;
-    lr[1][R_GM + c] -= 5.0 * l6;
-    lr[1][R_MIX + c] += 7.0 * l9;
-    lr[2][R_MIX + c] += 7.0 * l9;
-    lr[0][R_MIX + c] -= l9;
-    lr[3][R_MIX + c] -= l9;
-  }
   // back-projection
   double lun = 0.0, lut = 0.0, lic2 = 0.0;
   const double lA = lout[0] + un * lout[cn] + ut * lout[ct];
@@ -332,57 +320,45 @@ __device__ __forceinline__ void interface_values_rev(const double* r0, const dou
   lG[0] = -0.5 * lout[cn] + ic2 * lA;
   lG[2] = 0.5 * lout[cn] + ic2 * lA;
   lG[1] = lout[ct];
-  lic2 += (G[0] + G[2]) * lA;
+  lic2 += 2.0 * cb * A * lA;
   const double lBs = lout[3] + un * lout[3 + cn] + ut * lout[3 + ct];
   lun += Bsum * lout[3 + cn];
   lut += Bsum * lout[3 + ct];
   const double lGB1 = -0.5 * lout[3 + cn] + ic2 * lBs;
   const double lGB3 = 0.5 * lout[3 + cn] + ic2 * lBs;
-  lic2 += (GB1 + GB3) * lBs;
-  // per side and field: weighted values and the source with the same weights
+  lic2 += 2.0 * cb * Bsum * lBs;
+  // per side and field: weighted values and the source with the same weights (projections recomputed)
   double lupc = 0.0, lumc = 0.0, leps13 = 0.0;
-#pragma unroll
+#pragma unroll 1
   for (int side = 0; side < 2; ++side) {
-    const int os[3] = {side == 0 ? 0 : 3, side == 0 ? 1 : 2, side == 0 ? 2 : 1};
     const int fo = side == 0 ? R_FP : R_FM, go = side == 0 ? R_GP : R_GM;
     const double sg = side == 0 ? 1.0 : -1.0;
-    const double* qbs = qb + 3 * side;
+    double f[3][3], p[3][3];
+    project(side, f, p);
     double lf[3][3] = {}, lp[3][3] = {};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      // source: GB1 -= weighted(W0), GB3 += weighted(W2)
-      double ln1 = 0.0, ln2 = 0.0, ln3 = 0.0, lrr = 0.0;
-      if (k != 1) {
-        const double lw = k == 0 ? -lGB1 : lGB3;
-        const Weights& w = W[side][k];
-        const double S = fma(w.n1, qbs[0], fma(w.n2, qbs[1], w.n3 * qbs[2]));
-        ln1 = w.r * qbs[0] * lw;
-        ln2 = w.r * qbs[1] * lw;
-        ln3 = w.r * qbs[2] * lw;
-        lrr = S * lw;
-        lqb[3 * side] += w.n1 * w.r * lw;
-        lqb[3 * side + 1] += w.n2 * w.r * lw;
-        lqb[3 * side + 2] += w.n3 * w.r * lw;
-      }
-      const double le = hweno_side_rev(f[side][k], p[side][k], k == 1 ? eps2 : eps13, lG[k], ln1, ln2, ln3, lrr,
-                                       lf[k], lp[k]);
-      if (k != 1) leps13 += le;
-    }
+    // source: GB1 -= weighted(W0), GB3 += weighted(W2)
+    leps13 += hweno_side_rev<true>(f[0], p[0], eps13, lG[0], qb + 3 * side, -lGB1, lqb + 3 * side, lf[0], lp[0]);
+    (void)hweno_side_rev<false>(f[1], p[1], eps2, lG[1], nullptr, 0.0, nullptr, lf[1], lp[1]);
+    leps13 += hweno_side_rev<true>(f[2], p[2], eps13, lG[2], qb + 3 * side, lGB3, lqb + 3 * side, lf[2], lp[2]);
     // projections f = (upc F0 - Fn, -ut F0 + Ft, -umc F0 + Fn), p likewise with sg G
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
-      const double* r = rp[os[t]];
+      const int sl = side == 0 ? t : 3 - t;
+      const double* r = r0 + sl * sstep;
       const double F0 = RV(r, fo), G0 = sg * RV(r, go);
       lupc += F0 * lf[0][t] + G0 * lp[0][t];
       lut -= F0 * lf[1][t] + G0 * lp[1][t];
       lumc -= F0 * lf[2][t] + G0 * lp[2][t];
-      double* l = lr[os[t]];
-      l[fo] += upc * lf[0][t] - ut * lf[1][t] - umc * lf[2][t];
-      l[fo + cn] += -lf[0][t] + lf[2][t];
-      l[fo + ct] += lf[1][t];
-      l[go] += sg * (upc * lp[0][t] - ut * lp[1][t] - umc * lp[2][t]);
-      l[go + cn] += sg * (-lp[0][t] + lp[2][t]);
-      l[go + ct] += sg * lp[1][t];
+      // plus the derivative flux, linear in the records: 24 dx Ghat = 3 F+_{i-1} - 24 F+_i + 21 F+_{i+1}
+      // + G+_{i-1} - 2 G+_i - 5 G+_{i+1} from the left, mirrored from the right (per component)
+      const double kf = side == 0 ? (sl == 0 ? 3.0 : sl == 1 ? -24.0 : 21.0) : (sl == 3 ? -3.0 : sl == 2 ? 24.0 : -21.0);
+      const double kg = side == 0 ? (sl == 0 ? 1.0 : sl == 1 ? -2.0 : -5.0) : (sl == 3 ? 1.0 : sl == 2 ? -2.0 : -5.0);
+      lr(sl, fo) = fma(kf, lout[6], upc * lf[0][t] - ut * lf[1][t] - umc * lf[2][t]);
+      lr(sl, fo + cn) = fma(kf, lout[6 + cn], -lf[0][t] + lf[2][t]);
+      lr(sl, fo + ct) = fma(kf, lout[6 + ct], lf[1][t]);
+      lr(sl, go) = fma(kg, lout[6], sg * (upc * lp[0][t] - ut * lp[1][t] - umc * lp[2][t]));
+      lr(sl, go + cn) = fma(kg, lout[6 + cn], sg * (-lp[0][t] + lp[2][t]));
+      lr(sl, go + ct) = fma(kg, lout[6 + ct], sg * lp[1][t]);
     }
   }
   // eigen quantities
@@ -395,12 +371,31 @@ __device__ __forceinline__ void interface_values_rev(const double* r0, const dou
   double lhs = (8.0 * g * eps_w) * leps13 + (0.5 * g) * lgh;
   const double lrhs = smM * lub + smW * lvb;
   lhs -= rhs * rhs * lrhs;
-  lr[1][R_H] += lhs;
-  lr[2][R_H] += lhs;
-  lr[1][R_M] += rhs * lub;
-  lr[2][R_M] += rhs * lub;
-  lr[1][R_W] += rhs * lvb;
-  lr[2][R_W] += rhs * lvb;
+  lr(1, R_H) = lhs;
+  lr(2, R_H) = lhs;
+  lr(1, R_M) = rhs * lub;
+  lr(2, R_M) = rhs * lub;
+  lr(1, R_W) = rhs * lvb;
+  lr(2, R_W) = rhs * lvb;
+  // the remaining entries: mixed term 24 (Phi hat) = -M_{i-1} + 7 M_i + 7 M_{i+1} - M_{i+2}, and
+  // records that reach this interface through neither side
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double l9 = lout[9 + c];
+    lr(0, R_MIX + c) = -l9;
+    lr(1, R_MIX + c) = 7.0 * l9;
+    lr(2, R_MIX + c) = 7.0 * l9;
+    lr(3, R_MIX + c) = -l9;
+    lr(3, R_FP + c) = 0.0;
+    lr(3, R_GP + c) = 0.0;
+    lr(0, R_FM + c) = 0.0;
+    lr(0, R_GM + c) = 0.0;
+  }
+#pragma unroll
+  for (int f = R_H; f <= R_W; ++f) {
+    lr(0, f) = 0.0;
+    lr(3, f) = 0.0;
+  }
 #undef RV
 }
 

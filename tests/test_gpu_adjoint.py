@@ -179,14 +179,22 @@ def test_checkpointing_schedules_agree(hw):
     _, _, _, _, dts, gidx, obs = _oracle_problem(sc, nsteps, ng, 5)
     solver = hw.Solver.from_scenario(sc, hw.make_params())
     state, static, _, _ = _eq_static(sc)
+    def current():
+        now = [torch.empty_like(state[0]) for _ in range(9)]
+        hw.hw_get_state(solver.h, now, hw.HW_LAYOUT_EQUILIBRIUM)
+        torch.cuda.synchronize()
+        return torch.stack(now)
     grads = []
-    for snaps in (0, 1, 3, nsteps - 1):
+    for snaps in (0, 1, 3, nsteps - 1, A.HW_ADJ_TAPE, A.HW_ADJ_AUTO):
         A.load_problem(solver, state, static)
+        start = current()
         gs = torch.empty_like(state)
         gb = torch.empty_like(static)
         loss, nf = A.hw_adjoint_run(solver.h, dts, gidx, obs, snaps, [gs[q] for q in range(9)], [gb[q] for q in range(3)])
-        assert nf == nsteps + _dp_cost(nsteps, snaps)
+        # the tape (chosen by AUTO on a grid this small) recomputes nothing
+        assert nf == (nsteps if snaps < 0 else nsteps + _dp_cost(nsteps, snaps))
         grads.append((gs.cpu().numpy(), gb.cpu().numpy()))
+        assert torch.equal(current(), start)  # the solver is back at the initial state
     for gs, gb in grads[1:]:
         # equal up to the summation order of the atomic scatters
         np.testing.assert_allclose(gs, grads[0][0], rtol=1e-9, atol=1e-10 * np.abs(grads[0][0]).max())
@@ -203,7 +211,7 @@ def test_autograd_function(hw):
     state, static, _, _ = _eq_static(sc)
     s_ = state.clone().requires_grad_(True)
     b_ = static.clone().requires_grad_(True)
-    L = A.GaugeMisfit.apply(s_, b_, solver, dts, gidx, obs, 2)
+    L = A.GaugeMisfit.apply(s_, b_, solver, dts, gidx, obs)
     L.backward()
     A.load_problem(solver, state, static)
     gs = torch.empty_like(state)
