@@ -56,9 +56,14 @@ UNITS_PER_LAUNCH = {
 SMS, DFMA_PER_SM_CLK, SM_GHZ = 152, 2, 2.07
 PEAK_FP64_TFLOPS = SMS * DFMA_PER_SM_CLK * 2 * SM_GHZ / 1e3
 PEAK_FP64_OPS = SMS * DFMA_PER_SM_CLK * SM_GHZ * 1e9
-# DRAM bytes per unit from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum), valid only
-# for the kernel sources they were taken on (sha256 of the CUDA sources).
-TRAFFIC = {}
+# DRAM bytes per unit from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum of one stage-3
+# launch at 2048x1024, the state and interface planes above L2), valid only for the kernel sources they
+# were taken on (sources_sha); scaled to a launch by its units (traffic is proportional to them).
+TRAFFIC = {
+    "sweep_x": {"bytes_per_unit": 222.07, "sha": "ab86bc5dca6488cc"},
+    "sweep_y": {"bytes_per_unit": 230.77, "sha": "ab86bc5dca6488cc"},
+    "node": {"bytes_per_unit": 441.94, "sha": "ab86bc5dca6488cc"},
+}
 STATE_BYTES = 9 * NX * NY * 8
 
 
@@ -69,13 +74,16 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
+FORWARD_SOURCES = ("hw_device.cuh", "hw_stencil2d.cuh", "hw_kernels2d.cu", "hw_internal.h")
+
+
 def sources_sha():
+    """sha256 (16 hex digits) of the sources the timed 2D kernels are compiled from."""
     import hashlib
     d = os.path.join(ROOT, "paper_2208_01260_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in FORWARD_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -133,30 +141,51 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(n):
+def dist_setup(backend="nccl"):
+    """Rank layout from the launcher's environment; a process group only when WORLD_SIZE > 1."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if n > 0 else "gloo")
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
     return ws, rank, local
 
 
-def allreduce_max(x, ws):
+def _reduce(x, ws, op):
     if ws == 1:
-        return x
+        return float(x)
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def allreduce_max(x, ws):
+    import torch.distributed as dist
+    return _reduce(x, ws, dist.ReduceOp.MAX if ws > 1 else None)
+
+
+def allreduce_sum(x, ws):
+    import torch.distributed as dist
+    return _reduce(x, ws, dist.ReduceOp.SUM if ws > 1 else None)
 
 
 def barrier(ws):
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def job_rate(units_local, seconds_local, ws):
+    """Whole-job throughput: every rank's units over the slowest rank's time (each rank advances its own
+    replica; no data-path collective). Returns (units/s, max seconds, total units)."""
+    seconds = allreduce_max(seconds_local, ws)
+    units = allreduce_sum(units_local, ws)
+    return units / seconds, seconds, units
 
 
 def oracle_rate(seconds_budget=60.0):
@@ -186,7 +215,8 @@ def batched_compare(steps, n_inst=512):
     """Config 4: n_inst grids with nx, ny log-uniform in [64, 1024] on [0,1]^2, reflective, seeded
     bathymetry and surface hump, each at its own CFL dt. Aggregate point-updates/s of the batched form
     (one launch per phase over all grids, CUDA graph) and of the plain loop (one single-grid solver per
-    instance advanced one step at a time)."""
+    instance advanced one step at a time: with the library's cfl_dt() and rk3_step(dt), and, as a
+    stronger baseline, with the device-side dt of hw_advance)."""
     import torch
     import paper_2208_01260_gb300 as hw
     from paper_2208_01260_gb300 import scenarios as S
@@ -206,24 +236,37 @@ def batched_compare(steps, n_inst=512):
     ms_b = e0.elapsed_time(e1)
     b.close()
     solvers = [hw.Solver.from_scenario(sc, hw.make_params()) for sc in scs]
-    for s in solvers:
+
+    def plain_api_step(s):  # the library's own calls: cfl_dt() then rk3_step(dt)
+        s.rk3_step(s.cfl_dt())
+
+    def plain_device_dt_step(s):  # dt computed and applied on the device, no host round trip
         s.advance(1, use_graph=False)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(steps):
+
+    ms = {}
+    for name, fn in (("api", plain_api_step), ("device_dt", plain_device_dt_step)):
         for s in solvers:
-            s.advance(1, use_graph=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_p = e0.elapsed_time(e1)
+            fn(s)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            for s in solvers:
+                fn(s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms[name] = e0.elapsed_time(e1)
     for s in solvers:
         s.close()
     vb = pts * STAGES * steps / (ms_b * 1e-3)
-    vp = pts * STAGES * steps / (ms_p * 1e-3)
+    vp = pts * STAGES * steps / (ms["api"] * 1e-3)
+    vd = pts * STAGES * steps / (ms["device_dt"] * 1e-3)
     return {"instances": n_inst, "total_points": int(pts), "steps": steps, "value_batched": vb, "value_plain": vp,
-            "ratio": vb / vp, "ms_per_step_batched": ms_b / steps, "ms_per_step_plain": ms_p / steps,
-            "unit": UNIT, "plain": "hw_advance(1 step) per instance per step, eager",
-            "tiles": "autotuned per size class"}
+            "ratio": vb / vp, "ms_per_step_batched": ms_b / steps, "ms_per_step_plain": ms["api"] / steps,
+            "plain": "per instance per step: cfl_dt() then rk3_step(dt)",
+            "value_plain_device_dt": vd, "ratio_vs_device_dt_loop": vb / vd,
+            "ms_per_step_plain_device_dt": ms["device_dt"] / steps,
+            "plain_device_dt": "per instance per step: hw_advance(1 step), dt found and applied on the device",
+            "unit": UNIT, "tiles": "autotuned per size class"}
 
 
 def adjoint_cost(n=512, nsteps=400, snapshots=20):
@@ -343,8 +386,8 @@ def main():
         return run_reference(args)
 
     import torch
-    ws, rank, local = dist_setup(args.gpus)
-    torch.cuda.set_device(local)
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ws, rank, local = dist_setup("nccl")
     import paper_2208_01260_gb300 as hw
     from paper_2208_01260_gb300 import scenarios as S
 
@@ -369,8 +412,8 @@ def main():
         torch.cuda.synchronize()
     barrier(ws)
     ms = ev0.elapsed_time(ev1)
-    ms = allreduce_max(ms, ws)
-    value = ws * NX * NY * STAGES * args.steps / (ms * 1e-3)
+    value, sec, _ = job_rate(NX * NY * STAGES * args.steps, ms * 1e-3, ws)
+    ms = sec * 1e3
 
     # timed region 2: the same K steps with every kernel bracketed by events (per-kernel roofline)
     hw.hw_set_profiling(solver.h, True)
@@ -436,8 +479,8 @@ def main():
         solver.advance(1, use_graph=False)
         hw.hw_get_state(solver.h, hout, hw.HW_LAYOUT_PHYSICAL)
     torch.cuda.synchronize()
-    e2e_s = allreduce_max(time.perf_counter() - t0, ws)
-    e2e = {"value": ws * NX * NY * STAGES * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": STATE_BYTES,
+    e2e_v, e2e_s, _ = job_rate(NX * NY * STAGES * ke, time.perf_counter() - t0, ws)
+    e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": STATE_BYTES,
            "d2h_bytes_per_step": STATE_BYTES, "steps": ke}
 
     solver.sync()
