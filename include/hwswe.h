@@ -166,11 +166,21 @@ int hw_batch_time_tiles(hw_batch* b, int nids, const int* ids, int tx, int seg, 
 
 /* ---------------------------------------------------------------------------------------------
  * Discrete adjoint (2D, nonlinear weights and characteristic projection; limiter on or off).
+ * The paper has no adjoint: these calls reverse the discrete map it defines, i.e. one SSP-RK3 step
+ * (Sec. 2.2 eq. RK) of the 2D semi-discrete scheme (Sec. 3 eq. swe-form-2d-dis, with the reconstruction
+ * and source balance of Sec. 2.1 and the limiter of Sec. 2.2 applied per direction).
  * Gradients are with respect to the equilibrium state planes (eta, m, w, eta_x, m_x, w_x, eta_y, m_y,
  * w_y) and the static planes (b, b_x, b_y) taken as independent arrays (eta held fixed when b moves).
  * The time steps are given explicitly, so the adjoint differentiates the map the caller evaluates.
  * alpha = max(|u|+c) is differentiated through the first node attaining the maximum, with d|x| = dx at
- * x = 0.
+ * x = 0 (max is not differentiable where several nodes tie).
+ * All planes are caller-owned device arrays of nx*ny doubles, row-major [ny][nx], on the solver's
+ * device; the calls run on the solver's stream and return once the work is queued (hw_adjoint_run
+ * synchronises the stream). Errors: HW_ERR_ARG (null pointer, 1D solver, linear weights or no
+ * characteristic projection, gauge index outside the grid, grid above about 2^30 nodes), HW_ERR_STATE
+ * (before hw_init), HW_ERR_NOMEM (working buffers, snapshots or tape), HW_ERR_CUDA.
+ * Working buffers (about 180 planes of nx*ny doubles) are allocated at the first call and freed by
+ * hw_destroy.
  * ------------------------------------------------------------------------------------------- */
 /* Reverse of one hw_rk3_step(dt) taken from the solver's current state: lam_state (9 device planes,
  * equilibrium layout) holds the adjoint of the step's output on entry and of its input on return;

@@ -871,6 +871,9 @@ int check_adjoint_solver(hw_solver* s, hw::SolverView* v) {
   if (!v->d2) return afail(HW_ERR_ARG, "adjoint: 2D solvers only");
   if (v->params->linear_weights || !v->params->char_decomp)
     return afail(HW_ERR_ARG, "adjoint: needs nonlinear weights and characteristic projection");
+  // the record-adjoint kernel indexes (nx+4) ny + nx (ny+4) records with 32-bit integers
+  if (2 * ((long long)v->n + 2LL * (v->d2->nx + v->d2->ny)) >= (long long)INT_MAX)
+    return afail(HW_ERR_ARG, "adjoint: grid too large (more than about 2^30 nodes)");
   return HW_OK;
 }
 
