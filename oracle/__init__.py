@@ -91,6 +91,7 @@ def lib():
             ("orc_rk3_step1d", [gp, prp, C.c_double, pp, pp], C.c_int),
             ("orc_cfl_dt1d", [gp, prp, pp, pp], C.c_double),
             ("orc_gauge_loss_dual2d", [gp, prp, pp, pp, pp, pp, C.c_int, dp, ip, C.c_int, dp, dp], C.c_int),
+            ("orc_lake_run", [gp, prp, pp, pp, C.c_double, C.c_int, dp, ip], C.c_int),
         ]:
             f = getattr(L, name)
             f.argtypes = args
@@ -325,6 +326,23 @@ def gauge_loss_dual2d(grid, params, st, stat, dst, dstat, dts, gauge_idx, obs):
                                        gi.ctypes.data_as(C.POINTER(C.c_int)), len(gi), _d(ob), _d(out)),
            "orc_gauge_loss_dual2d")
     return out[0], out[1]
+
+
+PRECISION = {"single": 0, "double": 1, "double-double": 2}
+
+
+def lake_run(grid, params, st, stat, t_end, precision="double"):
+    """Run to t_end at the CFL step in single, double or double-double precision and return the L1 and
+    Linf deviations from the initial state ([h_L1, h_Linf, hu_L1, hu_Linf(, hv_L1, hv_Linf)]) and the
+    step count (Sec. 4, Tables 1-3)."""
+    nq = 3 if grid.dim == 2 else 2
+    S, a = _ptrs(st)
+    T, b = _ptrs(stat)
+    out = np.zeros(2 * nq)
+    steps = C.c_int(0)
+    _check(lib().orc_lake_run(C.byref(grid), C.byref(params), S, T, float(t_end), PRECISION[precision], _d(out),
+                              C.byref(steps)), "orc_lake_run")
+    return out, steps.value
 
 
 # ------------------------------------------------------------------------------------------------

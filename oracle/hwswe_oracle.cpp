@@ -26,7 +26,8 @@
 //   * boundary conditions: periodic, or reflective walls at the cell faces with the parity table.
 //
 // The scalar type is a template parameter: double for the reference values, a counting type for
-// the operation tally, and a forward-mode dual number for directional derivatives.
+// the operation tally, a forward-mode dual number for directional derivatives, and single and
+// double-double precision for the lake-at-rest rows of Tables 1-3.
 
 #include <cmath>
 #include <cstdint>
@@ -82,6 +83,80 @@ inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
 inline Dual sqrt(Dual a) { double s = std::sqrt(a.v); return Dual(s, a.d / (2.0 * s)); }
 inline double val(Dual a) { return a.v; }
 
+// Double-double number hi + lo (|lo| <= ulp(hi)/2), about 106 significant bits, for the well-balance
+// pin against the quadruple-precision rows of Tables 1-3. Error-free transformations: Knuth's TwoSum,
+// the FMA form of Dekker's TwoProduct; division and square root take one correction step each.
+// The file is compiled with -ffp-contract=off, which TwoSum needs.
+struct DD {
+  double hi, lo;
+  DD() : hi(0), lo(0) {}
+  DD(double x) : hi(x), lo(0) {}
+  DD(double h, double l) : hi(h), lo(l) {}
+};
+inline DD dd_two_sum(double a, double b) {
+  const double s = a + b, bb = s - a;
+  return DD(s, (a - (s - bb)) + (b - bb));
+}
+inline DD dd_fast_two_sum(double a, double b) {  // needs |a| >= |b| (or a == 0)
+  const double s = a + b;
+  return DD(s, b - (s - a));
+}
+inline DD dd_two_prod(double a, double b) {
+  const double p = a * b;
+  return DD(p, std::fma(a, b, -p));
+}
+inline DD operator+(DD a, DD b) {
+  DD s = dd_two_sum(a.hi, b.hi), t = dd_two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = dd_fast_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return dd_fast_two_sum(s.hi, s.lo);
+}
+inline DD operator-(DD a) { return DD(-a.hi, -a.lo); }
+inline DD operator-(DD a, DD b) { return a + (-b); }
+inline DD operator*(DD a, DD b) {
+  DD p = dd_two_prod(a.hi, b.hi);
+  p.lo += a.hi * b.lo + a.lo * b.hi;
+  return dd_fast_two_sum(p.hi, p.lo);
+}
+inline DD operator/(DD a, DD b) {
+  const double q1 = a.hi / b.hi;
+  const DD r1 = a - b * DD(q1);
+  const double q2 = r1.hi / b.hi;
+  const DD r2 = r1 - b * DD(q2);
+  const double q3 = r2.hi / b.hi;
+  return dd_fast_two_sum(q1, q2) + DD(q3);
+}
+inline DD& operator+=(DD& a, DD b) { a = a + b; return a; }
+inline bool operator<(DD a, DD b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+inline bool operator>(DD a, DD b) { return b < a; }
+inline DD sqrt(DD a) {
+  if (!(a.hi > 0.0)) return DD(std::sqrt(a.hi));
+  const double x = std::sqrt(a.hi);
+  const DD r = a - dd_two_prod(x, x);  // Newton: sqrt(a) ~ x + (a - x^2) / (2x)
+  return dd_fast_two_sum(x, r.hi / (2.0 * x));
+}
+inline double val(DD a) { return a.hi + a.lo; }
+
+// Single precision with every operation and constant in float (a plain float would let double
+// literals promote whole expressions to double).
+struct F32 {
+  float v;
+  F32() : v(0) {}
+  F32(double x) : v((float)x) {}
+};
+inline F32 f32(float x) { F32 r; r.v = x; return r; }
+inline F32 operator+(F32 a, F32 b) { return f32(a.v + b.v); }
+inline F32 operator-(F32 a, F32 b) { return f32(a.v - b.v); }
+inline F32 operator*(F32 a, F32 b) { return f32(a.v * b.v); }
+inline F32 operator/(F32 a, F32 b) { return f32(a.v / b.v); }
+inline F32 operator-(F32 a) { return f32(-a.v); }
+inline F32& operator+=(F32& a, F32 b) { a = a + b; return a; }
+inline bool operator<(F32 a, F32 b) { return a.v < b.v; }
+inline bool operator>(F32 a, F32 b) { return a.v > b.v; }
+inline F32 sqrt(F32 a) { return f32(std::sqrt(a.v)); }
+inline double val(F32 a) { return a.v; }
+
 inline double val(double a) { return a; }
 using std::sqrt;
 
@@ -90,11 +165,19 @@ template <class T> inline T make_scalar(double x, double dx);
 template <> inline double make_scalar<double>(double x, double) { return x; }
 template <> inline Cnt make_scalar<Cnt>(double x, double) { return Cnt(x); }
 template <> inline Dual make_scalar<Dual>(double x, double dx) { return Dual(x, dx); }
+template <> inline DD make_scalar<DD>(double x, double) { return DD(x); }
+template <> inline F32 make_scalar<F32>(double x, double) { return F32(x); }
 inline double dpart(double) { return 0.0; }
 inline double dpart(Cnt) { return 0.0; }
 inline double dpart(Dual a) { return a.d; }
 
 template <class T> inline T sq(T a) { return a * a; }
+// SSP-RK3 coefficient p/q in the working precision, so that a_k + b_k = 1 holds to that precision
+// (in double-double, 1/3 and 2/3 rounded to double would add a drift of 5.6e-17 per step); the
+// operation counter does not count it (it is a per-stage constant).
+template <class T> inline T rk_ratio(double p, double q) { return T(p) / T(q); }
+template <> inline double rk_ratio<double>(double p, double q) { return p / q; }
+template <> inline Cnt rk_ratio<Cnt>(double p, double q) { return Cnt(p / q); }
 // |x| with the derivative convention d|x| = dx for x >= 0.
 template <class T> inline T absv(T a) { return (a < T(0.0)) ? -a : a; }
 template <class T> inline T maxv(T a, T b) { return (b > a) ? b : a; }
@@ -676,8 +759,8 @@ void stage2d(const Grid& gr, const Params& pr, int k, double dt, const State2D<T
         for (int q = 0; q < 6; ++q) base[3 + q][o] = mod[q][o];
       }
   }
-  const double a = k == 1 ? 0.0 : (k == 2 ? 3.0 / 4.0 : 1.0 / 3.0);
-  const double b = k == 1 ? 1.0 : (k == 2 ? 1.0 / 4.0 : 2.0 / 3.0);
+  const T a = k == 1 ? T(0.0) : (k == 2 ? rk_ratio<T>(3.0, 4.0) : rk_ratio<T>(1.0, 3.0));
+  const T b = k == 1 ? T(1.0) : (k == 2 ? rk_ratio<T>(1.0, 4.0) : rk_ratio<T>(2.0, 3.0));
   for (int q = 0; q < 9; ++q) out[q].resize(n);
   for (int j = 0; j < gr.ny; ++j)
     for (int i = 0; i < gr.nx; ++i) {
@@ -828,8 +911,8 @@ void stage1d(const Grid& gr, const Params& pr, int k, double dt, const State1D<T
       base[3][i] = mod[1][i];
     }
   }
-  const double a = k == 1 ? 0.0 : (k == 2 ? 3.0 / 4.0 : 1.0 / 3.0);
-  const double b = k == 1 ? 1.0 : (k == 2 ? 1.0 / 4.0 : 2.0 / 3.0);
+  const T a = k == 1 ? T(0.0) : (k == 2 ? rk_ratio<T>(3.0, 4.0) : rk_ratio<T>(1.0, 3.0));
+  const T b = k == 1 ? T(1.0) : (k == 2 ? rk_ratio<T>(1.0, 4.0) : rk_ratio<T>(2.0, 3.0));
   for (int q = 0; q < 4; ++q) out[q].resize(nx);
   for (int i = 0; i < nx; ++i)
     for (int q = 0; q < 4; ++q) {
@@ -1132,4 +1215,115 @@ extern "C" int orc_gauge_loss_dual2d(const Grid* g, const Params* p, const doubl
   out2[0] = L.v;
   out2[1] = L.d;
   return 0;
+}
+
+// =============================================================================================
+// Lake at rest in single, double and double-double precision (Sec. 4, Ex. 4.2 Tables 1-2 and
+// Ex. 4.7 Table 3): the run to t_end at the CFL time step and the L1 / Linf deviations of h and the
+// discharges from the initial state (whose exact solution it is).
+// =============================================================================================
+namespace orc {
+template <class T>
+void set_state1d(const Grid& gr, State1D<T>& S, std::vector<T>* planes) {
+  for (int q = 0; q < 4; ++q) {
+    for (int i = 0; i < gr.nx; ++i) S.p[q].at(i, 0) = planes[q][i];
+    fill_ghosts(S.p[q], gr.bc_x, BC_PERIODIC, PAR1[q], 1.0);
+  }
+}
+
+inline bool last_step(double t, double dt, double t_end) { return dt >= (t_end - t) - 1e-12 * t_end; }
+
+// out: for each of the nq conserved planes (h first, then the discharges) its L1 and Linf deviation.
+template <class T>
+int lake_run1d(const Grid& gr, const Params& pr, const double* const* st, const double* const* stat, double t_end,
+               double* out, int* steps) {
+  State1D<T> S;
+  load_state1d(gr, st, stat, S);
+  std::vector<T> init[2];
+  for (int q = 0; q < 2; ++q)
+    for (int i = 0; i < gr.nx; ++i) init[q].push_back(S.p[q].at(i, 0));
+  double t = 0.0;
+  int n = 0;
+  while (t < t_end && n < 1000000) {
+    double dt = pr.cfl * gr.dx() / val(alpha1d(gr, pr, S));
+    const bool last = last_step(t, dt, t_end);
+    if (last) dt = t_end - t;
+    std::vector<T> B[4], O[4];
+    for (int k = 1; k <= 3; ++k) {
+      stage1d(gr, pr, k, dt, S, B, O, (T*)nullptr);
+      set_state1d(gr, S, O);
+    }
+    t = last ? t_end : t + dt;
+    ++n;
+  }
+  for (int q = 0; q < 2; ++q) {
+    double l1 = 0.0, li = 0.0;
+    for (int i = 0; i < gr.nx; ++i) {
+      const double e = std::fabs(val(S.p[q].at(i, 0) - init[q][i]));  // h - h0 = eta - eta0 (b is fixed)
+      l1 += e;
+      li = std::max(li, e);
+    }
+    out[2 * q] = l1 / gr.nx;
+    out[2 * q + 1] = li;
+  }
+  *steps = n;
+  return 0;
+}
+
+template <class T>
+int lake_run2d(const Grid& gr, const Params& pr, const double* const* st, const double* const* stat, double t_end,
+               double* out, int* steps) {
+  State2D<T> S;
+  load_state2d(gr, st, stat, S);
+  std::vector<T> init[3];
+  for (int q = 0; q < 3; ++q)
+    for (int j = 0; j < gr.ny; ++j)
+      for (int i = 0; i < gr.nx; ++i) init[q].push_back(S.p[q].at(i, j));
+  double t = 0.0;
+  int n = 0;
+  while (t < t_end && n < 1000000) {
+    T ax, ay;
+    alpha2d(gr, pr, S, ax, ay);
+    double dt = pr.cfl / (val(ax) / gr.dx() + val(ay) / gr.dy());
+    const bool last = last_step(t, dt, t_end);
+    if (last) dt = t_end - t;
+    std::vector<T> B[9], O[9];
+    for (int k = 1; k <= 3; ++k) {
+      stage2d(gr, pr, k, dt, S, B, O, (T*)nullptr);
+      set_state2d(gr, S, O);
+    }
+    t = last ? t_end : t + dt;
+    ++n;
+  }
+  const size_t nn = (size_t)gr.nx * gr.ny;
+  for (int q = 0; q < 3; ++q) {
+    double l1 = 0.0, li = 0.0;
+    for (int j = 0; j < gr.ny; ++j)
+      for (int i = 0; i < gr.nx; ++i) {
+        const double e = std::fabs(val(S.p[q].at(i, j) - init[q][(size_t)j * gr.nx + i]));
+        l1 += e;
+        li = std::max(li, e);
+      }
+    out[2 * q] = l1 / nn;
+    out[2 * q + 1] = li;
+  }
+  *steps = n;
+  return 0;
+}
+}  // namespace orc
+
+// precision: 0 single, 1 double, 2 double-double. out: L1, Linf of h, then of the discharge(s).
+extern "C" int orc_lake_run(const Grid* g, const Params* p, const double* const* st, const double* const* stat,
+                            double t_end, int precision, double* out, int* steps) {
+  if (check_grid(g) || !(t_end > 0.0) || !out || !steps) return -1;
+  if (g->dim == 1) {
+    if (precision == 0) return orc::lake_run1d<orc::F32>(*g, *p, st, stat, t_end, out, steps);
+    if (precision == 1) return orc::lake_run1d<double>(*g, *p, st, stat, t_end, out, steps);
+    if (precision == 2) return orc::lake_run1d<orc::DD>(*g, *p, st, stat, t_end, out, steps);
+  } else {
+    if (precision == 0) return orc::lake_run2d<orc::F32>(*g, *p, st, stat, t_end, out, steps);
+    if (precision == 1) return orc::lake_run2d<double>(*g, *p, st, stat, t_end, out, steps);
+    if (precision == 2) return orc::lake_run2d<orc::DD>(*g, *p, st, stat, t_end, out, steps);
+  }
+  return -1;
 }

@@ -1,6 +1,8 @@
 """Scheme-level pins of the CPU oracle: what the paper and the mathematics fix.
 
-  * lake at rest preserved to round-off (Prop. in Sec. 2.1 and Sec. 3; Tables 1-3 double rows)
+  * lake at rest preserved to round-off (Prop. in Sec. 2.1 and Sec. 3; Tables 1-3 double rows), and in
+    single and double-double precision the residual follows the unit round-off (Tables 1-3 single and
+    quadruple rows)
   * the limiter returns V^mod = 0 exactly at rest and changes smooth data by O(dx^4) (end of Sec. 2.2)
   * fifth-order truncation of the semi-discrete operator and fifth-order convergence of full runs
     (Ex. 4.1 and 4.6)
@@ -62,6 +64,61 @@ def test_lake_at_rest_2d_ex47(orc):
     assert np.abs(out[0] - 1.0).max() < max(100 * ref["h_Linf"], 1e-13)
     assert np.abs(out[1]).max() < max(100 * ref["hu_Linf"], 1e-13)
     assert np.abs(out[2]).max() < max(100 * ref["hv_Linf"], 1e-13)
+
+
+# unit round-off of each precision (double-double: about 106 significant bits); the paper's quadruple
+# rows are IEEE binary128 (113 bits)
+UNIT = {"single": 2.0 ** -24, "double": 2.0 ** -53, "double-double": 2.0 ** -106}
+U_QUAD = 2.0 ** -113
+
+
+@pytest.mark.parametrize("step,table", [(False, "table1_ex42_smooth"), (True, "table2_ex42_step")])
+def test_lake_at_rest_1d_three_precisions(orc, step, table):
+    """Ex. 4.2 (N=200, t=0.5) in single, double and double-double precision: the residual of h and hu is
+    a round-off effect, so residual / (unit round-off x 10) is of the same size in every precision (the
+    well-balance is exact), and each lies within the paper's row for that precision scaled to our
+    unit round-off."""
+    s = S.ex42(200, step=step)
+    g, p = grid_of(orc, s), orc.make_params()
+    st, stat = state_of(orc, s)
+    scaled = {}
+    for prec, u in UNIT.items():
+        out, n = orc.lake_run(g, p, st, stat, 0.5, prec)
+        assert n == 166
+        h_l1, h_li, m_l1, m_li = out
+        assert 0.0 < h_li and 0.0 < m_li  # the run did round, at every precision
+        scaled[prec] = h_li / (10.0 * u)
+        assert scaled[prec] < 3000.0 and m_li / (10.0 * u) < 3000.0, (prec, out)
+    # the same round-off multiple in each precision, within a factor of ten
+    assert max(scaled.values()) / min(scaled.values()) < 10.0, scaled
+    # against the paper's rows (order of magnitude)
+    sgl, quad = GOLD[table + "_single"], GOLD[table + "_quadruple"]
+    out, _ = orc.lake_run(g, p, st, stat, 0.5, "single")
+    assert sgl["h_L1"] / 10 < out[0] < 10 * sgl["h_L1"] and sgl["hu_L1"] / 10 < out[2] < 10 * sgl["hu_L1"]
+    out, _ = orc.lake_run(g, p, st, stat, 0.5, "double-double")
+    at_quad = out * (U_QUAD / UNIT["double-double"])
+    assert quad["h_L1"] / 30 < at_quad[0] < 30 * quad["h_L1"]
+    assert quad["hu_L1"] / 30 < at_quad[2] < 30 * quad["hu_L1"]
+
+
+def test_lake_at_rest_2d_ex47_three_precisions(orc):
+    """Ex. 4.7 (50x50 instead of the paper's 200x200 to keep the double-double run short, t=0.1) in three
+    precisions: the residual follows the unit round-off, and is within two decades of Table 3's rows
+    for single precision and (scaled to binary128) for quadruple precision."""
+    s = S.ex47(50)
+    g, p = grid_of(orc, s), orc.make_params()
+    st, stat = state_of(orc, s)
+    res = {}
+    for prec, u in UNIT.items():
+        out, n = orc.lake_run(g, p, st, stat, 0.1, prec)
+        res[prec] = out
+        assert out[1] < 3000.0 * u and max(out[3], out[5]) < 3000.0 * u, (prec, out)
+    assert max(res[k][1] / UNIT[k] for k in UNIT) / min(res[k][1] / UNIT[k] for k in UNIT) < 10.0
+    sgl, quad = GOLD["table3_ex47_single"], GOLD["table3_ex47_quadruple"]
+    assert sgl["h_L1"] / 100 < res["single"][0] < 100 * sgl["h_L1"]
+    at_quad = res["double-double"] * (U_QUAD / UNIT["double-double"])
+    assert quad["h_L1"] / 100 < at_quad[0] < 100 * quad["h_L1"]
+    assert quad["hu_L1"] / 100 < at_quad[2] < 100 * quad["hu_L1"]
 
 
 def test_lake_at_rest_2d_reflective_bumps(orc):
