@@ -18,8 +18,10 @@
  *   - The library owns every device buffer it allocates (hw_create) and frees them (hw_destroy).
  *     Caller arrays are only read (inputs) or written (outputs) during the call, never retained.
  *   - One solver is bound to one CUDA stream; a solver is not thread-safe.
- *   - Node layout: periodic directions place nodes at x0 + i dx, reflective directions at cell
- *     centres x0 + (i + 1/2) dx with walls at x0 and x1; dx = (x1 - x0) / nx.
+ *   - Node layout: periodic directions place nodes at x0 + i dx, reflective and transmissive
+ *     directions at cell centres x0 + (i + 1/2) dx with the boundaries at x0 and x1; dx = (x1 - x0) / nx.
+ *     Transmissive boundaries (the paper's Ex. 4.4-4.5 name none; this reading extrapolates at order
+ *     zero): each ghost node copies the nearest boundary node, values and derivatives alike.
  */
 #ifndef HWSWE_H
 #define HWSWE_H
@@ -39,6 +41,7 @@ extern "C" {
 
 #define HW_BC_PERIODIC 0
 #define HW_BC_REFLECTIVE 1
+#define HW_BC_OUTFLOW 2 /* transmissive: each ghost node copies the nearest boundary node (all variables) */
 
 #define HW_HOST 0
 #define HW_DEVICE 1

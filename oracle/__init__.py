@@ -33,6 +33,7 @@ _lib = None
 
 BC_PERIODIC = 0
 BC_REFLECTIVE = 1
+BC_OUTFLOW = 2  # transmissive: ghosts copy the boundary node
 
 
 class Grid(C.Structure):
@@ -131,11 +132,11 @@ def make_params(g=9.812, cfl=0.6, eps_w=1e-6, eps_lim=None, char_decomp=1, limit
 def node_coords(grid):
     """Node positions: periodic x_i = x0 + i dx; reflective cell-centred x_i = x0 + (i+1/2) dx."""
     dx = (grid.x1 - grid.x0) / grid.nx
-    x = grid.x0 + (np.arange(grid.nx) + (0.5 if grid.bc_x == BC_REFLECTIVE else 0.0)) * dx
+    x = grid.x0 + (np.arange(grid.nx) + (0.0 if grid.bc_x == BC_PERIODIC else 0.5)) * dx
     if grid.dim == 1:
         return x
     dy = (grid.y1 - grid.y0) / grid.ny
-    y = grid.y0 + (np.arange(grid.ny) + (0.5 if grid.bc_y == BC_REFLECTIVE else 0.0)) * dy
+    y = grid.y0 + (np.arange(grid.ny) + (0.0 if grid.bc_y == BC_PERIODIC else 0.5)) * dy
     return x, y
 
 

@@ -186,7 +186,7 @@ template <class T> inline T maxv(T a, T b) { return (b > a) ? b : a; }
 // Problem description
 // ---------------------------------------------------------------------------------------------
 
-enum { BC_PERIODIC = 0, BC_REFLECTIVE = 1 };
+enum { BC_PERIODIC = 0, BC_REFLECTIVE = 1, BC_OUTFLOW = 2 };
 
 struct Grid {
   int dim, nx, ny;
@@ -425,7 +425,8 @@ struct Plane {
   const T& at(int i, int j) const { return a[(size_t)(j + pady) * (nx + 2 * padx) + (i + padx)]; }
 };
 
-// Fill ghosts: periodic wrap, or mirror about the wall faces with parity +1 (even) / -1 (odd).
+// Fill ghosts: periodic wrap; mirror about the wall faces with parity +1 (even) / -1 (odd); or, for
+// transmissive boundaries, a copy of the boundary node (zero-order extrapolation of every variable).
 template <class T>
 void fill_ghosts(Plane<T>& p, int bc_x, int bc_y, double par_x, double par_y) {
   for (int j = 0; j < p.ny; ++j)
@@ -433,6 +434,9 @@ void fill_ghosts(Plane<T>& p, int bc_x, int bc_y, double par_x, double par_y) {
       if (bc_x == BC_PERIODIC) {
         p.at(-1 - k, j) = p.at(p.nx - 1 - k, j);
         p.at(p.nx + k, j) = p.at(k, j);
+      } else if (bc_x == BC_OUTFLOW) {
+        p.at(-1 - k, j) = p.at(0, j);
+        p.at(p.nx + k, j) = p.at(p.nx - 1, j);
       } else {
         p.at(-1 - k, j) = par_x * p.at(k, j);
         p.at(p.nx + k, j) = par_x * p.at(p.nx - 1 - k, j);
@@ -443,6 +447,9 @@ void fill_ghosts(Plane<T>& p, int bc_x, int bc_y, double par_x, double par_y) {
       if (bc_y == BC_PERIODIC) {
         p.at(i, -1 - k) = p.at(i, p.ny - 1 - k);
         p.at(i, p.ny + k) = p.at(i, k);
+      } else if (bc_y == BC_OUTFLOW) {
+        p.at(i, -1 - k) = p.at(i, 0);
+        p.at(i, p.ny + k) = p.at(i, p.ny - 1);
       } else {
         p.at(i, -1 - k) = par_y * p.at(i, k);
         p.at(i, p.ny + k) = par_y * p.at(i, p.ny - 1 - k);
@@ -942,7 +949,7 @@ int check_grid(const Grid* g) {
   if (!g || g->nx < 1 || g->ny < 1) return -1;
   if (g->dim == 1 && g->ny != 1) return -1;
   if (g->dim != 1 && g->dim != 2) return -1;
-  if (g->bc_x < 0 || g->bc_x > 1 || g->bc_y < 0 || g->bc_y > 1) return -1;
+  if (g->bc_x < 0 || g->bc_x > 2 || g->bc_y < 0 || g->bc_y > 2) return -1;
   if (g->nx < 2 || (g->dim == 2 && g->ny < 2)) return -1;  // reflective/periodic halo of 2 needs >= 2 nodes
   return 0;
 }

@@ -17,7 +17,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 __all__ = [
-    "HW_OK", "HW_BC_PERIODIC", "HW_BC_REFLECTIVE", "HW_HOST", "HW_DEVICE", "HW_LAYOUT_PHYSICAL",
+    "HW_OK", "HW_BC_PERIODIC", "HW_BC_REFLECTIVE", "HW_BC_OUTFLOW", "HW_HOST", "HW_DEVICE", "HW_LAYOUT_PHYSICAL",
     "HW_LAYOUT_EQUILIBRIUM", "HwError", "hw_grid", "hw_params", "lib", "make_grid", "make_params",
     "hw_create", "hw_destroy", "hw_init", "hw_rhs", "hw_alpha", "hw_cfl_dt", "hw_rk3_step", "hw_rk3_stage",
     "hw_advance", "hw_get_state", "hw_set_state", "hw_get_base", "hw_sync", "hw_version", "Solver",
@@ -31,6 +31,7 @@ HW_ERR = {-1: "HW_ERR_ARG", -2: "HW_ERR_DEPTH", -3: "HW_ERR_NONFINITE", -4: "HW_
           -6: "HW_ERR_STATE", -7: "HW_ERR_NOMEM"}
 HW_BC_PERIODIC = 0
 HW_BC_REFLECTIVE = 1
+HW_BC_OUTFLOW = 2
 HW_HOST = 0
 HW_DEVICE = 1
 HW_LAYOUT_PHYSICAL = 0

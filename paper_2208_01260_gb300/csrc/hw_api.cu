@@ -120,7 +120,7 @@ int hw_create(const hw_grid* grid, const hw_params* params, void* cuda_stream, h
   if (grid->dim != 1 && grid->dim != 2) return fail(HW_ERR_ARG, "hw_create: dim must be 1 or 2");
   if (grid->nx < 2 || (grid->dim == 2 && grid->ny < 2) || (grid->dim == 1 && grid->ny != 1))
     return fail(HW_ERR_ARG, "hw_create: need nx >= 2 (and ny >= 2 in 2D, ny == 1 in 1D)");
-  if (grid->bc_x < 0 || grid->bc_x > 1 || grid->bc_y < 0 || grid->bc_y > 1)
+  if (grid->bc_x < 0 || grid->bc_x > 2 || grid->bc_y < 0 || grid->bc_y > 2)
     return fail(HW_ERR_ARG, "hw_create: bad boundary condition");
   if (!(grid->x1 > grid->x0) || (grid->dim == 2 && !(grid->y1 > grid->y0)))
     return fail(HW_ERR_ARG, "hw_create: empty domain");

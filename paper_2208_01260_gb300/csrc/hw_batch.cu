@@ -418,7 +418,7 @@ int hw_batch_create(int n, const hw_grid* grids, const hw_params* params, void* 
   b->inited.assign(n, false);
   for (int i = 0; i < n; ++i) {
     const hw_grid& g = grids[i];
-    if (g.dim != 2 || g.nx < 2 || g.ny < 2 || g.bc_x < 0 || g.bc_x > 1 || g.bc_y < 0 || g.bc_y > 1 ||
+    if (g.dim != 2 || g.nx < 2 || g.ny < 2 || g.bc_x < 0 || g.bc_x > 2 || g.bc_y < 0 || g.bc_y > 2 ||
         !(g.x1 > g.x0) || !(g.y1 > g.y0) || (size_t)g.nx * g.ny > ((size_t)1 << 30)) {
       delete b;
       return bfail(HW_ERR_ARG, "hw_batch_create: every grid must be 2D with nx, ny >= 2 and a valid domain");

@@ -22,7 +22,7 @@
 
 namespace hw {
 
-enum { BC_PERIODIC = 0, BC_REFLECTIVE = 1 };
+enum { BC_PERIODIC = 0, BC_REFLECTIVE = 1, BC_OUTFLOW = 2 };
 
 // State planes: 0 eta, 1 m, 2 w, 3 H1', 4 M1', 5 W1', 6 H2', 7 M2', 8 W2' (2D);
 //               0 eta, 1 m, 2 H', 3 M' (1D).
@@ -38,16 +38,19 @@ __host__ __device__ constexpr double par_y2d(int q) {
 // 1D: eta +, m -, H' -, M' +, b +, dx b_x -.
 __host__ __device__ constexpr double par_1d(int q) { return (q == 1 || q == 2 || q == 5) ? -1.0 : 1.0; }
 
-// Map a node index that may lie up to n outside [0, n) onto the grid. flip = reflected.
+// Map a node index that may lie up to n outside [0, n) onto the grid. flip = reflected (the caller
+// applies the parity table); a transmissive boundary copies the boundary node.
 __device__ __forceinline__ int map_index(int i, int n, int bc, bool& flip) {
   flip = false;
   if (i < 0) {
     if (bc == BC_PERIODIC) return i + n;
+    if (bc == BC_OUTFLOW) return 0;
     flip = true;
     return -1 - i;
   }
   if (i >= n) {
     if (bc == BC_PERIODIC) return i - n;
+    if (bc == BC_OUTFLOW) return n - 1;
     flip = true;
     return 2 * n - 1 - i;
   }

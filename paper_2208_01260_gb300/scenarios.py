@@ -29,6 +29,7 @@ import numpy as np
 
 PERIODIC = 0
 REFLECTIVE = 1
+OUTFLOW = 2
 SEED_BASE = 2208012600
 
 
@@ -64,7 +65,7 @@ class Scenario:
 
 def axis(n: int, a: float, b: float, bc: int) -> np.ndarray:
     d = (b - a) / n
-    off = 0.5 if bc == REFLECTIVE else 0.0
+    off = 0.0 if bc == PERIODIC else 0.5
     return a + (np.arange(n, dtype=np.float64) + off) * d
 
 
@@ -176,6 +177,45 @@ def ex42(n: int = 200, step: bool = False) -> Scenario:
                     [-bx, np.zeros(n), bx], name="ex42" + ("step" if step else "smooth"))
 
 
+def ex43(n: int = 200, eps: float = 0.2, bc: int = OUTFLOW) -> Scenario:
+    """Ex. 4.3 perturbed lake at rest on [0,2]: b = 0.25 (cos(10 pi (x-1.5)) + 1) on [1.4,1.6] (eq. B-5),
+    h = 1 - b (+ eps on [1.1,1.2]), u = 0, to t = 0.2; eps = 0.2 or 1e-3 (the latter with epsilon 1e-10
+    in the weights). The waves stay inside the domain until t = 0.2, so the boundary does not act."""
+    x = axis(n, 0.0, 2.0, bc)
+    inb = (x >= 1.4) & (x <= 1.6)
+    b = np.where(inb, 0.25 * (np.cos(10.0 * math.pi * (x - 1.5)) + 1.0), 0.0)
+    bx = np.where(inb, -2.5 * math.pi * np.sin(10.0 * math.pi * (x - 1.5)), 0.0)
+    h = 1.0 - b + np.where((x >= 1.1) & (x <= 1.2), eps, 0.0)
+    return Scenario(1, n, 1, 0.0, 2.0, 0.0, 1.0, bc, PERIODIC, h, np.zeros(n), b, [-bx, np.zeros(n), bx],
+                    eps_w=1e-10 if eps < 0.01 else 1e-6, name="ex43_%g" % eps, meta=dict(t_end=0.2))
+
+
+def ex44(n: int = 200, bc: int = OUTFLOW) -> Scenario:
+    """Ex. 4.4 rarefaction and shocks over the wavy bottom b = 0.3 cos^30(pi/2 (x-1)) on [0,2] (eq. B-3),
+    domain [-10,10]: h = 2 - b, u = 1 for x <= 1; h = 0.35 - b, u = 0 beyond; to t = 1."""
+    x = axis(n, -10.0, 10.0, bc)
+    inb = (x >= 0.0) & (x <= 2.0)
+    c = np.cos(0.5 * math.pi * (x - 1.0))
+    b = np.where(inb, 0.3 * c ** 30, 0.0)
+    bx = np.where(inb, -0.3 * 30.0 * c ** 29 * np.sin(0.5 * math.pi * (x - 1.0)) * 0.5 * math.pi, 0.0)
+    left = x <= 1.0
+    h = np.where(left, 2.0, 0.35) - b
+    u = np.where(left, 1.0, 0.0)
+    return Scenario(1, n, 1, -10.0, 10.0, 0.0, 1.0, bc, PERIODIC, h, h * u, b, [-bx, -bx * u, bx],
+                    name="ex44", meta=dict(t_end=1.0))
+
+
+def ex45(n: int = 200, bc: int = OUTFLOW) -> Scenario:
+    """Ex. 4.5 dam break over a rectangular bump on (0,1500): b = 8 for |x - 750| <= 1500/8, h = 20 - b
+    left of 750 and 15 - b right of it, u = 0; to t = 15 and t = 60. All derivatives are zero."""
+    x = axis(n, 0.0, 1500.0, bc)
+    b = np.where(np.abs(x - 750.0) <= 187.5, 8.0, 0.0)
+    h = np.where(x <= 750.0, 20.0, 15.0) - b
+    z = np.zeros(n)
+    return Scenario(1, n, 1, 0.0, 1500.0, 0.0, 1.0, bc, PERIODIC, h, z.copy(), b, [z.copy(), z.copy(), z.copy()],
+                    name="ex45", meta=dict(t_end=(15.0, 60.0)))
+
+
 # ------------------------------------------------------------------------------------------------
 # 2D workloads
 # ------------------------------------------------------------------------------------------------
@@ -282,6 +322,22 @@ def ex48(nx: int = 200, ny: int = 100, bc=REFLECTIVE) -> Scenario:
     eta = 1.0 + np.where((X >= 0.05) & (X <= 0.15), 0.01, 0.0)
     z = np.zeros_like(X)
     return _still2d(X, Y, b, bx, by, eta, z, z, bc, bc, (0.0, 2.0, 0.0, 1.0), "ex48")
+
+
+def ex49(n: int = 200, bc: int = OUTFLOW) -> Scenario:
+    """Ex. 4.9 circular dam break on [0,2]^2: b = (cos(2 pi (x-0.5)) + 1)(cos(2 pi y) + 1) / 8 inside the
+    circle of radius 0.5 about (1.5, 1) (zero outside), h = 1.1 - b inside the circle of radius 0.1
+    about (1.25, 1) and 0.6 - b elsewhere, u = v = 0; to t = 0.15 (the waves stay inside the domain)."""
+    x = axis(n, 0.0, 2.0, bc)
+    X, Y = np.meshgrid(x, x)
+    inb = np.hypot(X - 1.5, Y - 1.0) <= 0.5
+    cx, cy = np.cos(2.0 * math.pi * (X - 0.5)) + 1.0, np.cos(2.0 * math.pi * Y) + 1.0
+    b = np.where(inb, cx * cy / 8.0, 0.0)
+    bx = np.where(inb, -2.0 * math.pi * np.sin(2.0 * math.pi * (X - 0.5)) * cy / 8.0, 0.0)
+    by = np.where(inb, -2.0 * math.pi * np.sin(2.0 * math.pi * Y) * cx / 8.0, 0.0)
+    eta = np.where(np.hypot(X - 1.25, Y - 1.0) <= 0.1, 1.1, 0.6)
+    z = np.zeros_like(X)
+    return _still2d(X, Y, b, bx, by, eta, z, z, bc, bc, (0.0, 2.0, 0.0, 2.0), "ex49", meta=dict(t_end=0.15))
 
 
 def adjoint_case(n: int = 512, seed: int = SEED_BASE + 5, hump_seed: int = 0) -> Scenario:
