@@ -60,10 +60,17 @@ typedef struct {
 /* Parameters (Sec. 2.1 eq. GHYZZ: eps = 1e-6, 1e-10 for tiny perturbations per Ex. 4.3; Sec. 4: CFL
  * 0.6, g = 9.812). eps_lim is the epsilon of the limiter weights (Sec. 2.2). char_decomp = 1 projects
  * on characteristic fields (Sec. 2.1); limiter = 1 applies the HWENO limiter (Sec. 2.2);
- * linear_weights = 1 replaces the nonlinear weights by the linear ones (accuracy tests only). */
+ * linear_weights = 1 replaces the nonlinear weights by the linear ones (accuracy tests only).
+ * precision: HW_FP64 (the scheme) or HW_FP32, the single-precision runs of Sec. 4 (Tables 1-3): the
+ * state, the interface values and the stage arithmetic in float, 2D single-grid solvers only (not the
+ * batched form, the adjoint or the 1D scheme). The initialisation, the b-only source terms, alpha's
+ * reduction keys, dt and time stay double, and every call still takes and returns double planes. */
+#define HW_FP64 0
+#define HW_FP32 1
 typedef struct {
   double g, cfl, eps_w, eps_lim;
   int char_decomp, limiter, linear_weights;
+  int precision;
 } hw_params;
 
 typedef struct hw_solver hw_solver;

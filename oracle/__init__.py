@@ -78,8 +78,10 @@ def lib():
             ("orc_pointwise2d", [C.c_double, dp, dp], None),
             ("orc_alpha2d", [gp, prp, pp, pp, dp], C.c_int),
             ("orc_rhs2d", [gp, prp, pp, pp, pp, dp], C.c_int),
+            ("orc_rhs2d_f32", [gp, prp, pp, pp, pp, dp], C.c_int),
             ("orc_limiter2d", [gp, prp, pp, pp, pp], C.c_int),
             ("orc_stage2d", [gp, prp, C.c_int, C.c_double, pp, pp, pp, pp, dp], C.c_int),
+            ("orc_stage2d_f32", [gp, prp, C.c_int, C.c_double, pp, pp, pp, pp, dp], C.c_int),
             ("orc_stage2d_points", [gp, prp, C.c_int, C.c_double, pp, pp, dp, C.c_int, ip, ip, dp, dp, dp],
              C.c_int),
             ("orc_rk3_step2d", [gp, prp, C.c_double, pp, pp], C.c_int),
@@ -221,14 +223,16 @@ def alpha2d(grid, params, st, stat):
     return out
 
 
-def rhs2d(grid, params, st, stat):
+def rhs2d(grid, params, st, stat, single=False):
+    """Right-hand side (9 planes) and alpha; single=True computes every operation in float."""
     shape = (grid.ny, grid.nx)
     S, a = _ptrs(st)
     T, b = _ptrs(stat)
     outs = [np.zeros(shape) for _ in range(9)]
     O, o = _ptrs(outs)
     al = np.zeros(2)
-    _check(lib().orc_rhs2d(C.byref(grid), C.byref(params), S, T, O, _d(al)), "orc_rhs2d")
+    fn = lib().orc_rhs2d_f32 if single else lib().orc_rhs2d
+    _check(fn(C.byref(grid), C.byref(params), S, T, O, _d(al)), "orc_rhs2d")
     return o, al
 
 
@@ -242,8 +246,9 @@ def limiter2d(grid, params, st, stat):
     return o
 
 
-def stage2d(grid, params, k, dt, st, stat, base=None):
-    """One SSP-RK3 stage. Returns (out planes, base planes, alpha). base is produced at k == 1."""
+def stage2d(grid, params, k, dt, st, stat, base=None, single=False):
+    """One SSP-RK3 stage. Returns (out planes, base planes, alpha). base is produced at k == 1.
+    single=True computes every operation in float (inputs rounded to float, outputs widened)."""
     shape = (grid.ny, grid.nx)
     S, a = _ptrs(st)
     T, b = _ptrs(stat)
@@ -252,7 +257,8 @@ def stage2d(grid, params, k, dt, st, stat, base=None):
     B, bb = _ptrs([np.array(x, dtype=np.float64, copy=True) for x in base])
     O, o = _ptrs([np.zeros(shape) for _ in range(9)])
     al = np.zeros(2)
-    _check(lib().orc_stage2d(C.byref(grid), C.byref(params), k, dt, S, T, B, O, _d(al)), "orc_stage2d")
+    fn = lib().orc_stage2d_f32 if single else lib().orc_stage2d
+    _check(fn(C.byref(grid), C.byref(params), k, dt, S, T, B, O, _d(al)), "orc_stage2d")
     return o, bb, al
 
 

@@ -955,6 +955,40 @@ int check_grid(const Grid* g) {
 }
 }  // namespace
 
+// One RHS / one stage of the 2D scheme in the scalar type T, from and to double planes.
+template <class T>
+int rhs2d_as(const Grid* g, const Params* p, const double* const* st, const double* const* stat, double* const* out,
+             double* a2) {
+  if (check_grid(g) || g->dim != 2) return -1;
+  orc::State2D<T> S;
+  orc::load_state2d(*g, st, stat, S);
+  T ax, ay;
+  orc::alpha2d(*g, *p, S, ax, ay);
+  std::vector<T> R[9];
+  orc::rhs2d(*g, *p, S, ax, ay, R);
+  to_ptrs(R, 9, out);
+  if (a2) { a2[0] = orc::val(ax); a2[1] = orc::val(ay); }
+  return 0;
+}
+template <class T>
+int stage2d_as(const Grid* g, const Params* p, int k, double dt, const double* const* st, const double* const* stat,
+               double* const* base, double* const* out, double* a2) {
+  if (check_grid(g) || g->dim != 2 || k < 1 || k > 3) return -1;
+  const size_t n = (size_t)g->nx * g->ny;
+  orc::State2D<T> S;
+  orc::load_state2d(*g, st, stat, S);
+  std::vector<T> B[9], O[9];
+  if (k > 1)
+    for (int q = 0; q < 9; ++q)
+      for (size_t o = 0; o < n; ++o) B[q].push_back(T(base[q][o]));
+  T al[2];
+  orc::stage2d(*g, *p, k, dt, S, B, O, al);
+  if (k == 1) to_ptrs(B, 9, base);
+  to_ptrs(O, 9, out);
+  if (a2) { a2[0] = orc::val(al[0]); a2[1] = orc::val(al[1]); }
+  return 0;
+}
+
 extern "C" {
 
 // ---- scalar pieces (pins) ----
@@ -1002,16 +1036,12 @@ int orc_alpha2d(const Grid* g, const Params* p, const double* const* st, const d
 }
 int orc_rhs2d(const Grid* g, const Params* p, const double* const* st, const double* const* stat, double* const* out,
               double* a2) {
-  if (check_grid(g) || g->dim != 2) return -1;
-  orc::State2D<double> S;
-  orc::load_state2d(*g, st, stat, S);
-  double ax, ay;
-  orc::alpha2d(*g, *p, S, ax, ay);
-  std::vector<double> R[9];
-  orc::rhs2d(*g, *p, S, ax, ay, R);
-  to_ptrs(R, 9, out);
-  if (a2) { a2[0] = ax; a2[1] = ay; }
-  return 0;
+  return rhs2d_as<double>(g, p, st, stat, out, a2);
+}
+// The same in single precision (every operation in float; inputs rounded to float, outputs widened).
+int orc_rhs2d_f32(const Grid* g, const Params* p, const double* const* st, const double* const* stat,
+                  double* const* out, double* a2) {
+  return rhs2d_as<orc::F32>(g, p, st, stat, out, a2);
 }
 int orc_limiter2d(const Grid* g, const Params* p, const double* const* st, const double* const* stat,
                   double* const* mod) {
@@ -1026,19 +1056,11 @@ int orc_limiter2d(const Grid* g, const Params* p, const double* const* st, const
 // One RK stage. base[9] is written for k == 1 and read for k = 2, 3.
 int orc_stage2d(const Grid* g, const Params* p, int k, double dt, const double* const* st,
                 const double* const* stat, double* const* base, double* const* out, double* a2) {
-  if (check_grid(g) || g->dim != 2 || k < 1 || k > 3) return -1;
-  const size_t n = (size_t)g->nx * g->ny;
-  orc::State2D<double> S;
-  orc::load_state2d(*g, st, stat, S);
-  std::vector<double> B[9], O[9];
-  if (k > 1)
-    for (int q = 0; q < 9; ++q) B[q].assign(base[q], base[q] + n);
-  double al[2];
-  orc::stage2d(*g, *p, k, dt, S, B, O, al);
-  if (k == 1) to_ptrs(B, 9, base);
-  to_ptrs(O, 9, out);
-  if (a2) { a2[0] = al[0]; a2[1] = al[1]; }
-  return 0;
+  return stage2d_as<double>(g, p, k, dt, st, stat, base, out, a2);
+}
+int orc_stage2d_f32(const Grid* g, const Params* p, int k, double dt, const double* const* st,
+                    const double* const* stat, double* const* base, double* const* out, double* a2) {
+  return stage2d_as<orc::F32>(g, p, k, dt, st, stat, base, out, a2);
 }
 // Stage output at selected nodes only (sampled parity at sizes the full oracle grid would be slow
 // on). alpha2 gives the stage's alpha (computed over the full grid by orc_alpha2d); base holds the

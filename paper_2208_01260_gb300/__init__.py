@@ -56,7 +56,8 @@ class hw_grid(C.Structure):
 
 class hw_params(C.Structure):
     _fields_ = [("g", C.c_double), ("cfl", C.c_double), ("eps_w", C.c_double), ("eps_lim", C.c_double),
-                ("char_decomp", C.c_int), ("limiter", C.c_int), ("linear_weights", C.c_int)]
+                ("char_decomp", C.c_int), ("limiter", C.c_int), ("linear_weights", C.c_int),
+                ("precision", C.c_int)]
 
 
 def lib():
@@ -106,8 +107,14 @@ def make_grid(nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=HW_BC_PERIODIC, bc_
     return hw_grid(dim, nx, ny, x0, x1, y0, y1, bc_x, bc_y)
 
 
-def make_params(g=9.812, cfl=0.6, eps_w=1e-6, eps_lim=None, char_decomp=1, limiter=1, linear_weights=0):
-    return hw_params(g, cfl, eps_w, eps_w if eps_lim is None else eps_lim, char_decomp, limiter, linear_weights)
+HW_FP64 = 0
+HW_FP32 = 1
+
+
+def make_params(g=9.812, cfl=0.6, eps_w=1e-6, eps_lim=None, char_decomp=1, limiter=1, linear_weights=0,
+                precision=HW_FP64):
+    return hw_params(g, cfl, eps_w, eps_w if eps_lim is None else eps_lim, char_decomp, limiter, linear_weights,
+                     precision)
 
 
 # ------------------------------------------------------------------------------------------------

@@ -63,6 +63,13 @@ struct hw_solver {
   unsigned long long* nsteps = nullptr;  // steps that advanced (dt > 0)
   hw::Dev2D d2{};
   hw::Dev1D d1{};
+  // single precision (params.precision == HW_FP32, 2D): the state, base and interface planes in float;
+  // the double planes above then serve the initialisation and the exchange with the caller
+  bool fp32 = false;
+  float* FA[9] = {};
+  float* FB[9] = {};
+  float* fbase[9] = {};
+  hw::Dev2DT<float> f2{};
   cudaGraphExec_t graph = nullptr;
   double graph_t_end = -1.0;
   // profiling: event pairs recorded around launches, resolved in hw_get_profile
@@ -74,6 +81,8 @@ struct hw_solver {
 
   double** state() { return cur == 0 ? SA : SB; }
   double** other() { return cur == 0 ? SB : SA; }
+  float** fstate() { return cur == 0 ? FA : FB; }
+  float** fother() { return cur == 0 ? FB : FA; }
   bool is2d() const { return grid.dim == 2; }
 };
 
@@ -102,17 +111,35 @@ static int dalloc(hw_solver* s, double** p, size_t count) {
   return HW_OK;
 }
 
+static int falloc(hw_solver* s, float** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(float));
+  if (e != cudaSuccess) return fail(HW_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  s->allocs.push_back(q);
+  *p = (float*)q;
+  return HW_OK;
+}
+
 static void bind_state(hw_solver* s, double** S) {
   for (int q = 0; q < s->nstate; ++q) {
     if (s->is2d()) s->d2.S[q] = S[q];
     else s->d1.S[q] = S[q];
   }
+  if (s->fp32)
+    for (int q = 0; q < 9; ++q) s->f2.S[q] = s->fstate()[q];
+}
+
+// Cast count planes of n values between the double and float buffers of a single-precision solver.
+static void cast_planes(hw_solver* s, void* const* src, void* const* dst, int count, int to_float, size_t n) {
+  hw::Ptr12 a{}, b{};
+  for (int q = 0; q < count; ++q) { a.p[q] = src[q]; b.p[q] = dst[q]; }
+  hw::launch_cast_planes(count, n, a, b, to_float, s->stream);
 }
 
 extern "C" {
 
 const char* hw_last_error(void) { return g_err.c_str(); }
-const char* hw_version(void) { return "hwswe-gb300 0.1 (sm_103a, FP64)"; }
+const char* hw_version(void) { return "hwswe-gb300 0.2 (sm_103a, FP64; FP32 variant)"; }
 
 int hw_create(const hw_grid* grid, const hw_params* params, void* cuda_stream, hw_solver** out) {
   if (!grid || !params || !out) return fail(HW_ERR_ARG, "hw_create: null argument");
@@ -128,6 +155,10 @@ int hw_create(const hw_grid* grid, const hw_params* params, void* cuda_stream, h
     return fail(HW_ERR_ARG, "hw_create: grid too large (more than 2^31 nodes)");
   if (!(params->g > 0) || !(params->eps_w > 0) || !(params->eps_lim > 0) || !(params->cfl > 0))
     return fail(HW_ERR_ARG, "hw_create: g, cfl, eps_w and eps_lim must be positive");
+  if (params->precision != HW_FP64 && params->precision != HW_FP32)
+    return fail(HW_ERR_ARG, "hw_create: precision must be HW_FP64 or HW_FP32");
+  if (params->precision == HW_FP32 && grid->dim != 2)
+    return fail(HW_ERR_ARG, "hw_create: HW_FP32 is available for 2D grids only");
 
   hw_solver* s = new hw_solver();
   s->grid = *grid;
@@ -166,6 +197,21 @@ int hw_create(const hw_grid* grid, const hw_params* params, void* cuda_stream, h
     for (int q = 0; q < 6; ++q) { A(&d.qbx[q], (size_t)(nx + 1) * ny); A(&d.qby[q], (size_t)nx * (ny + 1)); }
     for (int q = 0; q < 2; ++q) { A(&d.sv[q], s->n); A(&d.sq[q], s->n); }
     if (rc == HW_OK && hw::set_kernel_attributes2d() != 0) rc = fail(HW_ERR_CUDA, "hw_create: kernel attributes");
+    if (params->precision == HW_FP32) {
+      s->fp32 = true;
+      hw::Dev2DT<float>& f = s->f2;
+      auto F = [&](float** p, size_t cnt) { if (rc == HW_OK) rc = falloc(s, p, cnt); };
+      for (int q = 0; q < 9; ++q) { F(&s->FA[q], s->n); F(&s->FB[q], s->n); F(&s->fbase[q], s->n); }
+      f.nx = d.nx; f.ny = d.ny; f.bc_x = d.bc_x; f.bc_y = d.bc_y;
+      f.dx = d.dx; f.dy = d.dy; f.inv_dx = d.inv_dx; f.inv_dy = d.inv_dy;
+      f.g = d.g; f.eps_w = d.eps_w; f.eps_lim = d.eps_lim;
+      f.c_bx = d.c_bx; f.c_by = d.c_by; f.c_gx = d.c_gx; f.c_gy = d.c_gy; f.c_mx = d.c_mx; f.c_my = d.c_my;
+      for (int q = 0; q < 3; ++q) F(&f.stat[q], s->n);
+      for (int q = 0; q < 2; ++q) F(&f.bxy[q], s->n);
+      for (int q = 0; q < 12; ++q) { F(&f.X[q], (size_t)(nx + 1) * ny); F(&f.Y[q], (size_t)nx * (ny + 1)); }
+      for (int q = 0; q < 6; ++q) { F(&f.qbx[q], (size_t)(nx + 1) * ny); F(&f.qby[q], (size_t)nx * (ny + 1)); }
+      for (int q = 0; q < 2; ++q) { F(&f.sv[q], s->n); F(&f.sq[q], s->n); }
+    }
   } else {
     hw::Dev1D& d = s->d1;
     d.nx = nx; d.bc = grid->bc_x; d.dx = dx; d.inv_dx = 1.0 / dx;
@@ -242,6 +288,24 @@ int hw_init(hw_solver* s, const double* h, const double* hu, const double* hv, c
     s->cur = 0;
     bind_state(s, s->SA);
     hw::launch_init2d(s->d2, pin, s->status, s->stream);
+    if (s->fp32) {
+      // the state and the b-only terms of the double initialisation, rounded to float
+      const hw::Dev2D& d = s->d2;
+      hw::Dev2DT<float>& f = s->f2;
+      void* src[12];
+      void* dst[12];
+      for (int q = 0; q < 9; ++q) { src[q] = s->SA[q]; dst[q] = s->FA[q]; }
+      for (int q = 0; q < 3; ++q) { src[9 + q] = d.stat[q]; dst[9 + q] = f.stat[q]; }
+      cast_planes(s, src, dst, 12, 1, s->n);
+      for (int q = 0; q < 2; ++q) { src[q] = d.bxy[q]; dst[q] = f.bxy[q]; src[2 + q] = d.sv[q]; dst[2 + q] = f.sv[q];
+                                    src[4 + q] = d.sq[q]; dst[4 + q] = f.sq[q]; }
+      cast_planes(s, src, dst, 6, 1, s->n);
+      for (int q = 0; q < 6; ++q) { src[q] = d.qbx[q]; dst[q] = f.qbx[q]; }
+      cast_planes(s, src, dst, 6, 1, (size_t)(d.nx + 1) * d.ny);
+      for (int q = 0; q < 6; ++q) { src[q] = d.qby[q]; dst[q] = f.qby[q]; }
+      cast_planes(s, src, dst, 6, 1, (size_t)d.nx * (d.ny + 1));
+      bind_state(s, s->SA);
+    }
   } else {
     const double* in[6] = {h, hu, b, deriv[0], deriv[1], deriv[2]};
     hw::PhysIn1D pin;
@@ -261,7 +325,11 @@ int hw_init(hw_solver* s, const double* h, const double* hu, const double* hv, c
 static void enqueue_alpha(hw_solver* s, bool with_dt, double t_end) {
   bind_state(s, s->state());
   timed(s, HW_PROF_ALPHA, [&] {
-    if (s->is2d()) {
+    if (s->fp32) {
+      hw::launch_alpha2d(s->f2, s->amax, s->status, s->stream);
+      hw::launch_finish_alpha2d(s->d2, s->amax, s->alpha, with_dt ? s->dt : nullptr, s->params.cfl,
+                                with_dt ? s->t : nullptr, t_end, s->stream);
+    } else if (s->is2d()) {
       hw::launch_alpha2d(s->d2, s->amax, s->status, s->stream);
       hw::launch_finish_alpha2d(s->d2, s->amax, s->alpha, with_dt ? s->dt : nullptr, s->params.cfl,
                                 with_dt ? s->t : nullptr, t_end, s->stream);
@@ -280,7 +348,15 @@ static void enqueue_stage(hw_solver* s, int k) {
   double** out = s->other();
   bind_state(s, in);
   const bool lin = s->params.linear_weights != 0, chr = s->params.char_decomp != 0;
-  if (s->is2d()) {
+  if (s->fp32) {
+    float** fout = s->fother();
+    timed(s, HW_PROF_SWEEP_X, [&] { hw::launch_sweep_x2d(s->f2, s->alpha, lin, chr, s->stream); });
+    timed(s, HW_PROF_SWEEP_Y, [&] { hw::launch_sweep_y2d(s->f2, s->alpha, lin, chr, s->stream); });
+    hw::StageArgsT<float> sa{};
+    sa.k = k; sa.limiter = s->params.limiter; sa.dt = s->dt;
+    for (int q = 0; q < 9; ++q) { sa.out[q] = fout[q]; sa.base[q] = s->fbase[q]; }
+    timed(s, HW_PROF_NODE, [&] { hw::launch_node2d(s->f2, sa, hw::MODE_STAGE, lin, chr, s->stream); });
+  } else if (s->is2d()) {
     timed(s, HW_PROF_SWEEP_X, [&] { hw::launch_sweep_x2d(s->d2, s->alpha, lin, chr, s->stream); });
     timed(s, HW_PROF_SWEEP_Y, [&] { hw::launch_sweep_y2d(s->d2, s->alpha, lin, chr, s->stream); });
     hw::StageArgs sa{};
@@ -429,7 +505,19 @@ int hw_rhs(hw_solver* s, double* const* out, int ptr_kind) {
   for (int q = 0; q < s->nstate; ++q) dst[q] = ptr_kind == HW_DEVICE ? out[q] : s->staging[q];
   const bool lin = s->params.linear_weights != 0, chr = s->params.char_decomp != 0;
   bind_state(s, s->state());
-  if (s->is2d()) {
+  if (s->fp32) {
+    // float right-hand side into the spare state buffer, then widened into the output planes
+    float** scratch = s->fother();
+    hw::launch_sweep_x2d(s->f2, s->alpha, lin, chr, s->stream);
+    hw::launch_sweep_y2d(s->f2, s->alpha, lin, chr, s->stream);
+    hw::StageArgsT<float> sa{};
+    for (int q = 0; q < 9; ++q) sa.rhs_out[q] = scratch[q];
+    hw::launch_node2d(s->f2, sa, hw::MODE_RHS, lin, chr, s->stream);
+    void* src[9];
+    void* dd[9];
+    for (int q = 0; q < 9; ++q) { src[q] = scratch[q]; dd[q] = dst[q]; }
+    cast_planes(s, src, dd, 9, 0, s->n);
+  } else if (s->is2d()) {
     hw::launch_sweep_x2d(s->d2, s->alpha, lin, chr, s->stream);
     hw::launch_sweep_y2d(s->d2, s->alpha, lin, chr, s->stream);
     hw::StageArgs sa{};
@@ -448,7 +536,10 @@ int hw_rhs(hw_solver* s, double* const* out, int ptr_kind) {
   return ptr_kind == HW_HOST ? read_status(s) : HW_OK;
 }
 
-static int export_planes(hw_solver* s, double** src_state, double* const* out, int layout, int ptr_kind) {
+// src_state: double planes, or (single precision) float planes fsrc widened first into the double
+// buffer SB, which a single-precision solver uses only as scratch.
+static int export_planes(hw_solver* s, double** src_state, double* const* out, int layout, int ptr_kind,
+                         float** fsrc = nullptr) {
   if (!out) return fail(HW_ERR_ARG, "null output");
   if (layout != HW_LAYOUT_PHYSICAL && layout != HW_LAYOUT_EQUILIBRIUM) return fail(HW_ERR_ARG, "bad layout");
   if (ptr_kind != HW_HOST && ptr_kind != HW_DEVICE) return fail(HW_ERR_ARG, "bad ptr_kind");
@@ -456,6 +547,13 @@ static int export_planes(hw_solver* s, double** src_state, double* const* out, i
   for (int q = 0; q < s->nstate; ++q) {
     if (!out[q]) return fail(HW_ERR_ARG, "null output plane");
     dst.p[q] = ptr_kind == HW_DEVICE ? out[q] : s->staging[q];
+  }
+  if (fsrc) {
+    void* a[9];
+    void* b[9];
+    for (int q = 0; q < 9; ++q) { a[q] = fsrc[q]; b[q] = s->SB[q]; }
+    cast_planes(s, a, b, 9, 0, s->n);
+    src_state = s->SB;
   }
   bind_state(s, src_state);
   if (s->is2d()) hw::launch_convert2d(s->d2, src, dst, layout, 0, s->stream);
@@ -473,12 +571,14 @@ static int export_planes(hw_solver* s, double** src_state, double* const* out, i
 int hw_get_state(hw_solver* s, double* const* out, int layout, int ptr_kind) {
   if (!s) return fail(HW_ERR_ARG, "hw_get_state: null solver");
   if (!s->inited) return fail(HW_ERR_STATE, "hw_get_state: call hw_init first");
+  if (s->fp32) return export_planes(s, nullptr, out, layout, ptr_kind, s->fstate());
   return export_planes(s, s->state(), out, layout, ptr_kind);
 }
 
 int hw_get_base(hw_solver* s, double* const* out, int ptr_kind) {
   if (!s) return fail(HW_ERR_ARG, "hw_get_base: null solver");
   if (!s->inited) return fail(HW_ERR_STATE, "hw_get_base: call hw_init first");
+  if (s->fp32) return export_planes(s, nullptr, out, HW_LAYOUT_EQUILIBRIUM, ptr_kind, s->fbase);
   return export_planes(s, s->base, out, HW_LAYOUT_EQUILIBRIUM, ptr_kind);
 }
 
@@ -491,9 +591,17 @@ int hw_set_state(hw_solver* s, const double* const* in, int layout, int ptr_kind
   if (rc) return rc;
   hw::Ptr9 src{}, dst{};
   for (int q = 0; q < s->nstate; ++q) src.p[q] = (double*)dev[q];
-  bind_state(s, s->state());
+  bind_state(s, s->fp32 ? s->SB : s->state());
   if (s->is2d()) hw::launch_convert2d(s->d2, src, dst, layout, 1, s->stream);
   else hw::launch_convert1d(s->d1, src, dst, layout, 1, s->stream);
+  if (s->fp32) {
+    // converted in double into the scratch buffer, then rounded into the float state
+    void* a[9];
+    void* b[9];
+    for (int q = 0; q < 9; ++q) { a[q] = s->SB[q]; b[q] = s->fstate()[q]; }
+    cast_planes(s, a, b, 9, 1, s->n);
+    bind_state(s, s->state());
+  }
   CUDA_OK(cudaGetLastError());
   if (ptr_kind == HW_HOST) CUDA_OK(cudaStreamSynchronize(s->stream));
   return HW_OK;
@@ -505,6 +613,7 @@ namespace hw {
 int solver_view(hw_solver* s, SolverView* v) {
   if (!s) return fail(HW_ERR_ARG, "null solver");
   if (!s->inited) return fail(HW_ERR_STATE, "call hw_init first");
+  if (s->fp32) return fail(HW_ERR_ARG, "the adjoint needs an HW_FP64 solver");
   v->stream = s->stream;
   v->d2 = s->is2d() ? &s->d2 : nullptr;
   v->state = s->state();

@@ -407,6 +407,7 @@ extern "C" {
 int hw_batch_create(int n, const hw_grid* grids, const hw_params* params, void* cuda_stream, hw_batch** out) {
   if (!grids || !params || !out || n < 1) return bfail(HW_ERR_ARG, "hw_batch_create: bad argument");
   *out = nullptr;
+  if (params->precision != HW_FP64) return bfail(HW_ERR_ARG, "hw_batch_create: the batched form is HW_FP64 only");
   if (!(params->g > 0) || !(params->eps_w > 0) || !(params->eps_lim > 0) || !(params->cfl > 0))
     return bfail(HW_ERR_ARG, "hw_batch_create: g, cfl, eps_w and eps_lim must be positive");
   hw_batch* b = new hw_batch();

@@ -18,6 +18,7 @@
 //     Newton step (Householder order 3 for 1/x and for 1/sqrt(x)), accurate to a few ulp.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace hw {
@@ -88,6 +89,11 @@ __device__ __forceinline__ double fast_rsqrt(double x) {
   return fma(r, u, r);
 }
 
+// Single precision (the FP32 variant, memory-bound on GB300, where the FP32 pipe is cheap): the
+// correctly rounded intrinsics.
+__device__ __forceinline__ float fast_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float fast_rsqrt(float x) { return __frsqrt_rn(x); }
+
 // Non-negative double -> ordered 64-bit key (for an exact, order-independent atomicMax).
 __device__ __forceinline__ unsigned long long dkey(double x) {
   return (unsigned long long)__double_as_longlong(x);
@@ -95,6 +101,7 @@ __device__ __forceinline__ unsigned long long dkey(double x) {
 __device__ __forceinline__ double dabs(double x) {
   return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
 }
+__device__ __forceinline__ float dabs(float x) { return fabsf(x); }
 
 // ---------------------------------------------------------------------------------------------
 // One characteristic field, one upwind side, scaled data (Sec. 2.1 Step 1).
@@ -109,45 +116,66 @@ __device__ __forceinline__ double dabs(double x) {
 //   beta1 = p1^2 + 13/3 A1^2 + 781/20 B1^2, beta2 = p1^2 + 13/3 A2^2 + 781/20 B2^2,
 //   beta3 = p1^2 + 13/12 e^2 + 781/80 g3^2.
 // ---------------------------------------------------------------------------------------------
-struct Weights {
+// R is the working precision: double for the scheme, float for the single-precision variant. Constants
+// are written as R(...) so that a float instantiation does no double arithmetic.
+template <class R>
+struct WeightsT {
   // omega_l = n_l * r (n_3 already carries gamma_3 / gamma_1 = 4/3)
-  double n1, n2, n3, r;
+  R n1, n2, n3, r;
 };
+using Weights = WeightsT<double>;
 
-template <bool LINEAR>
-__device__ __forceinline__ double hweno_side(double f0, double f1, double f2, double p0, double p1, double p2,
-                                             double eps, Weights& W) {
-  const double d1 = f0 - f1, d2 = f1 - f2;
-  const double B1 = fma(2.0, d1, p0 + p1);
-  const double A1 = B1 + (d1 + p1);
-  const double B2 = fma(2.0, d2, p1 + p2);
-  const double A2 = B2 + (d2 + p1);
-  const double P = fma(0.5, p1, f1);
-  const double e = fma(-2.0, f1, f0 + f2);
-  const double q1 = fma(1.0 / 6.0, A1, P);
-  const double q2 = fma(-1.0 / 6.0, A2, P);
-  const double q3 = fma(1.0 / 12.0, e, P);
-  if (LINEAR) {
-    W.n1 = 0.3; W.n2 = 0.3; W.n3 = 0.4; W.r = 1.0;
-    return fma(0.3, q1, fma(0.3, q2, 0.4 * q3));
+// Unnormalised weights proportional to w_1/t_1^2, w_2/t_2^2, w_3/t_3^2 (t_l = beta_l + eps). In double the
+// products of the other two squares (one reciprocal); in float, where t^4 can overflow on large jumps,
+// (t_min/t_l)^2, each at most 1.
+template <class R>
+__device__ __forceinline__ void inverse_square_weights(R t1, R t2, R t3, R& n1, R& n2, R& n3) {
+  if constexpr (std::is_same<R, double>::value) {
+    const R s1 = t1 * t1, s2 = t2 * t2, s3 = t3 * t3;
+    n1 = s2 * s3;
+    n2 = s1 * s3;
+    n3 = s1 * s2;
+  } else {
+    const R m = fminf(fminf(t1, t2), t3);
+    const R a1 = m * fast_rcp(t1), a2 = m * fast_rcp(t2), a3 = m * fast_rcp(t3);
+    n1 = a1 * a1;
+    n2 = a2 * a2;
+    n3 = a3 * a3;
   }
-  const double g3 = fma(2.0, p1, f0 - f2);
-  const double pp = p1 * p1;
-  const double b1 = fma((781.0 / 20.0) * B1, B1, fma((13.0 / 3.0) * A1, A1, pp));
-  const double b2 = fma((781.0 / 20.0) * B2, B2, fma((13.0 / 3.0) * A2, A2, pp));
-  const double b3 = fma((781.0 / 80.0) * g3, g3, fma((13.0 / 12.0) * e, e, pp));
-  const double t1 = b1 + eps, t2 = b2 + eps, t3 = b3 + eps;
-  const double s1 = t1 * t1, s2 = t2 * t2, s3 = t3 * t3;
+}
+
+template <bool LINEAR, class R>
+__device__ __forceinline__ R hweno_side(R f0, R f1, R f2, R p0, R p1, R p2, R eps, WeightsT<R>& W) {
+  const R d1 = f0 - f1, d2 = f1 - f2;
+  const R B1 = fma(R(2.0), d1, p0 + p1);
+  const R A1 = B1 + (d1 + p1);
+  const R B2 = fma(R(2.0), d2, p1 + p2);
+  const R A2 = B2 + (d2 + p1);
+  const R P = fma(R(0.5), p1, f1);
+  const R e = fma(R(-2.0), f1, f0 + f2);
+  const R q1 = fma(R(1.0 / 6.0), A1, P);
+  const R q2 = fma(R(-1.0 / 6.0), A2, P);
+  const R q3 = fma(R(1.0 / 12.0), e, P);
+  if (LINEAR) {
+    W.n1 = R(0.3); W.n2 = R(0.3); W.n3 = R(0.4); W.r = R(1.0);
+    return fma(R(0.3), q1, fma(R(0.3), q2, R(0.4) * q3));
+  }
+  const R g3 = fma(R(2.0), p1, f0 - f2);
+  const R pp = p1 * p1;
+  const R b1 = fma(R(781.0 / 20.0) * B1, B1, fma(R(13.0 / 3.0) * A1, A1, pp));
+  const R b2 = fma(R(781.0 / 20.0) * B2, B2, fma(R(13.0 / 3.0) * A2, A2, pp));
+  const R b3 = fma(R(781.0 / 80.0) * g3, g3, fma(R(13.0 / 12.0) * e, e, pp));
+  R n3;
+  inverse_square_weights(b1 + eps, b2 + eps, b3 + eps, W.n1, W.n2, n3);
   // gamma = (3, 3, 4)/10 -> proportional to (1, 1, 4/3)
-  W.n1 = s2 * s3;
-  W.n2 = s1 * s3;
-  W.n3 = (4.0 / 3.0) * (s1 * s2);
+  W.n3 = R(4.0 / 3.0) * n3;
   W.r = fast_rcp(W.n1 + W.n2 + W.n3);
   return fma(W.n1, q1, fma(W.n2, q2, W.n3 * q3)) * W.r;
 }
 
 // The source reconstructed with the same weights (Sec. 2.1 Step 2) from precomputed candidates.
-__device__ __forceinline__ double weighted(const Weights& W, double c1, double c2, double c3) {
+template <class R>
+__device__ __forceinline__ R weighted(const WeightsT<R>& W, R c1, R c2, R c3) {
   return fma(W.n1, c1, fma(W.n2, c2, W.n3 * c3)) * W.r;
 }
 
@@ -156,23 +184,22 @@ __device__ __forceinline__ double weighted(const Weights& W, double c1, double c
 // Returns the scaled dx*nu^mod. p'_1 = 2(m1-m0) - nl, p'_2 = 2(m2-m1) - nr, p'_3 = (m2-m0)/2,
 // beta^L_1 = p'_1^2 + 13/3 (m1-m0-nl)^2, beta^L_2 = p'_2^2 + 13/3 (m2-m1-nr)^2,
 // beta^L_3 = p'_3^2 + 13/12 (m2 - 2 m1 + m0)^2, d = (1,1,2)/4.
-template <bool LINEAR>
-__device__ __forceinline__ double limiter_field(double m0, double m1, double m2, double nl, double nr, double eps) {
-  const double dl = m1 - m0, dr = m2 - m1;
-  const double pl = fma(2.0, dl, -nl);
-  const double pr = fma(2.0, dr, -nr);
-  const double pc2 = dl + dr;  // 2 p'_3
-  if (LINEAR) return fma(0.25, pl + pr, 0.25 * pc2);
-  const double al = dl - nl, ar = dr - nr, ac = dr - dl;
-  const double b1 = fma((13.0 / 3.0) * al, al, pl * pl);
-  const double b2 = fma((13.0 / 3.0) * ar, ar, pr * pr);
-  const double b3 = fma((13.0 / 12.0) * ac, ac, (0.25 * pc2) * pc2);
-  const double t1 = b1 + eps, t2 = b2 + eps, t3 = b3 + eps;
-  const double s1 = t1 * t1, s2 = t2 * t2, s3 = t3 * t3;
-  // d = (1, 1, 2)/4 -> proportional to (1, 1, 2); p'_3 = pc2 / 2 so its term is s1 s2 pc2
-  const double n1 = s2 * s3, n2 = s1 * s3, n3 = s1 * s2;
-  const double den = fma(2.0, n3, n1 + n2);
-  const double num = fma(n1, pl, fma(n2, pr, n3 * pc2));
+template <bool LINEAR, class R>
+__device__ __forceinline__ R limiter_field(R m0, R m1, R m2, R nl, R nr, R eps) {
+  const R dl = m1 - m0, dr = m2 - m1;
+  const R pl = fma(R(2.0), dl, -nl);
+  const R pr = fma(R(2.0), dr, -nr);
+  const R pc2 = dl + dr;  // 2 p'_3
+  if (LINEAR) return fma(R(0.25), pl + pr, R(0.25) * pc2);
+  const R al = dl - nl, ar = dr - nr, ac = dr - dl;
+  const R b1 = fma(R(13.0 / 3.0) * al, al, pl * pl);
+  const R b2 = fma(R(13.0 / 3.0) * ar, ar, pr * pr);
+  const R b3 = fma(R(13.0 / 12.0) * ac, ac, (R(0.25) * pc2) * pc2);
+  // d = (1, 1, 2)/4 -> proportional to (1, 1, 2); p'_3 = pc2 / 2 so its term is n3 pc2
+  R n1, n2, n3;
+  inverse_square_weights(b1 + eps, b2 + eps, b3 + eps, n1, n2, n3);
+  const R den = fma(R(2.0), n3, n1 + n2);
+  const R num = fma(n1, pl, fma(n2, pr, n3 * pc2));
   return num * fast_rcp(den);
 }
 

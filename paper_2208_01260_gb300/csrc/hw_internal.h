@@ -11,34 +11,43 @@ namespace hw {
 enum { MODE_STAGE = 0, MODE_RHS = 1 };
 enum { HW_STATUS_DEPTH = 1, HW_STATUS_NONFINITE = 2, HW_STATUS_TIMEOUT = 4, HW_STATUS_BOUNDS = 8 };
 
-// Everything a 2D kernel needs, passed by value.
-struct Dev2D {
+// Everything a 2D kernel needs, passed by value. R is the precision of the planes (double for the
+// scheme, float for the single-precision variant); grid constants stay double.
+template <class R>
+struct Dev2DT {
   int nx, ny, bc_x, bc_y;
   double dx, dy, inv_dx, inv_dy, g, eps_w, eps_lim;
   // assembly constants: 1/(2dx), 1/(2dy), 1/(24dx), 1/(24dy), 1/(12dx), 1/(12dy)
   double c_bx, c_by, c_gx, c_gy, c_mx, c_my;
-  double* S[9];      // current state (eta, m, w, dx V, dy Q)
-  double* stat[3];   // b, dx b_x, dy b_y
-  double* bxy[2];    // b_x, b_y (physical, for conversions and static terms)
-  double* X[12];     // x-interface values, pitch nx+1
-  double* Y[12];     // y-interface values, pitch nx, ny+1 rows
-  double* qbx[6];    // source candidates at x-interfaces ('+' q1..q3, '-' q1..q3)
-  double* qby[6];
-  double* sv[2];     // static derivative-source terms of the V equations (m, w components)
-  double* sq[2];     // ... of the Q equations
+  R* S[9];      // current state (eta, m, w, dx V, dy Q)
+  R* stat[3];   // b, dx b_x, dy b_y
+  R* bxy[2];    // b_x, b_y (physical, for conversions and static terms)
+  R* X[12];     // x-interface values, pitch nx+1
+  R* Y[12];     // y-interface values, pitch nx, ny+1 rows
+  R* qbx[6];    // source candidates at x-interfaces ('+' q1..q3, '-' q1..q3)
+  R* qby[6];
+  R* sv[2];     // static derivative-source terms of the V equations (m, w components)
+  R* sq[2];     // ... of the Q equations
 };
+using Dev2D = Dev2DT<double>;
 
-struct StageArgs {
+template <class R>
+struct StageArgsT {
   int k;             // RK stage 1..3
   int limiter;
   const double* dt;  // device scalar
-  double* out[9];
-  double* base[9];
-  double* rhs_out[9];
+  R* out[9];
+  R* base[9];
+  R* rhs_out[9];
 };
+using StageArgs = StageArgsT<double>;
 
 struct Ptr9 {
   double* p[9];
+};
+
+struct Ptr12 {
+  void* p[12];  // planes of either precision
 };
 
 struct PhysIn {
@@ -80,6 +89,13 @@ void launch_sweep_y2d(const Dev2D& d, const double* alpha, bool linear, bool chr
 void launch_node2d(const Dev2D& d, const StageArgs& sa, int mode, bool linear, bool chr, cudaStream_t st);
 void launch_init2d(const Dev2D& d, const PhysIn& in, int* status, cudaStream_t st);
 void launch_convert2d(const Dev2D& d, const Ptr9& src, const Ptr9& dst, int layout, int dir, cudaStream_t st);
+// single-precision variant of the stage kernels, and plane casts between precisions
+void launch_alpha2d(const Dev2DT<float>& d, unsigned long long* amax, int* status, cudaStream_t st);
+void launch_sweep_x2d(const Dev2DT<float>& d, const double* alpha, bool linear, bool chr, cudaStream_t st);
+void launch_sweep_y2d(const Dev2DT<float>& d, const double* alpha, bool linear, bool chr, cudaStream_t st);
+void launch_node2d(const Dev2DT<float>& d, const StageArgsT<float>& sa, int mode, bool linear, bool chr,
+                   cudaStream_t st);
+void launch_cast_planes(int nplanes, size_t n, const Ptr12& src, const Ptr12& dst, int to_float, cudaStream_t st);
 
 // record an error message for hw_last_error (hw_api.cu); returns code
 int set_last_error(int code, const char* msg);

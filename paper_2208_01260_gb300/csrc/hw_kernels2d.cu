@@ -18,19 +18,19 @@ namespace hw {
 constexpr int XS_T = 128;
 constexpr int XS_N = XS_T + 3;
 
-template <bool LINEAR, bool CHAR>
-__global__ void __launch_bounds__(XS_T) k_sweep_x(Dev2D d, const double* __restrict__ alpha) {
-  __shared__ double sm[NREC * XS_N];
+template <bool LINEAR, bool CHAR, class R>
+__global__ void __launch_bounds__(XS_T) k_sweep_x(Dev2DT<R> d, const double* __restrict__ alpha) {
+  __shared__ R sm[NREC * XS_N];
   const int j = blockIdx.y;
   const int k0 = blockIdx.x * XS_T;
-  const double ax = alpha[0];
+  const R ax = R(alpha[0]);
   for (int t = threadIdx.x; t < XS_N; t += XS_T) {
     const int i = k0 - 2 + t;
     if (i > d.nx + 1) break;
-    Node12 n;
+    Node12T<R> n;
     load_node(d, i, j, n);
-    double rec[NREC];
-    node_record<0>(n, d.g, ax, rec);
+    R rec[NREC];
+    node_record<0>(n, R(d.g), ax, rec);
 #pragma unroll
     for (int f = 0; f < NREC; ++f) sm[f * XS_N + t] = rec[f];
   }
@@ -39,11 +39,11 @@ __global__ void __launch_bounds__(XS_T) k_sweep_x(Dev2D d, const double* __restr
   if (k > d.nx) return;
   const int t = threadIdx.x;
   const size_t o = (size_t)j * (d.nx + 1) + k;
-  double qb[6];
+  R qb[6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qbx[q] + o);
-  double out[12];
-  interface_values<0, LINEAR, CHAR>(sm + t, sm + t + 1, sm + t + 2, sm + t + 3, XS_N, qb, d.g, d.eps_w, out);
+  R out[12];
+  interface_values<0, LINEAR, CHAR>(sm + t, sm + t + 1, sm + t + 2, sm + t + 3, XS_N, qb, R(d.g), R(d.eps_w), out);
 #pragma unroll
   for (int q = 0; q < 12; ++q) d.X[q][o] = out[q];
 }
@@ -54,43 +54,44 @@ __global__ void __launch_bounds__(XS_T) k_sweep_x(Dev2D d, const double* __restr
 // ---------------------------------------------------------------------------------------------
 constexpr int YS_W = 32;
 
-template <bool LINEAR, bool CHAR>
-__global__ void __launch_bounds__(YS_W) k_sweep_y(Dev2D d, const double* __restrict__ alpha, int seg) {
-  extern __shared__ double ring[];  // [4 slots][NREC][YS_W]
+template <bool LINEAR, bool CHAR, class R>
+__global__ void __launch_bounds__(YS_W) k_sweep_y(Dev2DT<R> d, const double* __restrict__ alpha, int seg) {
+  extern __shared__ __align__(16) unsigned char ring_raw[];
+  R* ring = reinterpret_cast<R*>(ring_raw);  // [4 slots][NREC][YS_W]
   const int i = blockIdx.x * YS_W + threadIdx.x;
   if (i >= d.nx) return;
   const int k0 = blockIdx.y * seg;
-  const double ay = alpha[1];
+  const R ay = R(alpha[1]);
   const int rend = min(k0 + seg, d.ny + 1);
   const int stride = YS_W;  // field stride inside one slot
   for (int r = k0 - 2; r <= rend; ++r) {
-    Node12 n;
+    Node12T<R> n;
     load_node(d, i, r, n);
-    double rec[NREC];
-    node_record<1>(n, d.g, ay, rec);
-    double* slot = ring + (size_t)(r & 3) * NREC * YS_W + threadIdx.x;
+    R rec[NREC];
+    node_record<1>(n, R(d.g), ay, rec);
+    R* slot = ring + (size_t)(r & 3) * NREC * YS_W + threadIdx.x;
 #pragma unroll
     for (int f = 0; f < NREC; ++f) slot[f * stride] = rec[f];
     const int k = r - 1;
     if (k >= k0 && k < k0 + seg && k <= d.ny) {
-      const double* s0 = ring + (size_t)((k - 2) & 3) * NREC * YS_W + threadIdx.x;
-      const double* s1 = ring + (size_t)((k - 1) & 3) * NREC * YS_W + threadIdx.x;
-      const double* s2 = ring + (size_t)((k) & 3) * NREC * YS_W + threadIdx.x;
-      const double* s3 = ring + (size_t)((k + 1) & 3) * NREC * YS_W + threadIdx.x;
+      const R* s0 = ring + (size_t)((k - 2) & 3) * NREC * YS_W + threadIdx.x;
+      const R* s1 = ring + (size_t)((k - 1) & 3) * NREC * YS_W + threadIdx.x;
+      const R* s2 = ring + (size_t)((k) & 3) * NREC * YS_W + threadIdx.x;
+      const R* s3 = ring + (size_t)((k + 1) & 3) * NREC * YS_W + threadIdx.x;
       const size_t o = (size_t)k * d.nx + i;
-      double qb[6];
+      R qb[6];
 #pragma unroll
       for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qby[q] + o);
-      double out[12];
-      interface_values<1, LINEAR, CHAR>(s0, s1, s2, s3, stride, qb, d.g, d.eps_w, out);
+      R out[12];
+      interface_values<1, LINEAR, CHAR>(s0, s1, s2, s3, stride, qb, R(d.g), R(d.eps_w), out);
 #pragma unroll
       for (int q = 0; q < 12; ++q) d.Y[q][o] = out[q];
     }
   }
 }
 
-template <int MODE, bool LINEAR, bool CHAR>
-__global__ void __launch_bounds__(256) k_node2d(Dev2D d, StageArgs sa) {
+template <int MODE, bool LINEAR, bool CHAR, class R>
+__global__ void __launch_bounds__(256) k_node2d(Dev2DT<R> d, StageArgsT<R> sa) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y;
   if (i >= d.nx || j >= d.ny) return;
@@ -101,21 +102,24 @@ __global__ void __launch_bounds__(256) k_node2d(Dev2D d, StageArgs sa) {
 // alpha_x, alpha_y = max over nodes of |u| + c, |v| + c (exact max via ordered 64-bit keys),
 // plus a status flag for non-finite or non-positive depth.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_alpha2d(Dev2D d, unsigned long long* amax, int* status) {
+template <class R>
+__global__ void __launch_bounds__(256) k_alpha2d(Dev2DT<R> d, unsigned long long* amax, int* status) {
   unsigned long long kx = 0, ky = 0;
   int bad = 0;
   const size_t n = (size_t)d.nx * d.ny;
+  // the largest finite value of the working precision
+  const R big = std::is_same<R, double>::value ? R(1e300) : R(3e38);
   for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
-    const double h = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
-    if (!(h > 0.0) || !(h < 1e300)) { bad = 1; continue; }
-    const double rh = fast_rcp(h);
-    const double gh = d.g * h;
-    const double c = gh * fast_rsqrt(gh);
-    const double u = __ldg(d.S[1] + o) * rh, v = __ldg(d.S[2] + o) * rh;
-    const double ax = dabs(u) + c, ay = dabs(v) + c;
-    if (!(ax < 1e300) || !(ay < 1e300)) { bad = 1; continue; }
-    kx = max(kx, dkey(ax));
-    ky = max(ky, dkey(ay));
+    const R h = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
+    if (!(h > R(0.0)) || !(h < big)) { bad = 1; continue; }
+    const R rh = fast_rcp(h);
+    const R gh = R(d.g) * h;
+    const R c = gh * fast_rsqrt(gh);
+    const R u = __ldg(d.S[1] + o) * rh, v = __ldg(d.S[2] + o) * rh;
+    const R ax = dabs(u) + c, ay = dabs(v) + c;
+    if (!(ax < big) || !(ay < big)) { bad = 1; continue; }
+    kx = max(kx, dkey((double)ax));  // the key of the value widened to double (exact)
+    ky = max(ky, dkey((double)ay));
   }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) {
@@ -306,10 +310,10 @@ __global__ void k_static2d(Dev2D d) {
 // ---------------------------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------------------------
-template <bool L, bool C>
-static void launch_sx(const Dev2D& d, const double* alpha, cudaStream_t st) {
+template <bool L, bool C, class R>
+static void launch_sx(const Dev2DT<R>& d, const double* alpha, cudaStream_t st) {
   dim3 gx((d.nx + 1 + XS_T - 1) / XS_T, d.ny);
-  k_sweep_x<L, C><<<gx, XS_T, 0, st>>>(d, alpha);
+  k_sweep_x<L, C, R><<<gx, XS_T, 0, st>>>(d, alpha);
 }
 
 // Segment length of the y-sweep: one balanced wave of resident blocks when the grid allows it
@@ -329,39 +333,46 @@ static int sweep_y_segment(int nx, int ny, int blocks_per_sm) {
   return std::max(seg, std::min(8, ny + 1));
 }
 
-template <bool L, bool C>
-static void launch_sy(const Dev2D& d, const double* alpha, cudaStream_t st) {
-  const size_t smem = (size_t)4 * NREC * YS_W * sizeof(double);
+template <bool L, bool C, class R>
+static void launch_sy(const Dev2DT<R>& d, const double* alpha, cudaStream_t st) {
+  const size_t smem = (size_t)4 * NREC * YS_W * sizeof(R);
   static int bps = -1;
   if (bps < 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_sweep_y<L, C>, YS_W, smem) != cudaSuccess) bps = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_sweep_y<L, C, R>, YS_W, smem) != cudaSuccess) bps = 1;
   }
   const int seg = sweep_y_segment(d.nx, d.ny, bps);
   dim3 gy((d.nx + YS_W - 1) / YS_W, (d.ny + 1 + seg - 1) / seg);
-  k_sweep_y<L, C><<<gy, YS_W, smem, st>>>(d, alpha, seg);
+  k_sweep_y<L, C, R><<<gy, YS_W, smem, st>>>(d, alpha, seg);
 }
 
-template <int MODE, bool L, bool C>
-static void launch_node(const Dev2D& d, const StageArgs& sa, cudaStream_t st) {
+template <int MODE, bool L, bool C, class R>
+static void launch_node(const Dev2DT<R>& d, const StageArgsT<R>& sa, cudaStream_t st) {
   dim3 g((d.nx + 31) / 32, (d.ny + 7) / 8);
-  k_node2d<MODE, L, C><<<g, dim3(32, 8), 0, st>>>(d, sa);
+  k_node2d<MODE, L, C, R><<<g, dim3(32, 8), 0, st>>>(d, sa);
 }
 
 int set_kernel_attributes2d() {
   const int smem = 4 * NREC * YS_W * (int)sizeof(double);
   cudaError_t e = cudaSuccess;
-  e = cudaFuncSetAttribute(k_sweep_y<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_y<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_y<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_y<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = cudaFuncSetAttribute(k_sweep_y<false, true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_y<true, true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_y<false, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_y<true, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e == cudaSuccess ? 0 : -1;
 }
 
-void launch_alpha2d(const Dev2D& d, unsigned long long* amax, int* status, cudaStream_t st) {
+template <class R>
+static void alpha2d_impl(const Dev2DT<R>& d, unsigned long long* amax, int* status, cudaStream_t st) {
   cudaMemsetAsync(amax, 0, 2 * sizeof(unsigned long long), st);
   const size_t n = (size_t)d.nx * d.ny;
   int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 8);
-  k_alpha2d<<<blocks, 256, 0, st>>>(d, amax, status);
+  k_alpha2d<R><<<blocks, 256, 0, st>>>(d, amax, status);
+}
+void launch_alpha2d(const Dev2D& d, unsigned long long* amax, int* status, cudaStream_t st) {
+  alpha2d_impl(d, amax, status, st);
+}
+void launch_alpha2d(const Dev2DT<float>& d, unsigned long long* amax, int* status, cudaStream_t st) {
+  alpha2d_impl(d, amax, status, st);
 }
 
 void launch_finish_alpha2d(const Dev2D& d, const unsigned long long* amax, double* alpha, double* dt_out,
@@ -369,17 +380,18 @@ void launch_finish_alpha2d(const Dev2D& d, const unsigned long long* amax, doubl
   k_finish_alpha2d<<<1, 1, 0, st>>>(amax, alpha, dt_out, cfl, d.inv_dx, d.inv_dy, t_now, t_end);
 }
 
-void launch_sweep_x2d(const Dev2D& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
+template <class R>
+static void sweep_x_impl(const Dev2DT<R>& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
   if (linear) { if (chr) launch_sx<true, true>(d, alpha, st); else launch_sx<true, false>(d, alpha, st); }
   else        { if (chr) launch_sx<false, true>(d, alpha, st); else launch_sx<false, false>(d, alpha, st); }
 }
-
-void launch_sweep_y2d(const Dev2D& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
+template <class R>
+static void sweep_y_impl(const Dev2DT<R>& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
   if (linear) { if (chr) launch_sy<true, true>(d, alpha, st); else launch_sy<true, false>(d, alpha, st); }
   else        { if (chr) launch_sy<false, true>(d, alpha, st); else launch_sy<false, false>(d, alpha, st); }
 }
-
-void launch_node2d(const Dev2D& d, const StageArgs& sa, int mode, bool linear, bool chr, cudaStream_t st) {
+template <class R>
+static void node_impl(const Dev2DT<R>& d, const StageArgsT<R>& sa, int mode, bool linear, bool chr, cudaStream_t st) {
   if (mode == MODE_RHS) {
     if (linear) { if (chr) launch_node<MODE_RHS, true, true>(d, sa, st); else launch_node<MODE_RHS, true, false>(d, sa, st); }
     else        { if (chr) launch_node<MODE_RHS, false, true>(d, sa, st); else launch_node<MODE_RHS, false, false>(d, sa, st); }
@@ -387,6 +399,41 @@ void launch_node2d(const Dev2D& d, const StageArgs& sa, int mode, bool linear, b
     if (linear) { if (chr) launch_node<MODE_STAGE, true, true>(d, sa, st); else launch_node<MODE_STAGE, true, false>(d, sa, st); }
     else        { if (chr) launch_node<MODE_STAGE, false, true>(d, sa, st); else launch_node<MODE_STAGE, false, false>(d, sa, st); }
   }
+}
+
+void launch_sweep_x2d(const Dev2D& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
+  sweep_x_impl(d, alpha, linear, chr, st);
+}
+void launch_sweep_y2d(const Dev2D& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
+  sweep_y_impl(d, alpha, linear, chr, st);
+}
+void launch_node2d(const Dev2D& d, const StageArgs& sa, int mode, bool linear, bool chr, cudaStream_t st) {
+  node_impl(d, sa, mode, linear, chr, st);
+}
+void launch_sweep_x2d(const Dev2DT<float>& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
+  sweep_x_impl(d, alpha, linear, chr, st);
+}
+void launch_sweep_y2d(const Dev2DT<float>& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
+  sweep_y_impl(d, alpha, linear, chr, st);
+}
+void launch_node2d(const Dev2DT<float>& d, const StageArgsT<float>& sa, int mode, bool linear, bool chr,
+                   cudaStream_t st) {
+  node_impl(d, sa, mode, linear, chr, st);
+}
+
+// Plane conversion between precisions (the single-precision variant keeps double copies for the
+// initialisation and the exchange with the caller).
+__global__ void k_cast_planes(int nplanes, size_t n, Ptr12 src, Ptr12 dst, int to_float) {
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+    for (int q = 0; q < nplanes; ++q) {
+      if (to_float) ((float*)dst.p[q])[o] = (float)((const double*)src.p[q])[o];
+      else ((double*)dst.p[q])[o] = (double)((const float*)src.p[q])[o];
+    }
+}
+
+void launch_cast_planes(int nplanes, size_t n, const Ptr12& src, const Ptr12& dst, int to_float, cudaStream_t st) {
+  int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 16);
+  k_cast_planes<<<blocks, 256, 0, st>>>(nplanes, n, src, dst, to_float);
 }
 
 void launch_init2d(const Dev2D& d, const PhysIn& in, int* status, cudaStream_t st) {

@@ -64,6 +64,7 @@ extern "C" int hw_rhs1d_noalloc(const hw_grid* grid, const hw_params* params, co
     return noalloc_fail(HW_ERR_ARG, "hw_rhs1d_noalloc: nx exceeds HW_NOALLOC_MAX_NX (16384); use hw_create/hw_rhs");
   if (grid->bc_x < 0 || grid->bc_x > 2) return noalloc_fail(HW_ERR_ARG, "hw_rhs1d_noalloc: bad boundary condition");
   if (!(grid->x1 > grid->x0)) return noalloc_fail(HW_ERR_ARG, "hw_rhs1d_noalloc: empty domain");
+  if (params->precision != HW_FP64) return noalloc_fail(HW_ERR_ARG, "hw_rhs1d_noalloc: HW_FP64 only");
   if (!(params->g > 0) || !(params->eps_w > 0))
     return noalloc_fail(HW_ERR_ARG, "hw_rhs1d_noalloc: g and eps_w must be positive");
   for (int q = 0; q < 3; ++q)

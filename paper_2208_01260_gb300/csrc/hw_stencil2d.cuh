@@ -11,27 +11,30 @@ namespace hw {
 // ---------------------------------------------------------------------------------------------
 // Loading a node with boundary mapping
 // ---------------------------------------------------------------------------------------------
-struct Node12 {
-  double v[12];  // eta m w H1' M1' W1' H2' M2' W2' b bxs bys
+template <class R>
+struct Node12T {
+  R v[12];  // eta m w H1' M1' W1' H2' M2' W2' b bxs bys
 };
+using Node12 = Node12T<double>;
 
-__device__ __forceinline__ void load_node(const Dev2D& d, int i, int j, Node12& n) {
+template <class R>
+__device__ __forceinline__ void load_node(const Dev2DT<R>& d, int i, int j, Node12T<R>& n) {
   bool fx, fy;
   const int ii = map_index(i, d.nx, d.bc_x, fx);
   const int jj = map_index(j, d.ny, d.bc_y, fy);
   const size_t o = (size_t)jj * d.nx + ii;
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
-    double x = __ldg(d.S[q] + o);
-    if (fx) x *= par_x2d(q);
-    if (fy) x *= par_y2d(q);
+    R x = __ldg(d.S[q] + o);
+    if (fx) x *= R(par_x2d(q));
+    if (fy) x *= R(par_y2d(q));
     n.v[q] = x;
   }
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    double x = __ldg(d.stat[q] + o);
-    if (fx) x *= par_x2d(9 + q);
-    if (fy) x *= par_y2d(9 + q);
+    R x = __ldg(d.stat[q] + o);
+    if (fx) x *= R(par_x2d(9 + q));
+    if (fy) x *= R(par_y2d(9 + q));
     n.v[9 + q] = x;
   }
 }
@@ -40,25 +43,25 @@ __device__ __forceinline__ void load_node(const Dev2D& d, int i, int j, Node12& 
 enum { R_FP = 0, R_FM = 3, R_GP = 6, R_GM = 9, R_MIX = 12, R_H = 15, R_M = 16, R_W = 17, NREC = 18 };
 
 // Pointwise fluxes of eq. (swe-form-2d-e) and their chain-rule derivatives of eq. (swe-form-2d-h),
-// split with the global alpha (Sec. 2.1 Step 1, without the factor 1/2). DIR = 0: x-sweep record
+// split with the global alpha (Sec. R(2.1) Step 1, without the factor 1/2). DIR = 0: x-sweep record
 // (F1, d_x F1 for the split, d_y F1 for the mixed term); DIR = 1: y-sweep record (F2, d_y F2, d_x F2).
-template <int DIR>
-__device__ __forceinline__ void node_record(const Node12& n, double g, double alpha, double rec[NREC]) {
-  const double eta = n.v[0], m = n.v[1], w = n.v[2], b = n.v[9];
-  const double h = eta - b;
-  const double rh = fast_rcp(h);
-  const double u = m * rh, v = w * rh;
-  const double gh = g * h, ge = g * eta;
-  const double pres = ge * fma(0.5, eta, -b);  // g/2 (eta^2 - 2 eta b)
-  const double uv = u * v;
+template <int DIR, class R>
+__device__ __forceinline__ void node_record(const Node12T<R>& n, R g, R alpha, R rec[NREC]) {
+  const R eta = n.v[0], m = n.v[1], w = n.v[2], b = n.v[9];
+  const R h = eta - b;
+  const R rh = fast_rcp(h);
+  const R u = m * rh, v = w * rh;
+  const R gh = g * h, ge = g * eta;
+  const R pres = ge * fma(R(0.5), eta, -b);  // g/2 (eta^2 - 2 eta b)
+  const R uv = u * v;
   // derivative data along the sweep (split) and across it (mixed)
   const int qs = DIR == 0 ? 3 : 6, qm = DIR == 0 ? 6 : 3;
-  const double Hs = n.v[qs], Ms = n.v[qs + 1], Ws = n.v[qs + 2], Bs = n.v[DIR == 0 ? 10 : 11];
-  const double Hm = n.v[qm], Mm = n.v[qm + 1], Wm = n.v[qm + 2], Bm = n.v[DIR == 0 ? 11 : 10];
-  double F[3], Gs[3], Gm[3];
-  const double mv = m * v;
+  const R Hs = n.v[qs], Ms = n.v[qs + 1], Ws = n.v[qs + 2], Bs = n.v[DIR == 0 ? 10 : 11];
+  const R Hm = n.v[qm], Mm = n.v[qm + 1], Wm = n.v[qm + 2], Bm = n.v[DIR == 0 ? 11 : 10];
+  R F[3], Gs[3], Gm[3];
+  const R mv = m * v;
   if (DIR == 0) {
-    const double uu = u * u, a1 = gh - uu, a2 = uu - ge, u2 = u + u;
+    const R uu = u * u, a1 = gh - uu, a2 = uu - ge, u2 = u + u;
     F[0] = m; F[1] = fma(m, u, pres); F[2] = mv;
     Gs[0] = Ms;
     Gs[1] = fma(u2, Ms, fma(a1, Hs, a2 * Bs));
@@ -67,7 +70,7 @@ __device__ __forceinline__ void node_record(const Node12& n, double g, double al
     Gm[1] = fma(u2, Mm, fma(a1, Hm, a2 * Bm));
     Gm[2] = fma(uv, Bm - Hm, fma(v, Mm, u * Wm));
   } else {
-    const double vv = v * v, a1 = gh - vv, a2 = vv - ge, v2 = v + v;
+    const R vv = v * v, a1 = gh - vv, a2 = vv - ge, v2 = v + v;
     F[0] = w; F[1] = mv; F[2] = fma(w, v, pres);
     Gs[0] = Ws;
     Gs[1] = fma(uv, Bs - Hs, fma(v, Ms, u * Ws));
@@ -76,7 +79,7 @@ __device__ __forceinline__ void node_record(const Node12& n, double g, double al
     Gm[1] = fma(uv, Bm - Hm, fma(v, Mm, u * Wm));
     Gm[2] = fma(v2, Wm, fma(a1, Hm, a2 * Bm));
   }
-  const double U[3] = {eta, m, w}, D[3] = {Hs, Ms, Ws};
+  const R U[3] = {eta, m, w}, D[3] = {Hs, Ms, Ws};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     rec[R_FP + c] = fma(alpha, U[c], F[c]);
@@ -96,44 +99,44 @@ __device__ __forceinline__ void node_record(const Node12& n, double g, double al
 // where dS is the spacing along the sweep and dT the spacing across it.
 // qb[6] = source candidates q_1..q_3 of (b, dS b_s) for the '+' side then the mirrored '-' side.
 // ---------------------------------------------------------------------------------------------
-template <int DIR, bool LINEAR, bool CHAR>
-__device__ __forceinline__ void interface_values(const double* r0, const double* r1, const double* r2,
-                                                 const double* r3, int stride, const double qb[6], double g,
-                                                 double eps_w, double out[12]) {
+template <int DIR, bool LINEAR, bool CHAR, class R>
+__device__ __forceinline__ void interface_values(const R* r0, const R* r1, const R* r2,
+                                                 const R* r3, int stride, const R qb[6], R g,
+                                                 R eps_w, R out[12]) {
 #define RV(r, f) (r)[(f) * stride]
   // interface state: h = (h_i + h_{i+1})/2, u = (m_i + m_{i+1})/(h_i + h_{i+1}), v likewise
-  const double hs = RV(r1, R_H) + RV(r2, R_H);
-  const double rhs = fast_rcp(hs);
-  const double ub = (RV(r1, R_M) + RV(r2, R_M)) * rhs;
-  const double vb = (RV(r1, R_W) + RV(r2, R_W)) * rhs;
-  const double gh = (0.5 * g) * hs;
-  const double rs = fast_rsqrt(gh);
-  const double cb = gh * rs;
-  const double ic2 = 0.5 * rs;  // 1/(2c)
+  const R hs = RV(r1, R_H) + RV(r2, R_H);
+  const R rhs = fast_rcp(hs);
+  const R ub = (RV(r1, R_M) + RV(r2, R_M)) * rhs;
+  const R vb = (RV(r1, R_W) + RV(r2, R_W)) * rhs;
+  const R gh = (R(0.5) * g) * hs;
+  const R rs = fast_rsqrt(gh);
+  const R cb = gh * rs;
+  const R ic2 = R(0.5) * rs;  // 1/(2c)
   // normal / tangential velocity of this sweep
-  const double un = DIR == 0 ? ub : vb, ut = DIR == 0 ? vb : ub;
-  const double upc = un + cb, umc = un - cb;
+  const R un = DIR == 0 ? ub : vb, ut = DIR == 0 ? vb : ub;
+  const R upc = un + cb, umc = un - cb;
   // component indices: normal momentum and tangential momentum
   const int cn = DIR == 0 ? 1 : 2, ct = DIR == 0 ? 2 : 1;
   // scaled epsilon: fields 1, 3 carry s = 4c, field 2 carries s = 2 (both 2 without projection)
-  const double eps13 = CHAR ? (8.0 * g * eps_w) * hs : 4.0 * eps_w;
-  const double eps2 = 4.0 * eps_w;
+  const R eps13 = CHAR ? (R(8.0) * g * eps_w) * hs : R(4.0) * eps_w;
+  const R eps2 = R(4.0) * eps_w;
 
-  double G[3], GB1 = 0.0, GB3 = 0.0;  // per-field sums over both sides; source fields 1 and 3
-  const double* rp[4] = {r0, r1, r2, r3};
+  R G[3], GB1 = R(0.0), GB3 = R(0.0);  // per-field sums over both sides; source fields 1 and 3
+  const R* rp[4] = {r0, r1, r2, r3};
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     // '+' uses nodes 0,1,2 of (F+, G+); '-' uses nodes 3,2,1 of (F-, G-) with the derivative negated.
     const int o0 = side == 0 ? 0 : 3, o1 = side == 0 ? 1 : 2, o2 = side == 0 ? 2 : 1;
     const int fo = side == 0 ? R_FP : R_FM, go = side == 0 ? R_GP : R_GM;
-    const double sg = side == 0 ? 1.0 : -1.0;
-    double f[3][3], p[3][3];  // [field][stencil point]
+    const R sg = side == 0 ? R(1.0) : -R(1.0);
+    R f[3][3], p[3][3];  // [field][stencil point]
     const int os[3] = {o0, o1, o2};
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
-      const double* r = rp[os[t]];
-      const double F0 = RV(r, fo), Fn = RV(r, fo + cn), Ft = RV(r, fo + ct);
-      const double G0 = sg * RV(r, go), Gn = sg * RV(r, go + cn), Gt = sg * RV(r, go + ct);
+      const R* r = rp[os[t]];
+      const R F0 = RV(r, fo), Fn = RV(r, fo + cn), Ft = RV(r, fo + ct);
+      const R G0 = sg * RV(r, go), Gn = sg * RV(r, go + cn), Gt = sg * RV(r, go + ct);
       if (CHAR) {
         // rows of L without 1/(2c): (un+c, -1, 0), (-ut, 0, 1), (-(un-c), 1, 0) on (rho, normal, tangential)
         f[0][t] = fma(upc, F0, -Fn);
@@ -147,12 +150,12 @@ __device__ __forceinline__ void interface_values(const double* r0, const double*
         p[0][t] = G0; p[1][t] = Gn; p[2][t] = Gt;
       }
     }
-    const double* qbs = qb + 3 * side;
+    const R* qbs = qb + 3 * side;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      Weights W;
-      const double e = (k == 1) ? eps2 : eps13;
-      const double v = hweno_side<LINEAR>(f[k][0], f[k][1], f[k][2], p[k][0], p[k][1], p[k][2], e, W);
+      WeightsT<R> W;
+      const R e = (k == 1) ? eps2 : eps13;
+      const R v = hweno_side<LINEAR>(f[k][0], f[k][1], f[k][2], p[k][0], p[k][1], p[k][2], e, W);
       G[k] = side == 0 ? v : G[k] + v;
       if (CHAR) {
         // source data per field: (-b, 0, +b) (row entries of the normal-momentum column)
@@ -164,33 +167,33 @@ __device__ __forceinline__ void interface_values(const double* r0, const double*
     }
   }
   // back to physical components: 2 Fhat = R diag(1/s) G * 2
-  double F2[3], B2[3];
+  R F2[3], B2[3];
   if (CHAR) {
-    const double A = (G[0] + G[2]) * ic2;
+    const R A = (G[0] + G[2]) * ic2;
     F2[0] = A;
-    F2[cn] = fma(un, A, 0.5 * (G[2] - G[0]));
+    F2[cn] = fma(un, A, R(0.5) * (G[2] - G[0]));
     F2[ct] = fma(ut, A, G[1]);
-    const double Bs = (GB1 + GB3) * ic2;
+    const R Bs = (GB1 + GB3) * ic2;
     B2[0] = Bs;
-    B2[cn] = fma(un, Bs, 0.5 * (GB3 - GB1));
+    B2[cn] = fma(un, Bs, R(0.5) * (GB3 - GB1));
     B2[ct] = ut * Bs;
   } else {
     F2[0] = G[0]; F2[cn] = G[1]; F2[ct] = G[2];
-    B2[0] = 0.0; B2[cn] = GB1; B2[ct] = 0.0;
+    B2[0] = R(0.0); B2[cn] = GB1; B2[ct] = R(0.0);
   }
   // derivative-equation flux (eq. Rec-phi, component-wise): 24 dS Ghat = 3 fpart + gpart
   // mixed term (eq. mixed): 12 dT Mhat = 7 (X_i + X_{i+1}) - (X_{i-1} + X_{i+2})
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const double fpart =
-        fma(7.0, RV(r2, R_FP + c) - RV(r1, R_FM + c),
-            fma(8.0, RV(r2, R_FM + c) - RV(r1, R_FP + c), RV(r0, R_FP + c) - RV(r3, R_FM + c)));
-    const double gpart = fma(-5.0, RV(r2, R_GP + c) + RV(r1, R_GM + c),
-                             fma(-2.0, RV(r1, R_GP + c) + RV(r2, R_GM + c), RV(r0, R_GP + c) + RV(r3, R_GM + c)));
+    const R fpart =
+        fma(R(7.0), RV(r2, R_FP + c) - RV(r1, R_FM + c),
+            fma(R(8.0), RV(r2, R_FM + c) - RV(r1, R_FP + c), RV(r0, R_FP + c) - RV(r3, R_FM + c)));
+    const R gpart = fma(-R(5.0), RV(r2, R_GP + c) + RV(r1, R_GM + c),
+                             fma(-R(2.0), RV(r1, R_GP + c) + RV(r2, R_GM + c), RV(r0, R_GP + c) + RV(r3, R_GM + c)));
     out[c] = F2[c];
     out[3 + c] = B2[c];
-    out[6 + c] = fma(3.0, fpart, gpart);
-    out[9 + c] = fma(7.0, RV(r1, R_MIX + c) + RV(r2, R_MIX + c), -(RV(r0, R_MIX + c) + RV(r3, R_MIX + c)));
+    out[6 + c] = fma(R(3.0), fpart, gpart);
+    out[9 + c] = fma(R(7.0), RV(r1, R_MIX + c) + RV(r2, R_MIX + c), -(RV(r0, R_MIX + c) + RV(r3, R_MIX + c)));
   }
 #undef RV
 }
@@ -198,20 +201,16 @@ __device__ __forceinline__ void interface_values(const double* r0, const double*
 // ---------------------------------------------------------------------------------------------
 // Node kernel: RHS assembly, limiter, RK combination (or the bare RHS).
 // ---------------------------------------------------------------------------------------------
-struct NodeLim {
-  double U[3], D[3];
-};
-
-// Limiter along one direction at one node (Sec. 2.2), scaled data. L-rows without 1/(2c):
+// Limiter along one direction at one node (Sec. R(2.2)), scaled data. L-rows without 1/(2c):
 // x: (u+c, -1, 0), (-v, 0, 1), (-(u-c), 1, 0); y: (v+c, 0, -1), (-u, 1, 0), (-(v-c), 0, 1).
-template <int DIR, bool LINEAR, bool CHAR>
-__device__ __forceinline__ void limit_dir(const double Um[3], const double U0[3], const double Up[3],
-                                          const double Dm[3], const double Dp[3], double u, double v, double c,
-                                          double ic2, double gh, double eps, double out[3]) {
+template <int DIR, bool LINEAR, bool CHAR, class R>
+__device__ __forceinline__ void limit_dir(const R Um[3], const R U0[3], const R Up[3],
+                                          const R Dm[3], const R Dp[3], R u, R v, R c,
+                                          R ic2, R gh, R eps, R out[3]) {
   const int cn = DIR == 0 ? 1 : 2, ct = DIR == 0 ? 2 : 1;
-  const double un = DIR == 0 ? u : v, ut = DIR == 0 ? v : u;
-  const double upc = un + c, umc = un - c;
-  auto proj = [&](const double* a, double o[3]) {
+  const R un = DIR == 0 ? u : v, ut = DIR == 0 ? v : u;
+  const R upc = un + c, umc = un - c;
+  auto proj = [&](const R* a, R o[3]) {
     if (CHAR) {
       o[0] = fma(upc, a[0], -a[cn]);
       o[1] = fma(-ut, a[0], a[ct]);
@@ -220,16 +219,16 @@ __device__ __forceinline__ void limit_dir(const double Um[3], const double U0[3]
       o[0] = a[0]; o[1] = a[cn]; o[2] = a[ct];
     }
   };
-  double m0[3], m1[3], m2[3], nl[3], nr[3];
+  R m0[3], m1[3], m2[3], nl[3], nr[3];
   proj(Um, m0); proj(U0, m1); proj(Up, m2); proj(Dm, nl); proj(Dp, nr);
-  const double e13 = CHAR ? (4.0 * eps) * gh : eps;
-  double nu[3];
+  const R e13 = CHAR ? (R(4.0) * eps) * gh : eps;
+  R nu[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) nu[k] = limiter_field<LINEAR>(m0[k], m1[k], m2[k], nl[k], nr[k], k == 1 ? eps : e13);
   if (CHAR) {
-    const double A = (nu[0] + nu[2]) * ic2;
+    const R A = (nu[0] + nu[2]) * ic2;
     out[0] = A;
-    out[cn] = fma(un, A, 0.5 * (nu[2] - nu[0]));
+    out[cn] = fma(un, A, R(0.5) * (nu[2] - nu[0]));
     out[ct] = fma(ut, A, nu[1]);
   } else {
     out[0] = nu[0]; out[cn] = nu[1]; out[ct] = nu[2];
@@ -237,12 +236,12 @@ __device__ __forceinline__ void limit_dir(const double Um[3], const double U0[3]
 }
 
 // RHS assembly, limiter and RK combination (or the bare RHS) at node (i, j) of one grid.
-template <int MODE, bool LINEAR, bool CHAR>
-__device__ __forceinline__ void node_update(const Dev2D& d, const StageArgs& sa, int i, int j) {
+template <int MODE, bool LINEAR, bool CHAR, class R>
+__device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT<R>& sa, int i, int j) {
   const size_t o = (size_t)j * d.nx + i;
   const size_t ox = (size_t)j * (d.nx + 1) + i;  // left x-interface; right is ox + 1
   const size_t oy = (size_t)j * d.nx + i;        // lower y-interface; upper is oy + nx
-  double cur[9];
+  R cur[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) cur[q] = __ldg(d.S[q] + o);
   if (MODE == MODE_STAGE && !(*sa.dt > 0.0)) {
@@ -251,79 +250,82 @@ __device__ __forceinline__ void node_update(const Dev2D& d, const StageArgs& sa,
     for (int q = 0; q < 9; ++q) sa.out[q][o] = cur[q];
     return;
   }
-  const double eta = cur[0], H1 = cur[3], H2 = cur[6];
-  const double g = d.g;
-  const double ge = g * eta;
+  const R eta = cur[0], H1 = cur[3], H2 = cur[6];
+  const R g = R(d.g);
+  // grid constants in the working precision
+  const R c_bx = R(d.c_bx), c_by = R(d.c_by), c_gx = R(d.c_gx), c_gy = R(d.c_gy), c_mx = R(d.c_mx),
+          c_my = R(d.c_my);
+  const R ge = g * eta;
   // ---- RHS (eq. swe-form-2d-dis) in scaled units: R_U, dx R_V, dy R_Q ----
-  double R[9];
+  R Rv[9];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const double dFx = __ldg(d.X[c] + ox + 1) - __ldg(d.X[c] + ox);
-    const double dFy = __ldg(d.Y[c] + oy + d.nx) - __ldg(d.Y[c] + oy);
-    const double dbx = __ldg(d.X[3 + c] + ox + 1) - __ldg(d.X[3 + c] + ox);
-    const double dby = __ldg(d.Y[3 + c] + oy + d.nx) - __ldg(d.Y[3 + c] + oy);
-    const double dGx = __ldg(d.X[6 + c] + ox + 1) - __ldg(d.X[6 + c] + ox);
-    const double dGy = __ldg(d.Y[6 + c] + oy + d.nx) - __ldg(d.Y[6 + c] + oy);
-    const double dMx = __ldg(d.X[9 + c] + ox + 1) - __ldg(d.X[9 + c] + ox);
-    const double dMy = __ldg(d.Y[9 + c] + oy + d.nx) - __ldg(d.Y[9 + c] + oy);
-    const double db = fma(d.c_bx, dbx, d.c_by * dby);  // [b~]_x/dx + [b-]_y/dy
-    R[c] = fma(-ge, db, fma(-d.c_bx, dFx, -d.c_by * dFy));
-    double rv = fma(-d.c_gx, dGx, -d.c_my * dMy);
-    double rq = fma(-d.c_mx, dMx, -d.c_gy * dGy);
+    const R dFx = __ldg(d.X[c] + ox + 1) - __ldg(d.X[c] + ox);
+    const R dFy = __ldg(d.Y[c] + oy + d.nx) - __ldg(d.Y[c] + oy);
+    const R dbx = __ldg(d.X[3 + c] + ox + 1) - __ldg(d.X[3 + c] + ox);
+    const R dby = __ldg(d.Y[3 + c] + oy + d.nx) - __ldg(d.Y[3 + c] + oy);
+    const R dGx = __ldg(d.X[6 + c] + ox + 1) - __ldg(d.X[6 + c] + ox);
+    const R dGy = __ldg(d.Y[6 + c] + oy + d.nx) - __ldg(d.Y[6 + c] + oy);
+    const R dMx = __ldg(d.X[9 + c] + ox + 1) - __ldg(d.X[9 + c] + ox);
+    const R dMy = __ldg(d.Y[9 + c] + oy + d.nx) - __ldg(d.Y[9 + c] + oy);
+    const R db = fma(c_bx, dbx, c_by * dby);  // [b~]_x/dx + [b-]_y/dy
+    Rv[c] = fma(-ge, db, fma(-c_bx, dFx, -c_by * dFy));
+    R rv = fma(-c_gx, dGx, -c_my * dMy);
+    R rq = fma(-c_mx, dMx, -c_gy * dGy);
     if (c > 0) {
       rv = fma(-ge, __ldg(d.sv[c - 1] + o), rv);
       rq = fma(-ge, __ldg(d.sq[c - 1] + o), rq);
     }
-    R[3 + c] = fma(-g * H1, db, rv);
-    R[6 + c] = fma(-g * H2, db, rq);
+    Rv[3 + c] = fma(-g * H1, db, rv);
+    Rv[6 + c] = fma(-g * H2, db, rq);
   }
   if (MODE == MODE_RHS) {
     // physical units: R_V = (dx R_V)/dx, R_Q = (dy R_Q)/dy
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-      const double s = q < 3 ? 1.0 : (q < 6 ? d.inv_dx : d.inv_dy);
-      sa.rhs_out[q][o] = R[q] * s;
+      const R s = q < 3 ? R(1.0) : R(q < 6 ? d.inv_dx : d.inv_dy);
+      sa.rhs_out[q][o] = Rv[q] * s;
     }
     return;
   }
-  // ---- limiter (Sec. 2.2, dimension by dimension) ----
-  double mod[6];
+  // ---- limiter (Sec. R(2.2), dimension by dimension) ----
+  R mod[6];
   if (sa.limiter) {
-    const double b0 = __ldg(d.stat[0] + o);
-    const double h = eta - b0;
-    const double gh = g * h;
-    const double rh = fast_rcp(h);
-    const double u = cur[1] * rh, v = cur[2] * rh;
-    const double rs = fast_rsqrt(gh);
-    const double c = gh * rs, ic2 = 0.5 * rs;
-    Node12 nm, np;
+    const R b0 = __ldg(d.stat[0] + o);
+    const R h = eta - b0;
+    const R gh = g * h;
+    const R rh = fast_rcp(h);
+    const R u = cur[1] * rh, v = cur[2] * rh;
+    const R rs = fast_rsqrt(gh);
+    const R c = gh * rs, ic2 = R(0.5) * rs;
+    Node12T<R> nm, np;
     // x neighbours
     load_node(d, i - 1, j, nm);
     load_node(d, i + 1, j, np);
-    limit_dir<0, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 3, np.v + 3, u, v, c, ic2, gh, d.eps_lim, mod);
+    limit_dir<0, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 3, np.v + 3, u, v, c, ic2, gh, R(d.eps_lim), mod);
     load_node(d, i, j - 1, nm);
     load_node(d, i, j + 1, np);
-    limit_dir<1, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 6, np.v + 6, u, v, c, ic2, gh, d.eps_lim, mod + 3);
+    limit_dir<1, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 6, np.v + 6, u, v, c, ic2, gh, R(d.eps_lim), mod + 3);
   } else {
 #pragma unroll
     for (int q = 0; q < 6; ++q) mod[q] = cur[3 + q];
   }
   // ---- SSP-RK3 combination (eq. RK) ----
-  const double dt = *sa.dt;
+  const R dt = R(*sa.dt);
   if (sa.k == 1) {
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-      const double cq = q < 3 ? cur[q] : mod[q - 3];
+      const R cq = q < 3 ? cur[q] : mod[q - 3];
       if (sa.base) sa.base[q][o] = cq;
-      sa.out[q][o] = fma(dt, R[q], cq);
+      sa.out[q][o] = fma(dt, Rv[q], cq);
     }
   } else {
-    const double a = sa.k == 2 ? 0.75 : 1.0 / 3.0;
-    const double b = sa.k == 2 ? 0.25 : 2.0 / 3.0;
+    const R a = sa.k == 2 ? R(0.75) : R(1.0) / R(3.0);
+    const R b = sa.k == 2 ? R(0.25) : R(2.0) / R(3.0);
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-      const double cq = q < 3 ? cur[q] : mod[q - 3];
-      sa.out[q][o] = fma(a, __ldg(sa.base[q] + o), b * fma(dt, R[q], cq));
+      const R cq = q < 3 ? cur[q] : mod[q - 3];
+      sa.out[q][o] = fma(a, __ldg(sa.base[q] + o), b * fma(dt, Rv[q], cq));
     }
   }
 }
