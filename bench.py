@@ -269,6 +269,53 @@ def batched_compare(steps, n_inst=512):
             "unit": UNIT, "tiles": "autotuned per size class"}
 
 
+# Algorithmic DRAM bytes per unit in single precision (4-byte planes): a sweep reads each node's 12
+# state/static values and the interface's 6 source candidates and writes 12 interface values (30 planes);
+# the node kernel reads 9 state, 3 static, 24 interface, 4 static-source and (stages 2-3) 9 base planes
+# and writes 9 state and (stage 1) 9 base planes, 58 planes on average over the three stages; alpha reads
+# eta, m, w, b.
+ALGO_BYTES_FP32 = {"sweep_x": 30 * 4, "sweep_y": 30 * 4, "node": 58 * 4, "alpha": 4 * 4}
+
+
+def fp32_variant(steps, warmup=3):
+    """The same 2048^2 workload in single precision (the paper's single-precision runs): rate from the
+    captured graph, and per kernel the algorithmic bytes over its event-timed duration against HBM."""
+    import torch
+    import paper_2208_01260_gb300 as hw
+    from paper_2208_01260_gb300 import scenarios as S
+    sc = S.bumps2d(NX, NY, strip=0.01)
+    s = hw.Solver.from_scenario(sc, hw.make_params(precision=hw.HW_FP32))
+    stream = torch.cuda.current_stream()
+    s.advance(warmup, use_graph=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.advance(steps, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    hw.hw_set_profiling(s.h, True)
+    s.advance(steps, use_graph=False)
+    torch.cuda.synchronize()
+    prof = hw.hw_get_profile(s.h)
+    hw.hw_set_profiling(s.h, False)
+    hbm, _ = hbm_peak()
+    kernels = {}
+    for k in ("sweep_x", "sweep_y", "node", "alpha"):
+        tot, n = prof[k]
+        if n == 0:
+            continue
+        nl = n if k != "alpha" else n // 2
+        avg_s = tot / nl * 1e-3
+        gbs = ALGO_BYTES_FP32[k] * UNITS_PER_LAUNCH[k] / avg_s / 1e9
+        kernels[k] = {"ms_avg": avg_s * 1e3, "algorithmic_gbs": gbs, "hbm_frac": gbs / hbm}
+    s.close()
+    return {"value": NX * NY * STAGES * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "steps": steps, "dtype": "f32", "kernels": kernels, "hbm_peak_gbs": hbm,
+            "note": "single-precision variant of the same workload (well-balance to float round-off); "
+                    "not the headline, which is FP64"}
+
+
 def adjoint_cost(n=512, nsteps=400, snapshots=20):
     """Config 5: gauge misfit over 32 gauges and `nsteps` steps at n x n (bottom of the benchmark plus
     a surface hump, reflective; observations from a run with another hump; the unperturbed CFL step
@@ -373,6 +420,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--batched-steps", type=int, default=6, help="steps of the batched comparison (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=400, help="steps of the adjoint cost measurement (0 = skip)")
+    ap.add_argument("--fp32-steps", type=int, default=200, help="steps of the single-precision variant (0 = skip)")
     ap.add_argument("--nx", type=int, default=2048, help="smaller grids for profiling captures only")
     ap.add_argument("--ny", type=int, default=2048)
     args = ap.parse_args()
@@ -499,6 +547,8 @@ def main():
         line["batched"] = batched_compare(args.batched_steps)
     if args.adjoint_steps > 0 and (NX, NY) == (2048, 2048):
         line["adjoint"] = adjoint_cost(nsteps=args.adjoint_steps)
+    if args.fp32_steps > 0:
+        line["fp32"] = fp32_variant(args.fp32_steps)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, desc, threads, el = oracle_rate()
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,

@@ -69,6 +69,7 @@ struct hw_solver {
   float* FA[9] = {};
   float* FB[9] = {};
   float* fbase[9] = {};
+  float* fsc = nullptr;  // alpha_x, alpha_y, dt rounded to float (refreshed before every stage)
   hw::Dev2DT<float> f2{};
   cudaGraphExec_t graph = nullptr;
   double graph_t_end = -1.0;
@@ -203,9 +204,11 @@ int hw_create(const hw_grid* grid, const hw_params* params, void* cuda_stream, h
       auto F = [&](float** p, size_t cnt) { if (rc == HW_OK) rc = falloc(s, p, cnt); };
       for (int q = 0; q < 9; ++q) { F(&s->FA[q], s->n); F(&s->FB[q], s->n); F(&s->fbase[q], s->n); }
       f.nx = d.nx; f.ny = d.ny; f.bc_x = d.bc_x; f.bc_y = d.bc_y;
-      f.dx = d.dx; f.dy = d.dy; f.inv_dx = d.inv_dx; f.inv_dy = d.inv_dy;
-      f.g = d.g; f.eps_w = d.eps_w; f.eps_lim = d.eps_lim;
-      f.c_bx = d.c_bx; f.c_by = d.c_by; f.c_gx = d.c_gx; f.c_gy = d.c_gy; f.c_mx = d.c_mx; f.c_my = d.c_my;
+      f.dx = (float)d.dx; f.dy = (float)d.dy; f.inv_dx = (float)d.inv_dx; f.inv_dy = (float)d.inv_dy;
+      f.g = (float)d.g; f.eps_w = (float)d.eps_w; f.eps_lim = (float)d.eps_lim;
+      f.c_bx = (float)d.c_bx; f.c_by = (float)d.c_by; f.c_gx = (float)d.c_gx; f.c_gy = (float)d.c_gy;
+      f.c_mx = (float)d.c_mx; f.c_my = (float)d.c_my;
+      F(&s->fsc, 4);
       for (int q = 0; q < 3; ++q) F(&f.stat[q], s->n);
       for (int q = 0; q < 2; ++q) F(&f.bxy[q], s->n);
       for (int q = 0; q < 12; ++q) { F(&f.X[q], (size_t)(nx + 1) * ny); F(&f.Y[q], (size_t)nx * (ny + 1)); }
@@ -350,10 +353,11 @@ static void enqueue_stage(hw_solver* s, int k) {
   const bool lin = s->params.linear_weights != 0, chr = s->params.char_decomp != 0;
   if (s->fp32) {
     float** fout = s->fother();
-    timed(s, HW_PROF_SWEEP_X, [&] { hw::launch_sweep_x2d(s->f2, s->alpha, lin, chr, s->stream); });
-    timed(s, HW_PROF_SWEEP_Y, [&] { hw::launch_sweep_y2d(s->f2, s->alpha, lin, chr, s->stream); });
+    timed(s, HW_PROF_OTHER, [&] { hw::launch_scalars_to_float(s->alpha, s->dt, s->fsc, s->stream); });
+    timed(s, HW_PROF_SWEEP_X, [&] { hw::launch_sweep_x2d(s->f2, s->fsc, lin, chr, s->stream); });
+    timed(s, HW_PROF_SWEEP_Y, [&] { hw::launch_sweep_y2d(s->f2, s->fsc, lin, chr, s->stream); });
     hw::StageArgsT<float> sa{};
-    sa.k = k; sa.limiter = s->params.limiter; sa.dt = s->dt;
+    sa.k = k; sa.limiter = s->params.limiter; sa.dt = s->fsc + 2;
     for (int q = 0; q < 9; ++q) { sa.out[q] = fout[q]; sa.base[q] = s->fbase[q]; }
     timed(s, HW_PROF_NODE, [&] { hw::launch_node2d(s->f2, sa, hw::MODE_STAGE, lin, chr, s->stream); });
   } else if (s->is2d()) {
@@ -508,8 +512,9 @@ int hw_rhs(hw_solver* s, double* const* out, int ptr_kind) {
   if (s->fp32) {
     // float right-hand side into the spare state buffer, then widened into the output planes
     float** scratch = s->fother();
-    hw::launch_sweep_x2d(s->f2, s->alpha, lin, chr, s->stream);
-    hw::launch_sweep_y2d(s->f2, s->alpha, lin, chr, s->stream);
+    hw::launch_scalars_to_float(s->alpha, s->dt, s->fsc, s->stream);
+    hw::launch_sweep_x2d(s->f2, s->fsc, lin, chr, s->stream);
+    hw::launch_sweep_y2d(s->f2, s->fsc, lin, chr, s->stream);
     hw::StageArgsT<float> sa{};
     for (int q = 0; q < 9; ++q) sa.rhs_out[q] = scratch[q];
     hw::launch_node2d(s->f2, sa, hw::MODE_RHS, lin, chr, s->stream);

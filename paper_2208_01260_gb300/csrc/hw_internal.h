@@ -11,14 +11,14 @@ namespace hw {
 enum { MODE_STAGE = 0, MODE_RHS = 1 };
 enum { HW_STATUS_DEPTH = 1, HW_STATUS_NONFINITE = 2, HW_STATUS_TIMEOUT = 4, HW_STATUS_BOUNDS = 8 };
 
-// Everything a 2D kernel needs, passed by value. R is the precision of the planes (double for the
-// scheme, float for the single-precision variant); grid constants stay double.
+// Everything a 2D kernel needs, passed by value. R is the working precision (double for the scheme,
+// float for the single-precision variant) of the planes and of the grid constants.
 template <class R>
 struct Dev2DT {
   int nx, ny, bc_x, bc_y;
-  double dx, dy, inv_dx, inv_dy, g, eps_w, eps_lim;
+  R dx, dy, inv_dx, inv_dy, g, eps_w, eps_lim;
   // assembly constants: 1/(2dx), 1/(2dy), 1/(24dx), 1/(24dy), 1/(12dx), 1/(12dy)
-  double c_bx, c_by, c_gx, c_gy, c_mx, c_my;
+  R c_bx, c_by, c_gx, c_gy, c_mx, c_my;
   R* S[9];      // current state (eta, m, w, dx V, dy Q)
   R* stat[3];   // b, dx b_x, dy b_y
   R* bxy[2];    // b_x, b_y (physical, for conversions and static terms)
@@ -35,7 +35,7 @@ template <class R>
 struct StageArgsT {
   int k;             // RK stage 1..3
   int limiter;
-  const double* dt;  // device scalar
+  const R* dt;       // device scalar
   R* out[9];
   R* base[9];
   R* rhs_out[9];
@@ -91,8 +91,10 @@ void launch_init2d(const Dev2D& d, const PhysIn& in, int* status, cudaStream_t s
 void launch_convert2d(const Dev2D& d, const Ptr9& src, const Ptr9& dst, int layout, int dir, cudaStream_t st);
 // single-precision variant of the stage kernels, and plane casts between precisions
 void launch_alpha2d(const Dev2DT<float>& d, unsigned long long* amax, int* status, cudaStream_t st);
-void launch_sweep_x2d(const Dev2DT<float>& d, const double* alpha, bool linear, bool chr, cudaStream_t st);
-void launch_sweep_y2d(const Dev2DT<float>& d, const double* alpha, bool linear, bool chr, cudaStream_t st);
+void launch_sweep_x2d(const Dev2DT<float>& d, const float* alpha, bool linear, bool chr, cudaStream_t st);
+void launch_sweep_y2d(const Dev2DT<float>& d, const float* alpha, bool linear, bool chr, cudaStream_t st);
+// alpha[2] and dt of the double scalars, rounded into out[0..2] (once per stage of the float variant)
+void launch_scalars_to_float(const double* alpha, const double* dt, float* out, cudaStream_t st);
 void launch_node2d(const Dev2DT<float>& d, const StageArgsT<float>& sa, int mode, bool linear, bool chr,
                    cudaStream_t st);
 void launch_cast_planes(int nplanes, size_t n, const Ptr12& src, const Ptr12& dst, int to_float, cudaStream_t st);

@@ -19,11 +19,11 @@ constexpr int XS_T = 128;
 constexpr int XS_N = XS_T + 3;
 
 template <bool LINEAR, bool CHAR, class R>
-__global__ void __launch_bounds__(XS_T) k_sweep_x(Dev2DT<R> d, const double* __restrict__ alpha) {
+__global__ void __launch_bounds__(XS_T) k_sweep_x(Dev2DT<R> d, const R* __restrict__ alpha) {
   __shared__ R sm[NREC * XS_N];
   const int j = blockIdx.y;
   const int k0 = blockIdx.x * XS_T;
-  const R ax = R(alpha[0]);
+  const R ax = alpha[0];
   for (int t = threadIdx.x; t < XS_N; t += XS_T) {
     const int i = k0 - 2 + t;
     if (i > d.nx + 1) break;
@@ -55,13 +55,13 @@ __global__ void __launch_bounds__(XS_T) k_sweep_x(Dev2DT<R> d, const double* __r
 constexpr int YS_W = 32;
 
 template <bool LINEAR, bool CHAR, class R>
-__global__ void __launch_bounds__(YS_W) k_sweep_y(Dev2DT<R> d, const double* __restrict__ alpha, int seg) {
+__global__ void __launch_bounds__(YS_W) k_sweep_y(Dev2DT<R> d, const R* __restrict__ alpha, int seg) {
   extern __shared__ __align__(16) unsigned char ring_raw[];
   R* ring = reinterpret_cast<R*>(ring_raw);  // [4 slots][NREC][YS_W]
   const int i = blockIdx.x * YS_W + threadIdx.x;
   if (i >= d.nx) return;
   const int k0 = blockIdx.y * seg;
-  const R ay = R(alpha[1]);
+  const R ay = alpha[1];
   const int rend = min(k0 + seg, d.ny + 1);
   const int stride = YS_W;  // field stride inside one slot
   for (int r = k0 - 2; r <= rend; ++r) {
@@ -104,31 +104,55 @@ __global__ void __launch_bounds__(256) k_node2d(Dev2DT<R> d, StageArgsT<R> sa) {
 // ---------------------------------------------------------------------------------------------
 template <class R>
 __global__ void __launch_bounds__(256) k_alpha2d(Dev2DT<R> d, unsigned long long* amax, int* status) {
-  unsigned long long kx = 0, ky = 0;
   int bad = 0;
   const size_t n = (size_t)d.nx * d.ny;
-  // the largest finite value of the working precision
-  const R big = std::is_same<R, double>::value ? R(1e300) : R(3e38);
-  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
-    const R h = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
-    if (!(h > R(0.0)) || !(h < big)) { bad = 1; continue; }
-    const R rh = fast_rcp(h);
-    const R gh = R(d.g) * h;
-    const R c = gh * fast_rsqrt(gh);
-    const R u = __ldg(d.S[1] + o) * rh, v = __ldg(d.S[2] + o) * rh;
-    const R ax = dabs(u) + c, ay = dabs(v) + c;
-    if (!(ax < big) || !(ay < big)) { bad = 1; continue; }
-    kx = max(kx, dkey((double)ax));  // the key of the value widened to double (exact)
-    ky = max(ky, dkey((double)ay));
-  }
+  if constexpr (std::is_same<R, double>::value) {
+    unsigned long long kx = 0, ky = 0;
+    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+      const double h = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
+      if (!(h > 0.0) || !(h < 1e300)) { bad = 1; continue; }
+      const double rh = fast_rcp(h);
+      const double gh = d.g * h;
+      const double c = gh * fast_rsqrt(gh);
+      const double u = __ldg(d.S[1] + o) * rh, v = __ldg(d.S[2] + o) * rh;
+      const double ax = dabs(u) + c, ay = dabs(v) + c;
+      if (!(ax < 1e300) || !(ay < 1e300)) { bad = 1; continue; }
+      kx = max(kx, dkey(ax));
+      ky = max(ky, dkey(ay));
+    }
 #pragma unroll
-  for (int s = 16; s > 0; s >>= 1) {
-    kx = max(kx, __shfl_xor_sync(0xffffffffu, kx, s));
-    ky = max(ky, __shfl_xor_sync(0xffffffffu, ky, s));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(amax, kx);
-    atomicMax(amax + 1, ky);
+    for (int s = 16; s > 0; s >>= 1) {
+      kx = max(kx, __shfl_xor_sync(0xffffffffu, kx, s));
+      ky = max(ky, __shfl_xor_sync(0xffffffffu, ky, s));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(amax, kx);
+      atomicMax(amax + 1, ky);
+    }
+  } else {
+    // float: the maximum in float, widened to a double key once per warp (the FP64 pipe is narrow)
+    float mx = 0.0f, my = 0.0f;
+    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+      const float h = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
+      if (!(h > 0.0f) || !(h < 3e38f)) { bad = 1; continue; }
+      const float rh = fast_rcp(h);
+      const float gh = d.g * h;
+      const float c = gh * fast_rsqrt(gh);
+      const float u = __ldg(d.S[1] + o) * rh, v = __ldg(d.S[2] + o) * rh;
+      const float ax = fabsf(u) + c, ay = fabsf(v) + c;
+      if (!(ax < 3e38f) || !(ay < 3e38f)) { bad = 1; continue; }
+      mx = fmaxf(mx, ax);
+      my = fmaxf(my, ay);
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+      my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, s));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(amax, dkey((double)mx));
+      atomicMax(amax + 1, dkey((double)my));
+    }
   }
   if (bad) atomicOr(status, HW_STATUS_DEPTH);
 }
@@ -311,7 +335,7 @@ __global__ void k_static2d(Dev2D d) {
 // Host launchers
 // ---------------------------------------------------------------------------------------------
 template <bool L, bool C, class R>
-static void launch_sx(const Dev2DT<R>& d, const double* alpha, cudaStream_t st) {
+static void launch_sx(const Dev2DT<R>& d, const R* alpha, cudaStream_t st) {
   dim3 gx((d.nx + 1 + XS_T - 1) / XS_T, d.ny);
   k_sweep_x<L, C, R><<<gx, XS_T, 0, st>>>(d, alpha);
 }
@@ -334,7 +358,7 @@ static int sweep_y_segment(int nx, int ny, int blocks_per_sm) {
 }
 
 template <bool L, bool C, class R>
-static void launch_sy(const Dev2DT<R>& d, const double* alpha, cudaStream_t st) {
+static void launch_sy(const Dev2DT<R>& d, const R* alpha, cudaStream_t st) {
   const size_t smem = (size_t)4 * NREC * YS_W * sizeof(R);
   static int bps = -1;
   if (bps < 0) {
@@ -381,12 +405,12 @@ void launch_finish_alpha2d(const Dev2D& d, const unsigned long long* amax, doubl
 }
 
 template <class R>
-static void sweep_x_impl(const Dev2DT<R>& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
+static void sweep_x_impl(const Dev2DT<R>& d, const R* alpha, bool linear, bool chr, cudaStream_t st) {
   if (linear) { if (chr) launch_sx<true, true>(d, alpha, st); else launch_sx<true, false>(d, alpha, st); }
   else        { if (chr) launch_sx<false, true>(d, alpha, st); else launch_sx<false, false>(d, alpha, st); }
 }
 template <class R>
-static void sweep_y_impl(const Dev2DT<R>& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
+static void sweep_y_impl(const Dev2DT<R>& d, const R* alpha, bool linear, bool chr, cudaStream_t st) {
   if (linear) { if (chr) launch_sy<true, true>(d, alpha, st); else launch_sy<true, false>(d, alpha, st); }
   else        { if (chr) launch_sy<false, true>(d, alpha, st); else launch_sy<false, false>(d, alpha, st); }
 }
@@ -410,10 +434,10 @@ void launch_sweep_y2d(const Dev2D& d, const double* alpha, bool linear, bool chr
 void launch_node2d(const Dev2D& d, const StageArgs& sa, int mode, bool linear, bool chr, cudaStream_t st) {
   node_impl(d, sa, mode, linear, chr, st);
 }
-void launch_sweep_x2d(const Dev2DT<float>& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
+void launch_sweep_x2d(const Dev2DT<float>& d, const float* alpha, bool linear, bool chr, cudaStream_t st) {
   sweep_x_impl(d, alpha, linear, chr, st);
 }
-void launch_sweep_y2d(const Dev2DT<float>& d, const double* alpha, bool linear, bool chr, cudaStream_t st) {
+void launch_sweep_y2d(const Dev2DT<float>& d, const float* alpha, bool linear, bool chr, cudaStream_t st) {
   sweep_y_impl(d, alpha, linear, chr, st);
 }
 void launch_node2d(const Dev2DT<float>& d, const StageArgsT<float>& sa, int mode, bool linear, bool chr,
@@ -429,6 +453,16 @@ __global__ void k_cast_planes(int nplanes, size_t n, Ptr12 src, Ptr12 dst, int t
       if (to_float) ((float*)dst.p[q])[o] = (float)((const double*)src.p[q])[o];
       else ((double*)dst.p[q])[o] = (double)((const float*)src.p[q])[o];
     }
+}
+
+__global__ void k_scalars_to_float(const double* alpha, const double* dt, float* out) {
+  out[0] = (float)alpha[0];
+  out[1] = (float)alpha[1];
+  out[2] = (float)*dt;
+}
+
+void launch_scalars_to_float(const double* alpha, const double* dt, float* out, cudaStream_t st) {
+  k_scalars_to_float<<<1, 1, 0, st>>>(alpha, dt, out);
 }
 
 void launch_cast_planes(int nplanes, size_t n, const Ptr12& src, const Ptr12& dst, int to_float, cudaStream_t st) {
