@@ -86,6 +86,7 @@ CASES = [
     ("strip_and_hump", _strip_and_hump, {}),
     ("strip_and_hump_no_limiter", _strip_and_hump, {"limiter": 0}),
     ("no_limiter", lambda: S.hump2d(32, 28, seed=63), {"limiter": 0}),
+    ("hump_transmissive", lambda: S.hump2d(40, 33, seed=61, hump_max=0.05, bc=S.OUTFLOW), {}),
 ]
 
 

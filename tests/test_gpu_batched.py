@@ -23,7 +23,8 @@ def _mixed_batch():
     sizes = [(64, 64), (100, 37), (257, 130), (33, 301), (150, 150), (2, 5), (513, 70)]
     out = []
     for k, (nx, ny) in enumerate(sizes):
-        sc = S.hump2d(nx, ny, seed=100 + k, bc=S.PERIODIC if k % 3 == 2 else S.REFLECTIVE)
+        bc = (S.REFLECTIVE, S.OUTFLOW, S.PERIODIC)[k % 3]
+        sc = S.hump2d(nx, ny, seed=100 + k, bc=bc)
         out.append(sc)
     return out
 
