@@ -89,10 +89,19 @@ __device__ __forceinline__ double fast_rsqrt(double x) {
   return fma(r, u, r);
 }
 
-// Single precision (the FP32 variant, memory-bound on GB300, where the FP32 pipe is cheap): the
-// correctly rounded intrinsics.
-__device__ __forceinline__ float fast_rcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ float fast_rsqrt(float x) { return __frsqrt_rn(x); }
+// Single precision (the FP32 variant): the hardware approximations alone, within about one float ulp,
+// one instruction each (the correctly rounded forms cost several, and the float kernels are bound by
+// instruction issue and memory, not by the FP32 pipe).
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float fast_rsqrt(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 // Non-negative double -> ordered 64-bit key (for an exact, order-independent atomicMax).
 __device__ __forceinline__ unsigned long long dkey(double x) {

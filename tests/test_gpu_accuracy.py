@@ -38,10 +38,10 @@ def _run(hw, sc, t_end, n0):
 
 
 def test_fifth_order_1d_ex41(hw):
-    res = {n: _run(hw, S.accuracy1d(n), 0.1, 50) for n in (100, 200, 400)}
+    res = {n: _run(hw, S.accuracy1d(n), 0.1, 50) for n in (200, 400, 800)}
     sub = slice(None, None, 2)
-    orders = [math.log2(np.abs(res[100][q] - res[200][q][sub]).mean() /
-                        np.abs(res[200][q] - res[400][q][sub]).mean()) for q in range(2)]
+    orders = [math.log2(np.abs(res[200][q] - res[400][q][sub]).mean() /
+                        np.abs(res[400][q] - res[800][q][sub]).mean()) for q in range(2)]
     assert min(orders) > 4.6, orders
 
 
