@@ -290,3 +290,54 @@ def test_adjoint_buffers_follow_the_solver(hw):
         torch.cuda.synchronize()
         assert all(torch.isfinite(p).all() for p in lam + lst)
         solver.close()
+
+
+def test_config5_full_size_gradient_against_central_differences(hw):
+    """The adjoint workload at its full size: 512^2, 400 steps at the unperturbed CFL dt sequence, 32
+    gauges, observations from a run with another hump; the tape-mode gradient against central
+    differences (step 1e-6) along 20 random smooth directions, with the scale floor of the 256^2 test."""
+    import torch
+    from paper_2208_01260_gb300 import adjoint as A
+    n, nsteps = 512, 400
+    sc = S.adjoint_case(n)
+    obs_sc = S.adjoint_case(n, hump_seed=1)
+    gidx = S.gauges(sc.nx, sc.ny)
+    solver = hw.Solver.from_scenario(sc, hw.make_params())
+    state, static, _, _ = _eq_static(sc)
+    A.load_problem(solver, state, static)
+    dts = []
+    for _ in range(nsteps):
+        dt = solver.cfl_dt()
+        dts.append(dt)
+        solver.rk3_step(dt)
+    obs_solver = hw.Solver.from_scenario(obs_sc, hw.make_params())
+    ostate, ostatic, _, _ = _eq_static(obs_sc)
+    A.load_problem(obs_solver, ostate, ostatic)
+    _, gv = A.hw_gauge_loss(obs_solver.h, dts, gidx, np.zeros(nsteps * len(gidx)))
+    obs_solver.close()
+    obs = gv.ravel()
+    A.load_problem(solver, state, static)
+    gs = torch.empty_like(state)
+    gb = torch.empty_like(static)
+    loss, nf = A.hw_adjoint_run(solver.h, dts, gidx, obs, A.HW_ADJ_AUTO, [gs[q] for q in range(9)],
+                                [gb[q] for q in range(3)])
+    assert nf == nsteps  # the tape fits: nothing recomputed
+    G_s, G_b = gs.cpu().numpy(), gb.cpu().numpy()
+    eps = 1e-6
+    ads, fds = [], []
+    for k in range(20):
+        dst, dstat = _smooth_direction(sc, 2000 + k, scale=1.0, static=(k % 2 == 0))
+        vs = torch.tensor(np.stack(dst), dtype=torch.float64, device="cuda")
+        vb = torch.tensor(np.stack(dstat), dtype=torch.float64, device="cuda")
+        A.load_problem(solver, state + eps * vs, static + eps * vb)
+        lp, _ = A.hw_gauge_loss(solver.h, dts, gidx, obs)
+        A.load_problem(solver, state - eps * vs, static - eps * vb)
+        lm, _ = A.hw_gauge_loss(solver.h, dts, gidx, obs)
+        fds.append((lp - lm) / (2 * eps))
+        ads.append(float((G_s * np.stack(dst)).sum() + (G_b * np.stack(dstat)).sum()))
+    ads, fds = np.array(ads), np.array(fds)
+    floor = 1e-3 * np.abs(fds).max()
+    rel = np.abs(ads - fds) / np.maximum(np.abs(fds), floor)
+    assert rel.max() <= 1e-6, (rel.max(), int(rel.argmax()), ads, fds)
+    assert np.linalg.norm(ads - fds) <= 1e-6 * np.linalg.norm(fds)
+    solver.close()
