@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(YS_W) k_sweep_y(Dev2DT<R> d, const R* __restri
 }
 
 template <int MODE, bool LINEAR, bool CHAR, class R>
-__global__ void __launch_bounds__(256) k_node2d(Dev2DT<R> d, StageArgsT<R> sa) {
+__global__ void __launch_bounds__(256, 3) k_node2d(Dev2DT<R> d, StageArgsT<R> sa) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y;
   if (i >= d.nx || j >= d.ny) return;
