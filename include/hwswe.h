@@ -32,8 +32,8 @@ extern "C" {
 
 #define HW_OK 0
 #define HW_ERR_ARG (-1)       /* invalid argument, size or pointer kind                          */
-#define HW_ERR_DEPTH (-2)     /* h <= 0 or non-finite state (the scheme has no wet/dry treatment) */
-#define HW_ERR_NONFINITE (-3) /* non-finite input                                                 */
+#define HW_ERR_DEPTH (-2)     /* h <= 0 in the state (the scheme has no wet/dry treatment)        */
+#define HW_ERR_NONFINITE (-3) /* NaN or Inf in the state (depth or velocities)                    */
 #define HW_ERR_CUDA (-4)      /* a CUDA runtime call failed (message in hw_last_error)            */
 #define HW_ERR_TIMEOUT (-5)   /* a bounded device wait gave up                                    */
 #define HW_ERR_STATE (-6)     /* call out of order (e.g. rk3_step before init)                    */
@@ -86,7 +86,8 @@ int hw_destroy(hw_solver* s);
  *   2D: h, hu, hv, b: nx*ny each; deriv[8] = h_x, hu_x, hv_x, h_y, hu_y, hv_y, b_x, b_y.
  *   1D: h, hu, b: nx each (hv ignored, may be NULL); deriv[3] = h_x, hu_x, b_x.
  * Precomputes the parts of the source terms that depend on b only. Returns HW_ERR_DEPTH if any
- * h <= 0 or is not finite (the state is still loaded). Synchronises the stream. */
+ * h <= 0 and HW_ERR_NONFINITE if any h is NaN or infinite (the state is still loaded). Synchronises the
+ * stream. */
 int hw_init(hw_solver* s, const double* h, const double* hu, const double* hv, const double* b,
             const double* const* deriv, int ptr_kind);
 
@@ -98,7 +99,8 @@ int hw_init(hw_solver* s, const double* h, const double* hu, const double* hv, c
 int hw_rhs(hw_solver* s, double* const* out, int ptr_kind);
 
 /* Lax-Friedrichs constants of the current state: alpha[0] = max(|u|+c), alpha[1] = max(|v|+c) (2D;
- * 0 in 1D). Synchronises the stream. HW_ERR_DEPTH if the state has h <= 0 or non-finite values. */
+ * 0 in 1D). Synchronises the stream. HW_ERR_DEPTH if the state has h <= 0, HW_ERR_NONFINITE if it
+ * holds a NaN or an infinite depth or velocity. */
 int hw_alpha(hw_solver* s, double* alpha);
 
 /* CFL time step of the current state (Sec. 4, CFL from params): 2D dt = cfl / (alpha_x/dx +
@@ -142,6 +144,14 @@ int hw_get_base(hw_solver* s, double* const* out, int ptr_kind);
 #define HW_PROF_N 5
 int hw_set_profiling(hw_solver* s, int on);
 int hw_get_profile(hw_solver* s, double* ms, int* launches);
+
+/* Simulated time and the number of steps that advanced it (dt > 0), kept on the device by hw_rk3_step
+ * and hw_advance. Together with hw_get_state / hw_set_state they checkpoint and resume a run: a
+ * solver restored with hw_init (for b), hw_set_state and hw_set_time continues exactly as the
+ * original would (bitwise when the grid spacing is a power of two, so that the layout conversions are
+ * exact). hw_get_time synchronises the stream. */
+int hw_get_time(hw_solver* s, double* t, long long* steps);
+int hw_set_time(hw_solver* s, double t, long long steps);
 
 /* ---------------------------------------------------------------------------------------------
  * Batched form: n independent 2D grids of uneven sizes (all HW_BC_* allowed, shared parameters) that

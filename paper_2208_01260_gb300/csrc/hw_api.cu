@@ -6,10 +6,18 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/hwswe.h"
 #include "hw_internal.h"
 
 namespace {
+
+// NVTX range for the duration of one API call (a no-op unless a profiler is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 thread_local std::string g_err;
 
@@ -272,7 +280,7 @@ static int read_status(hw_solver* s) {
   if (st) {
     CUDA_OK(cudaMemsetAsync(s->status, 0, sizeof(int), s->stream));
     if (st & hw::HW_STATUS_TIMEOUT) return fail(HW_ERR_TIMEOUT, "device wait timed out");
-    if (st & hw::HW_STATUS_DEPTH) return fail(HW_ERR_DEPTH, "non-positive or non-finite depth in the state");
+    if (st & hw::HW_STATUS_DEPTH) return fail(HW_ERR_DEPTH, "non-positive depth in the state");
     return fail(HW_ERR_NONFINITE, "non-finite value");
   }
   return HW_OK;
@@ -280,6 +288,7 @@ static int read_status(hw_solver* s) {
 
 int hw_init(hw_solver* s, const double* h, const double* hu, const double* hv, const double* b,
             const double* const* deriv, int ptr_kind) {
+  Range nvtx_range("hw_init");
   if (!s || !h || !hu || !b || !deriv) return fail(HW_ERR_ARG, "hw_init: null argument");
   if (s->is2d()) {
     if (!hv) return fail(HW_ERR_ARG, "hw_init: hv required in 2D");
@@ -347,6 +356,8 @@ static void enqueue_alpha(hw_solver* s, bool with_dt, double t_end) {
 // One stage: sweeps on the current state (alpha already in s->alpha), node kernel into the other
 // buffer, then swap.
 static void enqueue_stage(hw_solver* s, int k) {
+  static const char* kNames[4] = {"", "stage 1", "stage 2", "stage 3"};
+  Range nvtx_range(kNames[k]);
   double** in = s->state();
   double** out = s->other();
   bind_state(s, in);
@@ -378,6 +389,7 @@ static void enqueue_stage(hw_solver* s, int k) {
 }
 
 int hw_rk3_stage(hw_solver* s, int k, double dt) {
+  Range nvtx_range("hw_rk3_stage");
   if (!s) return fail(HW_ERR_ARG, "hw_rk3_stage: null solver");
   if (!s->inited) return fail(HW_ERR_STATE, "hw_rk3_stage: call hw_init first");
   if (k < 1 || k > 3) return fail(HW_ERR_ARG, "hw_rk3_stage: k must be 1, 2 or 3");
@@ -390,6 +402,7 @@ int hw_rk3_stage(hw_solver* s, int k, double dt) {
 }
 
 int hw_rk3_step(hw_solver* s, double dt) {
+  Range nvtx_range("hw_rk3_step");
   if (!s) return fail(HW_ERR_ARG, "hw_rk3_step: null solver");
   if (!s->inited) return fail(HW_ERR_STATE, "hw_rk3_step: call hw_init first");
   if (!(dt >= 0) || !(dt < 1e300)) return fail(HW_ERR_ARG, "hw_rk3_step: dt must be finite and >= 0");
@@ -415,6 +428,7 @@ static void enqueue_cfl_step(hw_solver* s, double t_end) {
 }
 
 int hw_advance(hw_solver* s, int nsteps, double t_end, int use_graph, double* t_out, int* steps_out) {
+  Range nvtx_range("hw_advance");
   if (!s) return fail(HW_ERR_ARG, "hw_advance: null solver");
   if (!s->inited) return fail(HW_ERR_STATE, "hw_advance: call hw_init first");
   if (nsteps < 0) return fail(HW_ERR_ARG, "hw_advance: nsteps < 0");
@@ -490,6 +504,7 @@ int hw_alpha(hw_solver* s, double* alpha) {
 }
 
 int hw_cfl_dt(hw_solver* s, double* dt_out) {
+  Range nvtx_range("hw_cfl_dt");
   if (!s || !dt_out) return fail(HW_ERR_ARG, "hw_cfl_dt: null argument");
   if (!s->inited) return fail(HW_ERR_STATE, "hw_cfl_dt: call hw_init first");
   enqueue_alpha(s, true, -1.0);
@@ -499,6 +514,7 @@ int hw_cfl_dt(hw_solver* s, double* dt_out) {
 }
 
 int hw_rhs(hw_solver* s, double* const* out, int ptr_kind) {
+  Range nvtx_range("hw_rhs");
   if (!s || !out) return fail(HW_ERR_ARG, "hw_rhs: null argument");
   if (!s->inited) return fail(HW_ERR_STATE, "hw_rhs: call hw_init first");
   if (ptr_kind != HW_HOST && ptr_kind != HW_DEVICE) return fail(HW_ERR_ARG, "hw_rhs: bad ptr_kind");
@@ -574,6 +590,7 @@ static int export_planes(hw_solver* s, double** src_state, double* const* out, i
 }
 
 int hw_get_state(hw_solver* s, double* const* out, int layout, int ptr_kind) {
+  Range nvtx_range("hw_get_state");
   if (!s) return fail(HW_ERR_ARG, "hw_get_state: null solver");
   if (!s->inited) return fail(HW_ERR_STATE, "hw_get_state: call hw_init first");
   if (s->fp32) return export_planes(s, nullptr, out, layout, ptr_kind, s->fstate());
@@ -588,6 +605,7 @@ int hw_get_base(hw_solver* s, double* const* out, int ptr_kind) {
 }
 
 int hw_set_state(hw_solver* s, const double* const* in, int layout, int ptr_kind) {
+  Range nvtx_range("hw_set_state");
   if (!s || !in) return fail(HW_ERR_ARG, "hw_set_state: null argument");
   if (!s->inited) return fail(HW_ERR_STATE, "hw_set_state: call hw_init first (it loads b)");
   if (layout != HW_LAYOUT_PHYSICAL && layout != HW_LAYOUT_EQUILIBRIUM) return fail(HW_ERR_ARG, "bad layout");
@@ -660,6 +678,26 @@ int hw_get_profile(hw_solver* s, double* ms, int* launches) {
   }
   s->recs.clear();
   s->ev_used = 0;
+  return HW_OK;
+}
+
+int hw_get_time(hw_solver* s, double* t, long long* steps) {
+  if (!s || !t || !steps) return fail(HW_ERR_ARG, "hw_get_time: null argument");
+  unsigned long long n = 0;
+  CUDA_OK(cudaMemcpyAsync(t, s->t, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_OK(cudaMemcpyAsync(&n, s->nsteps, sizeof(n), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_OK(cudaStreamSynchronize(s->stream));
+  *steps = (long long)n;
+  return HW_OK;
+}
+
+int hw_set_time(hw_solver* s, double t, long long steps) {
+  if (!s) return fail(HW_ERR_ARG, "hw_set_time: null solver");
+  if (!(t >= 0.0) || !(t < 1e300) || steps < 0) return fail(HW_ERR_ARG, "hw_set_time: bad time or step count");
+  const unsigned long long n = (unsigned long long)steps;
+  CUDA_OK(cudaMemcpyAsync(s->t, &t, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  CUDA_OK(cudaMemcpyAsync(s->nsteps, &n, sizeof(n), cudaMemcpyHostToDevice, s->stream));
+  CUDA_OK(cudaStreamSynchronize(s->stream));
   return HW_OK;
 }
 

@@ -239,16 +239,16 @@ __global__ void __launch_bounds__(256) k_alpha1d(Dev1D d, unsigned long long* am
   int bad = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.nx; i += gridDim.x * blockDim.x) {
     const double h = __ldg(d.S[0] + i) - __ldg(d.stat[0] + i);
-    if (!(h > 0.0) || !(h < 1e300)) { bad = 1; continue; }
+    if (!(h > 0.0) || !(h < 1e300)) { bad |= h == h ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE; continue; }
     const double gh = d.g * h;
     const double a = dabs(__ldg(d.S[1] + i) * fast_rcp(h)) + gh * fast_rsqrt(gh);
-    if (!(a < 1e300)) { bad = 1; continue; }
+    if (!(a < 1e300)) { bad |= HW_STATUS_NONFINITE; continue; }
     k = max(k, dkey(a));
   }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) k = max(k, __shfl_xor_sync(0xffffffffu, k, s));
   if ((threadIdx.x & 31) == 0) atomicMax(amax, k);
-  if (bad) atomicOr(status, HW_STATUS_DEPTH);
+  if (bad) atomicOr(status, bad);
 }
 
 __global__ void k_finish_alpha1d(const unsigned long long* amax, double* alpha, double* dt_out, double cfl,
@@ -275,7 +275,7 @@ __global__ void k_finish_alpha1d(const unsigned long long* amax, double* alpha, 
 __global__ void k_init1d(Dev1D d, PhysIn1D in, int* status) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.nx; i += gridDim.x * blockDim.x) {
     const double h = in.p[0][i], b = in.p[2][i], bx = in.p[5][i];
-    if (!(h > 0.0) || !(h < 1e300)) atomicOr(status, HW_STATUS_DEPTH);
+    if (!(h > 0.0) || !(h < 1e300)) atomicOr(status, h == h ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE);
     d.S[0][i] = h + b;
     d.S[1][i] = in.p[1][i];
     d.S[2][i] = d.dx * (in.p[3][i] + bx);

@@ -110,13 +110,13 @@ __global__ void __launch_bounds__(256) k_alpha2d(Dev2DT<R> d, unsigned long long
     unsigned long long kx = 0, ky = 0;
     for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
       const double h = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
-      if (!(h > 0.0) || !(h < 1e300)) { bad = 1; continue; }
+      if (!(h > 0.0) || !(h < 1e300)) { bad |= h == h ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE; continue; }
       const double rh = fast_rcp(h);
       const double gh = d.g * h;
       const double c = gh * fast_rsqrt(gh);
       const double u = __ldg(d.S[1] + o) * rh, v = __ldg(d.S[2] + o) * rh;
       const double ax = dabs(u) + c, ay = dabs(v) + c;
-      if (!(ax < 1e300) || !(ay < 1e300)) { bad = 1; continue; }
+      if (!(ax < 1e300) || !(ay < 1e300)) { bad |= HW_STATUS_NONFINITE; continue; }
       kx = max(kx, dkey(ax));
       ky = max(ky, dkey(ay));
     }
@@ -134,13 +134,13 @@ __global__ void __launch_bounds__(256) k_alpha2d(Dev2DT<R> d, unsigned long long
     float mx = 0.0f, my = 0.0f;
     for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
       const float h = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
-      if (!(h > 0.0f) || !(h < 3e38f)) { bad = 1; continue; }
+      if (!(h > 0.0f) || !(h < 3e38f)) { bad |= h == h ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE; continue; }
       const float rh = fast_rcp(h);
       const float gh = d.g * h;
       const float c = gh * fast_rsqrt(gh);
       const float u = __ldg(d.S[1] + o) * rh, v = __ldg(d.S[2] + o) * rh;
       const float ax = fabsf(u) + c, ay = fabsf(v) + c;
-      if (!(ax < 3e38f) || !(ay < 3e38f)) { bad = 1; continue; }
+      if (!(ax < 3e38f) || !(ay < 3e38f)) { bad |= HW_STATUS_NONFINITE; continue; }
       mx = fmaxf(mx, ax);
       my = fmaxf(my, ay);
     }
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256) k_alpha2d(Dev2DT<R> d, unsigned long long
       atomicMax(amax + 1, dkey((double)my));
     }
   }
-  if (bad) atomicOr(status, HW_STATUS_DEPTH);
+  if (bad) atomicOr(status, bad);
 }
 
 // alpha keys -> doubles; dt = cfl / (alpha_x/dx + alpha_y/dy), optionally clipped to t_end - t.
@@ -189,7 +189,7 @@ __global__ void k_init2d(Dev2D d, PhysIn in, int* status) {
   const size_t n = (size_t)d.nx * d.ny;
   for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
     const double h = in.p[0][o], b = in.p[3][o], bx = in.p[10][o], by = in.p[11][o];
-    if (!(h > 0.0) || !(h < 1e300)) atomicOr(status, HW_STATUS_DEPTH);
+    if (!(h > 0.0) || !(h < 1e300)) atomicOr(status, h == h ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE);
     d.S[0][o] = h + b;
     d.S[1][o] = in.p[1][o];
     d.S[2][o] = in.p[2][o];
