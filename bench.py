@@ -60,9 +60,9 @@ PEAK_FP64_OPS = SMS * DFMA_PER_SM_CLK * SM_GHZ * 1e9
 # launch at 2048x1024, the state and interface planes above L2), valid only for the kernel sources they
 # were taken on (sources_sha); scaled to a launch by its units (traffic is proportional to them).
 TRAFFIC = {
-    "sweep_x": {"bytes_per_unit": 222.35, "sha": "02854691bbee81aa"},
-    "sweep_y": {"bytes_per_unit": 230.33, "sha": "02854691bbee81aa"},
-    "node": {"bytes_per_unit": 441.74, "sha": "02854691bbee81aa"},
+    "sweep_x": {"bytes_per_unit": 222.68, "sha": "d06bea61b16abb9b"},
+    "sweep_y": {"bytes_per_unit": 230.34, "sha": "d06bea61b16abb9b"},
+    "node": {"bytes_per_unit": 442.63, "sha": "d06bea61b16abb9b"},
 }
 STATE_BYTES = 9 * NX * NY * 8
 

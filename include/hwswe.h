@@ -148,8 +148,8 @@ int hw_get_profile(hw_solver* s, double* ms, int* launches);
 /* Simulated time and the number of steps that advanced it (dt > 0), kept on the device by hw_rk3_step
  * and hw_advance. Together with hw_get_state / hw_set_state they checkpoint and resume a run: a
  * solver restored with hw_init (for b), hw_set_state and hw_set_time continues exactly as the
- * original would (bitwise when the grid spacing is a power of two, so that the layout conversions are
- * exact). hw_get_time synchronises the stream. */
+ * original would (bitwise with the equilibrium layout when the grid spacings are powers of two, so
+ * that the derivative scalings are exact). hw_get_time synchronises the stream. */
 int hw_get_time(hw_solver* s, double* t, long long* steps);
 int hw_set_time(hw_solver* s, double t, long long steps);
 

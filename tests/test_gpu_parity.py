@@ -279,17 +279,18 @@ def test_errors(hw):
 
 
 def test_checkpoint_and_resume_is_bitwise(hw):
-    """Checkpoint (state, time, step count) after 7 steps, restore into a fresh solver, continue: equal
-    bit for bit to the uninterrupted run (grid spacing 2^-6, so the layout conversions are exact)."""
+    """Checkpoint (state in the equilibrium layout, time, step count) after 7 steps, restore into a fresh
+    solver, continue: equal bit for bit to the uninterrupted run (grid spacing 2^-6, so the derivative
+    scalings are exact; the physical layout's h = eta - b would round)."""
     sc = S.hump2d(64, 64, seed=47)
     a = solver(hw, sc)
     a.advance(7, use_graph=False)
-    st = a.state(hw.HW_LAYOUT_PHYSICAL)
+    st = a.state(hw.HW_LAYOUT_EQUILIBRIUM)
     t, n = hw.hw_get_time(a.h)
     assert n == 7 and t > 0
     a.advance(5, t_end=10.0, use_graph=False)
     b = solver(hw, sc)
-    hw.hw_set_state(b.h, st, hw.HW_LAYOUT_PHYSICAL)
+    hw.hw_set_state(b.h, st, hw.HW_LAYOUT_EQUILIBRIUM)
     hw.hw_set_time(b.h, t, n)
     b.advance(5, t_end=10.0, use_graph=False)
     for x, y in zip(a.state(), b.state()):
