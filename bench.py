@@ -542,17 +542,24 @@ def main():
             "roofline": roofline, "kernels": kernels, "ms_per_step_profiled": ms_prof / args.steps,
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clk.summary(), "e2e": e2e}
+    # secondary measurements: a failure is reported in the line instead of losing the headline
+    def extra(key, fn):
+        try:
+            line[key] = fn()
+        except Exception as exc:  # noqa: BLE001
+            line[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     if args.batched_steps > 0 and (NX, NY) == (2048, 2048):
         solver.close()
-        line["batched"] = batched_compare(args.batched_steps)
+        extra("batched", lambda: batched_compare(args.batched_steps))
     if args.adjoint_steps > 0 and (NX, NY) == (2048, 2048):
-        line["adjoint"] = adjoint_cost(nsteps=args.adjoint_steps)
+        extra("adjoint", lambda: adjoint_cost(nsteps=args.adjoint_steps))
     if args.fp32_steps > 0:
-        line["fp32"] = fp32_variant(args.fp32_steps)
+        extra("fp32", lambda: fp32_variant(args.fp32_steps))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, desc, threads, el = oracle_rate()
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
-                                "seconds": el}
+        def cpu():
+            rate, desc, threads, el = oracle_rate()
+            return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc, "seconds": el}
+        extra("cpu_baseline", cpu)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
