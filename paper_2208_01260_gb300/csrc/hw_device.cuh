@@ -16,6 +16,9 @@
 //     p_1 = s_2 s_3, p_2 = s_1 s_3, p_3 = s_1 s_2, s_l = (beta_l + eps)^2, equal to eq. (GHYZZ).
 //   * Reciprocals and square roots use the hardware approximation plus one cubically convergent
 //     Newton step (Householder order 3 for 1/x and for 1/sqrt(x)), accurate to a few ulp.
+//   * The functions are templates on the working precision R: double for the scheme, float for the
+//     single-precision variant, which uses the hardware approximations alone and normalises the
+//     weights by the smallest beta_l + eps (products of four of them overflow float on large jumps).
 #pragma once
 #include <cstdint>
 #include <type_traits>

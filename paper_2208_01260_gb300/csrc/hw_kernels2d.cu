@@ -7,7 +7,8 @@
 //   k_node2d    eq. (swe-form-2d-dis) (source signs read as '-'), the HWENO limiter of Sec. 2.2
 //               applied dimension by dimension, and the SSP-RK3 combination of eq. (RK)
 // Interface values go through global memory: the FP64 pipe, not memory, bounds this scheme on
-// GB300, so each interface is computed exactly once.
+// GB300, so each interface is computed exactly once. Every kernel is instantiated for double and for
+// the single-precision variant (float planes and constants).
 #include "hw_stencil2d.cuh"
 
 namespace hw {
