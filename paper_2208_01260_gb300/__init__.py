@@ -7,6 +7,17 @@ library ``libhwswe.so`` built from ``csrc/``; there is no CPU fallback: if the l
 the first call raises.
 
 Scheme: Zhao & Zhang, arXiv:2208.01260 (Sec. 2 one-dimensional, Sec. 3 two-dimensional).
+
+Typical use::
+
+    import paper_2208_01260_gb300 as hw
+    from paper_2208_01260_gb300 import scenarios as S
+    s = hw.Solver.from_scenario(S.bumps2d(512, 256), hw.make_params())   # FP64; precision=hw.HW_FP32
+    t, n = s.advance(10 ** 6, t_end=0.1)                                # CFL steps, CUDA graph
+    eta, m, w = s.state()[:3]                                           # equilibrium layout
+
+``BatchedSolver`` advances many grids together; ``adjoint`` holds the gradient of a gauge misfit
+(``GaugeMisfit`` is a torch.autograd.Function); ``autotune`` picks the batched tile shapes.
 """
 from __future__ import annotations
 
@@ -17,7 +28,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 __all__ = [
-    "HW_OK", "HW_BC_PERIODIC", "HW_BC_REFLECTIVE", "HW_BC_OUTFLOW", "HW_HOST", "HW_DEVICE", "HW_LAYOUT_PHYSICAL",
+    "HW_OK", "HW_BC_PERIODIC", "HW_BC_REFLECTIVE", "HW_BC_OUTFLOW", "HW_FP64", "HW_FP32", "HW_HOST", "HW_DEVICE",
+    "HW_LAYOUT_PHYSICAL",
     "HW_LAYOUT_EQUILIBRIUM", "HwError", "hw_grid", "hw_params", "lib", "make_grid", "make_params",
     "hw_create", "hw_destroy", "hw_init", "hw_rhs", "hw_alpha", "hw_cfl_dt", "hw_rk3_step", "hw_rk3_stage",
     "hw_advance", "hw_get_state", "hw_set_state", "hw_get_base", "hw_sync", "hw_version", "Solver",
