@@ -60,9 +60,9 @@ PEAK_FP64_OPS = SMS * DFMA_PER_SM_CLK * SM_GHZ * 1e9
 # launch at 2048x1024, the state and interface planes above L2), valid only for the kernel sources they
 # were taken on (sources_sha); scaled to a launch by its units (traffic is proportional to them).
 TRAFFIC = {
-    "sweep_x": {"bytes_per_unit": 222.68, "sha": "eb53e4b4fbcb485e"},
-    "sweep_y": {"bytes_per_unit": 230.34, "sha": "eb53e4b4fbcb485e"},
-    "node": {"bytes_per_unit": 442.63, "sha": "eb53e4b4fbcb485e"},
+    "sweep_x": {"bytes_per_unit": 222.22, "sha": "f59f39eaa92897ad"},
+    "sweep_y": {"bytes_per_unit": 230.56, "sha": "f59f39eaa92897ad"},
+    "node": {"bytes_per_unit": 442.69, "sha": "f59f39eaa92897ad"},
 }
 STATE_BYTES = 9 * NX * NY * 8
 

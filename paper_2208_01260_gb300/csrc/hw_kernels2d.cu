@@ -16,7 +16,7 @@ namespace hw {
 // ---------------------------------------------------------------------------------------------
 // x-sweep: one block = XS_T consecutive x-interfaces k (between nodes k-1 and k) of one row.
 // ---------------------------------------------------------------------------------------------
-constexpr int XS_T = 128;
+constexpr int XS_T = 192;
 constexpr int XS_N = XS_T + 3;
 
 template <bool LINEAR, bool CHAR, class R>

@@ -1,8 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
 
-Sizes span several tiles of every kernel (x-sweep 128 interfaces, y-sweep 64x64, node 32x8) with
-ragged tails; the full-size 2048^2 workload is checked on sampled nodes the oracle computes one by
-one. See tests/_parity.py for the tolerances.
+Sizes span several tiles of every kernel (x-sweep 192 interfaces per row tile, y-sweep 32 columns per
+block, node 32x8) with ragged tails; the full-size 2048^2 workload is checked on sampled nodes the
+oracle computes one by one. See tests/_parity.py for the tolerances.
 """
 import math
 
@@ -42,6 +42,7 @@ CASES_2D = [
     ("linear", lambda: S.hump2d(40, 37, seed=24), {"linear_weights": 1}),
     ("tiny_eps", lambda: S.bumps2d(66, 33, strip=1e-3), {"eps_w": 1e-10}),
     ("min_grid", lambda: S.hump2d(2, 3, seed=25), {}),
+    ("three_x_tiles", lambda: S.hump2d(450, 40, seed=26), {}),
 ]
 
 
