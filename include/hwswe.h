@@ -123,7 +123,11 @@ int hw_rk3_stage(hw_solver* s, int k, double dt);
  * time advanced and *steps_out (may be NULL) the steps taken; synchronises the stream. */
 int hw_advance(hw_solver* s, int nsteps, double t_end, int use_graph, double* t_out, int* steps_out);
 
-/* Read / write the state. layout is HW_LAYOUT_*; out/in hold 9 (2D) or 4 (1D) planes. */
+/* Read / write the state (the variables of Sec. 2 / Sec. 3: the physical layout h, hu, hv and their
+ * derivatives, or the equilibrium layout eta = h + b, m, w and theirs). layout is HW_LAYOUT_*; out/in
+ * hold 9 (2D) or 4 (1D) caller-owned planes of nx*ny doubles, host or device per ptr_kind; the
+ * solver's buffers are written by a set. Synchronous for HW_HOST. HW_ERR_ARG on null planes or a bad
+ * layout, HW_ERR_STATE before hw_init. */
 int hw_get_state(hw_solver* s, double* const* out, int layout, int ptr_kind);
 int hw_set_state(hw_solver* s, const double* const* in, int layout, int ptr_kind);
 
@@ -131,7 +135,7 @@ int hw_set_state(hw_solver* s, const double* const* in, int layout, int ptr_kind
  * equilibrium layout; out holds 9 (2D) or 4 (1D) planes. */
 int hw_get_base(hw_solver* s, double* const* out, int ptr_kind);
 
-/* Per-kernel timing of the hot path. While profiling is on, every kernel the solver launches is
+/* Per-kernel timing of the hot path (no counterpart in the paper). While profiling is on, every kernel the solver launches is
  * bracketed by CUDA events on the solver's stream and hw_advance runs without a CUDA graph.
  * hw_get_profile waits for the stream, returns per kernel class the accumulated device time in ms and
  * the launch count, then clears them. Classes (HW_PROF_*): alpha reduction, x-sweep, y-sweep, node
@@ -146,7 +150,7 @@ int hw_set_profiling(hw_solver* s, int on);
 int hw_get_profile(hw_solver* s, double* ms, int* launches);
 
 /* Simulated time and the number of steps that advanced it (dt > 0), kept on the device by hw_rk3_step
- * and hw_advance. Together with hw_get_state / hw_set_state they checkpoint and resume a run: a
+ * and hw_advance (no counterpart in the paper; t is the time of the run of Sec. 4's examples). Together with hw_get_state / hw_set_state they checkpoint and resume a run: a
  * solver restored with hw_init (for b), hw_set_state and hw_set_time continues exactly as the
  * original would (bitwise with the equilibrium layout when the grid spacings are powers of two, so
  * that the derivative scalings are exact). hw_get_time synchronises the stream. */
@@ -154,8 +158,9 @@ int hw_get_time(hw_solver* s, double* t, long long* steps);
 int hw_set_time(hw_solver* s, double t, long long steps);
 
 /* ---------------------------------------------------------------------------------------------
- * Batched form: n independent 2D grids of uneven sizes (all HW_BC_* allowed, shared parameters) that
- * advance together, each with its own CFL time step computed on the device (Sec. 4: dt from the CFL
+ * Batched form (no counterpart in the paper, which runs one grid at a time): n independent 2D grids of
+ * uneven sizes (all HW_BC_* allowed, shared parameters, HW_FP64), each advanced by the scheme of Sec. 3
+ * with SSP-RK3 (Sec. 2.2 eq. RK), together, each with its own CFL time step computed on the device (Sec. 4: dt from the CFL
  * number and alpha of that grid). Each phase of an RK stage is one launch over the tiles of all grids,
  * and two steps run from one CUDA graph. Every grid's result equals a single-grid solver's
  * (hw_create + hw_advance) to rounding; tile shapes do not change it at all.
