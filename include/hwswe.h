@@ -160,8 +160,8 @@ int hw_set_time(hw_solver* s, double t, long long steps);
 /* ---------------------------------------------------------------------------------------------
  * Batched form (no counterpart in the paper, which runs one grid at a time): n independent 2D grids of
  * uneven sizes (all HW_BC_* allowed, shared parameters, HW_FP64), each advanced by the scheme of Sec. 3
- * with SSP-RK3 (Sec. 2.2 eq. RK), together, each with its own CFL time step computed on the device (Sec. 4: dt from the CFL
- * number and alpha of that grid). Each phase of an RK stage is one launch over the tiles of all grids,
+ * with SSP-RK3 (Sec. 2.2 eq. RK), together, each with its own CFL time step computed on the device
+ * (Sec. 4: dt from the CFL number and alpha of that grid). Each phase of an RK stage is one launch over the tiles of all grids,
  * and two steps run from one CUDA graph. Every grid's result equals a single-grid solver's
  * (hw_create + hw_advance) to rounding; tile shapes do not change it at all.
  * ------------------------------------------------------------------------------------------- */
