@@ -216,16 +216,19 @@ def oracle_rate(seconds_budget=60.0):
     return NX * NY * stages / elapsed, desc, threads, elapsed
 
 
-def batched_compare(steps, n_inst=512):
-    """Config 4: n_inst grids with nx, ny log-uniform in [64, 1024] on [0,1]^2, reflective, seeded
-    bathymetry and surface hump, each at its own CFL dt. Aggregate point-updates/s of the batched form
-    (one launch per phase over all grids, CUDA graph) and of the plain loop (one single-grid solver per
-    instance advanced one step at a time: with the library's cfl_dt() and rk3_step(dt), and, as a
-    stronger baseline, with the device-side dt of hw_advance)."""
+def batched_compare(steps, n_inst=512, fixed=None):
+    """Config 4: n_inst grids with nx, ny log-uniform in [64, 1024] (or all of size `fixed`) on
+    [0,1]^2, reflective, seeded bathymetry and surface hump, each at its own CFL dt. Aggregate
+    point-updates/s of the batched form (one launch per phase over all grids, CUDA graph) and of the
+    plain loop (one single-grid solver per instance advanced one step at a time: with the library's
+    cfl_dt() and rk3_step(dt), and, as a stronger baseline, with the device-side dt of hw_advance)."""
     import torch
     import paper_2208_01260_gb300 as hw
     from paper_2208_01260_gb300 import scenarios as S
-    nxs, nys = S.batch_sizes(n_inst)
+    if fixed:
+        nxs, nys = np.full(n_inst, fixed[0]), np.full(n_inst, fixed[1])
+    else:
+        nxs, nys = S.batch_sizes(n_inst)
     scs = [S.batch_scenario(i, int(nxs[i]), int(nys[i])) for i in range(n_inst)]
     pts = float(sum(int(a) * int(b) for a, b in zip(nxs, nys)))
     stream = torch.cuda.current_stream()
@@ -556,6 +559,9 @@ def main():
     if args.batched_steps > 0 and (NX, NY) == (2048, 2048):
         solver.close()
         extra("batched", lambda: batched_compare(args.batched_steps))
+        # the regime the batched form is for: grids too small to fill the GPU one launch at a time
+        extra("batched_small_grids", lambda: dict(batched_compare(args.batched_steps, n_inst=1024, fixed=(64, 64)),
+                                                  workload="1024 grids of 64x64 (not config 4)"))
     if args.adjoint_steps > 0 and (NX, NY) == (2048, 2048):
         extra("adjoint", lambda: adjoint_cost(nsteps=args.adjoint_steps))
     if args.fp32_steps > 0:
