@@ -329,7 +329,7 @@ __device__ __forceinline__ void interface_values_rev(const double* r0, int sstep
   lic2 += 2.0 * cb * Bsum * lBs;
   // per side and field: weighted values and the source with the same weights (projections recomputed)
   double lupc = 0.0, lumc = 0.0, leps13 = 0.0;
-#pragma unroll 1
+#pragma unroll
   for (int side = 0; side < 2; ++side) {
     const int fo = side == 0 ? R_FP : R_FM, go = side == 0 ? R_GP : R_GM;
     const double sg = side == 0 ? 1.0 : -1.0;
@@ -360,6 +360,7 @@ __device__ __forceinline__ void interface_values_rev(const double* r0, int sstep
       lr(sl, go + cn) = fma(kg, lout[6 + cn], sg * (-lp[0][t] + lp[2][t]));
       lr(sl, go + ct) = fma(kg, lout[6 + ct], sg * lp[1][t]);
     }
+    asm volatile("" ::: "memory");  // keep the two sides apart in the schedule (register pressure)
   }
   // eigen quantities
   lun += lupc + lumc;
