@@ -383,6 +383,7 @@ __global__ void __launch_bounds__(256) k_adj_limiter(AdjDev A) {
   const double rs = fast_rsqrt(gh), c = gh * rs, ic2 = 0.5 * rs;
   double lu = 0.0, lv = 0.0, lc = 0.0, lic2 = 0.0, lgh = 0.0;
   double l0[12] = {};
+#pragma unroll
   for (int dir = 0; dir < 2; ++dir) {
     double lo[3];
 #pragma unroll
@@ -412,6 +413,7 @@ __global__ void __launch_bounds__(256) k_adj_limiter(AdjDev A) {
     }
     scatter_node(A, im, jm, lm12, true, false);
     scatter_node(A, ip, jp, lp12, true, false);
+    asm volatile("" ::: "memory");  // one direction's data live at a time
   }
   // node eigen quantities: u = m/h, v = w/h, c = gh rs, ic2 = rs/2, rs = gh^-1/2, gh = g h, h = eta - b
   const double lrs = 0.5 * lic2 + gh * lc;
