@@ -313,7 +313,7 @@ def fp32_variant(steps, warmup=3):
         tot, n = prof[k]
         if n == 0:
             continue
-        nl = n if k != "alpha" else n // 2
+        nl = n if k != "alpha" else prof["sweep_x"][1]
         avg_s = tot / nl * 1e-3
         gbs = ALGO_BYTES_FP32[k] * UNITS_PER_LAUNCH[k] / avg_s / 1e9
         kernels[k] = {"ms_avg": avg_s * 1e3, "algorithmic_gbs": gbs, "hbm_frac": gbs / hbm}
@@ -492,7 +492,7 @@ def main():
         tot, n = prof[k]
         if n == 0:
             continue
-        nl = n if k != "alpha" else n // 2  # the alpha class counts reduction + finish launches
+        nl = n if k != "alpha" else prof["sweep_x"][1]  # alpha: its kernels once per stage
         avg_s = tot / nl * 1e-3
         units = UNITS_PER_LAUNCH[k]
         tf = ALGO[k]["flops"] * units / avg_s / 1e12

@@ -757,7 +757,7 @@ int forward_record(const hw::SolverView& v, AdjBuffers* B, const StepTape& T, do
     for (int c = 0; c < 3; ++c) { d.X[3 + c] = T.dbx[k - 1][c]; d.Y[3 + c] = T.dby[k - 1][c]; }
     d.X[0] = T.fx[k - 1];
     d.Y[0] = T.fy[k - 1];
-    double* amax = B->lalpha;  // scratch for the keys (reset below)
+    double* amax = B->lalpha + 5;  // scratch for the reduction keys (3 slots)
     hw::launch_alpha2d(d, (unsigned long long*)amax, (int*)(B->lalpha + 2), st);
     hw::launch_finish_alpha2d(d, (const unsigned long long*)amax, T.alpha + 2 * (k - 1), nullptr, v.params->cfl,
                               nullptr, -1.0, st);

@@ -84,7 +84,7 @@ struct hw_solver {
   // profiling: event pairs recorded around launches, resolved in hw_get_profile
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
-  struct Rec { int cls; cudaEvent_t a, b; };
+  struct Rec { int cls, kernels; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   size_t ev_used = 0;
 
@@ -95,9 +95,9 @@ struct hw_solver {
   bool is2d() const { return grid.dim == 2; }
 };
 
-// Bracket the launches enqueued by fn() with a pair of events when profiling.
+// Bracket the launches enqueued by fn() (kernels of them) with a pair of events when profiling.
 template <class Fn>
-static void timed(hw_solver* s, int cls, Fn&& fn) {
+static void timed(hw_solver* s, int cls, Fn&& fn, int kernels = 1) {
   if (!s->profiling) { fn(); return; }
   while (s->ev_pool.size() < s->ev_used + 2) {
     cudaEvent_t e;
@@ -108,7 +108,7 @@ static void timed(hw_solver* s, int cls, Fn&& fn) {
   cudaEventRecord(a, s->stream);
   fn();
   cudaEventRecord(b, s->stream);
-  s->recs.push_back({cls, a, b});
+  s->recs.push_back({cls, kernels, a, b});
 }
 
 static int dalloc(hw_solver* s, double** p, size_t count) {
@@ -184,12 +184,12 @@ int hw_create(const hw_grid* grid, const hw_params* params, void* cuda_stream, h
   double* misc = nullptr;
   A(&misc, 16);
   if (rc != HW_OK) { hw_destroy(s); return rc; }
-  s->amax = (unsigned long long*)misc;
-  s->alpha = misc + 2;
-  s->dt = misc + 4;  // dt[0] = step, dt[1] = time after the step (written by the CFL kernel)
-  s->t = misc + 6;
-  s->status = (int*)(misc + 7);
-  s->nsteps = (unsigned long long*)(misc + 8);
+  s->amax = (unsigned long long*)misc;  // 3 slots: alpha_x, alpha_y keys and the coarse pass's maxima
+  s->alpha = misc + 3;
+  s->dt = misc + 5;  // dt[0] = step, dt[1] = time after the step (written by the CFL kernel)
+  s->t = misc + 7;
+  s->status = (int*)(misc + 8);
+  s->nsteps = (unsigned long long*)(misc + 9);
 
   const double dx = (grid->x1 - grid->x0) / nx;
   if (grid->dim == 2) {
@@ -350,7 +350,7 @@ static void enqueue_alpha(hw_solver* s, bool with_dt, double t_end) {
       hw::launch_finish_alpha1d(s->d1, s->amax, s->alpha, with_dt ? s->dt : nullptr, s->params.cfl,
                                 with_dt ? s->t : nullptr, t_end, s->stream);
     }
-  });
+  }, s->is2d() && !s->fp32 ? 3 : 2);  // reduction (two passes in 2D double) and finish
 }
 
 // One stage: sweeps on the current state (alpha already in s->alpha), node kernel into the other
@@ -673,8 +673,7 @@ int hw_get_profile(hw_solver* s, double* ms, int* launches) {
     float t = 0.f;
     CUDA_OK(cudaEventElapsedTime(&t, r.a, r.b));
     ms[r.cls] += t;
-    // launches per record: alpha = reduction + finish; others one kernel each
-    launches[r.cls] += r.cls == HW_PROF_ALPHA ? 2 : 1;
+    launches[r.cls] += r.kernels;
   }
   s->recs.clear();
   s->ev_used = 0;

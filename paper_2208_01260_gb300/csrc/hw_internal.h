@@ -81,6 +81,7 @@ struct PhysIn1D {
 
 // launchers (hw_kernels2d.cu)
 int set_kernel_attributes2d();
+// amax: 3 device slots (the alpha_x and alpha_y keys, and scratch of the reduction); cleared here.
 void launch_alpha2d(const Dev2D& d, unsigned long long* amax, int* status, cudaStream_t st);
 void launch_finish_alpha2d(const Dev2D& d, const unsigned long long* amax, double* alpha, double* dt_out,
                            double cfl, const double* t_now, double t_end, cudaStream_t st);

@@ -1,6 +1,6 @@
 // 2D kernels of the well-balanced fifth-order FD HWENO scheme (Zhao & Zhang, arXiv:2208.01260,
 // Sec. 3) for sm_103a. One RK stage is four launches on the solver's stream:
-//   k_alpha2d   global Lax-Friedrichs constants alpha_x = max(|u|+c), alpha_y = max(|v|+c)
+//   k_alpha2d_* global Lax-Friedrichs constants alpha_x = max(|u|+c), alpha_y = max(|v|+c)
 //   k_sweep_x   x-interfaces: Sec. 2.1 Steps 1-2 along x for (F1, Phi1, tilde-b, tilde-B1) and the
 //               mixed term Psi1 of eq. (mixed)
 //   k_sweep_y   y-interfaces: Steps 1-2 along y for (F2, Psi2, bar-b, bar-B2) and the mixed Phi2
@@ -102,58 +102,131 @@ __global__ void __launch_bounds__(256, 3) k_node2d(Dev2DT<R> d, StageArgsT<R> sa
 // ---------------------------------------------------------------------------------------------
 // alpha_x, alpha_y = max over nodes of |u| + c, |v| + c (exact max via ordered 64-bit keys),
 // plus a status flag for non-finite or non-positive depth.
+// In double, two passes keep the FP64 pipe out of most nodes: a coarse pass evaluates |u| + c in float
+// (from the depth formed in double, converted by integer operations) and reduces the float maxima M; an
+// exact pass re-evaluates every node in float and computes the double value only where the float one is
+// within a relative 1e-5 of M (or cannot be trusted: values outside float's range, NaN, infinity). The
+// float values are within about 1e-6 of the double ones, so the node attaining the double maximum is
+// always re-evaluated and the result is the exact double maximum (a re-evaluated node contributes to
+// both directions, which is harmless: no node's value exceeds a direction's maximum).
 // ---------------------------------------------------------------------------------------------
-template <class R>
-__global__ void __launch_bounds__(256) k_alpha2d(Dev2DT<R> d, unsigned long long* amax, int* status) {
+// double -> float by truncation with integer operations (the FP64 pipe stays free): relative error
+// below 2^-23 for values in float's normal range. Values below it become 0 (tiny is true); values
+// above it, infinities and NaN set huge.
+__device__ __forceinline__ float d2f_trunc(double x, bool& tiny, bool& huge) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  tiny = e <= 1023 - 127;
+  huge = e >= 1023 + 128;
+  const unsigned int sign = (unsigned int)((unsigned long long)b >> 32) & 0x80000000u;
+  const unsigned int f = sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)((b >> 29) & 0x7fffff);
+  return tiny ? 0.0f : __uint_as_float(f);
+}
+
+// Float estimates of |u| + c and |v| + c at node o from the depth formed in double. exact: the node
+// needs the double evaluation regardless (a depth or momentum outside float's range, NaN, infinity);
+// neg: the depth is negative.
+__device__ __forceinline__ void alpha_coarse(const Dev2D& d, size_t o, float& ax, float& ay, bool& exact,
+                                             bool& neg) {
+  const double hd = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
+  bool t0, h0, t1, h1, t2, h2;
+  const float h = d2f_trunc(hd, t0, h0);
+  const float m = d2f_trunc(__ldg(d.S[1] + o), t1, h1);
+  const float w = d2f_trunc(__ldg(d.S[2] + o), t2, h2);
+  exact = t0 || h0 || h1 || h2;
+  neg = h < 0.0f;
+  const float rh = fast_rcp(h);
+  const float gh = (float)d.g * h;
+  const float c = gh * fast_rsqrt(gh);
+  ax = fabsf(m) * rh + c;
+  ay = fabsf(w) * rh + c;
+}
+
+__global__ void __launch_bounds__(256) k_alpha2d_coarse(Dev2D d, unsigned long long* amax, int* status) {
+  const size_t n = (size_t)d.nx * d.ny;
+  float mx = 0.0f, my = 0.0f;
+  int bad = 0;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    float ax, ay;
+    bool exact, neg;
+    alpha_coarse(d, o, ax, ay, exact, neg);
+    if (exact) continue;  // the exact pass evaluates (and, if need be, flags) this node
+    if (neg) { bad |= HW_STATUS_DEPTH; continue; }
+    mx = fmaxf(mx, ax);
+    my = fmaxf(my, ay);
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+    my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, s));
+  }
+  // non-negative floats order as their bit patterns; both maxima share the third 64-bit slot
+  unsigned int* m32 = reinterpret_cast<unsigned int*>(amax + 2);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(m32, __float_as_uint(mx));
+    atomicMax(m32 + 1, __float_as_uint(my));
+  }
+  if (bad) atomicOr(status, bad);
+}
+
+__global__ void __launch_bounds__(256) k_alpha2d_exact(Dev2D d, unsigned long long* amax, int* status) {
+  const size_t n = (size_t)d.nx * d.ny;
+  const unsigned int* m32 = reinterpret_cast<const unsigned int*>(amax + 2);
+  const float tx = __uint_as_float(m32[0]) * (1.0f - 1e-5f), ty = __uint_as_float(m32[1]) * (1.0f - 1e-5f);
+  unsigned long long kx = 0, ky = 0;
+  int bad = 0;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    float fx, fy;
+    bool exact, neg;
+    alpha_coarse(d, o, fx, fy, exact, neg);
+    if (!exact && (neg || (fx < tx && fy < ty))) continue;
+    const double hd = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
+    if (!(hd > 0.0) || !(hd < 1e300)) { bad |= hd == hd ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE; continue; }
+    const double rh = fast_rcp(hd);
+    const double gh = d.g * hd;
+    const double c = gh * fast_rsqrt(gh);
+    const double ax = dabs(__ldg(d.S[1] + o) * rh) + c, ay = dabs(__ldg(d.S[2] + o) * rh) + c;
+    if (!(ax < 1e300) || !(ay < 1e300)) { bad |= HW_STATUS_NONFINITE; continue; }
+    kx = max(kx, dkey(ax));
+    ky = max(ky, dkey(ay));
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    kx = max(kx, __shfl_xor_sync(0xffffffffu, kx, s));
+    ky = max(ky, __shfl_xor_sync(0xffffffffu, ky, s));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (kx) atomicMax(amax, kx);
+    if (ky) atomicMax(amax + 1, ky);
+  }
+  if (bad) atomicOr(status, bad);
+}
+
+// Single precision: the maximum in float, widened to a double key once per warp.
+__global__ void __launch_bounds__(256) k_alpha2d_f32(Dev2DT<float> d, unsigned long long* amax, int* status) {
   int bad = 0;
   const size_t n = (size_t)d.nx * d.ny;
-  if constexpr (std::is_same<R, double>::value) {
-    unsigned long long kx = 0, ky = 0;
-    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
-      const double h = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
-      if (!(h > 0.0) || !(h < 1e300)) { bad |= h == h ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE; continue; }
-      const double rh = fast_rcp(h);
-      const double gh = d.g * h;
-      const double c = gh * fast_rsqrt(gh);
-      const double u = __ldg(d.S[1] + o) * rh, v = __ldg(d.S[2] + o) * rh;
-      const double ax = dabs(u) + c, ay = dabs(v) + c;
-      if (!(ax < 1e300) || !(ay < 1e300)) { bad |= HW_STATUS_NONFINITE; continue; }
-      kx = max(kx, dkey(ax));
-      ky = max(ky, dkey(ay));
-    }
+  float mx = 0.0f, my = 0.0f;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const float h = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
+    if (!(h > 0.0f) || !(h < 3e38f)) { bad |= h == h ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE; continue; }
+    const float rh = fast_rcp(h);
+    const float gh = d.g * h;
+    const float c = gh * fast_rsqrt(gh);
+    const float u = __ldg(d.S[1] + o) * rh, v = __ldg(d.S[2] + o) * rh;
+    const float ax = fabsf(u) + c, ay = fabsf(v) + c;
+    if (!(ax < 3e38f) || !(ay < 3e38f)) { bad |= HW_STATUS_NONFINITE; continue; }
+    mx = fmaxf(mx, ax);
+    my = fmaxf(my, ay);
+  }
 #pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-      kx = max(kx, __shfl_xor_sync(0xffffffffu, kx, s));
-      ky = max(ky, __shfl_xor_sync(0xffffffffu, ky, s));
-    }
-    if ((threadIdx.x & 31) == 0) {
-      atomicMax(amax, kx);
-      atomicMax(amax + 1, ky);
-    }
-  } else {
-    // float: the maximum in float, widened to a double key once per warp (the FP64 pipe is narrow)
-    float mx = 0.0f, my = 0.0f;
-    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
-      const float h = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
-      if (!(h > 0.0f) || !(h < 3e38f)) { bad |= h == h ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE; continue; }
-      const float rh = fast_rcp(h);
-      const float gh = d.g * h;
-      const float c = gh * fast_rsqrt(gh);
-      const float u = __ldg(d.S[1] + o) * rh, v = __ldg(d.S[2] + o) * rh;
-      const float ax = fabsf(u) + c, ay = fabsf(v) + c;
-      if (!(ax < 3e38f) || !(ay < 3e38f)) { bad |= HW_STATUS_NONFINITE; continue; }
-      mx = fmaxf(mx, ax);
-      my = fmaxf(my, ay);
-    }
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
-      my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, s));
-    }
-    if ((threadIdx.x & 31) == 0) {
-      atomicMax(amax, dkey((double)mx));
-      atomicMax(amax + 1, dkey((double)my));
-    }
+  for (int s = 16; s > 0; s >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+    my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, s));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(amax, dkey((double)mx));
+    atomicMax(amax + 1, dkey((double)my));
   }
   if (bad) atomicOr(status, bad);
 }
@@ -386,18 +459,18 @@ int set_kernel_attributes2d() {
   return e == cudaSuccess ? 0 : -1;
 }
 
-template <class R>
-static void alpha2d_impl(const Dev2DT<R>& d, unsigned long long* amax, int* status, cudaStream_t st) {
-  cudaMemsetAsync(amax, 0, 2 * sizeof(unsigned long long), st);
+void launch_alpha2d(const Dev2D& d, unsigned long long* amax, int* status, cudaStream_t st) {
+  cudaMemsetAsync(amax, 0, 3 * sizeof(unsigned long long), st);
   const size_t n = (size_t)d.nx * d.ny;
   int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 8);
-  k_alpha2d<R><<<blocks, 256, 0, st>>>(d, amax, status);
-}
-void launch_alpha2d(const Dev2D& d, unsigned long long* amax, int* status, cudaStream_t st) {
-  alpha2d_impl(d, amax, status, st);
+  k_alpha2d_coarse<<<blocks, 256, 0, st>>>(d, amax, status);
+  k_alpha2d_exact<<<blocks, 256, 0, st>>>(d, amax, status);
 }
 void launch_alpha2d(const Dev2DT<float>& d, unsigned long long* amax, int* status, cudaStream_t st) {
-  alpha2d_impl(d, amax, status, st);
+  cudaMemsetAsync(amax, 0, 3 * sizeof(unsigned long long), st);
+  const size_t n = (size_t)d.nx * d.ny;
+  int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 8);
+  k_alpha2d_f32<<<blocks, 256, 0, st>>>(d, amax, status);
 }
 
 void launch_finish_alpha2d(const Dev2D& d, const unsigned long long* amax, double* alpha, double* dt_out,
