@@ -556,6 +556,9 @@ def main():
             line[key] = fn()
         except Exception as exc:  # noqa: BLE001
             line[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+    # (only in single-GPU runs: a scaling run measures the headline alone)
+    if ws > 1:
+        args.batched_steps = args.adjoint_steps = args.fp32_steps = 0
     if args.batched_steps > 0 and (NX, NY) == (2048, 2048):
         solver.close()
         extra("batched", lambda: batched_compare(args.batched_steps))
