@@ -297,3 +297,24 @@ def test_checkpoint_and_resume_is_bitwise(hw):
     for x, y in zip(a.state(), b.state()):
         assert np.array_equal(x, y)
     assert hw.hw_get_time(a.h) == hw.hw_get_time(b.h)
+
+
+def test_time_and_state_api_errors(hw):
+    import ctypes as C
+    sc = S.hump2d(32, 32, seed=48)
+    s = solver(hw, sc)
+    L = hw.lib()
+    with pytest.raises(hw.HwError) as e:
+        hw.hw_set_time(s.h, -1.0, 0)
+    assert e.value.code == -1
+    with pytest.raises(hw.HwError) as e:
+        hw.hw_set_time(s.h, 0.0, -5)
+    assert e.value.code == -1
+    assert L.hw_get_time(s.h.ptr, None, None) == -1
+    # a resumed float solver keeps its time too
+    s32 = hw.Solver.from_scenario(sc, hw.make_params(precision=hw.HW_FP32))
+    s32.advance(3, use_graph=False)
+    t, n = hw.hw_get_time(s32.h)
+    assert n == 3 and t > 0
+    base = s32.base()
+    assert len(base) == 9 and np.isfinite(base[0]).all()
