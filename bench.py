@@ -60,9 +60,9 @@ PEAK_FP64_OPS = SMS * DFMA_PER_SM_CLK * SM_GHZ * 1e9
 # launch at 2048x1024, the state and interface planes above L2), valid only for the kernel sources they
 # were taken on (sources_sha); scaled to a launch by its units (traffic is proportional to them).
 TRAFFIC = {
-    "sweep_x": {"bytes_per_unit": 222.22, "sha": "f59f39eaa92897ad"},
-    "sweep_y": {"bytes_per_unit": 230.56, "sha": "f59f39eaa92897ad"},
-    "node": {"bytes_per_unit": 442.69, "sha": "f59f39eaa92897ad"},
+    "sweep_x": {"bytes_per_unit": 222.53, "sha": "1792e4f9339f5edc"},
+    "sweep_y": {"bytes_per_unit": 230.34, "sha": "1792e4f9339f5edc"},
+    "node": {"bytes_per_unit": 442.79, "sha": "1792e4f9339f5edc"},
 }
 STATE_BYTES = 9 * NX * NY * 8
 
