@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libhwswe.so")
-SOURCES = ["hw_api.cu", "hw_kernels2d.cu", "hw_kernels1d.cu", "hw_noalloc.cu", "hw_batch.cu", "hw_adjoint.cu"]
+SOURCES = ["hw_api.cu", "hw_kernels2d.cu", "hw_kernels1d.cu", "hw_noalloc.cu", "hw_batch.cu", "hw_adjoint.cu",
+           "hw_selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

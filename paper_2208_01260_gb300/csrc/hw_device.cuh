@@ -23,6 +23,7 @@
 #include <cstdint>
 #include <type_traits>
 #include <cuda_runtime.h>
+#include "hw_fp64_int.h"
 
 namespace hw {
 
@@ -137,16 +138,42 @@ struct WeightsT {
 };
 using Weights = WeightsT<double>;
 
+// Multiplication policies. MulFP64 multiplies on the FP64 pipe (DMUL, never contracted into an fma);
+// MulInt forms the same bits on the integer pipes (hw_fp64_int.h) and records whether any product
+// left its fast path, in which case the caller recomputes the block with MulFP64. k(c, x) multiplies
+// by a literal constant c. Float data is multiplied natively by both.
+struct MulFP64 {
+  __device__ __forceinline__ double operator()(double x, double y) { return __dmul_rn(x, y); }
+  __device__ __forceinline__ float operator()(float x, float y) { return x * y; }
+  __device__ __forceinline__ double k(double c, double x) { return __dmul_rn(x, c); }
+  __device__ __forceinline__ float k(float c, float x) { return c * x; }
+};
+struct MulInt {
+  bool bad = false;
+  __device__ __forceinline__ double operator()(double x, double y) {
+    double r;
+    bad |= !f64_mul_int(x, y, r);
+    return r;
+  }
+  __device__ __forceinline__ float operator()(float x, float y) { return x * y; }
+  __device__ __forceinline__ double k(double c, double x) {
+    double r;
+    bad |= !f64_mul_int<true>(x, c, r);
+    return r;
+  }
+  __device__ __forceinline__ float k(float c, float x) { return c * x; }
+};
+
 // Unnormalised weights proportional to w_1/t_1^2, w_2/t_2^2, w_3/t_3^2 (t_l = beta_l + eps). In double the
 // products of the other two squares (one reciprocal); in float, where t^4 can overflow on large jumps,
 // (t_min/t_l)^2, each at most 1.
-template <class R>
-__device__ __forceinline__ void inverse_square_weights(R t1, R t2, R t3, R& n1, R& n2, R& n3) {
+template <class R, class M>
+__device__ __forceinline__ void inverse_square_weights(R t1, R t2, R t3, R& n1, R& n2, R& n3, M& mul) {
   if constexpr (std::is_same<R, double>::value) {
-    const R s1 = t1 * t1, s2 = t2 * t2, s3 = t3 * t3;
-    n1 = s2 * s3;
-    n2 = s1 * s3;
-    n3 = s1 * s2;
+    const R s1 = mul(t1, t1), s2 = mul(t2, t2), s3 = mul(t3, t3);
+    n1 = mul(s2, s3);
+    n2 = mul(s1, s3);
+    n3 = mul(s1, s2);
   } else {
     const R m = fminf(fminf(t1, t2), t3);
     const R a1 = m * fast_rcp(t1), a2 = m * fast_rcp(t2), a3 = m * fast_rcp(t3);
@@ -156,8 +183,8 @@ __device__ __forceinline__ void inverse_square_weights(R t1, R t2, R t3, R& n1, 
   }
 }
 
-template <bool LINEAR, class R>
-__device__ __forceinline__ R hweno_side(R f0, R f1, R f2, R p0, R p1, R p2, R eps, WeightsT<R>& W) {
+template <bool LINEAR, class R, class M>
+__device__ __forceinline__ R hweno_side_m(R f0, R f1, R f2, R p0, R p1, R p2, R eps, WeightsT<R>& W, M& mul) {
   const R d1 = f0 - f1, d2 = f1 - f2;
   const R B1 = fma(R(2.0), d1, p0 + p1);
   const R A1 = B1 + (d1 + p1);
@@ -170,25 +197,37 @@ __device__ __forceinline__ R hweno_side(R f0, R f1, R f2, R p0, R p1, R p2, R ep
   const R q3 = fma(R(1.0 / 12.0), e, P);
   if (LINEAR) {
     W.n1 = R(0.3); W.n2 = R(0.3); W.n3 = R(0.4); W.r = R(1.0);
-    return fma(R(0.3), q1, fma(R(0.3), q2, R(0.4) * q3));
+    return fma(R(0.3), q1, fma(R(0.3), q2, mul.k(R(0.4), q3)));
   }
   const R g3 = fma(R(2.0), p1, f0 - f2);
-  const R pp = p1 * p1;
-  const R b1 = fma(R(781.0 / 20.0) * B1, B1, fma(R(13.0 / 3.0) * A1, A1, pp));
-  const R b2 = fma(R(781.0 / 20.0) * B2, B2, fma(R(13.0 / 3.0) * A2, A2, pp));
-  const R b3 = fma(R(781.0 / 80.0) * g3, g3, fma(R(13.0 / 12.0) * e, e, pp));
+  const R pp = mul(p1, p1);
+  const R b1 = fma(mul.k(R(781.0 / 20.0), B1), B1, fma(mul.k(R(13.0 / 3.0), A1), A1, pp));
+  const R b2 = fma(mul.k(R(781.0 / 20.0), B2), B2, fma(mul.k(R(13.0 / 3.0), A2), A2, pp));
+  const R b3 = fma(mul.k(R(781.0 / 80.0), g3), g3, fma(mul.k(R(13.0 / 12.0), e), e, pp));
   R n3;
-  inverse_square_weights(b1 + eps, b2 + eps, b3 + eps, W.n1, W.n2, n3);
+  inverse_square_weights(b1 + eps, b2 + eps, b3 + eps, W.n1, W.n2, n3, mul);
   // gamma = (3, 3, 4)/10 -> proportional to (1, 1, 4/3)
-  W.n3 = R(4.0 / 3.0) * n3;
+  W.n3 = mul.k(R(4.0 / 3.0), n3);
   W.r = fast_rcp(W.n1 + W.n2 + W.n3);
-  return fma(W.n1, q1, fma(W.n2, q2, W.n3 * q3)) * W.r;
+  return mul(fma(W.n1, q1, fma(W.n2, q2, mul(W.n3, q3))), W.r);
+}
+
+// One side on the FP64 pipe (the 1D kernels, the batched form and the adjoint's recomputation).
+template <bool LINEAR, class R>
+__device__ __forceinline__ R hweno_side(R f0, R f1, R f2, R p0, R p1, R p2, R eps, WeightsT<R>& W) {
+  MulFP64 mf;
+  return hweno_side_m<LINEAR>(f0, f1, f2, p0, p1, p2, eps, W, mf);
 }
 
 // The source reconstructed with the same weights (Sec. 2.1 Step 2) from precomputed candidates.
+template <class R, class M>
+__device__ __forceinline__ R weighted_m(const WeightsT<R>& W, R c1, R c2, R c3, M& mul) {
+  return mul(fma(W.n1, c1, fma(W.n2, c2, mul(W.n3, c3))), W.r);
+}
 template <class R>
 __device__ __forceinline__ R weighted(const WeightsT<R>& W, R c1, R c2, R c3) {
-  return fma(W.n1, c1, fma(W.n2, c2, W.n3 * c3)) * W.r;
+  MulFP64 mf;
+  return weighted_m(W, c1, c2, c3, mf);
 }
 
 // Limiter for one characteristic field (eqs. step1-dxi, limiter-1d), scaled data:
@@ -196,23 +235,28 @@ __device__ __forceinline__ R weighted(const WeightsT<R>& W, R c1, R c2, R c3) {
 // Returns the scaled dx*nu^mod. p'_1 = 2(m1-m0) - nl, p'_2 = 2(m2-m1) - nr, p'_3 = (m2-m0)/2,
 // beta^L_1 = p'_1^2 + 13/3 (m1-m0-nl)^2, beta^L_2 = p'_2^2 + 13/3 (m2-m1-nr)^2,
 // beta^L_3 = p'_3^2 + 13/12 (m2 - 2 m1 + m0)^2, d = (1,1,2)/4.
-template <bool LINEAR, class R>
-__device__ __forceinline__ R limiter_field(R m0, R m1, R m2, R nl, R nr, R eps) {
+template <bool LINEAR, class R, class M>
+__device__ __forceinline__ R limiter_field_m(R m0, R m1, R m2, R nl, R nr, R eps, M& mul) {
   const R dl = m1 - m0, dr = m2 - m1;
   const R pl = fma(R(2.0), dl, -nl);
   const R pr = fma(R(2.0), dr, -nr);
   const R pc2 = dl + dr;  // 2 p'_3
-  if (LINEAR) return fma(R(0.25), pl + pr, R(0.25) * pc2);
+  if (LINEAR) return fma(R(0.25), pl + pr, mul.k(R(0.25), pc2));
   const R al = dl - nl, ar = dr - nr, ac = dr - dl;
-  const R b1 = fma(R(13.0 / 3.0) * al, al, pl * pl);
-  const R b2 = fma(R(13.0 / 3.0) * ar, ar, pr * pr);
-  const R b3 = fma(R(13.0 / 12.0) * ac, ac, (R(0.25) * pc2) * pc2);
+  const R b1 = fma(mul.k(R(13.0 / 3.0), al), al, mul(pl, pl));
+  const R b2 = fma(mul.k(R(13.0 / 3.0), ar), ar, mul(pr, pr));
+  const R b3 = fma(mul.k(R(13.0 / 12.0), ac), ac, mul(mul.k(R(0.25), pc2), pc2));
   // d = (1, 1, 2)/4 -> proportional to (1, 1, 2); p'_3 = pc2 / 2 so its term is n3 pc2
   R n1, n2, n3;
-  inverse_square_weights(b1 + eps, b2 + eps, b3 + eps, n1, n2, n3);
+  inverse_square_weights(b1 + eps, b2 + eps, b3 + eps, n1, n2, n3, mul);
   const R den = fma(R(2.0), n3, n1 + n2);
-  const R num = fma(n1, pl, fma(n2, pr, n3 * pc2));
-  return num * fast_rcp(den);
+  const R num = fma(n1, pl, fma(n2, pr, mul(n3, pc2)));
+  return mul(num, fast_rcp(den));
+}
+template <bool LINEAR, class R>
+__device__ __forceinline__ R limiter_field(R m0, R m1, R m2, R nl, R nr, R eps) {
+  MulFP64 mf;
+  return limiter_field_m<LINEAR>(m0, m1, m2, nl, nr, eps, mf);
 }
 
 }  // namespace hw

@@ -19,8 +19,13 @@ namespace hw {
 constexpr int XS_T = 192;
 constexpr int XS_N = XS_T + 3;
 
+// The double kernels move the multiplications of the nonlinear weights to the integer pipes
+// (bit-identical products, hw_fp64_int.h): the FP64 pipe is their bound, the integer pipes idle.
+template <class R>
+constexpr bool kIntMul = std::is_same<R, double>::value;
+
 template <bool LINEAR, bool CHAR, class R>
-__global__ void __launch_bounds__(XS_T) k_sweep_x(Dev2DT<R> d, const R* __restrict__ alpha) {
+__global__ void __launch_bounds__(XS_T, 2) k_sweep_x(Dev2DT<R> d, const R* __restrict__ alpha) {
   __shared__ R sm[NREC * XS_N];
   const int j = blockIdx.y;
   const int k0 = blockIdx.x * XS_T;
@@ -44,7 +49,7 @@ __global__ void __launch_bounds__(XS_T) k_sweep_x(Dev2DT<R> d, const R* __restri
 #pragma unroll
   for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qbx[q] + o);
   R out[12];
-  interface_values<0, LINEAR, CHAR>(sm + t, sm + t + 1, sm + t + 2, sm + t + 3, XS_N, qb, R(d.g), R(d.eps_w), out);
+  interface_values<0, LINEAR, CHAR, kIntMul<R>>(sm + t, sm + t + 1, sm + t + 2, sm + t + 3, XS_N, qb, R(d.g), R(d.eps_w), out);
 #pragma unroll
   for (int q = 0; q < 12; ++q) d.X[q][o] = out[q];
 }
@@ -56,7 +61,7 @@ __global__ void __launch_bounds__(XS_T) k_sweep_x(Dev2DT<R> d, const R* __restri
 constexpr int YS_W = 32;
 
 template <bool LINEAR, bool CHAR, class R>
-__global__ void __launch_bounds__(YS_W) k_sweep_y(Dev2DT<R> d, const R* __restrict__ alpha, int seg) {
+__global__ void __launch_bounds__(YS_W, 12) k_sweep_y(Dev2DT<R> d, const R* __restrict__ alpha, int seg) {
   extern __shared__ __align__(16) unsigned char ring_raw[];
   R* ring = reinterpret_cast<R*>(ring_raw);  // [4 slots][NREC][YS_W]
   const int i = blockIdx.x * YS_W + threadIdx.x;
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(YS_W) k_sweep_y(Dev2DT<R> d, const R* __restri
 #pragma unroll
       for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qby[q] + o);
       R out[12];
-      interface_values<1, LINEAR, CHAR>(s0, s1, s2, s3, stride, qb, R(d.g), R(d.eps_w), out);
+      interface_values<1, LINEAR, CHAR, kIntMul<R>>(s0, s1, s2, s3, stride, qb, R(d.g), R(d.eps_w), out);
 #pragma unroll
       for (int q = 0; q < 12; ++q) d.Y[q][o] = out[q];
     }
@@ -96,7 +101,7 @@ __global__ void __launch_bounds__(256, 3) k_node2d(Dev2DT<R> d, StageArgsT<R> sa
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y;
   if (i >= d.nx || j >= d.ny) return;
-  node_update<MODE, LINEAR, CHAR>(d, sa, i, j);
+  node_update<MODE, LINEAR, CHAR, kIntMul<R>>(d, sa, i, j);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -99,10 +99,11 @@ __device__ __forceinline__ void node_record(const Node12T<R>& n, R g, R alpha, R
 // where dS is the spacing along the sweep and dT the spacing across it.
 // qb[6] = source candidates q_1..q_3 of (b, dS b_s) for the '+' side then the mirrored '-' side.
 // ---------------------------------------------------------------------------------------------
-template <int DIR, bool LINEAR, bool CHAR, class R>
-__device__ __forceinline__ void interface_values(const R* r0, const R* r1, const R* r2,
-                                                 const R* r3, int stride, const R qb[6], R g,
-                                                 R eps_w, R out[12]) {
+// `mul` multiplies the nonlinear weights (MulFP64 or MulInt, see hw_device.cuh).
+template <int DIR, bool LINEAR, bool CHAR, class R, class M>
+__device__ __forceinline__ void interface_values_m(const R* r0, const R* r1, const R* r2,
+                                                   const R* r3, int stride, const R qb[6], R g,
+                                                   R eps_w, R out[12], M& mul) {
 #define RV(r, f) (r)[(f) * stride]
   // interface state: h = (h_i + h_{i+1})/2, u = (m_i + m_{i+1})/(h_i + h_{i+1}), v likewise
   const R hs = RV(r1, R_H) + RV(r2, R_H);
@@ -155,14 +156,14 @@ __device__ __forceinline__ void interface_values(const R* r0, const R* r1, const
     for (int k = 0; k < 3; ++k) {
       WeightsT<R> W;
       const R e = (k == 1) ? eps2 : eps13;
-      const R v = hweno_side<LINEAR>(f[k][0], f[k][1], f[k][2], p[k][0], p[k][1], p[k][2], e, W);
+      const R v = hweno_side_m<LINEAR>(f[k][0], f[k][1], f[k][2], p[k][0], p[k][1], p[k][2], e, W, mul);
       G[k] = side == 0 ? v : G[k] + v;
       if (CHAR) {
         // source data per field: (-b, 0, +b) (row entries of the normal-momentum column)
-        if (k == 0) GB1 -= weighted(W, qbs[0], qbs[1], qbs[2]);
-        if (k == 2) GB3 += weighted(W, qbs[0], qbs[1], qbs[2]);
+        if (k == 0) GB1 -= weighted_m(W, qbs[0], qbs[1], qbs[2], mul);
+        if (k == 2) GB3 += weighted_m(W, qbs[0], qbs[1], qbs[2], mul);
       } else {
-        if (k == 1) GB1 += weighted(W, qbs[0], qbs[1], qbs[2]);  // the normal-momentum component itself
+        if (k == 1) GB1 += weighted_m(W, qbs[0], qbs[1], qbs[2], mul);  // the normal-momentum component itself
       }
     }
   }
@@ -198,15 +199,35 @@ __device__ __forceinline__ void interface_values(const R* r0, const R* r1, const
 #undef RV
 }
 
+// One interface. IMUL: the multiplications of the nonlinear weights run on the integer pipes
+// (hw_fp64_int.h), bit-identical to DMUL; if any of them leaves the integer fast path (subnormal,
+// infinite or NaN data), the interface is recomputed on the FP64 pipe from the same records.
+template <int DIR, bool LINEAR, bool CHAR, bool IMUL = false, class R>
+__device__ __forceinline__ void interface_values(const R* r0, const R* r1, const R* r2,
+                                                 const R* r3, int stride, const R qb[6], R g,
+                                                 R eps_w, R out[12]) {
+  if constexpr (IMUL && !LINEAR && std::is_same<R, double>::value) {
+    MulInt mi;
+    interface_values_m<DIR, LINEAR, CHAR>(r0, r1, r2, r3, stride, qb, g, eps_w, out, mi);
+    if (mi.bad) {
+      MulFP64 mf;
+      interface_values_m<DIR, LINEAR, CHAR>(r0, r1, r2, r3, stride, qb, g, eps_w, out, mf);
+    }
+  } else {
+    MulFP64 mf;
+    interface_values_m<DIR, LINEAR, CHAR>(r0, r1, r2, r3, stride, qb, g, eps_w, out, mf);
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Node kernel: RHS assembly, limiter, RK combination (or the bare RHS).
 // ---------------------------------------------------------------------------------------------
 // Limiter along one direction at one node (Sec. R(2.2)), scaled data. L-rows without 1/(2c):
 // x: (u+c, -1, 0), (-v, 0, 1), (-(u-c), 1, 0); y: (v+c, 0, -1), (-u, 1, 0), (-(v-c), 0, 1).
-template <int DIR, bool LINEAR, bool CHAR, class R>
+template <int DIR, bool LINEAR, bool CHAR, class R, class M>
 __device__ __forceinline__ void limit_dir(const R Um[3], const R U0[3], const R Up[3],
                                           const R Dm[3], const R Dp[3], R u, R v, R c,
-                                          R ic2, R gh, R eps, R out[3]) {
+                                          R ic2, R gh, R eps, R out[3], M& mul) {
   const int cn = DIR == 0 ? 1 : 2, ct = DIR == 0 ? 2 : 1;
   const R un = DIR == 0 ? u : v, ut = DIR == 0 ? v : u;
   const R upc = un + c, umc = un - c;
@@ -224,7 +245,7 @@ __device__ __forceinline__ void limit_dir(const R Um[3], const R U0[3], const R 
   const R e13 = CHAR ? (R(4.0) * eps) * gh : eps;
   R nu[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) nu[k] = limiter_field<LINEAR>(m0[k], m1[k], m2[k], nl[k], nr[k], k == 1 ? eps : e13);
+  for (int k = 0; k < 3; ++k) nu[k] = limiter_field_m<LINEAR>(m0[k], m1[k], m2[k], nl[k], nr[k], k == 1 ? eps : e13, mul);
   if (CHAR) {
     const R A = (nu[0] + nu[2]) * ic2;
     out[0] = A;
@@ -236,7 +257,8 @@ __device__ __forceinline__ void limit_dir(const R Um[3], const R U0[3], const R 
 }
 
 // RHS assembly, limiter and RK combination (or the bare RHS) at node (i, j) of one grid.
-template <int MODE, bool LINEAR, bool CHAR, class R>
+// IMUL: the limiter's weight multiplications run on the integer pipes (see interface_values).
+template <int MODE, bool LINEAR, bool CHAR, bool IMUL = false, class R>
 __device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT<R>& sa, int i, int j) {
   const size_t o = (size_t)j * d.nx + i;
   const size_t ox = (size_t)j * (d.nx + 1) + i;  // left x-interface; right is ox + 1
@@ -298,14 +320,28 @@ __device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT
     const R u = cur[1] * rh, v = cur[2] * rh;
     const R rs = fast_rsqrt(gh);
     const R c = gh * rs, ic2 = R(0.5) * rs;
-    Node12T<R> nm, np;
-    // x neighbours
-    load_node(d, i - 1, j, nm);
-    load_node(d, i + 1, j, np);
-    limit_dir<0, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 3, np.v + 3, u, v, c, ic2, gh, R(d.eps_lim), mod);
-    load_node(d, i, j - 1, nm);
-    load_node(d, i, j + 1, np);
-    limit_dir<1, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 6, np.v + 6, u, v, c, ic2, gh, R(d.eps_lim), mod + 3);
+    // both directions; with IMUL, if any product leaves the integer fast path, both directions are
+    // recomputed on the FP64 pipe (neighbours reloaded)
+    auto limit = [&](auto& mul) {
+      Node12T<R> nm, np;
+      load_node(d, i - 1, j, nm);
+      load_node(d, i + 1, j, np);
+      limit_dir<0, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 3, np.v + 3, u, v, c, ic2, gh, R(d.eps_lim), mod, mul);
+      load_node(d, i, j - 1, nm);
+      load_node(d, i, j + 1, np);
+      limit_dir<1, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 6, np.v + 6, u, v, c, ic2, gh, R(d.eps_lim), mod + 3, mul);
+    };
+    if constexpr (IMUL && !LINEAR && std::is_same<R, double>::value) {
+      MulInt mi;
+      limit(mi);
+      if (mi.bad) {
+        MulFP64 mf;
+        limit(mf);
+      }
+    } else {
+      MulFP64 mf;
+      limit(mf);
+    }
   } else {
 #pragma unroll
     for (int q = 0; q < 6; ++q) mod[q] = cur[3 + q];

@@ -4,6 +4,7 @@ Sizes span several tiles of every kernel (x-sweep 192 interfaces per row tile, y
 block, node 32x8) with ragged tails; the full-size 2048^2 workload is checked on sampled nodes the
 oracle computes one by one. See tests/_parity.py for the tolerances.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -33,6 +34,15 @@ def oparams(orc, sc, **pk):
     return orc.make_params(eps_w=pk.pop("eps_w", sc.eps_w), **pk)
 
 
+def tiny_derivatives(sc, scale=1e-160):
+    """The left half of the domain with every derivative plane scaled to ~1e-160: squares and products
+    of the projected derivative data there underflow, so the kernels' integer-pipe weight products leave
+    their fast path and those interfaces and limiter nodes are recomputed on the FP64 pipe."""
+    x = S.axis(sc.nx, sc.x0, sc.x1, sc.bc_x)
+    f = np.where(x < 0.5 * (sc.x0 + sc.x1), scale, 1.0)[None, :]
+    return dataclasses.replace(sc, deriv=[d * f for d in sc.deriv], name=sc.name + "_tiny_derivs")
+
+
 CASES_2D = [
     ("hump_reflective", lambda: S.hump2d(70, 45, seed=21), {}),
     ("hump_periodic", lambda: S.hump2d(131, 67, seed=22, bc=S.PERIODIC), {}),
@@ -43,6 +53,7 @@ CASES_2D = [
     ("tiny_eps", lambda: S.bumps2d(66, 33, strip=1e-3), {"eps_w": 1e-10}),
     ("min_grid", lambda: S.hump2d(2, 3, seed=25), {}),
     ("three_x_tiles", lambda: S.hump2d(450, 40, seed=26), {}),
+    ("int_mul_fallback", lambda: tiny_derivatives(S.hump2d(70, 45, seed=27)), {}),
 ]
 
 
