@@ -143,6 +143,7 @@ using Weights = WeightsT<double>;
 // left its fast path, in which case the caller recomputes the block with MulFP64. k(c, x) multiplies
 // by a literal constant c. Float data is multiplied natively by both.
 struct MulFP64 {
+  static constexpr bool bad = false;
   __device__ __forceinline__ double operator()(double x, double y) { return __dmul_rn(x, y); }
   __device__ __forceinline__ float operator()(float x, float y) { return x * y; }
   __device__ __forceinline__ double k(double c, double x) { return __dmul_rn(x, c); }

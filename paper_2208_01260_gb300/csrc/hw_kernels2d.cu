@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(XS_T, 2) k_sweep_x(Dev2DT<R> d, const R* __res
     Node12T<R> n;
     load_node(d, i, j, n);
     R rec[NREC];
-    node_record<0>(n, R(d.g), ax, rec);
+    node_record<0, kIntMul<R>>(n, R(d.g), ax, rec);
 #pragma unroll
     for (int f = 0; f < NREC; ++f) sm[f * XS_N + t] = rec[f];
   }
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(YS_W, 12) k_sweep_y(Dev2DT<R> d, const R* __re
     Node12T<R> n;
     load_node(d, i, r, n);
     R rec[NREC];
-    node_record<1>(n, R(d.g), ay, rec);
+    node_record<1, kIntMul<R>>(n, R(d.g), ay, rec);
     R* slot = ring + (size_t)(r & 3) * NREC * YS_W + threadIdx.x;
 #pragma unroll
     for (int f = 0; f < NREC; ++f) slot[f * stride] = rec[f];

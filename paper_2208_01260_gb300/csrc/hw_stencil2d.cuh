@@ -45,39 +45,39 @@ enum { R_FP = 0, R_FM = 3, R_GP = 6, R_GM = 9, R_MIX = 12, R_H = 15, R_M = 16, R
 // Pointwise fluxes of eq. (swe-form-2d-e) and their chain-rule derivatives of eq. (swe-form-2d-h),
 // split with the global alpha (Sec. R(2.1) Step 1, without the factor 1/2). DIR = 0: x-sweep record
 // (F1, d_x F1 for the split, d_y F1 for the mixed term); DIR = 1: y-sweep record (F2, d_y F2, d_x F2).
-template <int DIR, class R>
-__device__ __forceinline__ void node_record(const Node12T<R>& n, R g, R alpha, R rec[NREC]) {
+template <int DIR, class R, class M>
+__device__ __forceinline__ void node_record_m(const Node12T<R>& n, R g, R alpha, R rec[NREC], M& mul) {
   const R eta = n.v[0], m = n.v[1], w = n.v[2], b = n.v[9];
   const R h = eta - b;
   const R rh = fast_rcp(h);
-  const R u = m * rh, v = w * rh;
-  const R gh = g * h, ge = g * eta;
-  const R pres = ge * fma(R(0.5), eta, -b);  // g/2 (eta^2 - 2 eta b)
-  const R uv = u * v;
+  const R u = mul(m, rh), v = mul(w, rh);
+  const R gh = mul(g, h), ge = mul(g, eta);
+  const R pres = mul(ge, fma(R(0.5), eta, -b));  // g/2 (eta^2 - 2 eta b)
+  const R uv = mul(u, v);
   // derivative data along the sweep (split) and across it (mixed)
   const int qs = DIR == 0 ? 3 : 6, qm = DIR == 0 ? 6 : 3;
   const R Hs = n.v[qs], Ms = n.v[qs + 1], Ws = n.v[qs + 2], Bs = n.v[DIR == 0 ? 10 : 11];
   const R Hm = n.v[qm], Mm = n.v[qm + 1], Wm = n.v[qm + 2], Bm = n.v[DIR == 0 ? 11 : 10];
   R F[3], Gs[3], Gm[3];
-  const R mv = m * v;
+  const R mv = mul(m, v);
   if (DIR == 0) {
-    const R uu = u * u, a1 = gh - uu, a2 = uu - ge, u2 = u + u;
+    const R uu = mul(u, u), a1 = gh - uu, a2 = uu - ge, u2 = u + u;
     F[0] = m; F[1] = fma(m, u, pres); F[2] = mv;
     Gs[0] = Ms;
-    Gs[1] = fma(u2, Ms, fma(a1, Hs, a2 * Bs));
-    Gs[2] = fma(uv, Bs - Hs, fma(v, Ms, u * Ws));
+    Gs[1] = fma(u2, Ms, fma(a1, Hs, mul(a2, Bs)));
+    Gs[2] = fma(uv, Bs - Hs, fma(v, Ms, mul(u, Ws)));
     Gm[0] = Mm;
-    Gm[1] = fma(u2, Mm, fma(a1, Hm, a2 * Bm));
-    Gm[2] = fma(uv, Bm - Hm, fma(v, Mm, u * Wm));
+    Gm[1] = fma(u2, Mm, fma(a1, Hm, mul(a2, Bm)));
+    Gm[2] = fma(uv, Bm - Hm, fma(v, Mm, mul(u, Wm)));
   } else {
-    const R vv = v * v, a1 = gh - vv, a2 = vv - ge, v2 = v + v;
+    const R vv = mul(v, v), a1 = gh - vv, a2 = vv - ge, v2 = v + v;
     F[0] = w; F[1] = mv; F[2] = fma(w, v, pres);
     Gs[0] = Ws;
-    Gs[1] = fma(uv, Bs - Hs, fma(v, Ms, u * Ws));
-    Gs[2] = fma(v2, Ws, fma(a1, Hs, a2 * Bs));
+    Gs[1] = fma(uv, Bs - Hs, fma(v, Ms, mul(u, Ws)));
+    Gs[2] = fma(v2, Ws, fma(a1, Hs, mul(a2, Bs)));
     Gm[0] = Wm;
-    Gm[1] = fma(uv, Bm - Hm, fma(v, Mm, u * Wm));
-    Gm[2] = fma(v2, Wm, fma(a1, Hm, a2 * Bm));
+    Gm[1] = fma(uv, Bm - Hm, fma(v, Mm, mul(u, Wm)));
+    Gm[2] = fma(v2, Wm, fma(a1, Hm, mul(a2, Bm)));
   }
   const R U[3] = {eta, m, w}, D[3] = {Hs, Ms, Ws};
 #pragma unroll
@@ -93,13 +93,30 @@ __device__ __forceinline__ void node_record(const Node12T<R>& n, R g, R alpha, R
   rec[R_W] = w;
 }
 
+// The record; IMUL: products on the integer pipes, recomputed on the FP64 pipe if any leaves the
+// integer fast path.
+template <int DIR, bool IMUL = false, class R>
+__device__ __forceinline__ void node_record(const Node12T<R>& n, R g, R alpha, R rec[NREC]) {
+  if constexpr (IMUL && std::is_same<R, double>::value) {
+    MulInt mi;
+    node_record_m<DIR>(n, g, alpha, rec, mi);
+    if (mi.bad) {
+      MulFP64 mf;
+      node_record_m<DIR>(n, g, alpha, rec, mf);
+    }
+  } else {
+    MulFP64 mf;
+    node_record_m<DIR>(n, g, alpha, rec, mf);
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // One interface from the four stencil records (nodes i-1, i, i+1, i+2 along the sweep).
 // Outputs (12): 2 Fhat, 2 bhat, 24 dS Ghat (derivative-equation flux), 12 dT Mhat (mixed term),
 // where dS is the spacing along the sweep and dT the spacing across it.
 // qb[6] = source candidates q_1..q_3 of (b, dS b_s) for the '+' side then the mirrored '-' side.
 // ---------------------------------------------------------------------------------------------
-// `mul` multiplies the nonlinear weights (MulFP64 or MulInt, see hw_device.cuh).
+// `mul` forms the products (MulFP64 or MulInt, see hw_device.cuh).
 template <int DIR, bool LINEAR, bool CHAR, class R, class M>
 __device__ __forceinline__ void interface_values_m(const R* r0, const R* r1, const R* r2,
                                                    const R* r3, int stride, const R qb[6], R g,
@@ -108,20 +125,20 @@ __device__ __forceinline__ void interface_values_m(const R* r0, const R* r1, con
   // interface state: h = (h_i + h_{i+1})/2, u = (m_i + m_{i+1})/(h_i + h_{i+1}), v likewise
   const R hs = RV(r1, R_H) + RV(r2, R_H);
   const R rhs = fast_rcp(hs);
-  const R ub = (RV(r1, R_M) + RV(r2, R_M)) * rhs;
-  const R vb = (RV(r1, R_W) + RV(r2, R_W)) * rhs;
-  const R gh = (R(0.5) * g) * hs;
+  const R ub = mul(RV(r1, R_M) + RV(r2, R_M), rhs);
+  const R vb = mul(RV(r1, R_W) + RV(r2, R_W), rhs);
+  const R gh = mul(mul.k(R(0.5), g), hs);
   const R rs = fast_rsqrt(gh);
-  const R cb = gh * rs;
-  const R ic2 = R(0.5) * rs;  // 1/(2c)
+  const R cb = mul(gh, rs);
+  const R ic2 = mul.k(R(0.5), rs);  // 1/(2c)
   // normal / tangential velocity of this sweep
   const R un = DIR == 0 ? ub : vb, ut = DIR == 0 ? vb : ub;
   const R upc = un + cb, umc = un - cb;
   // component indices: normal momentum and tangential momentum
   const int cn = DIR == 0 ? 1 : 2, ct = DIR == 0 ? 2 : 1;
   // scaled epsilon: fields 1, 3 carry s = 4c, field 2 carries s = 2 (both 2 without projection)
-  const R eps13 = CHAR ? (R(8.0) * g * eps_w) * hs : R(4.0) * eps_w;
-  const R eps2 = R(4.0) * eps_w;
+  const R eps2 = mul.k(R(4.0), eps_w);
+  const R eps13 = CHAR ? mul(mul(mul.k(R(8.0), g), eps_w), hs) : eps2;
 
   R G[3], GB1 = R(0.0), GB3 = R(0.0);  // per-field sums over both sides; source fields 1 and 3
   const R* rp[4] = {r0, r1, r2, r3};
@@ -170,14 +187,14 @@ __device__ __forceinline__ void interface_values_m(const R* r0, const R* r1, con
   // back to physical components: 2 Fhat = R diag(1/s) G * 2
   R F2[3], B2[3];
   if (CHAR) {
-    const R A = (G[0] + G[2]) * ic2;
+    const R A = mul(G[0] + G[2], ic2);
     F2[0] = A;
-    F2[cn] = fma(un, A, R(0.5) * (G[2] - G[0]));
+    F2[cn] = fma(un, A, mul.k(R(0.5), G[2] - G[0]));
     F2[ct] = fma(ut, A, G[1]);
-    const R Bs = (GB1 + GB3) * ic2;
+    const R Bs = mul(GB1 + GB3, ic2);
     B2[0] = Bs;
-    B2[cn] = fma(un, Bs, R(0.5) * (GB3 - GB1));
-    B2[ct] = ut * Bs;
+    B2[cn] = fma(un, Bs, mul.k(R(0.5), GB3 - GB1));
+    B2[ct] = mul(ut, Bs);
   } else {
     F2[0] = G[0]; F2[cn] = G[1]; F2[ct] = G[2];
     B2[0] = R(0.0); B2[cn] = GB1; B2[ct] = R(0.0);
@@ -199,9 +216,9 @@ __device__ __forceinline__ void interface_values_m(const R* r0, const R* r1, con
 #undef RV
 }
 
-// One interface. IMUL: the multiplications of the nonlinear weights run on the integer pipes
-// (hw_fp64_int.h), bit-identical to DMUL; if any of them leaves the integer fast path (subnormal,
-// infinite or NaN data), the interface is recomputed on the FP64 pipe from the same records.
+// One interface. IMUL: the multiplications run on the integer pipes (hw_fp64_int.h), bit-identical
+// to DMUL; if any of them leaves the integer fast path (subnormal, infinite or NaN data), the
+// interface is recomputed on the FP64 pipe from the same records.
 template <int DIR, bool LINEAR, bool CHAR, bool IMUL = false, class R>
 __device__ __forceinline__ void interface_values(const R* r0, const R* r1, const R* r2,
                                                  const R* r3, int stride, const R qb[6], R g,
@@ -242,24 +259,25 @@ __device__ __forceinline__ void limit_dir(const R Um[3], const R U0[3], const R 
   };
   R m0[3], m1[3], m2[3], nl[3], nr[3];
   proj(Um, m0); proj(U0, m1); proj(Up, m2); proj(Dm, nl); proj(Dp, nr);
-  const R e13 = CHAR ? (R(4.0) * eps) * gh : eps;
+  const R e13 = CHAR ? mul(mul.k(R(4.0), eps), gh) : eps;
   R nu[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) nu[k] = limiter_field_m<LINEAR>(m0[k], m1[k], m2[k], nl[k], nr[k], k == 1 ? eps : e13, mul);
   if (CHAR) {
-    const R A = (nu[0] + nu[2]) * ic2;
+    const R A = mul(nu[0] + nu[2], ic2);
     out[0] = A;
-    out[cn] = fma(un, A, R(0.5) * (nu[2] - nu[0]));
+    out[cn] = fma(un, A, mul.k(R(0.5), nu[2] - nu[0]));
     out[ct] = fma(ut, A, nu[1]);
   } else {
     out[0] = nu[0]; out[cn] = nu[1]; out[ct] = nu[2];
   }
 }
 
-// RHS assembly, limiter and RK combination (or the bare RHS) at node (i, j) of one grid.
-// IMUL: the limiter's weight multiplications run on the integer pipes (see interface_values).
-template <int MODE, bool LINEAR, bool CHAR, bool IMUL = false, class R>
-__device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT<R>& sa, int i, int j) {
+// RHS assembly, limiter and RK combination (or the bare RHS) at node (i, j) of one grid, products
+// formed by `mul`. With MulInt nothing is written when a product left the integer fast path
+// (mul.bad); the caller then recomputes the node with MulFP64 from the same (unchanged) inputs.
+template <int MODE, bool LINEAR, bool CHAR, class R, class M>
+__device__ __forceinline__ void node_update_m(const Dev2DT<R>& d, const StageArgsT<R>& sa, int i, int j, M& mul) {
   const size_t o = (size_t)j * d.nx + i;
   const size_t ox = (size_t)j * (d.nx + 1) + i;  // left x-interface; right is ox + 1
   const size_t oy = (size_t)j * d.nx + i;        // lower y-interface; upper is oy + nx
@@ -277,7 +295,7 @@ __device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT
   // grid constants in the working precision
   const R c_bx = R(d.c_bx), c_by = R(d.c_by), c_gx = R(d.c_gx), c_gy = R(d.c_gy), c_mx = R(d.c_mx),
           c_my = R(d.c_my);
-  const R ge = g * eta;
+  const R ge = mul(g, eta);
   // ---- RHS (eq. swe-form-2d-dis) in scaled units: R_U, dx R_V, dy R_Q ----
   R Rv[9];
 #pragma unroll
@@ -290,23 +308,24 @@ __device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT
     const R dGy = __ldg(d.Y[6 + c] + oy + d.nx) - __ldg(d.Y[6 + c] + oy);
     const R dMx = __ldg(d.X[9 + c] + ox + 1) - __ldg(d.X[9 + c] + ox);
     const R dMy = __ldg(d.Y[9 + c] + oy + d.nx) - __ldg(d.Y[9 + c] + oy);
-    const R db = fma(c_bx, dbx, c_by * dby);  // [b~]_x/dx + [b-]_y/dy
-    Rv[c] = fma(-ge, db, fma(-c_bx, dFx, -c_by * dFy));
-    R rv = fma(-c_gx, dGx, -c_my * dMy);
-    R rq = fma(-c_mx, dMx, -c_gy * dGy);
+    const R db = fma(c_bx, dbx, mul(c_by, dby));  // [b~]_x/dx + [b-]_y/dy
+    Rv[c] = fma(-ge, db, fma(-c_bx, dFx, -mul(c_by, dFy)));
+    R rv = fma(-c_gx, dGx, -mul(c_my, dMy));
+    R rq = fma(-c_mx, dMx, -mul(c_gy, dGy));
     if (c > 0) {
       rv = fma(-ge, __ldg(d.sv[c - 1] + o), rv);
       rq = fma(-ge, __ldg(d.sq[c - 1] + o), rq);
     }
-    Rv[3 + c] = fma(-g * H1, db, rv);
-    Rv[6 + c] = fma(-g * H2, db, rq);
+    Rv[3 + c] = fma(-mul(g, H1), db, rv);
+    Rv[6 + c] = fma(-mul(g, H2), db, rq);
   }
   if (MODE == MODE_RHS) {
+    if (mul.bad) return;
     // physical units: R_V = (dx R_V)/dx, R_Q = (dy R_Q)/dy
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
       const R s = q < 3 ? R(1.0) : R(q < 6 ? d.inv_dx : d.inv_dy);
-      sa.rhs_out[q][o] = Rv[q] * s;
+      sa.rhs_out[q][o] = mul(Rv[q], s);
     }
     return;
   }
@@ -315,33 +334,19 @@ __device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT
   if (sa.limiter) {
     const R b0 = __ldg(d.stat[0] + o);
     const R h = eta - b0;
-    const R gh = g * h;
+    const R gh = mul(g, h);
     const R rh = fast_rcp(h);
-    const R u = cur[1] * rh, v = cur[2] * rh;
+    const R u = mul(cur[1], rh), v = mul(cur[2], rh);
     const R rs = fast_rsqrt(gh);
-    const R c = gh * rs, ic2 = R(0.5) * rs;
-    // both directions; with IMUL, if any product leaves the integer fast path, both directions are
-    // recomputed on the FP64 pipe (neighbours reloaded)
-    auto limit = [&](auto& mul) {
-      Node12T<R> nm, np;
-      load_node(d, i - 1, j, nm);
-      load_node(d, i + 1, j, np);
-      limit_dir<0, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 3, np.v + 3, u, v, c, ic2, gh, R(d.eps_lim), mod, mul);
-      load_node(d, i, j - 1, nm);
-      load_node(d, i, j + 1, np);
-      limit_dir<1, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 6, np.v + 6, u, v, c, ic2, gh, R(d.eps_lim), mod + 3, mul);
-    };
-    if constexpr (IMUL && !LINEAR && std::is_same<R, double>::value) {
-      MulInt mi;
-      limit(mi);
-      if (mi.bad) {
-        MulFP64 mf;
-        limit(mf);
-      }
-    } else {
-      MulFP64 mf;
-      limit(mf);
-    }
+    const R c = mul(gh, rs), ic2 = mul.k(R(0.5), rs);
+    Node12T<R> nm, np;
+    // x neighbours
+    load_node(d, i - 1, j, nm);
+    load_node(d, i + 1, j, np);
+    limit_dir<0, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 3, np.v + 3, u, v, c, ic2, gh, R(d.eps_lim), mod, mul);
+    load_node(d, i, j - 1, nm);
+    load_node(d, i, j + 1, np);
+    limit_dir<1, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 6, np.v + 6, u, v, c, ic2, gh, R(d.eps_lim), mod + 3, mul);
   } else {
 #pragma unroll
     for (int q = 0; q < 6; ++q) mod[q] = cur[3 + q];
@@ -349,6 +354,7 @@ __device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT
   // ---- SSP-RK3 combination (eq. RK) ----
   const R dt = R(*sa.dt);
   if (sa.k == 1) {
+    if (mul.bad) return;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
       const R cq = q < 3 ? cur[q] : mod[q - 3];
@@ -358,11 +364,32 @@ __device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT
   } else {
     const R a = sa.k == 2 ? R(0.75) : R(1.0) / R(3.0);
     const R b = sa.k == 2 ? R(0.25) : R(2.0) / R(3.0);
+    R res[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
       const R cq = q < 3 ? cur[q] : mod[q - 3];
-      sa.out[q][o] = fma(a, __ldg(sa.base[q] + o), b * fma(dt, Rv[q], cq));
+      res[q] = fma(a, __ldg(sa.base[q] + o), mul(b, fma(dt, Rv[q], cq)));
     }
+    if (mul.bad) return;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sa.out[q][o] = res[q];
+  }
+}
+
+// The node update. IMUL: products on the integer pipes (bit-identical to DMUL); if any leaves the
+// integer fast path, the node is recomputed on the FP64 pipe.
+template <int MODE, bool LINEAR, bool CHAR, bool IMUL = false, class R>
+__device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT<R>& sa, int i, int j) {
+  if constexpr (IMUL && !LINEAR && std::is_same<R, double>::value) {
+    MulInt mi;
+    node_update_m<MODE, LINEAR, CHAR>(d, sa, i, j, mi);
+    if (mi.bad) {
+      MulFP64 mf;
+      node_update_m<MODE, LINEAR, CHAR>(d, sa, i, j, mf);
+    }
+  } else {
+    MulFP64 mf;
+    node_update_m<MODE, LINEAR, CHAR>(d, sa, i, j, mf);
   }
 }
 
