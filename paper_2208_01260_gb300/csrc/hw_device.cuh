@@ -141,18 +141,13 @@ using Weights = WeightsT<double>;
 // Multiplication policies. MulFP64 multiplies on the FP64 pipe (DMUL, never contracted into an fma);
 // MulInt forms the same bits on the integer pipes (hw_fp64_int.h) and records whether any product
 // left its fast path, in which case the caller recomputes the block with MulFP64. k(c, x) multiplies
-// by a literal constant c; add(x, y) adds (on the integer pipes for MulInt). Float data is handled
-// natively by both.
+// by a literal constant c. Float data is multiplied natively by both.
 struct MulFP64 {
   static constexpr bool bad = false;
   __device__ __forceinline__ double operator()(double x, double y) { return __dmul_rn(x, y); }
   __device__ __forceinline__ float operator()(float x, float y) { return x * y; }
   __device__ __forceinline__ double k(double c, double x) { return __dmul_rn(x, c); }
   __device__ __forceinline__ float k(float c, float x) { return c * x; }
-  __device__ __forceinline__ double add(double x, double y) { return __dadd_rn(x, y); }
-  __device__ __forceinline__ float add(float x, float y) { return x + y; }
-  template <class R>
-  __device__ __forceinline__ R nadd(R x, R y) { return add(x, y); }
 };
 struct MulInt {
   bool bad = false;
@@ -168,14 +163,6 @@ struct MulInt {
     return r;
   }
   __device__ __forceinline__ float k(float c, float x) { return c * x; }
-  __device__ __forceinline__ double add(double x, double y) {
-    double r;
-    bad |= !f64_add_int(x, y, r);
-    return r;
-  }
-  __device__ __forceinline__ float add(float x, float y) { return x + y; }
-  __device__ __forceinline__ double nadd(double x, double y) { return __dadd_rn(x, y); }
-  __device__ __forceinline__ float nadd(float x, float y) { return x + y; }
 };
 
 // Unnormalised weights proportional to w_1/t_1^2, w_2/t_2^2, w_3/t_3^2 (t_l = beta_l + eps). In double the
@@ -219,10 +206,10 @@ __device__ __forceinline__ R hweno_side_m(R f0, R f1, R f2, R p0, R p1, R p2, R 
   const R b2 = fma(mul.k(R(781.0 / 20.0), B2), B2, fma(mul.k(R(13.0 / 3.0), A2), A2, pp));
   const R b3 = fma(mul.k(R(781.0 / 80.0), g3), g3, fma(mul.k(R(13.0 / 12.0), e), e, pp));
   R n3;
-  inverse_square_weights(mul.add(b1, eps), mul.add(b2, eps), mul.add(b3, eps), W.n1, W.n2, n3, mul);
+  inverse_square_weights(b1 + eps, b2 + eps, b3 + eps, W.n1, W.n2, n3, mul);
   // gamma = (3, 3, 4)/10 -> proportional to (1, 1, 4/3)
   W.n3 = mul.k(R(4.0 / 3.0), n3);
-  W.r = fast_rcp(mul.add(mul.add(W.n1, W.n2), W.n3));
+  W.r = fast_rcp(W.n1 + W.n2 + W.n3);
   return mul(fma(W.n1, q1, fma(W.n2, q2, mul(W.n3, q3))), W.r);
 }
 
@@ -262,8 +249,8 @@ __device__ __forceinline__ R limiter_field_m(R m0, R m1, R m2, R nl, R nr, R eps
   const R b3 = fma(mul.k(R(13.0 / 12.0), ac), ac, mul(mul.k(R(0.25), pc2), pc2));
   // d = (1, 1, 2)/4 -> proportional to (1, 1, 2); p'_3 = pc2 / 2 so its term is n3 pc2
   R n1, n2, n3;
-  inverse_square_weights(mul.add(b1, eps), mul.add(b2, eps), mul.add(b3, eps), n1, n2, n3, mul);
-  const R den = fma(R(2.0), n3, mul.add(n1, n2));
+  inverse_square_weights(b1 + eps, b2 + eps, b3 + eps, n1, n2, n3, mul);
+  const R den = fma(R(2.0), n3, n1 + n2);
   const R num = fma(n1, pl, fma(n2, pr, mul(n3, pc2)));
   return mul(num, fast_rcp(den));
 }

@@ -1,4 +1,4 @@
-// IEEE-754 binary64 multiplication and addition on the integer pipes.
+// IEEE-754 binary64 multiplication on the integer pipes.
 //
 // GB300 issues FP64 arithmetic at 2 lane-operations per SM per cycle, while its integer and FP32
 // pipes, which the FP64-bound kernels of this library leave almost idle, issue tens of times more.
@@ -101,52 +101,6 @@ HW_FP64_INT_FN bool f64_mul_int(double x, double y, double& out) {
   const uint32_t s = (ah ^ bh) & 0x80000000u;
   const uint64_t packed = ((uint64_t)(uint32_t)(E - 1) << 52) + m;  // hidden bit carries into E
   out = f64_from_words(zero ? 0u : (uint32_t)packed, zero ? s : (s | (uint32_t)(packed >> 32)));
-  return ok;
-}
-
-HW_FP64_INT_FN int u64_clz(uint64_t v) {
-#if defined(__CUDA_ARCH__)
-  return __clzll((long long)v);
-#else
-  return v ? __builtin_clzll(v) : 64;
-#endif
-}
-
-// x+y rounded to nearest even on the integer pipes; false (out unspecified) when an operand is
-// infinite or NaN or the sum is subnormal or overflows. Zero and subnormal operands are exact on the
-// fast path. Method: order the operands by magnitude, align the smaller significand (10 guard bits,
-// the bits shifted out folded into a sticky bit), add or subtract, normalise with a leading-zero
-// count and round to nearest even at the 53rd bit (Muller et al., Sec. 8.3).
-HW_FP64_INT_FN bool f64_add_int(double x, double y, double& out) {
-  uint32_t al, ah, bl, bh;
-  f64_words(x, al, ah);
-  f64_words(y, bl, bh);
-  const uint64_t A = ((uint64_t)(ah & 0x7fffffffu) << 32) | al, B = ((uint64_t)(bh & 0x7fffffffu) << 32) | bl;
-  const bool sw = B > A;
-  const uint64_t P = sw ? B : A, Q = sw ? A : B;  // |P| >= |Q|
-  const uint32_t sp = (sw ? bh : ah) & 0x80000000u;
-  const bool sub = ((ah ^ bh) & 0x80000000u) != 0;
-  const uint32_t ph = (uint32_t)(P >> 32), qh = (uint32_t)(Q >> 32);
-  const int ep = (int)(ph >> 20), eq = (int)(qh >> 20);
-  // significands (hidden bit only for normal numbers) in [2^62, 2^63) for normal operands
-  const uint64_t mp = ((uint64_t)((ph & 0xfffffu) | ((uint32_t)(ep != 0) << 20)) << 42) | ((uint64_t)(uint32_t)P << 10);
-  const uint64_t mq = ((uint64_t)((qh & 0xfffffu) | ((uint32_t)(eq != 0) << 20)) << 42) | ((uint64_t)(uint32_t)Q << 10);
-  const int epp = ep + (ep == 0), eqq = eq + (eq == 0);  // subnormals scale like exponent 1
-  int d = epp - eqq;
-  d = d < 63 ? d : 63;
-  const uint64_t kept = mq >> d;
-  const uint64_t mqs = kept | (uint64_t)((kept << d) != mq);  // sticky
-  const uint64_t S0 = sub ? mp - mqs : mp + mqs;
-  const int lz = u64_clz(S0);
-  const uint64_t S = S0 << (lz & 63);                        // leading one at bit 63
-  const int E = epp + 1 - lz;                                 // biased exponent of the result
-  const uint32_t low = (uint32_t)S;
-  const uint64_t up = ((low >> 10) & 1u) & (((low & 0x3ffu) != 0u) | ((low >> 11) & 1u));
-  const uint64_t m = (S >> 11) + up;                          // [2^52, 2^53]
-  const bool zero = S0 == 0;                                  // exact cancellation or two zeros
-  const bool ok = (ep != 0x7ff) & (eq != 0x7ff) & (zero | ((unsigned)(E - 1) < 2045u));
-  const uint64_t packed = ((uint64_t)(uint32_t)(E - 1) << 52) + m;
-  out = f64_from_words(zero ? 0u : (uint32_t)packed, zero ? (ah & bh & 0x80000000u) : (sp | (uint32_t)(packed >> 32)));
   return ok;
 }
 

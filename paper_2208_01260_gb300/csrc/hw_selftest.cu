@@ -1,5 +1,5 @@
-// Device self-check of the integer-pipe binary64 multiply and add (hw_fp64_int.h) against the FP64
-// pipe's DMUL and DADD on the device itself (hwswe.h: hw_selftest_fp64_int).
+// Device self-check of the integer-pipe binary64 multiply (hw_fp64_int.h) against the FP64 pipe's
+// DMUL on the device itself (hwswe.h: hw_selftest_mul_int).
 #include <cuda_runtime.h>
 
 #include "hw_fp64_int.h"
@@ -16,7 +16,7 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
-__global__ void k_selftest(int op, long long n, unsigned long long seed, unsigned long long* cnt) {
+__global__ void k_selftest_mul(long long n, unsigned long long seed, unsigned long long* cnt) {
   const unsigned long long SGN_FRAC = 0x800fffffffffffffull;
   unsigned long long acc = 0, bad = 0, missed = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -50,22 +50,16 @@ __global__ void k_selftest(int op, long long n, unsigned long long seed, unsigne
       default:
         break;
     }
-    if (op == 1 && ((c >> 40) & 1)) {  // additions: also near-cancelling and widely separated operands
-      if ((c >> 41) & 1) b = (a ^ ((c >> 42) & 0xffffull)) ^ 0x8000000000000000ull;
-      else b = (b & SGN_FRAC) | (unsigned long long)(((a >> 52) & 0x7ff) - (c >> 44) % 70) << 52;
-    }
     const double x = __longlong_as_double((long long)a), y = __longlong_as_double((long long)b);
-    const double t = op == 0 ? __dmul_rn(x, y) : __dadd_rn(x, y);
+    const double t = __dmul_rn(x, y);
     double r;
-    if (op == 0 ? f64_mul_int(x, y, r) : f64_add_int(x, y, r)) {
+    if (f64_mul_int(x, y, r)) {
       ++acc;
       bad += __double_as_longlong(r) != __double_as_longlong(t);
     } else {
       const unsigned ex = (unsigned)(a >> 52) & 0x7ffu, ey = (unsigned)(b >> 52) & 0x7ffu;
       const double at = fabs(t);
-      const bool normal_in = op == 0 ? (ex != 0 && ey != 0) : true;
-      const bool normal_out = (at >= 0x1p-1021 && at < 0x1p1022) || (op == 1 && t == 0.0);
-      missed += (normal_in && ex != 0x7ff && ey != 0x7ff && normal_out);
+      missed += (ex != 0 && ex != 0x7ff && ey != 0 && ey != 0x7ff && at >= 0x1p-1021 && at < 0x1p1022);
     }
   }
   atomicAdd(cnt, acc);
@@ -76,14 +70,14 @@ __global__ void k_selftest(int op, long long n, unsigned long long seed, unsigne
 }  // namespace
 }  // namespace hw
 
-extern "C" int hw_selftest_fp64_int(int op, long long n, unsigned long long seed, long long* counts) {
-  if ((op != 0 && op != 1) || n < 1 || counts == nullptr) return HW_ERR_ARG;
+extern "C" int hw_selftest_mul_int(long long n, unsigned long long seed, long long* counts) {
+  if (n < 1 || counts == nullptr) return HW_ERR_ARG;
   unsigned long long* d = nullptr;
   if (cudaMalloc(&d, 3 * sizeof(unsigned long long)) != cudaSuccess) return HW_ERR_CUDA;
   unsigned long long h[3] = {0, 0, 0};
   cudaError_t e = cudaMemset(d, 0, sizeof(h));
   if (e == cudaSuccess) {
-    hw::k_selftest<<<1216, 256>>>(op, n, seed, d);
+    hw::k_selftest_mul<<<1216, 256>>>(n, seed, d);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);

@@ -1,6 +1,6 @@
-"""The integer-pipe binary64 multiply and add of the CUDA kernels (csrc/hw_fp64_int.h), compiled for the
-host: every result their fast paths accept equals the host's IEEE-754 arithmetic bit for bit, and they
-accept every finite operand pair whose result is normal (the kernels' data), plus signed zeros."""
+"""The integer-pipe binary64 multiply of the CUDA kernels (csrc/hw_fp64_int.h), compiled for the host:
+every product its fast path accepts equals the host's IEEE-754 multiply bit for bit, and it accepts
+every product of normal operands whose result is normal (the kernels' data), plus signed zeros."""
 import os
 import shutil
 import subprocess
@@ -25,15 +25,6 @@ def checker(tmp_path_factory):
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_integer_multiply_matches_ieee(checker, seed):
     r = subprocess.run([checker, "3000000", str(seed)], capture_output=True, text=True)
-    assert r.returncode == 0, r.stdout + r.stderr
-    accepted, bad, missed = (int(v) for v in r.stdout.split()[-3:])
-    assert bad == 0 and missed == 0
-    assert accepted > 2000000
-
-
-@pytest.mark.parametrize("seed", [1, 2, 3])
-def test_integer_add_matches_ieee(checker, seed):
-    r = subprocess.run([checker, "3000000", str(seed), "add"], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     accepted, bad, missed = (int(v) for v in r.stdout.split()[-3:])
     assert bad == 0 and missed == 0
