@@ -138,16 +138,17 @@ struct WeightsT {
 };
 using Weights = WeightsT<double>;
 
-// Multiplication policies. MulFP64 multiplies on the FP64 pipe (DMUL, never contracted into an fma);
-// MulInt forms the same bits on the integer pipes (hw_fp64_int.h) and records whether any product
-// left its fast path, in which case the caller recomputes the block with MulFP64. k(c, x) multiplies
-// by a literal constant c. Float data is multiplied natively by both.
+// Multiplication policies. MulFP64 is the plain product on the FP64 pipe (the compiler may fuse it
+// with a following add into an fma); MulInt forms the correctly rounded product on the integer pipes
+// (hw_fp64_int.h, bit-identical to DMUL) and records whether any product left its fast path, in which
+// case the caller recomputes the block with MulFP64. k(c, x) multiplies by a literal constant c. Float
+// data is multiplied natively by both.
 struct MulFP64 {
   static constexpr bool bad = false;
-  __device__ __forceinline__ double operator()(double x, double y) { return __dmul_rn(x, y); }
-  __device__ __forceinline__ float operator()(float x, float y) { return x * y; }
-  __device__ __forceinline__ double k(double c, double x) { return __dmul_rn(x, c); }
-  __device__ __forceinline__ float k(float c, float x) { return c * x; }
+  template <class R>
+  __device__ __forceinline__ R operator()(R x, R y) { return x * y; }
+  template <class R>
+  __device__ __forceinline__ R k(R c, R x) { return c * x; }
 };
 struct MulInt {
   bool bad = false;

@@ -21,8 +21,8 @@ constexpr int XS_N = XS_T + 3;
 
 // The double kernels move part of their products and sums to the integer pipes (bit-identical
 // results, hw_fp64_int.h): the FP64 pipe is their bound, the integer pipes idle. How much moves is
-// set per kernel by measurement: the x-sweep the reconstruction and weights (its records and
-// interface state stay on the FP64 pipe), the y-sweep also the interface state, the node kernel all.
+// set per kernel by measurement: the x-sweep the reconstruction and weights, the y-sweep also the
+// interface state, the node kernel all; the node records stay on the FP64 pipe.
 template <class R>
 constexpr bool kIntMul = std::is_same<R, double>::value;
 template <class R>
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(XS_T, 2) k_sweep_x(Dev2DT<R> d, const R* __res
     Node12T<R> n;
     load_node(d, i, j, n);
     R rec[NREC];
-    node_record<0, false>(n, R(d.g), ax, rec);
+    node_record<0>(n, R(d.g), ax, rec);
 #pragma unroll
     for (int f = 0; f < NREC; ++f) sm[f * XS_N + t] = rec[f];
   }
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(YS_W, 12) k_sweep_y(Dev2DT<R> d, const R* __re
     Node12T<R> n;
     load_node(d, i, r, n);
     R rec[NREC];
-    node_record<1, kIntMul<R>>(n, R(d.g), ay, rec);
+    node_record<1>(n, R(d.g), ay, rec);
     R* slot = ring + (size_t)(r & 3) * NREC * YS_W + threadIdx.x;
 #pragma unroll
     for (int f = 0; f < NREC; ++f) slot[f * stride] = rec[f];

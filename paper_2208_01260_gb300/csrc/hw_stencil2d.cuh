@@ -93,21 +93,11 @@ __device__ __forceinline__ void node_record_m(const Node12T<R>& n, R g, R alpha,
   rec[R_W] = w;
 }
 
-// The record; IMUL: products on the integer pipes, recomputed on the FP64 pipe if any leaves the
-// integer fast path.
-template <int DIR, bool IMUL = false, class R>
+// The record on the FP64 pipe (moving its products to the integer pipes measured slower).
+template <int DIR, class R>
 __device__ __forceinline__ void node_record(const Node12T<R>& n, R g, R alpha, R rec[NREC]) {
-  if constexpr (IMUL && std::is_same<R, double>::value) {
-    MulInt mi;
-    node_record_m<DIR>(n, g, alpha, rec, mi);
-    if (mi.bad) {
-      MulFP64 mf;
-      node_record_m<DIR>(n, g, alpha, rec, mf);
-    }
-  } else {
-    MulFP64 mf;
-    node_record_m<DIR>(n, g, alpha, rec, mf);
-  }
+  MulFP64 mf;
+  node_record_m<DIR>(n, g, alpha, rec, mf);
 }
 
 // ---------------------------------------------------------------------------------------------
