@@ -125,7 +125,7 @@ __device__ __forceinline__ float dabs(float x) { return fabsf(x); }
 // Algebra (exact rearrangement of the printed q_l and beta_l):
 //   d1 = f0 - f1, d2 = f1 - f2, B1 = 2 d1 + p0 + p1, A1 = B1 + d1 + p1, B2 = 2 d2 + p1 + p2,
 //   A2 = B2 + d2 + p1, e = f0 - 2 f1 + f2, g3 = f0 - f2 + 2 p1, P = f1 + p1/2;
-//   q1 = P + A1/6, q2 = P - A2/6, q3 = P + e/12;
+//   q1 = P + A1/6, q2 = P - A2/6, q3 = P + e/12 (weights summing to 1 leave P outside the weighted sum);
 //   beta1 = p1^2 + 13/3 A1^2 + 781/20 B1^2, beta2 = p1^2 + 13/3 A2^2 + 781/20 B2^2,
 //   beta3 = p1^2 + 13/12 e^2 + 781/80 g3^2.
 // ---------------------------------------------------------------------------------------------
@@ -194,10 +194,10 @@ __device__ __forceinline__ R hweno_side_m(R f0, R f1, R f2, R p0, R p1, R p2, R 
   const R A2 = B2 + (d2 + p1);
   const R P = fma(R(0.5), p1, f1);
   const R e = fma(R(-2.0), f1, f0 + f2);
-  const R q1 = fma(R(1.0 / 6.0), A1, P);
-  const R q2 = fma(R(-1.0 / 6.0), A2, P);
-  const R q3 = fma(R(1.0 / 12.0), e, P);
   if (LINEAR) {
+    const R q1 = fma(R(1.0 / 6.0), A1, P);
+    const R q2 = fma(R(-1.0 / 6.0), A2, P);
+    const R q3 = fma(R(1.0 / 12.0), e, P);
     W.n1 = R(0.3); W.n2 = R(0.3); W.n3 = R(0.4); W.r = R(1.0);
     return fma(R(0.3), q1, fma(R(0.3), q2, mul.k(R(0.4), q3)));
   }
@@ -211,7 +211,9 @@ __device__ __forceinline__ R hweno_side_m(R f0, R f1, R f2, R p0, R p1, R p2, R 
   // gamma = (3, 3, 4)/10 -> proportional to (1, 1, 4/3)
   W.n3 = mul.k(R(4.0 / 3.0), n3);
   W.r = fast_rcp(W.n1 + W.n2 + W.n3);
-  return mul(fma(W.n1, q1, fma(W.n2, q2, mul(W.n3, q3))), W.r);
+  // sum(omega_l q_l) = P + (n1 A1 - n2 A2 + (n3'/2) e) / (6 (n1 + n2 + n3')), n3' = W.n3
+  const R z = fma(mul.k(R(0.5), W.n3), e, fma(-W.n2, A2, mul(W.n1, A1)));
+  return fma(mul.k(R(1.0 / 6.0), W.r), z, P);
 }
 
 // One side on the FP64 pipe (the 1D kernels, the batched form and the adjoint's recomputation).
