@@ -5,7 +5,8 @@
 // grids no longer leave the GPU idle. Two steps are captured in a CUDA graph. Tile shapes (interfaces
 // per x-tile, interfaces per y-segment) are per instance, chosen by the autotuner. The arithmetic is
 // the single-grid kernels' (hw_stencil2d.cuh), so each instance's result equals a single-grid
-// solver's to rounding (the compiler may contract multiply-adds differently in the two kernels).
+// solver's to rounding (the compiler may contract multiply-adds differently in the two kernels),
+// with the same share of products on the integer pipes (bit-identical binary64, hw_fp64_int.h).
 // No block ever waits on another block.
 #include <algorithm>
 #include <string>
@@ -129,7 +130,7 @@ __global__ void k_btime(BatchDev B, int n) {
 
 // ---- x-sweep: items (inst, first row, first interface) ----
 template <bool LINEAR, bool CHAR>
-__global__ void __launch_bounds__(BX_THREADS) k_bsweep_x(BatchDev B, const int4* __restrict__ items, int nitems) {
+__global__ void __launch_bounds__(BX_THREADS, 3) k_bsweep_x(BatchDev B, const int4* __restrict__ items, int nitems) {
   __shared__ double sm[NREC * BX_MAXN];
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int4 it = items[w];
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(BX_THREADS) k_bsweep_x(BatchDev B, const int4*
 #pragma unroll
       for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qbx[q] + o);
       double out[12];
-      interface_values<0, LINEAR, CHAR>(sm + t0, sm + t0 + 1, sm + t0 + 2, sm + t0 + 3, stride, qb, d.g, d.eps_w, out);
+      interface_values<0, LINEAR, CHAR, 1>(sm + t0, sm + t0 + 1, sm + t0 + 2, sm + t0 + 3, stride, qb, d.g, d.eps_w, out);
 #pragma unroll
       for (int q = 0; q < 12; ++q) d.X[q][o] = out[q];
     }
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(BX_THREADS) k_bsweep_x(BatchDev B, const int4*
 
 // ---- y-sweep: items (inst, first column, first interface); each thread marches its column ----
 template <bool LINEAR, bool CHAR>
-__global__ void __launch_bounds__(BY_W) k_bsweep_y(BatchDev B, const int4* __restrict__ items, int nitems) {
+__global__ void __launch_bounds__(BY_W, 12) k_bsweep_y(BatchDev B, const int4* __restrict__ items, int nitems) {
   extern __shared__ double ring[];  // [4][NREC][BY_W]
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int4 it = items[w];
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(BY_W) k_bsweep_y(BatchDev B, const int4* __res
 #pragma unroll
         for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qby[q] + o);
         double out[12];
-        interface_values<1, LINEAR, CHAR>(s0, s1, s2, s3, BY_W, qb, d.g, d.eps_w, out);
+        interface_values<1, LINEAR, CHAR, 2>(s0, s1, s2, s3, BY_W, qb, d.g, d.eps_w, out);
 #pragma unroll
         for (int q = 0; q < 12; ++q) d.Y[q][o] = out[q];
       }
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(BY_W) k_bsweep_y(BatchDev B, const int4* __res
 
 // ---- node update: items (inst, first column, first row) of 32 x 8 tiles ----
 template <bool LINEAR, bool CHAR>
-__global__ void __launch_bounds__(256) k_bnode(BatchDev B, const int4* __restrict__ items, int nitems) {
+__global__ void __launch_bounds__(256, 2) k_bnode(BatchDev B, const int4* __restrict__ items, int nitems) {
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int4 it = items[w];
     const BInst I = B.inst[it.x];
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(256) k_bnode(BatchDev B, const int4* __restric
       sa.base[q] = B.base[q] + I.off_n;
       sa.rhs_out[q] = nullptr;
     }
-    node_update<MODE_STAGE, LINEAR, CHAR>(d, sa, i, j);
+    node_update<MODE_STAGE, LINEAR, CHAR, true>(d, sa, i, j);
   }
 }
 
