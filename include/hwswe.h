@@ -255,16 +255,18 @@ int hw_adjoint_run(hw_solver* s, int nsteps, const double* dts, const int* gauge
 int hw_rhs1d_noalloc(const hw_grid* grid, const hw_params* params, const double* h, const double* hu,
                      const double* b, const double* const* deriv, double* const* out, void* cuda_stream);
 
-/* Self-check of the integer-pipe FP64 multiply that the 2D double kernels use for the products of
- * their nonlinear weights (no counterpart in the paper; an implementation device of this library).
- * On the current device, n seeded pseudo-random operand pairs (mixed distributions: the scheme's
- * range, short significands, near-squares, signed zeros, the edges of the normal range, subnormal,
- * infinite and NaN operands) are multiplied by the integer path and by the FP64 pipe's DMUL. counts
- * (host, 3 entries): products the integer fast path accepted, accepted products that differ from
- * DMUL in any bit, and products of normal operands with a normal result that the fast path rejected
- * (both must be 0). Synchronous on the legacy default stream; allocates and frees 24 bytes.
- * HW_ERR_ARG for n < 1 or counts == NULL, HW_ERR_CUDA on a CUDA failure. */
-int hw_selftest_mul_int(long long n, unsigned long long seed, long long* counts);
+/* Self-check of the integer-pipe FP64 arithmetic that the 2D double kernels use for part of their
+ * products and reciprocals (no counterpart in the paper; an implementation device of this library).
+ * On the current device, n seeded pseudo-random operands go through the integer path and the FP64 pipe.
+ * op 0, products against DMUL (operand mix: the scheme's range, short significands, near-squares,
+ * signed zeros, the edges of the normal range, subnormal, infinite and NaN operands); op 1, reciprocals
+ * against the correctly rounded __drcp_rn (significands near 1 and 2, every exponent). counts (host,
+ * 3 entries): results the integer fast path accepted; accepted results that differ from the FP64
+ * pipe's in any bit (op 0) or by more than one ulp (op 1); operands the fast path must take but
+ * rejected (normal operands with a normal result). The last two must be 0. Synchronous on the legacy
+ * default stream; allocates and frees 24 bytes. HW_ERR_ARG for another op, n < 1 or counts == NULL,
+ * HW_ERR_CUDA on a CUDA failure. */
+int hw_selftest_fp64_int(int op, long long n, unsigned long long seed, long long* counts);
 
 /* Wait for the stream and return the device status as an HW_ERR_* code (HW_OK if clean). */
 int hw_sync(hw_solver* s);

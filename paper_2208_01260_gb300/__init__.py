@@ -33,7 +33,7 @@ __all__ = [
     "HW_LAYOUT_EQUILIBRIUM", "HwError", "hw_grid", "hw_params", "lib", "make_grid", "make_params",
     "hw_create", "hw_destroy", "hw_init", "hw_rhs", "hw_alpha", "hw_cfl_dt", "hw_rk3_step", "hw_rk3_stage",
     "hw_advance", "hw_get_state", "hw_set_state", "hw_get_base", "hw_sync", "hw_version", "Solver",
-    "hw_set_profiling", "hw_get_profile", "hw_get_time", "hw_set_time", "hw_rhs1d_noalloc", "hw_selftest_mul_int", "BatchedSolver", "hw_batch_create",
+    "hw_set_profiling", "hw_get_profile", "hw_get_time", "hw_set_time", "hw_rhs1d_noalloc", "hw_selftest_fp64_int", "BatchedSolver", "hw_batch_create",
     "hw_batch_destroy", "hw_batch_init", "hw_batch_run", "hw_batch_get_state", "hw_batch_get_time",
     "hw_batch_set_tiles", "hw_batch_get_tiles", "hw_batch_time_tiles",
 ]
@@ -99,7 +99,7 @@ def lib():
             "hw_get_profile": ([vp, dp, C.POINTER(C.c_int)], i),
             "hw_get_time": ([vp, dp, C.POINTER(C.c_longlong)], i),
             "hw_set_time": ([vp, C.c_double, C.c_longlong], i),
-            "hw_selftest_mul_int": ([C.c_longlong, C.c_ulonglong, C.POINTER(C.c_longlong)], i),
+            "hw_selftest_fp64_int": ([i, C.c_longlong, C.c_ulonglong, C.POINTER(C.c_longlong)], i),
             "hw_last_error": ([], C.c_char_p),
             "hw_version": ([], C.c_char_p),
         }
@@ -296,11 +296,12 @@ def hw_set_time(h: _Handle, t: float, steps: int):
     _check(lib().hw_set_time(h.ptr, float(t), int(steps)), "hw_set_time")
 
 
-def hw_selftest_mul_int(n: int, seed: int = 1):
-    """Device check of the integer-pipe FP64 multiply against DMUL on n operand pairs: returns
-    (accepted, mismatches, rejected normal products); the last two must be 0."""
+def hw_selftest_fp64_int(op: int, n: int, seed: int = 1):
+    """Device check of the integer-pipe FP64 multiply (op 0, bitwise against DMUL) or reciprocal (op 1,
+    within one ulp of the correctly rounded one) on n operands: returns (accepted, mismatches,
+    rejected operands that the fast path must take); the last two must be 0."""
     counts = (C.c_longlong * 3)()
-    _check(lib().hw_selftest_mul_int(int(n), int(seed), counts), "hw_selftest_mul_int")
+    _check(lib().hw_selftest_fp64_int(int(op), int(n), int(seed), counts), "hw_selftest_fp64_int")
     return tuple(int(v) for v in counts)
 
 

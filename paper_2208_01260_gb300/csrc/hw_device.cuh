@@ -141,16 +141,21 @@ using Weights = WeightsT<double>;
 // Multiplication policies. MulFP64 is the plain product on the FP64 pipe (the compiler may fuse it
 // with a following add into an fma); MulInt forms the correctly rounded product on the integer pipes
 // (hw_fp64_int.h, bit-identical to DMUL) and records whether any product left its fast path, in which
-// case the caller recomputes the block with MulFP64. k(c, x) multiplies by a literal constant c. Float
-// data is multiplied natively by both.
+// case the caller recomputes the block with MulFP64. k(c, x) multiplies by a literal constant c;
+// rcp(x) is the reciprocal (fast_rcp on the FP64 pipe; for MulIntT<true> the integer form, within one
+// ulp).
+// Float data is handled natively by both.
 struct MulFP64 {
   static constexpr bool bad = false;
   template <class R>
   __device__ __forceinline__ R operator()(R x, R y) { return x * y; }
   template <class R>
   __device__ __forceinline__ R k(R c, R x) { return c * x; }
+  template <class R>
+  __device__ __forceinline__ R rcp(R x) { return fast_rcp(x); }
 };
-struct MulInt {
+template <bool IRCP>
+struct MulIntT {
   bool bad = false;
   __device__ __forceinline__ double operator()(double x, double y) {
     double r;
@@ -164,7 +169,15 @@ struct MulInt {
     return r;
   }
   __device__ __forceinline__ float k(float c, float x) { return c * x; }
+  __device__ __forceinline__ double rcp(double x) {
+    if constexpr (!IRCP) return fast_rcp(x);
+    double r;
+    bad |= !f64_rcp_int(x, r);
+    return r;
+  }
+  __device__ __forceinline__ float rcp(float x) { return fast_rcp(x); }
 };
+using MulInt = MulIntT<true>;
 
 // Unnormalised weights proportional to w_1/t_1^2, w_2/t_2^2, w_3/t_3^2 (t_l = beta_l + eps). In double the
 // products of the other two squares (one reciprocal); in float, where t^4 can overflow on large jumps,
@@ -210,7 +223,7 @@ __device__ __forceinline__ R hweno_side_m(R f0, R f1, R f2, R p0, R p1, R p2, R 
   inverse_square_weights(b1 + eps, b2 + eps, b3 + eps, W.n1, W.n2, n3, mul);
   // gamma = (3, 3, 4)/10 -> proportional to (1, 1, 4/3)
   W.n3 = mul.k(R(4.0 / 3.0), n3);
-  W.r = fast_rcp(W.n1 + W.n2 + W.n3);
+  W.r = mul.rcp(W.n1 + W.n2 + W.n3);
   // sum(omega_l q_l) = P + (n1 A1 - n2 A2 + (n3'/2) e) / (6 (n1 + n2 + n3')), n3' = W.n3
   const R z = fma(mul.k(R(0.5), W.n3), e, fma(-W.n2, A2, mul(W.n1, A1)));
   return fma(mul.k(R(1.0 / 6.0), W.r), z, P);
@@ -255,7 +268,7 @@ __device__ __forceinline__ R limiter_field_m(R m0, R m1, R m2, R nl, R nr, R eps
   inverse_square_weights(b1 + eps, b2 + eps, b3 + eps, n1, n2, n3, mul);
   const R den = fma(R(2.0), n3, n1 + n2);
   const R num = fma(n1, pl, fma(n2, pr, mul(n3, pc2)));
-  return mul(num, fast_rcp(den));
+  return mul(num, mul.rcp(den));
 }
 template <bool LINEAR, class R>
 __device__ __forceinline__ R limiter_field(R m0, R m1, R m2, R nl, R nr, R eps) {

@@ -1,4 +1,4 @@
-// IEEE-754 binary64 multiplication on the integer pipes.
+// IEEE-754 binary64 multiplication (and a faithful reciprocal) on the integer pipes.
 //
 // GB300 issues FP64 arithmetic at 2 lane-operations per SM per cycle, while its integer and FP32
 // pipes, which the FP64-bound kernels of this library leave almost idle, issue tens of times more.
@@ -101,6 +101,80 @@ HW_FP64_INT_FN bool f64_mul_int(double x, double y, double& out) {
   const uint32_t s = (ah ^ bh) & 0x80000000u;
   const uint64_t packed = ((uint64_t)(uint32_t)(E - 1) << 52) + m;  // hidden bit carries into E
   out = f64_from_words(zero ? 0u : (uint32_t)packed, zero ? s : (s | (uint32_t)(packed >> 32)));
+  return ok;
+}
+
+// Seed of the reciprocal: 1/mf for mf in [1, 2) to about 22 bits (the SFU's approximation on the device).
+HW_FP64_INT_FN float f32_rcp_seed(float mf) {
+#if defined(__CUDA_ARCH__)
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(mf));
+  return r;
+#else
+  return 1.0f / mf;
+#endif
+}
+
+HW_FP64_INT_FN uint32_t f32_bits(float x) {
+#if defined(__CUDA_ARCH__)
+  return __float_as_uint(x);
+#else
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  return u;
+#endif
+}
+
+HW_FP64_INT_FN float f32_from_bits(uint32_t u) {
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(u);
+#else
+  float x;
+  memcpy(&x, &u, 4);
+  return x;
+#endif
+}
+
+HW_FP64_INT_FN int64_t s64_mulhi(int64_t a, int64_t b) {
+#if defined(__CUDA_ARCH__)
+  return __mul64hi(a, b);
+#else
+  return (int64_t)(((__int128)a * b) >> 64);
+#endif
+}
+
+// 1/x on the integer pipes, within one ulp (faithfully rounded; round to nearest of an approximation
+// accurate to about 2^-60). False (out unspecified) unless x is normal with a biased exponent of at most
+// 2044, i.e. the reciprocal is normal. Method (Newton-Raphson with a cubic step, e.g. Muller et al.,
+// Sec. 9.2): a seed Y0 ~ 2^83/M (22 bits) of the significand M in [2^52, 2^53) from the single-precision
+// reciprocal; the residual E = 2^83 - M*Y0 (exact in 64-bit two's complement for a seed error below
+// 2^-20); then 2^116/M ~ Y0 (2^33 + (E + E^2/2^83) / 2^50), rounded to 53 bits.
+template <int SEED_ERR = 0>
+HW_FP64_INT_FN bool f64_rcp_int(double x, double& out) {
+  uint32_t al, ah;
+  f64_words(x, al, ah);
+  const uint32_t ex = (ah >> 20) & 0x7ffu;
+  const uint32_t fh = ah & 0xfffffu;
+  const bool ok = (ex - 1u) < 2044u;
+  // seed from the leading 23 fraction bits: mf in [1, 2), r ~ 1/mf (about 1/2 to 1)
+  const float mf = f32_from_bits(0x3f800000u | (fh << 3) | (al >> 29));
+  const uint32_t rb = f32_bits(f32_rcp_seed(mf)) + (uint32_t)SEED_ERR;  // SEED_ERR: host tests only
+  // Y0 = r 2^31 from r's significand and exponent (125..127)
+  const uint32_t Y0 = ((rb & 0x7fffffu) | 0x800000u) << ((rb >> 23) - 119u);
+  const uint32_t mh = fh | 0x100000u;
+  // E = 2^83 - M Y0 mod 2^64, with M = mh 2^32 + al
+  const uint64_t Plo = ((uint64_t)(mh * Y0) << 32) + (uint64_t)al * Y0;
+  const int64_t E = -(int64_t)Plo;
+  const uint64_t aE = (uint64_t)(E < 0 ? -E : E);
+  const int64_t T = E + (int64_t)(u64_mulhi(aE, aE) >> 19);              // E + E^2 / 2^83
+  const int64_t corr = s64_mulhi(T, (int64_t)((uint64_t)Y0 << 31)) >> 17;  // Y0 T / 2^50
+  const uint64_t Y = ((uint64_t)Y0 << 33) + (uint64_t)corr;  // ~ 2^116 / M (mod 2^64), in (2^63, 2^64)
+  const uint64_t Q = (Y + 0x400u) >> 11;                       // 53-bit significand of 2^53/M
+  const bool pow2 = (fh | al) == 0u;
+  const uint32_t s = ah & 0x80000000u;
+  // result exponent: 2045 - ex (2046 - ex for a power-of-two significand, whose reciprocal is exact)
+  const uint64_t packed = ((uint64_t)(2044u - ex) << 52) + Q;
+  out = f64_from_words(pow2 ? 0u : (uint32_t)packed, s | (pow2 ? (2046u - ex) << 20 : (uint32_t)(packed >> 32)));
   return ok;
 }
 

@@ -1,5 +1,5 @@
-// Device self-check of the integer-pipe binary64 multiply (hw_fp64_int.h) against the FP64 pipe's
-// DMUL on the device itself (hwswe.h: hw_selftest_mul_int).
+// Device self-check of the integer-pipe binary64 multiply and reciprocal (hw_fp64_int.h) against the
+// FP64 pipe on the device itself (hwswe.h: hw_selftest_fp64_int).
 #include <cuda_runtime.h>
 
 #include "hw_fp64_int.h"
@@ -67,17 +67,46 @@ __global__ void k_selftest_mul(long long n, unsigned long long seed, unsigned lo
   atomicAdd(cnt + 2, missed);
 }
 
+// Reciprocals against the correctly rounded __drcp_rn: accepted results more than one ulp away count as
+// mismatches; operands with a normal reciprocal (biased exponent 1..2044) must be accepted.
+__global__ void k_selftest_rcp(long long n, unsigned long long seed, unsigned long long* cnt) {
+  unsigned long long acc = 0, bad = 0, missed = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long c = mix64(seed ^ (5ull * i));
+    unsigned long long a = mix64(c + 1);
+    if (c % 3 == 1) a = (a & 0x800fffffffffffffull) | (unsigned long long)(1000 + (c >> 8) % 48) << 52;
+    if (c % 3 == 2)  // significands near 1 and near 2, all exponents of the fast path
+      a = (a & 0x80000000000fffffull) | (unsigned long long)(1 + (c >> 8) % 2044) << 52 |
+          (((c >> 20) & 1) ? 0ull : 0x000ffffffff00000ull);
+    const double x = __longlong_as_double((long long)a);
+    const unsigned ex = (unsigned)(a >> 52) & 0x7ffu;
+    double r;
+    if (f64_rcp_int(x, r)) {
+      ++acc;
+      const long long d = __double_as_longlong(r) - __double_as_longlong(__drcp_rn(x));
+      bad += (d > 1 || d < -1);
+    } else {
+      missed += (ex >= 1 && ex <= 2044);
+    }
+  }
+  atomicAdd(cnt, acc);
+  atomicAdd(cnt + 1, bad);
+  atomicAdd(cnt + 2, missed);
+}
+
 }  // namespace
 }  // namespace hw
 
-extern "C" int hw_selftest_mul_int(long long n, unsigned long long seed, long long* counts) {
-  if (n < 1 || counts == nullptr) return HW_ERR_ARG;
+extern "C" int hw_selftest_fp64_int(int op, long long n, unsigned long long seed, long long* counts) {
+  if ((op != 0 && op != 1) || n < 1 || counts == nullptr) return HW_ERR_ARG;
   unsigned long long* d = nullptr;
   if (cudaMalloc(&d, 3 * sizeof(unsigned long long)) != cudaSuccess) return HW_ERR_CUDA;
   unsigned long long h[3] = {0, 0, 0};
   cudaError_t e = cudaMemset(d, 0, sizeof(h));
   if (e == cudaSuccess) {
-    hw::k_selftest_mul<<<1216, 256>>>(n, seed, d);
+    if (op == 0) hw::k_selftest_mul<<<1216, 256>>>(n, seed, d);
+    else hw::k_selftest_rcp<<<1216, 256>>>(n, seed, d);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);

@@ -208,15 +208,16 @@ __device__ __forceinline__ void interface_values_m(const R* r0, const R* r1, con
 }
 
 // One interface. IM: 0 all products on the FP64 pipe; 1 the reconstruction's and weights' products
-// on the integer pipes (hw_fp64_int.h, bit-identical to DMUL/DADD); 2 also those of the interface state
-// and back-projection. If any integer operation leaves its fast path (subnormal, infinite or NaN data),
+// and the weights' reciprocals on the integer pipes (hw_fp64_int.h: products bit-identical to DMUL,
+// reciprocals within one ulp); 2 the products of the reconstruction, weights, interface state and
+// back-projection, reciprocals on the FP64 pipe. If any integer operation leaves its fast path (subnormal, infinite or NaN data),
 // the interface is recomputed on the FP64 pipe from the same records.
 template <int DIR, bool LINEAR, bool CHAR, int IM = 0, class R>
 __device__ __forceinline__ void interface_values(const R* r0, const R* r1, const R* r2,
                                                  const R* r3, int stride, const R qb[6], R g,
                                                  R eps_w, R out[12]) {
   if constexpr (IM > 0 && !LINEAR && std::is_same<R, double>::value) {
-    MulInt mi;
+    MulIntT<IM != 2> mi;
     if constexpr (IM == 1) {
       MulFP64 ms;
       interface_values_m<DIR, LINEAR, CHAR>(r0, r1, r2, r3, stride, qb, g, eps_w, out, mi, ms);
