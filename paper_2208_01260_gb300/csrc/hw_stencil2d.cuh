@@ -115,7 +115,7 @@ __device__ __forceinline__ void interface_values_m(const R* r0, const R* r1, con
 #define RV(r, f) (r)[(f) * stride]
   // interface state: h = (h_i + h_{i+1})/2, u = (m_i + m_{i+1})/(h_i + h_{i+1}), v likewise
   const R hs = RV(r1, R_H) + RV(r2, R_H);
-  const R rhs = fast_rcp(hs);
+  const R rhs = mul.rcp(hs);
   const R ub = smul(RV(r1, R_M) + RV(r2, R_M), rhs);
   const R vb = smul(RV(r1, R_W) + RV(r2, R_W), rhs);
   const R gh = smul(smul.k(R(0.5), g), hs);
@@ -333,7 +333,7 @@ __device__ __forceinline__ void node_update_m(const Dev2DT<R>& d, const StageArg
     const R b0 = __ldg(d.stat[0] + o);
     const R h = eta - b0;
     const R gh = mul(g, h);
-    const R rh = fast_rcp(h);
+    const R rh = mul.rcp(h);
     const R u = mul(cur[1], rh), v = mul(cur[2], rh);
     const R rs = fast_rsqrt(gh);
     const R c = mul(gh, rs), ic2 = mul.k(R(0.5), rs);
