@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(BX_THREADS, 3) k_bsweep_x(BatchDev B, const in
 #pragma unroll
       for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qbx[q] + o);
       double out[12];
-      interface_values<0, LINEAR, CHAR, 1>(sm + t0, sm + t0 + 1, sm + t0 + 2, sm + t0 + 3, stride, qb, d.g, d.eps_w, out);
+      interface_values<0, LINEAR, CHAR, true>(sm + t0, sm + t0 + 1, sm + t0 + 2, sm + t0 + 3, stride, qb, d.g, d.eps_w, out);
 #pragma unroll
       for (int q = 0; q < 12; ++q) d.X[q][o] = out[q];
     }
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(BY_W, 12) k_bsweep_y(BatchDev B, const int4* _
 #pragma unroll
         for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qby[q] + o);
         double out[12];
-        interface_values<1, LINEAR, CHAR, 2>(s0, s1, s2, s3, BY_W, qb, d.g, d.eps_w, out);
+        interface_values<1, LINEAR, CHAR, true>(s0, s1, s2, s3, BY_W, qb, d.g, d.eps_w, out);
 #pragma unroll
         for (int q = 0; q < 12; ++q) d.Y[q][o] = out[q];
       }

@@ -124,7 +124,7 @@ __device__ __forceinline__ float dabs(float x) { return fabsf(x); }
 //
 // Algebra (exact rearrangement of the printed q_l and beta_l):
 //   d1 = f0 - f1, d2 = f1 - f2, B1 = 2 d1 + p0 + p1, A1 = B1 + d1 + p1, B2 = 2 d2 + p1 + p2,
-//   A2 = B2 + d2 + p1, e = f0 - 2 f1 + f2, g3 = f0 - f2 + 2 p1, P = f1 + p1/2;
+//   A2 = B2 + d2 + p1, e = d1 - d2 = f0 - 2 f1 + f2, g3 = f0 - f2 + 2 p1, P = f1 + p1/2;
 //   q1 = P + A1/6, q2 = P - A2/6, q3 = P + e/12 (weights summing to 1 leave P outside the weighted sum);
 //   beta1 = p1^2 + 13/3 A1^2 + 781/20 B1^2, beta2 = p1^2 + 13/3 A2^2 + 781/20 B2^2,
 //   beta3 = p1^2 + 13/12 e^2 + 781/80 g3^2.
@@ -206,7 +206,7 @@ __device__ __forceinline__ R hweno_side_m(R f0, R f1, R f2, R p0, R p1, R p2, R 
   const R B2 = fma(R(2.0), d2, p1 + p2);
   const R A2 = B2 + (d2 + p1);
   const R P = fma(R(0.5), p1, f1);
-  const R e = fma(R(-2.0), f1, f0 + f2);
+  const R e = d1 - d2;  // f0 - 2 f1 + f2
   if (LINEAR) {
     const R q1 = fma(R(1.0 / 6.0), A1, P);
     const R q2 = fma(R(-1.0 / 6.0), A2, P);
@@ -215,12 +215,13 @@ __device__ __forceinline__ R hweno_side_m(R f0, R f1, R f2, R p0, R p1, R p2, R 
     return fma(R(0.3), q1, fma(R(0.3), q2, mul.k(R(0.4), q3)));
   }
   const R g3 = fma(R(2.0), p1, f0 - f2);
-  const R pp = mul(p1, p1);
-  const R b1 = fma(mul.k(R(781.0 / 20.0), B1), B1, fma(mul.k(R(13.0 / 3.0), A1), A1, pp));
-  const R b2 = fma(mul.k(R(781.0 / 20.0), B2), B2, fma(mul.k(R(13.0 / 3.0), A2), A2, pp));
-  const R b3 = fma(mul.k(R(781.0 / 80.0), g3), g3, fma(mul.k(R(13.0 / 12.0), e), e, pp));
+  // t_l = beta_l + eps, with eps added once to the common term p1^2
+  const R ppe = mul(p1, p1) + eps;
+  const R t1 = fma(mul.k(R(781.0 / 20.0), B1), B1, fma(mul.k(R(13.0 / 3.0), A1), A1, ppe));
+  const R t2 = fma(mul.k(R(781.0 / 20.0), B2), B2, fma(mul.k(R(13.0 / 3.0), A2), A2, ppe));
+  const R t3 = fma(mul.k(R(781.0 / 80.0), g3), g3, fma(mul.k(R(13.0 / 12.0), e), e, ppe));
   R n3;
-  inverse_square_weights(b1 + eps, b2 + eps, b3 + eps, W.n1, W.n2, n3, mul);
+  inverse_square_weights(t1, t2, t3, W.n1, W.n2, n3, mul);
   // gamma = (3, 3, 4)/10 -> proportional to (1, 1, 4/3)
   W.n3 = mul.k(R(4.0 / 3.0), n3);
   W.r = mul.rcp(W.n1 + W.n2 + W.n3);

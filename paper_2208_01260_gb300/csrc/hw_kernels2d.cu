@@ -19,16 +19,11 @@ namespace hw {
 constexpr int XS_T = 192;
 constexpr int XS_N = XS_T + 3;
 
-// The double kernels move part of their products and sums to the integer pipes (bit-identical
-// results, hw_fp64_int.h): the FP64 pipe is their bound, the integer pipes idle. How much moves is
-// set per kernel by measurement: the x-sweep the reconstruction and weights, the y-sweep also the
-// interface state, the node kernel all; the node records stay on the FP64 pipe.
+// The double kernels form their products (and the node kernel also its reciprocals) on the integer
+// pipes (hw_fp64_int.h: products bit-identical to DMUL): the FP64 pipe is their bound, the integer
+// pipes idle. The node records stay on the FP64 pipe (moving them measured slower).
 template <class R>
 constexpr bool kIntMul = std::is_same<R, double>::value;
-template <class R>
-constexpr int kImX = std::is_same<R, double>::value ? 1 : 0;
-template <class R>
-constexpr int kImY = std::is_same<R, double>::value ? 2 : 0;
 
 template <bool LINEAR, bool CHAR, class R>
 __global__ void __launch_bounds__(XS_T, 2) k_sweep_x(Dev2DT<R> d, const R* __restrict__ alpha) {
@@ -55,7 +50,7 @@ __global__ void __launch_bounds__(XS_T, 2) k_sweep_x(Dev2DT<R> d, const R* __res
 #pragma unroll
   for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qbx[q] + o);
   R out[12];
-  interface_values<0, LINEAR, CHAR, kImX<R>>(sm + t, sm + t + 1, sm + t + 2, sm + t + 3, XS_N, qb, R(d.g), R(d.eps_w), out);
+  interface_values<0, LINEAR, CHAR, kIntMul<R>>(sm + t, sm + t + 1, sm + t + 2, sm + t + 3, XS_N, qb, R(d.g), R(d.eps_w), out);
 #pragma unroll
   for (int q = 0; q < 12; ++q) d.X[q][o] = out[q];
 }
@@ -95,7 +90,7 @@ __global__ void __launch_bounds__(YS_W, 12) k_sweep_y(Dev2DT<R> d, const R* __re
 #pragma unroll
       for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qby[q] + o);
       R out[12];
-      interface_values<1, LINEAR, CHAR, kImY<R>>(s0, s1, s2, s3, stride, qb, R(d.g), R(d.eps_w), out);
+      interface_values<1, LINEAR, CHAR, kIntMul<R>>(s0, s1, s2, s3, stride, qb, R(d.g), R(d.eps_w), out);
 #pragma unroll
       for (int q = 0; q < 12; ++q) d.Y[q][o] = out[q];
     }

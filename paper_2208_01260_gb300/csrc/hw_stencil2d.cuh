@@ -106,30 +106,29 @@ __device__ __forceinline__ void node_record(const Node12T<R>& n, R g, R alpha, R
 // where dS is the spacing along the sweep and dT the spacing across it.
 // qb[6] = source candidates q_1..q_3 of (b, dS b_s) for the '+' side then the mirrored '-' side.
 // ---------------------------------------------------------------------------------------------
-// `mul` forms the products of the reconstruction and its weights, `smul` those of the interface
-// state and the back-projection (MulFP64 or MulInt, see hw_device.cuh).
-template <int DIR, bool LINEAR, bool CHAR, class R, class M, class MS>
+// `mul` forms the products and reciprocals (MulFP64 or MulIntT, see hw_device.cuh).
+template <int DIR, bool LINEAR, bool CHAR, class R, class M>
 __device__ __forceinline__ void interface_values_m(const R* r0, const R* r1, const R* r2,
                                                    const R* r3, int stride, const R qb[6], R g,
-                                                   R eps_w, R out[12], M& mul, MS& smul) {
+                                                   R eps_w, R out[12], M& mul) {
 #define RV(r, f) (r)[(f) * stride]
   // interface state: h = (h_i + h_{i+1})/2, u = (m_i + m_{i+1})/(h_i + h_{i+1}), v likewise
   const R hs = RV(r1, R_H) + RV(r2, R_H);
   const R rhs = mul.rcp(hs);
-  const R ub = smul(RV(r1, R_M) + RV(r2, R_M), rhs);
-  const R vb = smul(RV(r1, R_W) + RV(r2, R_W), rhs);
-  const R gh = smul(smul.k(R(0.5), g), hs);
+  const R ub = mul(RV(r1, R_M) + RV(r2, R_M), rhs);
+  const R vb = mul(RV(r1, R_W) + RV(r2, R_W), rhs);
+  const R gh = mul(mul.k(R(0.5), g), hs);
   const R rs = fast_rsqrt(gh);
-  const R cb = smul(gh, rs);
-  const R ic2 = smul.k(R(0.5), rs);  // 1/(2c)
+  const R cb = mul(gh, rs);
+  const R ic2 = mul.k(R(0.5), rs);  // 1/(2c)
   // normal / tangential velocity of this sweep
   const R un = DIR == 0 ? ub : vb, ut = DIR == 0 ? vb : ub;
   const R upc = un + cb, umc = un - cb;
   // component indices: normal momentum and tangential momentum
   const int cn = DIR == 0 ? 1 : 2, ct = DIR == 0 ? 2 : 1;
   // scaled epsilon: fields 1, 3 carry s = 4c, field 2 carries s = 2 (both 2 without projection)
-  const R eps2 = smul.k(R(4.0), eps_w);
-  const R eps13 = CHAR ? smul(smul(smul.k(R(8.0), g), eps_w), hs) : eps2;
+  const R eps2 = mul.k(R(4.0), eps_w);
+  const R eps13 = CHAR ? mul(mul(mul.k(R(8.0), g), eps_w), hs) : eps2;
 
   R G[3], GB1 = R(0.0), GB3 = R(0.0);  // per-field sums over both sides; source fields 1 and 3
   const R* rp[4] = {r0, r1, r2, r3};
@@ -178,14 +177,14 @@ __device__ __forceinline__ void interface_values_m(const R* r0, const R* r1, con
   // back to physical components: 2 Fhat = R diag(1/s) G * 2
   R F2[3], B2[3];
   if (CHAR) {
-    const R A = smul(G[0] + G[2], ic2);
+    const R A = mul(G[0] + G[2], ic2);
     F2[0] = A;
-    F2[cn] = fma(un, A, smul.k(R(0.5), G[2] - G[0]));
+    F2[cn] = fma(un, A, mul.k(R(0.5), G[2] - G[0]));
     F2[ct] = fma(ut, A, G[1]);
-    const R Bs = smul(GB1 + GB3, ic2);
+    const R Bs = mul(GB1 + GB3, ic2);
     B2[0] = Bs;
-    B2[cn] = fma(un, Bs, smul.k(R(0.5), GB3 - GB1));
-    B2[ct] = smul(ut, Bs);
+    B2[cn] = fma(un, Bs, mul.k(R(0.5), GB3 - GB1));
+    B2[ct] = mul(ut, Bs);
   } else {
     F2[0] = G[0]; F2[cn] = G[1]; F2[ct] = G[2];
     B2[0] = R(0.0); B2[cn] = GB1; B2[ct] = R(0.0);
@@ -207,30 +206,24 @@ __device__ __forceinline__ void interface_values_m(const R* r0, const R* r1, con
 #undef RV
 }
 
-// One interface. IM: 0 all products on the FP64 pipe; 1 the reconstruction's and weights' products
-// and the weights' reciprocals on the integer pipes (hw_fp64_int.h: products bit-identical to DMUL,
-// reciprocals within one ulp); 2 the products of the reconstruction, weights, interface state and
-// back-projection, reciprocals on the FP64 pipe. If any integer operation leaves its fast path (subnormal, infinite or NaN data),
-// the interface is recomputed on the FP64 pipe from the same records.
-template <int DIR, bool LINEAR, bool CHAR, int IM = 0, class R>
+// One interface. IMUL: the products run on the integer pipes (hw_fp64_int.h, bit-identical to DMUL;
+// the reciprocals stay on the FP64 pipe: moving them raised spills); if any of them leaves the integer
+// fast path (subnormal, infinite or NaN data), the interface is recomputed on the FP64 pipe from the
+// same records.
+template <int DIR, bool LINEAR, bool CHAR, bool IMUL = false, class R>
 __device__ __forceinline__ void interface_values(const R* r0, const R* r1, const R* r2,
                                                  const R* r3, int stride, const R qb[6], R g,
                                                  R eps_w, R out[12]) {
-  if constexpr (IM > 0 && !LINEAR && std::is_same<R, double>::value) {
-    MulIntT<IM != 2> mi;
-    if constexpr (IM == 1) {
-      MulFP64 ms;
-      interface_values_m<DIR, LINEAR, CHAR>(r0, r1, r2, r3, stride, qb, g, eps_w, out, mi, ms);
-    } else {
-      interface_values_m<DIR, LINEAR, CHAR>(r0, r1, r2, r3, stride, qb, g, eps_w, out, mi, mi);
-    }
+  if constexpr (IMUL && !LINEAR && std::is_same<R, double>::value) {
+    MulIntT<false> mi;
+    interface_values_m<DIR, LINEAR, CHAR>(r0, r1, r2, r3, stride, qb, g, eps_w, out, mi);
     if (mi.bad) {
       MulFP64 mf;
-      interface_values_m<DIR, LINEAR, CHAR>(r0, r1, r2, r3, stride, qb, g, eps_w, out, mf, mf);
+      interface_values_m<DIR, LINEAR, CHAR>(r0, r1, r2, r3, stride, qb, g, eps_w, out, mf);
     }
   } else {
     MulFP64 mf;
-    interface_values_m<DIR, LINEAR, CHAR>(r0, r1, r2, r3, stride, qb, g, eps_w, out, mf, mf);
+    interface_values_m<DIR, LINEAR, CHAR>(r0, r1, r2, r3, stride, qb, g, eps_w, out, mf);
   }
 }
 
