@@ -24,9 +24,15 @@ constexpr int XS_N = XS_T + 3;
 // pipes idle. The node records stay on the FP64 pipe (moving them measured slower).
 template <class R>
 constexpr bool kIntMul = std::is_same<R, double>::value;
+// Blocks per SM the sweeps are compiled for: the double kernels carry the integer-pipe products in
+// registers (168 per thread); the float kernels are bound by memory and issue and want occupancy.
+template <class R>
+constexpr int kXsBlocks = std::is_same<R, double>::value ? 2 : 5;
+template <class R>
+constexpr int kYsBlocks = std::is_same<R, double>::value ? 12 : 32;
 
 template <bool LINEAR, bool CHAR, class R>
-__global__ void __launch_bounds__(XS_T, 2) k_sweep_x(Dev2DT<R> d, const R* __restrict__ alpha) {
+__global__ void __launch_bounds__(XS_T, kXsBlocks<R>) k_sweep_x(Dev2DT<R> d, const R* __restrict__ alpha) {
   __shared__ R sm[NREC * XS_N];
   const int j = blockIdx.y;
   const int k0 = blockIdx.x * XS_T;
@@ -62,7 +68,7 @@ __global__ void __launch_bounds__(XS_T, 2) k_sweep_x(Dev2DT<R> d, const R* __res
 constexpr int YS_W = 32;
 
 template <bool LINEAR, bool CHAR, class R>
-__global__ void __launch_bounds__(YS_W, 12) k_sweep_y(Dev2DT<R> d, const R* __restrict__ alpha, int seg) {
+__global__ void __launch_bounds__(YS_W, kYsBlocks<R>) k_sweep_y(Dev2DT<R> d, const R* __restrict__ alpha, int seg) {
   extern __shared__ __align__(16) unsigned char ring_raw[];
   R* ring = reinterpret_cast<R*>(ring_raw);  // [4 slots][NREC][YS_W]
   const int i = blockIdx.x * YS_W + threadIdx.x;
