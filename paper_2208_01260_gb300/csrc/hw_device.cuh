@@ -138,12 +138,11 @@ struct WeightsT {
 };
 using Weights = WeightsT<double>;
 
-// Multiplication policies. MulFP64 is the plain product on the FP64 pipe (the compiler may fuse it
-// with a following add into an fma); MulInt forms the correctly rounded product on the integer pipes
-// (hw_fp64_int.h, bit-identical to DMUL) and records whether any product left its fast path, in which
-// case the caller recomputes the block with MulFP64. k(c, x) multiplies by a literal constant c;
-// rcp(x) is the reciprocal (fast_rcp on the FP64 pipe; for MulIntT<true> the integer form, within one
-// ulp).
+// Arithmetic policies for products and reciprocals. MulFP64: the plain product on the FP64 pipe (the
+// compiler may fuse it with a following add into an fma) and fast_rcp. MulIntT: the correctly rounded
+// product on the integer pipes (hw_fp64_int.h, bit-identical to DMUL) and, with IRCP, the integer-pipe
+// reciprocal (within one ulp; else fast_rcp); it records whether any operation left its fast path, in
+// which case the caller recomputes the block with MulFP64. k(c, x) multiplies by a literal constant c.
 // Float data is handled natively by both.
 struct MulFP64 {
   static constexpr bool bad = false;

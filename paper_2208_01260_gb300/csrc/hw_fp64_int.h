@@ -7,12 +7,12 @@
 // result is bit-identical to the hardware DMUL instruction, and a kernel can move a share of its
 // multiplications off the FP64 pipe.
 //
-// Method (the schoolbook significand product, e.g. Muller et al., Handbook of Floating-Point
-// Arithmetic, Sec. 8.4): with significands Ma, Mb in [2^52, 2^53) shifted left by 10 bits, the exact
-// 128-bit product lies in [2^124, 2^126); its high word holds the 53 result bits plus 8 or 9 lower
-// bits, and the low word only contributes to the sticky bit. One normalising shift, a round-to-
-// nearest-even increment and the biased exponent sum (whose carry absorbs a significand that rounds
-// up to 2^53) give the result word.
+// Method (the schoolbook significand product of software floating-point, as described for example
+// in Muller et al., Handbook of Floating-Point Arithmetic): with significands Ma, Mb in [2^52, 2^53)
+// shifted left by 10 bits, the exact 128-bit product lies in [2^124, 2^126); its high word holds the
+// 53 result bits plus 8 or 9 lower bits, and the low word only contributes to the sticky bit. One
+// normalising shift, a round-to-nearest-even increment and the biased exponent sum (whose carry
+// absorbs a significand that rounds up to 2^53) give the result word.
 //
 // Zero operands (with a finite other operand) are handled on the fast path. The function reports
 // failure (and leaves `out` unspecified) when an operand is subnormal, infinite or NaN, or when the
@@ -144,11 +144,12 @@ HW_FP64_INT_FN int64_t s64_mulhi(int64_t a, int64_t b) {
 }
 
 // 1/x on the integer pipes, within one ulp (faithfully rounded; round to nearest of an approximation
-// accurate to about 2^-60). False (out unspecified) unless x is normal with a biased exponent of at most
-// 2044, i.e. the reciprocal is normal. Method (Newton-Raphson with a cubic step, e.g. Muller et al.,
-// Sec. 9.2): a seed Y0 ~ 2^83/M (22 bits) of the significand M in [2^52, 2^53) from the single-precision
-// reciprocal; the residual E = 2^83 - M*Y0 (exact in 64-bit two's complement for a seed error below
-// 2^-20); then 2^116/M ~ Y0 (2^33 + (E + E^2/2^83) / 2^50), rounded to 53 bits.
+// accurate to about 2^-60). False (out unspecified) unless x is normal with a biased exponent of at
+// most 2044, i.e. the reciprocal is normal. Method (Newton-Raphson iteration with a third-order step,
+// a textbook division algorithm): a seed Y0 ~ 2^83/M (22 bits) of the significand M in [2^52, 2^53)
+// from the single-precision reciprocal; the residual E = 2^83 - M*Y0 (exact in 64-bit two's
+// complement for a seed error below 2^-20); then 2^116/M ~ Y0 (2^33 + (E + E^2/2^83) / 2^50), rounded
+// to 53 bits. SEED_ERR perturbs the seed by that many single-precision ulps (host tests only).
 template <int SEED_ERR = 0>
 HW_FP64_INT_FN bool f64_rcp_int(double x, double& out) {
   uint32_t al, ah;
@@ -158,7 +159,7 @@ HW_FP64_INT_FN bool f64_rcp_int(double x, double& out) {
   const bool ok = (ex - 1u) < 2044u;
   // seed from the leading 23 fraction bits: mf in [1, 2), r ~ 1/mf (about 1/2 to 1)
   const float mf = f32_from_bits(0x3f800000u | (fh << 3) | (al >> 29));
-  const uint32_t rb = f32_bits(f32_rcp_seed(mf)) + (uint32_t)SEED_ERR;  // SEED_ERR: host tests only
+  const uint32_t rb = f32_bits(f32_rcp_seed(mf)) + (uint32_t)SEED_ERR;
   // Y0 = r 2^31 from r's significand and exponent (125..127)
   const uint32_t Y0 = ((rb & 0x7fffffu) | 0x800000u) << ((rb >> 23) - 119u);
   const uint32_t mh = fh | 0x100000u;
