@@ -72,10 +72,10 @@ __device__ __forceinline__ double hweno_side_rev(const double f[3], const double
   const double lpp = lb1 + lb2 + lb3;
   double lp1 = 2.0 * p[1] * lpp + 2.0 * lg3;
   double lf0 = lg3, lf2 = -lg3, lf1 = 0.0;
-  le += lq3 / 12.0;
+  le = fma(1.0 / 12.0, lq3, le);
   const double lP = lq1 + lq2 + lq3;
-  lA2 -= lq2 / 6.0;
-  lA1 += lq1 / 6.0;
+  lA2 = fma(-1.0 / 6.0, lq2, lA2);
+  lA1 = fma(1.0 / 6.0, lq1, lA1);
   lf0 += le;
   lf2 += le;
   lf1 -= 2.0 * le;
