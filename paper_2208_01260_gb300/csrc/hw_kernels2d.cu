@@ -24,12 +24,15 @@ constexpr int XS_N = XS_T + 3;
 // pipes idle. The node records stay on the FP64 pipe (moving them measured slower).
 template <class R>
 constexpr bool kIntMul = std::is_same<R, double>::value;
-// Blocks per SM the sweeps are compiled for: the double kernels carry the integer-pipe products in
-// registers (168 per thread); the float kernels are bound by memory and issue and want occupancy.
+// Blocks per SM the sweeps and the node kernel are compiled for: the double kernels carry the
+// integer-pipe products in registers (168 per thread in the sweeps); the float kernels are bound by
+// memory and issue and want occupancy.
 template <class R>
 constexpr int kXsBlocks = std::is_same<R, double>::value ? 2 : 5;
 template <class R>
 constexpr int kYsBlocks = std::is_same<R, double>::value ? 12 : 32;
+template <class R>
+constexpr int kNodeBlocks = std::is_same<R, double>::value ? 3 : 5;
 
 template <bool LINEAR, bool CHAR, class R>
 __global__ void __launch_bounds__(XS_T, kXsBlocks<R>) k_sweep_x(Dev2DT<R> d, const R* __restrict__ alpha) {
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(YS_W, kYsBlocks<R>) k_sweep_y(Dev2DT<R> d, con
 }
 
 template <int MODE, bool LINEAR, bool CHAR, class R>
-__global__ void __launch_bounds__(256, 3) k_node2d(Dev2DT<R> d, StageArgsT<R> sa) {
+__global__ void __launch_bounds__(256, kNodeBlocks<R>) k_node2d(Dev2DT<R> d, StageArgsT<R> sa) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y;
   if (i >= d.nx || j >= d.ny) return;
