@@ -10,7 +10,9 @@ Tolerances (derived in the design notes from the arithmetic):
   * after many steps: relative L1 per group sum|gpu - oracle| / sum|oracle| <= 1e-9 (1e-8 for
     discontinuous data).
 """
+import dataclasses
 import numpy as np
+from paper_2208_01260_gb300 import scenarios as S
 
 G = 9.812
 
@@ -67,3 +69,12 @@ def oracle_state(orc, sc):
     if sc.dim == 1:
         return orc.to_state1d(sc.h, sc.hu, sc.b, sc.deriv)
     return orc.to_state2d(sc.h, sc.hu, sc.hv, sc.b, sc.deriv)
+
+
+def tiny_derivatives(sc, scale=1e-160):
+    """The left half of the domain with every derivative plane scaled to ~1e-160: squares and products
+    of the projected derivative data there underflow, so the kernels' integer-pipe products leave their
+    fast path and those interfaces and nodes are recomputed on the FP64 pipe."""
+    x = S.axis(sc.nx, sc.x0, sc.x1, sc.bc_x)
+    f = np.where(x < 0.5 * (sc.x0 + sc.x1), scale, 1.0)[None, :]
+    return dataclasses.replace(sc, deriv=[d * f for d in sc.deriv], name=sc.name + "_tiny_derivs")

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2208_01260_gb300 import scenarios as S
-from _parity import normwise, stage_scales
+from _parity import normwise, stage_scales, tiny_derivatives
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +39,21 @@ def test_batched_equals_single_grid_solvers(hw):
         s = hw.Solver.from_scenario(sc, hw.make_params())
         ts, n = s.advance(5, use_graph=False)
         assert n == 5 and abs(ts - t[i]) <= 1e-14 * t[i]
+        ref = s.state()
+        stat = [sc.b, sc.deriv[6], sc.deriv[7]]
+        assert max(normwise(b.state(i), ref, stage_scales(ref, stat))) <= 1e-12
+
+
+def test_batched_fallback_instances_equal_single_grid_solvers(hw):
+    """Instances whose derivative data underflow in products (the batched kernels' FP64-pipe
+    recomputation of the affected interfaces and nodes) beside ordinary ones."""
+    scs = [tiny_derivatives(S.hump2d(70, 45, seed=27)), S.hump2d(64, 64, seed=5),
+           tiny_derivatives(S.hump2d(33, 40, seed=28, bc=S.PERIODIC))]
+    b = hw.BatchedSolver(scs)
+    b.run(3, use_graph=False)
+    for i, sc in enumerate(scs):
+        s = hw.Solver.from_scenario(sc, hw.make_params())
+        s.advance(3, use_graph=False)
         ref = s.state()
         stat = [sc.b, sc.deriv[6], sc.deriv[7]]
         assert max(normwise(b.state(i), ref, stage_scales(ref, stat))) <= 1e-12

@@ -4,14 +4,13 @@ Sizes span several tiles of every kernel (x-sweep 192 interfaces per row tile, y
 block, node 32x8) with ragged tails; the full-size 2048^2 workload is checked on sampled nodes the
 oracle computes one by one. See tests/_parity.py for the tolerances.
 """
-import dataclasses
 import math
 
 import numpy as np
 import pytest
 
 from paper_2208_01260_gb300 import scenarios as S
-from _parity import (normwise, oracle_grid, oracle_state, rel_l1, rhs_scales, stage_scales)
+from _parity import (normwise, oracle_grid, oracle_state, rel_l1, rhs_scales, stage_scales, tiny_derivatives)
 
 pytestmark = pytest.mark.gpu
 
@@ -32,15 +31,6 @@ def solver(hw, sc, **pk):
 
 def oparams(orc, sc, **pk):
     return orc.make_params(eps_w=pk.pop("eps_w", sc.eps_w), **pk)
-
-
-def tiny_derivatives(sc, scale=1e-160):
-    """The left half of the domain with every derivative plane scaled to ~1e-160: squares and products
-    of the projected derivative data there underflow, so the kernels' integer-pipe weight products leave
-    their fast path and those interfaces and limiter nodes are recomputed on the FP64 pipe."""
-    x = S.axis(sc.nx, sc.x0, sc.x1, sc.bc_x)
-    f = np.where(x < 0.5 * (sc.x0 + sc.x1), scale, 1.0)[None, :]
-    return dataclasses.replace(sc, deriv=[d * f for d in sc.deriv], name=sc.name + "_tiny_derivs")
 
 
 CASES_2D = [
