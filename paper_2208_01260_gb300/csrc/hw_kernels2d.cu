@@ -14,10 +14,12 @@
 namespace hw {
 
 // ---------------------------------------------------------------------------------------------
-// x-sweep: one block = XS_T consecutive x-interfaces k (between nodes k-1 and k) of one row.
+// x-sweep: one block of XS_T threads = XS_I = XS_T - 3 consecutive x-interfaces k (between nodes k-1
+// and k) of one row; each thread first forms one of the XS_N = XS_T node records the tile needs.
 // ---------------------------------------------------------------------------------------------
 constexpr int XS_T = 192;
-constexpr int XS_N = XS_T + 3;
+constexpr int XS_I = XS_T - 3;
+constexpr int XS_N = XS_T;
 
 // The double kernels form their products (and the node kernel also its reciprocals) on the integer
 // pipes (hw_fp64_int.h: products bit-identical to DMUL): the FP64 pipe is their bound, the integer
@@ -38,7 +40,7 @@ template <bool LINEAR, bool CHAR, class R>
 __global__ void __launch_bounds__(XS_T, kXsBlocks<R>) k_sweep_x(Dev2DT<R> d, const R* __restrict__ alpha) {
   __shared__ R sm[NREC * XS_N];
   const int j = blockIdx.y;
-  const int k0 = blockIdx.x * XS_T;
+  const int k0 = blockIdx.x * XS_I;
   const R ax = alpha[0];
   for (int t = threadIdx.x; t < XS_N; t += XS_T) {
     const int i = k0 - 2 + t;
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(XS_T, kXsBlocks<R>) k_sweep_x(Dev2DT<R> d, con
   }
   __syncthreads();
   const int k = k0 + threadIdx.x;
-  if (k > d.nx) return;
+  if (threadIdx.x >= XS_I || k > d.nx) return;
   const int t = threadIdx.x;
   const size_t o = (size_t)j * (d.nx + 1) + k;
   R qb[6];
@@ -425,7 +427,7 @@ __global__ void k_static2d(Dev2D d) {
 // ---------------------------------------------------------------------------------------------
 template <bool L, bool C, class R>
 static void launch_sx(const Dev2DT<R>& d, const R* alpha, cudaStream_t st) {
-  dim3 gx((d.nx + 1 + XS_T - 1) / XS_T, d.ny);
+  dim3 gx((d.nx + 1 + XS_I - 1) / XS_I, d.ny);
   k_sweep_x<L, C, R><<<gx, XS_T, 0, st>>>(d, alpha);
 }
 

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
 
-Sizes span several tiles of every kernel (x-sweep 192 interfaces per row tile, y-sweep 32 columns per
+Sizes span several tiles of every kernel (x-sweep 189 interfaces per row tile, y-sweep 32 columns per
 block, node 32x8) with ragged tails; the full-size 2048^2 workload is checked on sampled nodes the
 oracle computes one by one. See tests/_parity.py for the tolerances.
 """
