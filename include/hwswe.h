@@ -180,8 +180,9 @@ int hw_batch_run(hw_batch* b, int nsteps, int use_graph);
 int hw_batch_get_state(hw_batch* b, int i, double* const* out, int layout, int ptr_kind);
 /* Simulated time and step count of every grid (t[n], steps[n]; either may be NULL). */
 int hw_batch_get_time(hw_batch* b, double* t, int* steps);
-/* Tile shapes of grid i: tx = interfaces per x-tile (32, 64 or 128; 128/tx rows per tile), seg =
- * interfaces per y-segment (>= 1). Chosen by the autotuner; arithmetic is unaffected. */
+/* Tile shapes of grid i: tx = threads per row of an x-tile (32, 64 or 128; each row covers tx - 3
+ * interfaces and forms their tx node records, one per thread; 128/tx rows per tile), seg = interfaces
+ * per y-segment (>= 1). Chosen by the autotuner; arithmetic is unaffected. */
 int hw_batch_set_tiles(hw_batch* b, int i, int tx, int seg);
 int hw_batch_get_tiles(hw_batch* b, int i, int* tx, int* seg);
 /* Autotuner measurement: average ms of the batched x-sweep and y-sweep over the grids ids[nids] with

@@ -1,7 +1,8 @@
 """Tile-shape autotuner of the batched form.
 
-The batched kernels take two tile shapes per grid: the number of x-interfaces per x-tile (32, 64 or
-128, with 128/tx rows per tile) and the number of y-interfaces per y-segment. Neither changes the
+The batched kernels take two tile shapes per grid: the row width tx of an x-tile (32, 64 or 128
+threads, each row covering tx - 3 interfaces; 128/tx rows per tile) and the number of y-interfaces per
+y-segment. Neither changes the
 arithmetic. Grids are grouped in size classes (powers of two of nx for the x-tiles, of ny for the
 y-segments); for each class every candidate is timed on that class's grids with
 ``hw_batch_time_tiles`` (events around the batched sweep launches) and the fastest is kept. Results

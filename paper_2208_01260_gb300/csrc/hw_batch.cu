@@ -21,7 +21,8 @@ struct BInst {
   int nx, ny, bc_x, bc_y;
   double dx, dy, inv_dx, inv_dy, c_bx, c_by, c_gx, c_gy, c_mx, c_my;
   long long off_n, off_x, off_y;  // offsets of this grid in the pooled node / x-interface / y-interface planes
-  int tx, seg;                     // x-tile width (32, 64 or 128 interfaces; 128/tx rows per block), y segment
+  int tx, seg;                     // x-tile row width (32, 64 or 128 threads = tx - 3 interfaces and their
+                                   // tx node records; 128/tx rows per block), y segment
 };
 
 struct BatchDev {
@@ -67,7 +68,7 @@ __device__ __forceinline__ void make_dev(const BatchDev& B, const BInst& I, Dev2
 }
 
 constexpr int BX_THREADS = 128;
-constexpr int BX_MAXN = 4 * (32 + 3);  // largest rows x (tile + halo) over the tile widths 32, 64, 128
+constexpr int BX_MAXN = BX_THREADS;     // node records per block: one per thread
 constexpr int BY_W = 32;
 
 // ---- alpha per instance: items (inst, first node, count) ----
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(BX_THREADS, 3) k_bsweep_x(BatchDev B, const in
     const BInst I = B.inst[it.x];
     Dev2D d;
     make_dev(B, I, d);
-    const int tx = I.tx, R = BX_THREADS / tx, NN = tx + 3, stride = R * NN;
+    const int tx = I.tx, R = BX_THREADS / tx, NN = tx, stride = R * NN;  // tx - 3 interfaces per row
     const int j0 = it.y, k0 = it.z;
     const double ax = B.alpha[2 * it.x];
     for (int t = threadIdx.x; t < stride; t += BX_THREADS) {
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(BX_THREADS, 3) k_bsweep_x(BatchDev B, const in
     __syncthreads();
     const int r = threadIdx.x / tx, c = threadIdx.x - r * tx;
     const int j = j0 + r, k = k0 + c;
-    if (j < d.ny && k <= d.nx) {
+    if (c < tx - 3 && j < d.ny && k <= d.nx) {
       const int t0 = r * NN + c;
       const size_t o = (size_t)j * (d.nx + 1) + k;
       double qb[6];
@@ -308,7 +309,7 @@ void build_items(const std::vector<hw::BInst>& inst, const std::vector<int>& ids
     for (int o = 0; o < n; o += 4096) out[0].push_back(make_int4(i, o, std::min(4096, n - o), 0));
     const int R = hw::BX_THREADS / I.tx;
     for (int j = 0; j < I.ny; j += R)
-      for (int k = 0; k <= I.nx; k += I.tx) out[1].push_back(make_int4(i, j, k, 0));
+      for (int k = 0; k <= I.nx; k += I.tx - 3) out[1].push_back(make_int4(i, j, k, 0));
     for (int c = 0; c < I.nx; c += hw::BY_W)
       for (int k = 0; k <= I.ny; k += I.seg) out[2].push_back(make_int4(i, c, k, 0));
     for (int j = 0; j < I.ny; j += 8)
