@@ -215,7 +215,7 @@ __device__ __forceinline__ R hweno_side_m(R f0, R f1, R f2, R p0, R p1, R p2, R 
   }
   const R g3 = fma(R(2.0), p1, f0 - f2);
   // t_l = beta_l + eps, with eps added once to the common term p1^2
-  const R ppe = mul(p1, p1) + eps;
+  const R ppe = fma(p1, p1, eps);  // an fma either way: no product to move off the FP64 pipe
   const R t1 = fma(mul.k(R(781.0 / 20.0), B1), B1, fma(mul.k(R(13.0 / 3.0), A1), A1, ppe));
   const R t2 = fma(mul.k(R(781.0 / 20.0), B2), B2, fma(mul.k(R(13.0 / 3.0), A2), A2, ppe));
   const R t3 = fma(mul.k(R(781.0 / 80.0), g3), g3, fma(mul.k(R(13.0 / 12.0), e), e, ppe));

@@ -119,11 +119,11 @@ __device__ __forceinline__ void interface_values_m(const R* r0, const R* r1, con
   const R vb = mul(RV(r1, R_W) + RV(r2, R_W), rhs);
   const R gh = mul(mul.k(R(0.5), g), hs);
   const R rs = fast_rsqrt(gh);
-  const R cb = mul(gh, rs);
   const R ic2 = mul.k(R(0.5), rs);  // 1/(2c)
   // normal / tangential velocity of this sweep
   const R un = DIR == 0 ? ub : vb, ut = DIR == 0 ? vb : ub;
-  const R upc = un + cb, umc = un - cb;
+  // un +- c with c = gh / sqrt(gh): fmas (a product on the integer pipes would leave the adds)
+  const R upc = fma(gh, rs, un), umc = fma(-gh, rs, un);
   // component indices: normal momentum and tangential momentum
   const int cn = DIR == 0 ? 1 : 2, ct = DIR == 0 ? 2 : 1;
   // scaled epsilon: fields 1, 3 carry s = 4c, field 2 carries s = 2 (both 2 without projection)
