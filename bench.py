@@ -60,18 +60,18 @@ PEAK_FP64_OPS = SMS * DFMA_PER_SM_CLK * SM_GHZ * 1e9
 # launch at 2048x1024, the state and interface planes above L2), valid only for the kernel sources they
 # were taken on (sources_sha); scaled to a launch by its units (traffic is proportional to them).
 TRAFFIC = {
-    "sweep_x": {"bytes_per_unit": 223.8, "sha": "d402d878c9202073"},
-    "sweep_y": {"bytes_per_unit": 232.6, "sha": "d402d878c9202073"},
-    "node": {"bytes_per_unit": 529.9, "sha": "d402d878c9202073"},
+    "sweep_x": {"bytes_per_unit": 223.6, "sha": "948dbe4e090f69d4"},
+    "sweep_y": {"bytes_per_unit": 232.8, "sha": "948dbe4e090f69d4"},
+    "node": {"bytes_per_unit": 529.4, "sha": "948dbe4e090f69d4"},
 }
 # FP64-pipe instructions per unit (ncu: DFMA + DADD + DMUL thread instructions of one stage-3 launch at
 # 2048x1024 over its units). Part of the products run on the integer pipes (bit-identical binary64
 # multiplies), so these are below the algorithmic "ops" above; valid only for the kernel sources they
 # were taken on (sources_sha).
 FP64_PIPE_OPS = {
-    "sweep_x": {"ops_per_unit": 341.8, "sha": "d402d878c9202073"},
-    "sweep_y": {"ops_per_unit": 343.3, "sha": "d402d878c9202073"},
-    "node": {"ops_per_unit": 243.0, "sha": "d402d878c9202073"},
+    "sweep_x": {"ops_per_unit": 341.8, "sha": "948dbe4e090f69d4"},
+    "sweep_y": {"ops_per_unit": 343.3, "sha": "948dbe4e090f69d4"},
+    "node": {"ops_per_unit": 243.0, "sha": "948dbe4e090f69d4"},
 }
 STATE_BYTES = 9 * NX * NY * 8
 
