@@ -185,18 +185,20 @@ __device__ __forceinline__ void interface_adjoint_y(const AdjDev& A, int i, int 
   }
 }
 
-// ---- 2. x-interfaces (a block: AX_T consecutive interfaces of one row) ----
+// ---- 2. x-interfaces (a block of AX_T threads: AX_I = AX_T - 3 consecutive interfaces of one row and
+// their AX_N = AX_T node records, one per thread) ----
 // The four record adjoints of each interface collect in a shared-memory slab; after the block has
 // finished, each record sums its (up to) four contributions, so only the three records a block shares
 // with each neighbour are added atomically.
 constexpr int AX_T = 64;
-constexpr int AX_N = AX_T + 3;
+constexpr int AX_I = AX_T - 3;
+constexpr int AX_N = AX_T;
 
 __global__ void __launch_bounds__(AX_T) k_adj_sweep_x(AdjDev A) {
   __shared__ double sm[NREC * AX_N];
   __shared__ double slab[4 * NREC * AX_T];
   const Dev2D& d = A.d;
-  const int j = blockIdx.y, k0 = blockIdx.x * AX_T;
+  const int j = blockIdx.y, k0 = blockIdx.x * AX_I;
   const double ax = A.alpha[0];
   const int t = threadIdx.x;
   for (int u = t; u < AX_N; u += AX_T) {
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(AX_T) k_adj_sweep_x(AdjDev A) {
   }
   __syncthreads();
   const int k = k0 + t;
-  if (k <= d.nx) {
+  if (t < AX_I && k <= d.nx) {
     const size_t o = (size_t)j * (d.nx + 1) + k;
     double qb[6];
 #pragma unroll
@@ -224,14 +226,14 @@ __global__ void __launch_bounds__(AX_T) k_adj_sweep_x(AdjDev A) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) A.lqbx[q][o] += lqb[q];
   } else {
-    for (int e = 0; e < 4 * NREC; ++e) slab[e * AX_T + t] = 0.0;  // interfaces past the row's end
+    for (int e = 0; e < 4 * NREC; ++e) slab[e * AX_T + t] = 0.0;  // no interface (tile or row end)
   }
   __syncthreads();
   const size_t row = (size_t)j * (d.nx + 4);
   for (int u = t; u < AX_N; u += AX_T) {
     const int r = k0 - 2 + u;  // raw record index, -2 .. nx+1
     if (r > d.nx + 1) break;
-    const bool shared_slot = u < 3 || u >= AX_T;
+    const bool shared_slot = u < 3 || u >= AX_I;
     for (int f = 0; f < NREC; ++f) {
       double acc = 0.0;
 #pragma unroll
@@ -817,7 +819,7 @@ int reverse_recorded(const hw::SolverView& v, AdjBuffers* B, const StepTape& T, 
     ACUDA(cudaMemsetAsync(B->argmax, 0x7f, 2 * sizeof(int), st));
     const dim3 gn((d.nx + 31) / 32, (d.ny + 7) / 8), bn(32, 8);
     hw::k_adj_node_pre<<<gn, bn, 0, st>>>(A);
-    hw::k_adj_sweep_x<<<dim3((d.nx + 1 + hw::AX_T - 1) / hw::AX_T, d.ny), hw::AX_T, 0, st>>>(A);
+    hw::k_adj_sweep_x<<<dim3((d.nx + 1 + hw::AX_I - 1) / hw::AX_I, d.ny), hw::AX_T, 0, st>>>(A);
     hw::k_adj_sweep_y<<<dim3((d.nx + 31) / 32, (d.ny + 1 + hw::AY_R - 1) / hw::AY_R), hw::AY_T, hw::AY_SMEM, st>>>(A);
     const int nrec = (d.nx + 4) * d.ny + d.nx * (d.ny + 4);
     hw::k_adj_records<<<(nrec + 255) / 256, 256, 0, st>>>(A);
