@@ -14,7 +14,7 @@ from typing import Sequence
 
 import numpy as np
 
-from . import HW_DEVICE, HW_LAYOUT_EQUILIBRIUM, _check, _pp, _ptr, hw_init, hw_set_state, lib
+from . import HW_LAYOUT_EQUILIBRIUM, _check, _pp, _ptr, hw_init, hw_set_state, lib
 
 # storage modes of hw_adjoint_run besides a snapshot count (include/hwswe.h)
 HW_ADJ_TAPE = -1  # keep every stage of every step: no recomputation

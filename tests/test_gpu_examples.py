@@ -1,7 +1,6 @@
 """The paper's examples 4.3, 4.4, 4.5 and 4.9 and the transmissive boundary on the CUDA path, against
 the oracle: per stage (1e-12 normwise) on smooth data, at the final time (relative L1 1e-8, the
 discontinuous-data bound)."""
-import numpy as np
 import pytest
 
 from paper_2208_01260_gb300 import scenarios as S

@@ -4,7 +4,6 @@ Sizes span several tiles of every kernel (x-sweep 189 interfaces per row tile, y
 block, node 32x8) with ragged tails; the full-size 2048^2 workload is checked on sampled nodes the
 oracle computes one by one. See tests/_parity.py for the tolerances.
 """
-import math
 
 import numpy as np
 import pytest
@@ -301,7 +300,6 @@ def test_checkpoint_and_resume_is_bitwise(hw):
 
 
 def test_time_and_state_api_errors(hw):
-    import ctypes as C
     sc = S.hump2d(32, 32, seed=48)
     s = solver(hw, sc)
     L = hw.lib()
