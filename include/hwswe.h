@@ -261,12 +261,13 @@ int hw_rhs1d_noalloc(const hw_grid* grid, const hw_params* params, const double*
  * On the current device, n seeded pseudo-random operands go through the integer path and the FP64 pipe.
  * op 0, products against DMUL (operand mix: the scheme's range, short significands, near-squares,
  * signed zeros, the edges of the normal range, subnormal, infinite and NaN operands); op 1, reciprocals
- * against the correctly rounded __drcp_rn (significands near 1 and 2, every exponent). counts (host,
- * 3 entries): results the integer fast path accepted; accepted results that differ from the FP64
- * pipe's in any bit (op 0) or by more than one ulp (op 1); operands the fast path must take but
- * rejected (normal operands with a normal result). The last two must be 0. Synchronous on the legacy
- * default stream; allocates and frees 24 bytes. HW_ERR_ARG for another op, n < 1 or counts == NULL,
- * HW_ERR_CUDA on a CUDA failure. */
+ * against the correctly rounded __drcp_rn (significands near 1 and 2, every exponent); op 2, products
+ * by the literal constants the kernels multiply by (the constant-folded form), against DMUL. counts
+ * (host, 3 entries): results the integer fast path accepted; accepted results that differ from the
+ * FP64 pipe's in any bit (ops 0, 2) or by more than one ulp (op 1); operands the fast path must take
+ * but rejected (normal operands with a normal result; not counted for op 2). The last two must be 0.
+ * Synchronous on the legacy default stream; allocates and frees 24 bytes. HW_ERR_ARG for another op,
+ * n < 1 or counts == NULL, HW_ERR_CUDA on a CUDA failure. */
 int hw_selftest_fp64_int(int op, long long n, unsigned long long seed, long long* counts);
 
 /* Wait for the stream and return the device status as an HW_ERR_* code (HW_OK if clean). */

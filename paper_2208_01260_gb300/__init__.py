@@ -297,9 +297,10 @@ def hw_set_time(h: _Handle, t: float, steps: int):
 
 
 def hw_selftest_fp64_int(op: int, n: int, seed: int = 1):
-    """Device check of the integer-pipe FP64 multiply (op 0, bitwise against DMUL) or reciprocal (op 1,
-    within one ulp of the correctly rounded one) on n operands: returns (accepted, mismatches,
-    rejected operands that the fast path must take); the last two must be 0."""
+    """Device check of the integer-pipe FP64 multiply (op 0, bitwise against DMUL), reciprocal (op 1,
+    within one ulp of the correctly rounded one) or multiply by the kernels' literal constants (op 2,
+    bitwise) on n operands: returns (accepted, mismatches, rejected operands that the fast path must
+    take); the last two must be 0."""
     counts = (C.c_longlong * 3)()
     _check(lib().hw_selftest_fp64_int(int(op), int(n), int(seed), counts), "hw_selftest_fp64_int")
     return tuple(int(v) for v in counts)

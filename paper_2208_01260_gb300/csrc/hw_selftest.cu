@@ -67,6 +67,40 @@ __global__ void k_selftest_mul(long long n, unsigned long long seed, unsigned lo
   atomicAdd(cnt + 2, missed);
 }
 
+// Products by the literal constants the kernels multiply by (the folded-constant form of the integer
+// multiply), bit for bit against DMUL.
+__device__ __forceinline__ void const_check(double x, double c, unsigned long long& acc, unsigned long long& bad) {
+  double r;
+  if (f64_mul_int<true>(x, c, r)) {
+    ++acc;
+    bad += __double_as_longlong(r) != __double_as_longlong(__dmul_rn(x, c));
+  }
+}
+
+__global__ void k_selftest_const(long long n, unsigned long long seed, unsigned long long* cnt) {
+  unsigned long long acc = 0, bad = 0, missed = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long c = mix64(seed ^ (7ull * i));
+    unsigned long long a = mix64(c + 1);
+    if (c % 2) a = (a & 0x800fffffffffffffull) | (unsigned long long)(990 + (c >> 8) % 60) << 52;
+    const double x = __longlong_as_double((long long)a);
+    const_check(x, 781.0 / 20.0, acc, bad);
+    const_check(x, 13.0 / 3.0, acc, bad);
+    const_check(x, 781.0 / 80.0, acc, bad);
+    const_check(x, 13.0 / 12.0, acc, bad);
+    const_check(x, 4.0 / 3.0, acc, bad);
+    const_check(x, 0.5, acc, bad);
+    const_check(x, 1.0 / 6.0, acc, bad);
+    const_check(x, 0.25, acc, bad);
+    const_check(x, 4.0, acc, bad);
+    const_check(x, 8.0, acc, bad);
+  }
+  atomicAdd(cnt, acc);
+  atomicAdd(cnt + 1, bad);
+  atomicAdd(cnt + 2, missed);
+}
+
 // Reciprocals against the correctly rounded __drcp_rn: accepted results more than one ulp away count as
 // mismatches; operands with a normal reciprocal (biased exponent 1..2044) must be accepted.
 __global__ void k_selftest_rcp(long long n, unsigned long long seed, unsigned long long* cnt) {
@@ -99,14 +133,15 @@ __global__ void k_selftest_rcp(long long n, unsigned long long seed, unsigned lo
 }  // namespace hw
 
 extern "C" int hw_selftest_fp64_int(int op, long long n, unsigned long long seed, long long* counts) {
-  if ((op != 0 && op != 1) || n < 1 || counts == nullptr) return HW_ERR_ARG;
+  if (op < 0 || op > 2 || n < 1 || counts == nullptr) return HW_ERR_ARG;
   unsigned long long* d = nullptr;
   if (cudaMalloc(&d, 3 * sizeof(unsigned long long)) != cudaSuccess) return HW_ERR_CUDA;
   unsigned long long h[3] = {0, 0, 0};
   cudaError_t e = cudaMemset(d, 0, sizeof(h));
   if (e == cudaSuccess) {
     if (op == 0) hw::k_selftest_mul<<<1216, 256>>>(n, seed, d);
-    else hw::k_selftest_rcp<<<1216, 256>>>(n, seed, d);
+    else if (op == 1) hw::k_selftest_rcp<<<1216, 256>>>(n, seed, d);
+    else hw::k_selftest_const<<<1216, 256>>>(n, seed, d);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
