@@ -51,11 +51,18 @@ UNITS_PER_LAUNCH = {
     "node": NX * NY,
     "alpha": NX * NY,
 }
-# FP64 peak from the unit counts and the clock: 152 SMs x 2 DFMA per SM per cycle (the sustained FP64
-# pipe peak ncu reports on GB300) x 2 flops x 2.07 GHz.
+# FP64 peak: measured live on the benchmark's GPU (hw_measure_fp64_peak, independent fma chains on every
+# SM, median of 20 launches). The nominal figure from the unit counts and the clock (152 SMs x 2 DFMA per
+# SM per cycle, the FP64 pipe peak ncu reports on GB300, x 2 flops x 2.07 GHz) is kept for comparison.
 SMS, DFMA_PER_SM_CLK, SM_GHZ = 152, 2, 2.07
-PEAK_FP64_TFLOPS = SMS * DFMA_PER_SM_CLK * 2 * SM_GHZ / 1e3
+NOMINAL_FP64_TFLOPS = SMS * DFMA_PER_SM_CLK * 2 * SM_GHZ / 1e3
+PEAK_FP64_TFLOPS = NOMINAL_FP64_TFLOPS  # replaced by the measured figure in main()
 PEAK_FP64_OPS = SMS * DFMA_PER_SM_CLK * SM_GHZ * 1e9
+# Algorithmic DRAM bytes of one RK stage per node, the minimum a fused stage must move: stage 1 reads the
+# 9 state and 3 static planes and writes 9 state and 6 limited-derivative planes; stages 2 and 3 read the
+# 9 state, 3 static and 9 base planes and write 9 (limiter recomputed: 27 planes of 8 bytes on average).
+# The whole-step HBM fraction is taken against it.
+ALGO_BYTES_PER_NODE_STAGE = 216.0
 # DRAM bytes per unit from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum of one stage-3
 # launch at 2048x1024, the state and interface planes above L2), valid only for the kernel sources they
 # were taken on (sources_sha); scaled to a launch by its units (traffic is proportional to them).
@@ -456,6 +463,17 @@ def main():
     import paper_2208_01260_gb300 as hw
     from paper_2208_01260_gb300 import scenarios as S
 
+    # the FP64 roofline's denominator, measured on this GPU before the timed regions
+    global PEAK_FP64_TFLOPS, PEAK_FP64_OPS
+    with ClockSampler(local) as pclk:
+        best, median, peak_ms = hw.hw_measure_fp64_peak(20)
+    PEAK_FP64_OPS = median
+    PEAK_FP64_TFLOPS = 2.0 * median / 1e12
+    fp64_peak = {"fma_per_s_median": median, "fma_per_s_best": best, "tflops": PEAK_FP64_TFLOPS,
+                 "launch_ms": peak_ms, "clocks": pclk.summary(), "nominal_tflops": NOMINAL_FP64_TFLOPS,
+                 "how": "hw_measure_fp64_peak: 8 independent fma chains per thread, 8 x 256 threads per SM on "
+                        "every SM, 4096 iterations, median of 20 event-timed launches (fma = 2 flops)"}
+
     sc = S.bumps2d(NX, NY, strip=0.01)
     solver = hw.Solver.from_scenario(sc, hw.make_params())
     if (NX, NY) != (2048, 2048):
@@ -519,8 +537,9 @@ def main():
     kd = kernels[dom]
     roofline = {"bound": "alu", "achieved": kd["tflops"], "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
                 "frac": kd["frac"], "traffic": kd["traffic_bytes"], "kernel": "k_" + dom,
-                "peak_src": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (recipe unit counts and clock; "
-                            "ncu sustained-peak 2 DFMA/clk/SM)",
+                "peak_src": "measured",
+                "peak_how": "FP64 fma throughput measured live on this GPU before the timed region "
+                            "(hw_measure_fp64_peak, median of 20 launches; fma = 2 flops); see fp64_peak",
                 "algo_ops_frac": kd["algo_ops_frac"], "fp64_pipe_frac": kd["fp64_pipe_frac"],
                 "int_pipe_note": "part of the products run on the integer pipes (bit-identical binary64), so the "
                                  "algorithmic rate can exceed the FP64 pipe's share; fp64_pipe_frac is the pipe's own use",
@@ -528,9 +547,25 @@ def main():
                 "sources_sha": sha}
     step_ops = sum(ALGO[k]["ops"] * UNITS_PER_LAUNCH[k] for k in ALGO) * STAGES
     step_flops = sum(ALGO[k]["flops"] * UNITS_PER_LAUNCH[k] for k in ALGO) * STAGES
-    roofline["whole_step"] = {"tflops": step_flops / (ms / args.steps * 1e-3) / 1e12,
-                              "frac": step_flops / (ms / args.steps * 1e-3) / 1e12 / PEAK_FP64_TFLOPS,
-                              "algo_ops_frac": step_ops / (ms / args.steps * 1e-3) / PEAK_FP64_OPS}
+    step_s = ms / args.steps * 1e-3
+    roofline["whole_step"] = {"tflops": step_flops / step_s / 1e12,
+                              "frac": step_flops / step_s / 1e12 / PEAK_FP64_TFLOPS,
+                              "algo_ops_frac": step_ops / step_s / PEAK_FP64_OPS}
+    # the HBM roofline of the whole step: the algorithmic bytes a fused stage must move (216 B per node
+    # and stage) over the step time, against the measured copy bandwidth; next to it the bytes this design
+    # actually moves per node and stage (interfaces go through HBM so that no FP64 work is recomputed),
+    # from the ncu traffic of the three kernels when the sources match the capture
+    tr_node = None
+    if all(TRAFFIC[k]["sha"] == sha for k in ("sweep_x", "sweep_y", "node")):
+        tr_node = (TRAFFIC["sweep_x"]["bytes_per_unit"] * UNITS_PER_LAUNCH["sweep_x"]
+                   + TRAFFIC["sweep_y"]["bytes_per_unit"] * UNITS_PER_LAUNCH["sweep_y"]
+                   + TRAFFIC["node"]["bytes_per_unit"] * UNITS_PER_LAUNCH["node"]) / (NX * NY) + 2 * 32.0
+    roofline["hbm_frac_step"] = ALGO_BYTES_PER_NODE_STAGE * NX * NY * STAGES / step_s / 1e9 / hbm
+    roofline["hbm_step"] = {"algorithmic_bytes_per_node_stage": ALGO_BYTES_PER_NODE_STAGE,
+                            "algorithmic_gbs": ALGO_BYTES_PER_NODE_STAGE * NX * NY * STAGES / step_s / 1e9,
+                            "measured_dram_bytes_per_node_stage": tr_node,
+                            "measured_dram_gbs": (tr_node * NX * NY * STAGES / step_s / 1e9) if tr_node else None,
+                            "note": "bound: FP64 pipe, not HBM; the interface planes go through HBM by design"}
 
     # e2e through the public API with pinned host buffers: each step uploads the state (physical
     # layout, 9 planes), advances one RK3 step and downloads the state.
@@ -564,7 +599,7 @@ def main():
                        "timed_path": "hw_advance with a captured CUDA graph (2 steps per graph)"},
             "roofline": roofline, "kernels": kernels, "ms_per_step_profiled": ms_prof / args.steps,
             "gpu_launches": int(round(launches_per_step * args.steps)),
-            "clocks": clk.summary(), "e2e": e2e}
+            "clocks": clk.summary(), "e2e": e2e, "fp64_peak": fp64_peak}
     # secondary measurements: a failure is reported in the line instead of losing the headline
     def extra(key, fn):
         try:

@@ -246,8 +246,9 @@ int hw_adjoint_run(hw_solver* s, int nsteps, const double* dts, const int* gauge
  * h_x, hu_x, b_x) and outputs; the working memory (state, b-only source terms, interface values, the
  * alpha accumulator) is a file-scope device array sized for HW_NOALLOC_MAX_NX nodes, which every GPU
  * that loads the library holds until the process exits. Larger grids return HW_ERR_ARG.
- *   - The call allocates nothing and is stream-ordered on cuda_stream (NULL = legacy default stream);
- *     it does not check the depth (h must be > 0) and does not synchronise.
+ *   - The call allocates nothing. Its kernels run on cuda_stream (NULL = legacy default stream); it
+ *     then waits for that stream and returns HW_ERR_DEPTH if any h <= 0 and HW_ERR_NONFINITE if any
+ *     depth or velocity is NaN or infinite (the output planes then hold no usable values).
  *   - Every call reuses the same array and leaves its contents behind (it clears what must start at
  *     zero), so calls that may overlap on the GPU (other streams or unordered host threads) race.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
@@ -269,6 +270,15 @@ int hw_rhs1d_noalloc(const hw_grid* grid, const hw_params* params, const double*
  * Synchronous on the legacy default stream; allocates and frees 24 bytes. HW_ERR_ARG for another op,
  * n < 1 or counts == NULL, HW_ERR_CUDA on a CUDA failure. */
 int hw_selftest_fp64_int(int op, long long n, unsigned long long seed, long long* counts);
+
+/* FP64 throughput of the current GPU (no counterpart in the paper; the denominator of the FP64 roofline
+ * that bounds this scheme's kernels on GB300, whose FP64 pipe is narrow). A kernel of independent fused
+ * multiply-add chains (eight per thread, eight blocks of 256 threads on every SM) runs once to warm up
+ * and then `reps` times (1..1000), each launch timed with CUDA events. out (host, 3 entries): the best
+ * rate in FP64 fma per second (thread operations; one fma = 2 flops), the median rate, and the best
+ * launch time in ms. Synchronous on a private stream; allocates and frees a small result buffer.
+ * HW_ERR_ARG for bad arguments, HW_ERR_CUDA on a CUDA failure. */
+int hw_measure_fp64_peak(int reps, double* out);
 
 /* Wait for the stream and return the device status as an HW_ERR_* code (HW_OK if clean). */
 int hw_sync(hw_solver* s);

@@ -33,7 +33,7 @@ __all__ = [
     "HW_LAYOUT_EQUILIBRIUM", "HwError", "hw_grid", "hw_params", "lib", "make_grid", "make_params",
     "hw_create", "hw_destroy", "hw_init", "hw_rhs", "hw_alpha", "hw_cfl_dt", "hw_rk3_step", "hw_rk3_stage",
     "hw_advance", "hw_get_state", "hw_set_state", "hw_get_base", "hw_sync", "hw_version", "Solver",
-    "hw_set_profiling", "hw_get_profile", "hw_get_time", "hw_set_time", "hw_rhs1d_noalloc", "hw_selftest_fp64_int", "BatchedSolver", "hw_batch_create",
+    "hw_set_profiling", "hw_get_profile", "hw_get_time", "hw_set_time", "hw_rhs1d_noalloc", "hw_selftest_fp64_int", "hw_measure_fp64_peak", "BatchedSolver", "hw_batch_create",
     "hw_batch_destroy", "hw_batch_init", "hw_batch_run", "hw_batch_get_state", "hw_batch_get_time",
     "hw_batch_set_tiles", "hw_batch_get_tiles", "hw_batch_time_tiles",
 ]
@@ -100,6 +100,7 @@ def lib():
             "hw_get_time": ([vp, dp, C.POINTER(C.c_longlong)], i),
             "hw_set_time": ([vp, C.c_double, C.c_longlong], i),
             "hw_selftest_fp64_int": ([i, C.c_longlong, C.c_ulonglong, C.POINTER(C.c_longlong)], i),
+            "hw_measure_fp64_peak": ([i, dp], i),
             "hw_last_error": ([], C.c_char_p),
             "hw_version": ([], C.c_char_p),
         }
@@ -304,6 +305,13 @@ def hw_selftest_fp64_int(op: int, n: int, seed: int = 1):
     counts = (C.c_longlong * 3)()
     _check(lib().hw_selftest_fp64_int(int(op), int(n), int(seed), counts), "hw_selftest_fp64_int")
     return tuple(int(v) for v in counts)
+
+
+def hw_measure_fp64_peak(reps: int = 5):
+    """FP64 fma throughput of the current GPU: (best fma/s, median fma/s, best launch ms)."""
+    out = (C.c_double * 3)()
+    _check(lib().hw_measure_fp64_peak(int(reps), out), "hw_measure_fp64_peak")
+    return out[0], out[1], out[2]
 
 
 def hw_rhs1d_noalloc(grid: hw_grid, params: hw_params, hh, hu, b, deriv: Sequence, out: Sequence, stream=None):

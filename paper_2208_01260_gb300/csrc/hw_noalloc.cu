@@ -12,7 +12,10 @@
 //   * every call reuses the same array and leaves its contents behind, so calls that overlap on the
 //     GPU (different streams, or different host threads without ordering) race;
 //   * the first call on a device looks up the array's device address with cudaGetSymbolAddress
-//     while that device is current; make that first call before any stream capture.
+//     while that device is current; make that first call before any stream capture;
+//   * the kernels flag a non-positive or non-finite depth in a status word inside the array; each
+//     call clears it first and reads it back at the end (a 4-byte copy and a wait for the stream), so
+//     bad input is reported by the call that received it and never leaks into a later call.
 #include <mutex>
 #include <string>
 
@@ -101,6 +104,12 @@ extern "C" int hw_rhs1d_noalloc(const hw_grid* grid, const hw_params* params, co
   double* alpha = p + 2;                               // 2 slots
   int* status = (int*)(p + 4);                         // depth flag written by the kernels
 
+  // the status word keeps whatever the previous call left: clear it before this call's kernels
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e != cudaSuccess)
+    return noalloc_fail(HW_ERR_CUDA, (std::string("hw_rhs1d_noalloc: clearing the status failed: ") +
+                                      cudaGetErrorString(e)).c_str());
+
   hw::PhysIn1D in{};
   in.p[0] = h; in.p[1] = hu; in.p[2] = b;
   in.p[3] = deriv[0]; in.p[4] = deriv[1]; in.p[5] = deriv[2];
@@ -113,8 +122,17 @@ extern "C" int hw_rhs1d_noalloc(const hw_grid* grid, const hw_params* params, co
   hw::StageArgs1D sa{};
   for (int q = 0; q < 4; ++q) sa.rhs_out[q] = out[q];
   hw::launch_node1d(d, sa, hw::MODE_RHS, lin, chr, st);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess)
     return noalloc_fail(HW_ERR_CUDA, (std::string("hw_rhs1d_noalloc: launch failed: ") + cudaGetErrorString(e)).c_str());
+  // the depth check of the initialisation and of the alpha reduction: read the flag back
+  int flags = 0;
+  e = cudaMemcpyAsync(&flags, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess)
+    return noalloc_fail(HW_ERR_CUDA, (std::string("hw_rhs1d_noalloc: reading the status failed: ") +
+                                      cudaGetErrorString(e)).c_str());
+  if (flags & hw::HW_STATUS_DEPTH) return noalloc_fail(HW_ERR_DEPTH, "hw_rhs1d_noalloc: non-positive depth in the input");
+  if (flags) return noalloc_fail(HW_ERR_NONFINITE, "hw_rhs1d_noalloc: non-finite depth or velocity in the input");
   return HW_OK;
 }

@@ -163,6 +163,33 @@ def test_adjoint_run_matches_oracle_dual_numbers(hw):
         assert abs(gv - dL) <= 1e-7 * abs(dL) + 1e-12, (gv, dL)
 
 
+@pytest.mark.parametrize("bc", [S.REFLECTIVE, S.PERIODIC], ids=["reflective", "periodic"])
+def test_adjoint_run_matches_oracle_dual_numbers_multi_tile(hw, bc):
+    """A grid spanning three x-tiles of the adjoint x-sweep (61 interfaces each) and several y-segments,
+    so that the record adjoints a block shares with its neighbours (added with atomics) meet the oracle's
+    forward-mode derivative, on walls and on periodic wrap-around."""
+    import torch
+    import oracle
+    from paper_2208_01260_gb300 import adjoint as A
+    sc = S.hump2d(160, 48, seed=72, hump_max=0.05, bc=bc)
+    nsteps, ng = 4, 9
+    g, p, st, stat, dts, gidx, obs = _oracle_problem(sc, nsteps, ng, 4)
+    solver = hw.Solver.from_scenario(sc, hw.make_params())
+    state, static, _, _ = _eq_static(sc)
+    A.load_problem(solver, state, static)
+    gs = torch.empty_like(state)
+    gb = torch.empty_like(static)
+    loss, nf = A.hw_adjoint_run(solver.h, dts, gidx, obs, A.HW_ADJ_TAPE, [gs[q] for q in range(9)],
+                                [gb[q] for q in range(3)])
+    for seed in (4, 5):
+        dst, dstat = _smooth_direction(sc, seed)
+        L, dL = oracle.gauge_loss_dual2d(g, p, st, stat, dst, dstat, dts, gidx, obs)
+        assert abs(loss - L) <= 1e-10 * abs(L)
+        gv = float((gs.cpu().numpy() * np.stack(dst)).sum() + (gb.cpu().numpy() * np.stack(dstat)).sum())
+        assert abs(gv - dL) <= 1e-7 * abs(dL) + 1e-12, (gv, dL)
+    solver.close()
+
+
 @functools.lru_cache(None)
 def _dp_cost(n, s):
     if n == 1:

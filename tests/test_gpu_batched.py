@@ -1,11 +1,13 @@
-"""The batched form against single-grid solvers (same formulas, only the launch organisation
-differs; the two kernels may contract multiply-adds differently, so agreement is to rounding) and
-the autotuner (tile shapes never change the numbers: bitwise)."""
+"""The batched form against the CPU oracle (every instance of a mixed batch, one step at the per-stage
+tolerance and several steps at the many-step tolerance, times against the oracle's CFL steps), against
+single-grid solvers (same formulas, only the launch organisation differs; the two kernels may contract
+multiply-adds differently, so agreement is to rounding), and the autotuner (tile shapes never change
+the numbers: bitwise)."""
 import numpy as np
 import pytest
 
 from paper_2208_01260_gb300 import scenarios as S
-from _parity import normwise, stage_scales, tiny_derivatives
+from _parity import normwise, oracle_grid, oracle_state, rel_l1, stage_scales, tiny_derivatives
 
 pytestmark = pytest.mark.gpu
 
@@ -27,6 +29,43 @@ def _mixed_batch():
         sc = S.hump2d(nx, ny, seed=100 + k, bc=bc)
         out.append(sc)
     return out
+
+
+def _oracle_run(orc, sc, nsteps):
+    g = oracle_grid(orc, sc)
+    p = orc.make_params(eps_w=sc.eps_w)
+    cur, stat = oracle_state(orc, sc)
+    t = 0.0
+    for _ in range(nsteps):
+        dt = orc.cfl_dt2d(g, p, cur, stat)
+        cur = orc.rk3_step2d(g, p, dt, cur, stat)
+        t += dt
+    return cur, stat, t
+
+
+@pytest.mark.parametrize("nsteps,use_graph", [(1, False), (4, True)])
+def test_batched_matches_oracle(hw, orc, nsteps, use_graph):
+    """Every instance of the mixed batch (all three boundary conditions, a 2x5 grid, ragged x-tiles and
+    y-segments) against the oracle's SSP-RK3 steps (Sec. 2.2 eq. RK on the 2D scheme of Sec. 3) at the
+    oracle's own CFL time steps (Sec. 4): one step at the per-stage tolerance (normwise 1e-12), four
+    steps (two captured graphs) at relative L1 1e-9; the simulated time against the sum of the
+    oracle's steps."""
+    scs = _mixed_batch()
+    b = hw.BatchedSolver(scs)
+    b.run(nsteps, use_graph=use_graph)
+    t, steps = b.times()
+    assert list(steps) == [nsteps] * len(scs)
+    for i, sc in enumerate(scs):
+        ref, stat, tref = _oracle_run(orc, sc, nsteps)
+        got = b.state(i)
+        assert abs(t[i] - tref) <= 1e-13 * tref, (i, t[i], tref)
+        err = normwise(got, ref, stage_scales(ref, stat))
+        if nsteps == 1:
+            assert max(err) <= 1e-12, (i, err)
+        else:
+            assert max(rel_l1(got, ref)) <= 1e-9, (i, rel_l1(got, ref))
+            assert max(err) <= 1e-11, (i, err)
+    b.close()
 
 
 def test_batched_equals_single_grid_solvers(hw):

@@ -123,6 +123,30 @@ def test_lake_at_rest_gpu_2048(hw):
     assert res <= 1e-12, res
 
 
+def test_final_time_parity_2048(hw, orc):
+    """The benchmark workload at full size (2048^2, reflective, 8 bumps + 0.01 strip): 12 RK3 steps at
+    the CFL step, the GPU from its captured graph with the time step found on the device, the oracle with
+    its own steps; relative L1 per variable group at the discontinuous-data bound (1e-8), and the
+    simulated times."""
+    sc = S.bumps2d(2048, 2048, strip=0.01)
+    s = solver(hw, sc)
+    g, p = oracle_grid(orc, sc), oparams(orc, sc)
+    st, stat = oracle_state(orc, sc)
+    nsteps = 12
+    t, n = s.advance(nsteps, use_graph=True)
+    assert n == nsteps
+    got = s.state()
+    s.close()
+    cur, tref = st, 0.0
+    for _ in range(nsteps):
+        dt = orc.cfl_dt2d(g, p, cur, stat)
+        cur = orc.rk3_step2d(g, p, dt, cur, stat)
+        tref += dt
+    assert abs(t - tref) <= 1e-13 * tref, (t, tref)
+    err = rel_l1(got, cur)
+    assert max(err) <= 1e-8, err
+
+
 def test_sampled_parity_2048(hw, orc):
     """Full-size workload (2048^2, reflective, 8 bumps + strip), each stage on 3000 sampled nodes."""
     sc = S.bumps2d(2048, 2048, strip=0.01)

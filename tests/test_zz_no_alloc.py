@@ -5,7 +5,9 @@ GPU, or a time-critical loop that cannot pay for cudaMalloc); it keeps its worki
 device array inside the library. This test calls it through the C ABI twice in a row on different
 grids (the second call reuses the array the first one left behind), then once more on the first grid,
 and checks each result against hw_create + hw_init + hw_rhs on the same inputs with the tolerance of
-the other right-hand-side parity tests. It also checks that grids above the limit are rejected.
+the other right-hand-side parity tests; it does the same at exactly the largest grid the array holds.
+It also checks that grids above the limit are rejected, and that a depth error is reported by the
+call that received the bad input and not by the next valid call.
 """
 import numpy as np
 import pytest
@@ -63,6 +65,40 @@ def test_noalloc_matches_regular_entry_point(orc):
         assert all(np.all(np.isfinite(x)) for x in got)
         err = normwise(got, ref, _scales(orc, sc))
         assert max(err) <= 1e-12, err
+
+
+def test_noalloc_at_the_largest_grid(orc):
+    """nx = HW_NOALLOC_MAX_NX fills the array up to its last interface plane and its counters."""
+    import paper_2208_01260_gb300 as hw
+    sc = S.accuracy1d(16384)
+    p = hw.make_params(eps_w=sc.eps_w)
+    ref = _regular(hw, sc, p)
+    for _ in range(2):
+        got = _noalloc(hw, sc, p)
+        assert all(np.all(np.isfinite(x)) for x in got)
+        err = normwise(got, ref, _scales(orc, sc))
+        assert max(err) <= 1e-12, err
+
+
+def test_noalloc_reports_bad_depth_once():
+    """A host-made input with h <= 0 gives HW_ERR_DEPTH; the next call with valid input returns HW_OK."""
+    import dataclasses
+    import paper_2208_01260_gb300 as hw
+    sc = S.perturbed1d(perturb=0.05)
+    p = hw.make_params(eps_w=sc.eps_w)
+    h = sc.h.copy()
+    h[17] = -0.5
+    bad = dataclasses.replace(sc, h=h)
+    with pytest.raises(hw.HwError) as e:
+        _noalloc(hw, bad, p)
+    assert e.value.code == -2
+    h = sc.h.copy()
+    h[5] = float("nan")
+    with pytest.raises(hw.HwError) as e:
+        _noalloc(hw, dataclasses.replace(sc, h=h), p)
+    assert e.value.code == -3
+    got = _noalloc(hw, sc, p)
+    assert all(np.all(np.isfinite(x)) for x in got)
 
 
 def test_noalloc_rejects_grids_above_the_limit():
