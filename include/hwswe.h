@@ -237,6 +237,82 @@ int hw_adjoint_run(hw_solver* s, int nsteps, const double* dts, const int* gauge
                    const double* eta_obs, int snapshots, double* loss_out, double* const* grad_state,
                    double* const* grad_static, long long* forward_steps_out);
 
+/* ---------------------------------------------------------------------------------------------
+ * Block decomposition of one 2D grid (no counterpart in the paper, which runs one grid at a time). The
+ * nx x ny grid is split into px x py blocks, each advanced by its own solver on its own nodes plus a ring
+ * of 2 halo nodes on every side: an interface's stencil spans nodes i-1..i+2 (Sec. 2.1 Step 1) and the
+ * limiter's i-1..i+1 (Sec. 2.2). Before every RK stage the ring is refreshed from the neighbouring blocks
+ * (on the grid's own boundary: from the block itself, by the boundary condition), and alpha, global per
+ * direction and stage (Sec. 2.1 Step 1), is the maximum over the blocks' maxima. Every node of every
+ * block then computes from the same values as on the undecomposed grid: the result is hw_advance's, bit
+ * for bit. HW_FP64 only. The blocks may live in one process (hw_dd_*) or in one process per GPU, whose
+ * halo strips and alpha keys the caller moves (hw_part_*, hw_halo_*).
+ * ------------------------------------------------------------------------------------------- */
+#define HW_FACE_W 0 /* x lower */
+#define HW_FACE_E 1 /* x upper */
+#define HW_FACE_S 2 /* y lower */
+#define HW_FACE_N 3 /* y upper */
+#define HW_HALO_NEIGHBOR 0  /* the neighbouring block's 2 nodes next to the shared face (periodic: across the wrap) */
+#define HW_HALO_MIRROR 1    /* reflective wall: the block's own 2 nodes mirrored, signs by the parity table */
+#define HW_HALO_REPLICATE 2 /* transmissive boundary: the block's boundary node, twice */
+typedef struct {
+  int i0, j0, nx, ny; /* the block's nodes: [i0, i0 + nx) x [j0, j0 + ny) of the global grid */
+  int nbr[4];         /* per face (HW_FACE_*): the block across it for HW_HALO_NEIGHBOR, else the block itself */
+  int mode[4];        /* per face: HW_HALO_* */
+} hw_part_info;
+
+/* Host only (no CUDA call). Block `part` (= bx + px * by) of the grid split into px x py blocks of nearly
+ * equal size (the first nx % px block columns and ny % py block rows one node larger). HW_ERR_ARG unless
+ * the grid is 2D, 1 <= px, 1 <= py, 0 <= part < px * py and every block has at least 2 x 2 nodes. */
+int hw_dd_partition(const hw_grid* grid, int px, int py, int part, hw_part_info* out);
+
+/* The solver of one block (HW_FP64): a grid of (nx + 4) x (ny + 4) nodes, the block at offset (2, 2) of
+ * it, with the global grid's spacings exactly. Its own calls (hw_get_state, hw_destroy, ...) see the
+ * extended grid. */
+int hw_part_create(const hw_grid* grid, const hw_params* params, int px, int py, int part, void* cuda_stream,
+                   hw_solver** out);
+/* Initial data of the block's own nodes: 12 planes as hw_init (h, hu, hv, b, h_x, hu_x, hv_x, h_y, hu_y,
+ * hv_y, b_x, b_y), each pointing at the block's first node, rows ld >= the block's nx doubles apart. The
+ * ring holds still water until the set-1 exchange fills it; hw_part_finish_init then forms the b-only
+ * source terms. Both synchronise the stream; HW_ERR_DEPTH / HW_ERR_NONFINITE as hw_init. */
+int hw_part_init(hw_solver* s, const double* const* planes12, long long ld, int ptr_kind);
+int hw_part_finish_init(hw_solver* s);
+/* Halo strips (device arrays of doubles). Set 0: the 9 state planes (before every stage); set 1: those and
+ * the static planes b, dx b_x, dy b_y, b_x, b_y (once, between hw_part_init and hw_part_finish_init). The
+ * strip of a face holds, per plane, the 2 node rows (y faces) or columns (x faces) of the block next to
+ * that face, in increasing coordinate: x faces over the block's ny rows, y faces over the full extended
+ * width nx + 4, so that the y exchange, run after the x exchange, also fills the ring's corners.
+ * hw_halo_strip_size: *count = doubles per strip. hw_halo_pack: the block's strip of a face into `strip`.
+ * hw_halo_unpack: the ring on a face from `strip`, which is the neighbour's strip of the opposite face
+ * (HW_HALO_NEIGHBOR) or the block's own strip of this face (HW_HALO_MIRROR, HW_HALO_REPLICATE).
+ * Stream-ordered on the solver's stream. */
+int hw_halo_strip_size(hw_solver* s, int set, int face, long long* count);
+int hw_halo_pack(hw_solver* s, int set, int face, double* strip);
+int hw_halo_unpack(hw_solver* s, int set, int face, int mode, const double* strip);
+/* alpha keys of the block (device, 2 x 64-bit): max(|u|+c) and max(|v|+c) over its nodes and ring as the
+ * bit patterns of the non-negative doubles, so that the integer maximum over all blocks (an all-reduce
+ * with MAX) is the global alpha of Sec. 2.1 Step 1. Stream-ordered. */
+int hw_part_alpha_keys(hw_solver* s, unsigned long long* keys);
+/* RK stage k = 1, 2, 3 of the block (Sec. 2.2 eq. RK) with alpha from the global keys (device, 2): stage 1
+ * takes dt = the CFL step of that alpha (Sec. 4; clipped to end at t_end if t_end > 0), stage 3 advances
+ * the block's time. The ring must hold the stage's input. Stream-ordered. */
+int hw_part_stage(hw_solver* s, int k, const unsigned long long* keys, double t_end);
+/* out[0..1] = the maxima over n rows of keys (device, n x 2 keys as above; out device, 2): the alpha of
+ * several blocks held by one process, before the maximum over processes. Stream-ordered on cuda_stream. */
+int hw_dd_max_keys(const unsigned long long* keys, int n, unsigned long long* out, void* cuda_stream);
+
+/* All px x py blocks of one grid on the current GPU, the exchange as device copies between them: create,
+ * initialise from the global arrays (as hw_init), advance (as hw_advance, the same result bit for bit;
+ * with use_graph two steps of all blocks run from one CUDA graph), read the global state (as
+ * hw_get_state), destroy. */
+typedef struct hw_dd hw_dd;
+int hw_dd_create(const hw_grid* grid, const hw_params* params, int px, int py, void* cuda_stream, hw_dd** out);
+int hw_dd_init(hw_dd* d, const double* h, const double* hu, const double* hv, const double* b,
+               const double* const* deriv, int ptr_kind);
+int hw_dd_advance(hw_dd* d, int nsteps, double t_end, int use_graph, double* t_out, int* steps_out);
+int hw_dd_get_state(hw_dd* d, double* const* out, int layout, int ptr_kind);
+int hw_dd_destroy(hw_dd* d);
+
 /* Allocation-free variant of the 1D right-hand side: the same numbers as hw_create + hw_init + hw_rhs on
  * a 1D grid (out: 4 planes d/dt (eta, m, eta_x, m_x)), with every array pointer on the device. The paper
  * has no counterpart; this call exists for callers that must not allocate device memory, such as code

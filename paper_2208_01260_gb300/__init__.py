@@ -36,6 +36,9 @@ __all__ = [
     "hw_set_profiling", "hw_get_profile", "hw_get_time", "hw_set_time", "hw_rhs1d_noalloc", "hw_selftest_fp64_int", "hw_measure_fp64_peak", "BatchedSolver", "hw_batch_create",
     "hw_batch_destroy", "hw_batch_init", "hw_batch_run", "hw_batch_get_state", "hw_batch_get_time",
     "hw_batch_set_tiles", "hw_batch_get_tiles", "hw_batch_time_tiles",
+    "hw_part_info", "hw_dd_partition", "hw_part_create", "hw_part_init", "hw_part_finish_init", "hw_halo_strip_size",
+    "hw_halo_pack", "hw_halo_unpack", "hw_part_alpha_keys", "hw_part_stage", "hw_dd_create", "hw_dd_init",
+    "hw_dd_advance", "hw_dd_get_state", "hw_dd_destroy", "hw_dd_max_keys", "DecomposedSolver",
 ]
 
 HW_OK = 0
@@ -327,6 +330,186 @@ def hw_rhs1d_noalloc(grid: hw_grid, params: hw_params, hh, hu, b, deriv: Sequenc
     n = grid.nx
     _check(f(C.byref(grid), C.byref(params), _ptr(hh, n), _ptr(hu, n), _ptr(b, n), _pp([_ptr(a, n) for a in deriv]),
              _pp([_ptr(a, n, True) for a in out]), _stream_handle(stream)), "hw_rhs1d_noalloc")
+
+
+# ------------------------------------------------------------------------------------------------
+# block decomposition of one grid
+# ------------------------------------------------------------------------------------------------
+HW_FACE_W, HW_FACE_E, HW_FACE_S, HW_FACE_N = 0, 1, 2, 3
+HW_HALO_NEIGHBOR, HW_HALO_MIRROR, HW_HALO_REPLICATE = 0, 1, 2
+
+
+class hw_part_info(C.Structure):
+    _fields_ = [("i0", C.c_int), ("j0", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+                ("nbr", C.c_int * 4), ("mode", C.c_int * 4)]
+
+
+def _dd_sigs():
+    L = lib()
+    if getattr(L, "_dd_ready", False):
+        return L
+    vp, i, d, ll = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+    pp = C.POINTER(C.c_void_p)
+    for name, args in {
+        "hw_dd_partition": [C.POINTER(hw_grid), i, i, i, C.POINTER(hw_part_info)],
+        "hw_part_create": [C.POINTER(hw_grid), C.POINTER(hw_params), i, i, i, vp, C.POINTER(vp)],
+        "hw_part_init": [vp, pp, ll, i],
+        "hw_part_finish_init": [vp],
+        "hw_halo_strip_size": [vp, i, i, C.POINTER(ll)],
+        "hw_halo_pack": [vp, i, i, vp],
+        "hw_halo_unpack": [vp, i, i, i, vp],
+        "hw_part_alpha_keys": [vp, vp],
+        "hw_part_stage": [vp, i, vp, d],
+        "hw_dd_max_keys": [vp, i, vp, vp],
+        "hw_dd_create": [C.POINTER(hw_grid), C.POINTER(hw_params), i, i, vp, C.POINTER(vp)],
+        "hw_dd_init": [vp, vp, vp, vp, vp, pp, i],
+        "hw_dd_advance": [vp, i, d, i, C.POINTER(d), C.POINTER(i)],
+        "hw_dd_get_state": [vp, pp, i, i],
+        "hw_dd_destroy": [vp],
+    }.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = i
+    L._dd_ready = True
+    return L
+
+
+def hw_dd_partition(grid: hw_grid, px: int, py: int, part: int) -> hw_part_info:
+    """Block `part` of the grid split px x py (host only: no GPU needed)."""
+    out = hw_part_info()
+    _check(_dd_sigs().hw_dd_partition(C.byref(grid), int(px), int(py), int(part), C.byref(out)), "hw_dd_partition")
+    return out
+
+
+def _dev_ptr(t):
+    if t is None or not _is_torch(t) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("a contiguous CUDA tensor is required")
+    return C.c_void_p(t.data_ptr())
+
+
+def hw_part_create(grid: hw_grid, params: hw_params, px: int, py: int, part: int, stream=None) -> _Handle:
+    out = C.c_void_p()
+    _check(_dd_sigs().hw_part_create(C.byref(grid), C.byref(params), int(px), int(py), int(part),
+                                     _stream_handle(stream), C.byref(out)), "hw_part_create")
+    info = hw_dd_partition(grid, px, py, part)
+    ext = hw_grid(2, info.nx + 4, info.ny + 4, grid.x0, grid.x1, grid.y0, grid.y1, HW_BC_OUTFLOW, HW_BC_OUTFLOW)
+    h = _Handle(out, ext, params, ext.nx * ext.ny, 9)
+    h.info = info
+    return h
+
+
+def hw_part_init(h: _Handle, planes12: Sequence, ld: int):
+    """planes12: the block's own nodes of h, hu, hv, b, h_x, hu_x, hv_x, h_y, hu_y, hv_y, b_x, b_y (numpy or
+    CUDA, rows ld apart; each array's first element is the block's first node)."""
+    kind = _kind(planes12)
+    ptrs = []
+    for a in planes12:
+        if _is_torch(a):
+            ptrs.append(_dev_ptr(a))
+        else:
+            if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host planes must be C-contiguous float64 numpy arrays")
+            ptrs.append(C.c_void_p(a.ctypes.data))
+    _check(_dd_sigs().hw_part_init(h.ptr, _pp(ptrs), int(ld), kind), "hw_part_init")
+
+
+def hw_part_finish_init(h: _Handle):
+    _check(_dd_sigs().hw_part_finish_init(h.ptr), "hw_part_finish_init")
+
+
+def hw_halo_strip_size(h: _Handle, set_: int, face: int) -> int:
+    n = C.c_longlong()
+    _check(_dd_sigs().hw_halo_strip_size(h.ptr, int(set_), int(face), C.byref(n)), "hw_halo_strip_size")
+    return n.value
+
+
+def hw_halo_pack(h: _Handle, set_: int, face: int, strip):
+    _check(_dd_sigs().hw_halo_pack(h.ptr, int(set_), int(face), _dev_ptr(strip)), "hw_halo_pack")
+
+
+def hw_halo_unpack(h: _Handle, set_: int, face: int, mode: int, strip):
+    _check(_dd_sigs().hw_halo_unpack(h.ptr, int(set_), int(face), int(mode), _dev_ptr(strip)), "hw_halo_unpack")
+
+
+def hw_part_alpha_keys(h: _Handle, keys):
+    _check(_dd_sigs().hw_part_alpha_keys(h.ptr, _dev_ptr(keys)), "hw_part_alpha_keys")
+
+
+def hw_part_stage(h: _Handle, k: int, keys, t_end: float = -1.0):
+    _check(_dd_sigs().hw_part_stage(h.ptr, int(k), _dev_ptr(keys), float(t_end)), "hw_part_stage")
+
+
+def hw_dd_max_keys(keys, out, stream=None):
+    """out (2 int64, CUDA) = maxima over the rows of keys (n x 2 int64, CUDA)."""
+    n = keys.numel() // 2
+    _check(_dd_sigs().hw_dd_max_keys(_dev_ptr(keys), int(n), _dev_ptr(out), _stream_handle(stream)), "hw_dd_max_keys")
+
+
+class _DDHandle:
+    def __init__(self, ptr, grid):
+        self.ptr, self.grid = ptr, grid
+
+
+def hw_dd_create(grid: hw_grid, params: hw_params, px: int, py: int, stream=None) -> _DDHandle:
+    out = C.c_void_p()
+    _check(_dd_sigs().hw_dd_create(C.byref(grid), C.byref(params), int(px), int(py), _stream_handle(stream),
+                                   C.byref(out)), "hw_dd_create")
+    return _DDHandle(out, grid)
+
+
+def hw_dd_destroy(d: _DDHandle):
+    if d is not None and d.ptr:
+        _dd_sigs().hw_dd_destroy(d.ptr)
+        d.ptr = None
+
+
+def hw_dd_init(d: _DDHandle, hh, hu, hv, b, deriv: Sequence):
+    n = d.grid.nx * d.grid.ny
+    kind = _kind([hh, hu, hv, b, *deriv])
+    _check(_dd_sigs().hw_dd_init(d.ptr, _ptr(hh, n), _ptr(hu, n), _ptr(hv, n), _ptr(b, n),
+                                 _pp([_ptr(a, n) for a in deriv]), kind), "hw_dd_init")
+
+
+def hw_dd_advance(d: _DDHandle, nsteps: int, t_end: float = -1.0, use_graph: bool = True):
+    t, n = C.c_double(), C.c_int()
+    _check(_dd_sigs().hw_dd_advance(d.ptr, int(nsteps), float(t_end), int(bool(use_graph)), C.byref(t), C.byref(n)),
+           "hw_dd_advance")
+    return t.value, n.value
+
+
+def hw_dd_get_state(d: _DDHandle, out: Sequence, layout: int = HW_LAYOUT_EQUILIBRIUM):
+    n = d.grid.nx * d.grid.ny
+    _check(_dd_sigs().hw_dd_get_state(d.ptr, _pp([_ptr(a, n, True) for a in out]), int(layout), _kind(out)),
+           "hw_dd_get_state")
+
+
+class DecomposedSolver:
+    """One 2D grid split into px x py blocks on the current GPU (halo exchange between them on the device);
+    the same results as ``Solver``, bit for bit."""
+
+    def __init__(self, sc, px: int, py: int, params: Optional[hw_params] = None, stream=None):
+        self.grid = make_grid(sc.nx, sc.ny, sc.x0, sc.x1, sc.y0, sc.y1, sc.bc_x, sc.bc_y, dim=2)
+        self.params = params or make_params(eps_w=sc.eps_w)
+        self.h = hw_dd_create(self.grid, self.params, px, py, stream)
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in [sc.h, sc.hu, sc.hv, sc.b] + list(sc.deriv)]
+        hw_dd_init(self.h, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4:])
+
+    def close(self):
+        hw_dd_destroy(self.h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def advance(self, nsteps, t_end=-1.0, use_graph=True):
+        return hw_dd_advance(self.h, nsteps, t_end, use_graph)
+
+    def state(self, layout=HW_LAYOUT_EQUILIBRIUM):
+        out = [np.empty((self.grid.ny, self.grid.nx)) for _ in range(9)]
+        hw_dd_get_state(self.h, out, layout)
+        return out
 
 
 # ------------------------------------------------------------------------------------------------

@@ -81,6 +81,10 @@ struct hw_solver {
   hw::Dev2DT<float> f2{};
   cudaGraphExec_t graph = nullptr;
   double graph_t_end = -1.0;
+  // sub-domain of a block decomposition (hw_part_create): the grid above is the block extended by a
+  // ring of 2 halo nodes, the spacing is the global grid's, and part_info places the block
+  bool is_part = false;
+  hw_part_info part_info{};
   // profiling: event pairs recorded around launches, resolved in hw_get_profile
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -94,6 +98,13 @@ struct hw_solver {
   float** fother() { return cur == 0 ? FB : FA; }
   bool is2d() const { return grid.dim == 2; }
 };
+
+// Grid spacings and the assembly constants derived from them (a sub-domain takes the global grid's).
+static void set_spacing2d(hw::Dev2D& d, double dx, double dy) {
+  d.dx = dx; d.dy = dy; d.inv_dx = 1.0 / dx; d.inv_dy = 1.0 / dy;
+  d.c_bx = 0.5 / dx; d.c_by = 0.5 / dy; d.c_gx = 1.0 / (24.0 * dx); d.c_gy = 1.0 / (24.0 * dy);
+  d.c_mx = 1.0 / (12.0 * dx); d.c_my = 1.0 / (12.0 * dy);
+}
 
 // Bracket the launches enqueued by fn() (kernels of them) with a pair of events when profiling.
 template <class Fn>
@@ -196,10 +207,8 @@ int hw_create(const hw_grid* grid, const hw_params* params, void* cuda_stream, h
     hw::Dev2D& d = s->d2;
     const double dy = (grid->y1 - grid->y0) / ny;
     d.nx = nx; d.ny = ny; d.bc_x = grid->bc_x; d.bc_y = grid->bc_y;
-    d.dx = dx; d.dy = dy; d.inv_dx = 1.0 / dx; d.inv_dy = 1.0 / dy;
+    set_spacing2d(d, dx, dy);
     d.g = params->g; d.eps_w = params->eps_w; d.eps_lim = params->eps_lim;
-    d.c_bx = 0.5 / dx; d.c_by = 0.5 / dy; d.c_gx = 1.0 / (24.0 * dx); d.c_gy = 1.0 / (24.0 * dy);
-    d.c_mx = 1.0 / (12.0 * dx); d.c_my = 1.0 / (12.0 * dy);
     for (int q = 0; q < 3; ++q) A(&d.stat[q], s->n);
     for (int q = 0; q < 2; ++q) A(&d.bxy[q], s->n);
     for (int q = 0; q < 12; ++q) { A(&d.X[q], (size_t)(nx + 1) * ny); A(&d.Y[q], (size_t)nx * (ny + 1)); }
@@ -633,6 +642,26 @@ int hw_set_state(hw_solver* s, const double* const* in, int layout, int ptr_kind
 }  // extern "C"
 
 namespace hw {
+int part_planes(hw_solver* s, int set, double** planes, int* nplanes) {
+  double** S = s->state();
+  for (int q = 0; q < 9; ++q) planes[q] = S[q];
+  if (set == 1) {
+    for (int q = 0; q < 3; ++q) planes[9 + q] = s->d2.stat[q];
+    for (int q = 0; q < 2; ++q) planes[12 + q] = s->d2.bxy[q];
+  }
+  *nplanes = set == 1 ? 14 : 9;
+  return HW_OK;
+}
+const Dev2D* part_dev(hw_solver* s) { return &s->d2; }
+cudaStream_t solver_swap_stream(hw_solver* s, cudaStream_t st) {
+  cudaStream_t old = s->stream;
+  s->stream = st;
+  return old;
+}
+int solver_cur(hw_solver* s) { return s->cur; }
+cudaStream_t solver_stream(hw_solver* s) { return s->stream; }
+const hw_part_info* part_info(hw_solver* s) { return s && s->is_part ? &s->part_info : nullptr; }
+
 int solver_view(hw_solver* s, SolverView* v) {
   if (!s) return fail(HW_ERR_ARG, "null solver");
   if (!s->inited) return fail(HW_ERR_STATE, "call hw_init first");
@@ -658,6 +687,89 @@ int solver_set_state_planes(hw_solver* s, double* const* src) {
 }  // namespace hw
 
 extern "C" {
+
+// ---- one block of a block decomposition (declared in hwswe.h; the exchange is in hw_dd.cu) ----
+int hw_part_create(const hw_grid* grid, const hw_params* params, int px, int py, int part, void* cuda_stream,
+                   hw_solver** out) {
+  if (!grid || !params || !out) return fail(HW_ERR_ARG, "hw_part_create: null argument");
+  *out = nullptr;
+  if (params->precision != HW_FP64) return fail(HW_ERR_ARG, "hw_part_create: HW_FP64 only");
+  hw_part_info info{};
+  int rc = hw_dd_partition(grid, px, py, part, &info);
+  if (rc != HW_OK) return rc;
+  const double dx = (grid->x1 - grid->x0) / grid->nx, dy = (grid->y1 - grid->y0) / grid->ny;
+  hw_grid ext = *grid;
+  ext.nx = info.nx + 4;
+  ext.ny = info.ny + 4;
+  ext.x0 = grid->x0 + (info.i0 - 2) * dx;
+  ext.x1 = ext.x0 + ext.nx * dx;
+  ext.y0 = grid->y0 + (info.j0 - 2) * dy;
+  ext.y1 = ext.y0 + ext.ny * dy;
+  // the extended grid's own boundary only feeds ring nodes, which every exchange overwrites
+  ext.bc_x = ext.bc_y = HW_BC_OUTFLOW;
+  hw_solver* s = nullptr;
+  rc = hw_create(&ext, params, cuda_stream, &s);
+  if (rc != HW_OK) return rc;
+  set_spacing2d(s->d2, dx, dy);  // the global spacings exactly (ext.x1 - ext.x0 may round)
+  s->is_part = true;
+  s->part_info = info;
+  *out = s;
+  return HW_OK;
+}
+
+int hw_part_init(hw_solver* s, const double* const* planes12, long long ld, int ptr_kind) {
+  Range nvtx_range("hw_part_init");
+  if (!s || !s->is_part || !planes12) return fail(HW_ERR_ARG, "hw_part_init: null argument or not a block solver");
+  const hw_part_info& pi = s->part_info;
+  if (ld < pi.nx) return fail(HW_ERR_ARG, "hw_part_init: ld below the block's nx");
+  if (ptr_kind != HW_HOST && ptr_kind != HW_DEVICE) return fail(HW_ERR_ARG, "hw_part_init: bad ptr_kind");
+  const int nxe = s->grid.nx;
+  const cudaMemcpyKind kind = ptr_kind == HW_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  hw::PhysIn pin;
+  for (int q = 0; q < 12; ++q) {
+    if (!planes12[q]) return fail(HW_ERR_ARG, "hw_part_init: null plane");
+    CUDA_OK(cudaMemcpy2DAsync(s->staging[q] + 2 * (size_t)nxe + 2, nxe * sizeof(double), planes12[q],
+                              (size_t)ld * sizeof(double), pi.nx * sizeof(double), pi.ny, kind, s->stream));
+    pin.p[q] = s->staging[q];
+  }
+  hw::launch_fill_ring(s->staging, nxe, s->grid.ny, s->stream);
+  s->cur = 0;
+  bind_state(s, s->SA);
+  hw::launch_init2d(s->d2, pin, s->status, s->stream);
+  CUDA_OK(cudaGetLastError());
+  CUDA_OK(cudaMemsetAsync(s->t, 0, sizeof(double), s->stream));
+  s->inited = true;
+  return read_status(s);
+}
+
+int hw_part_finish_init(hw_solver* s) {
+  if (!s || !s->is_part || !s->inited) return fail(HW_ERR_ARG, "hw_part_finish_init: not an initialised block solver");
+  hw::launch_static2d(s->d2, s->stream);
+  CUDA_OK(cudaGetLastError());
+  return read_status(s);
+}
+
+int hw_part_alpha_keys(hw_solver* s, unsigned long long* keys) {
+  if (!s || !s->is_part || !keys) return fail(HW_ERR_ARG, "hw_part_alpha_keys: null argument or not a block solver");
+  if (!s->inited) return fail(HW_ERR_STATE, "hw_part_alpha_keys: call hw_part_init first");
+  bind_state(s, s->state());
+  hw::launch_alpha2d(s->d2, s->amax, s->status, s->stream);
+  CUDA_OK(cudaMemcpyAsync(keys, s->amax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s->stream));
+  return HW_OK;
+}
+
+int hw_part_stage(hw_solver* s, int k, const unsigned long long* keys, double t_end) {
+  if (!s || !s->is_part || !keys) return fail(HW_ERR_ARG, "hw_part_stage: null argument or not a block solver");
+  if (!s->inited) return fail(HW_ERR_STATE, "hw_part_stage: call hw_part_init first");
+  if (k < 1 || k > 3) return fail(HW_ERR_ARG, "hw_part_stage: k must be 1, 2 or 3");
+  bind_state(s, s->state());
+  hw::launch_finish_alpha2d(s->d2, keys, s->alpha, k == 1 ? s->dt : nullptr, s->params.cfl, k == 1 ? s->t : nullptr,
+                            t_end, s->stream);
+  enqueue_stage(s, k);
+  if (k == 3) k_add_time<<<1, 1, 0, s->stream>>>(s->t, s->dt, 1, s->nsteps);
+  CUDA_OK(cudaGetLastError());
+  return HW_OK;
+}
 
 int hw_set_profiling(hw_solver* s, int on) {
   if (!s) return fail(HW_ERR_ARG, "hw_set_profiling: null solver");

@@ -89,6 +89,8 @@ void launch_sweep_x2d(const Dev2D& d, const double* alpha, bool linear, bool chr
 void launch_sweep_y2d(const Dev2D& d, const double* alpha, bool linear, bool chr, cudaStream_t st);
 void launch_node2d(const Dev2D& d, const StageArgs& sa, int mode, bool linear, bool chr, cudaStream_t st);
 void launch_init2d(const Dev2D& d, const PhysIn& in, int* status, cudaStream_t st);
+// the b-only source terms alone (launch_init2d runs them after the conversion)
+void launch_static2d(const Dev2D& d, cudaStream_t st);
 void launch_convert2d(const Dev2D& d, const Ptr9& src, const Ptr9& dst, int layout, int dir, cudaStream_t st);
 // single-precision variant of the stage kernels, and plane casts between precisions
 void launch_alpha2d(const Dev2DT<float>& d, unsigned long long* amax, int* status, cudaStream_t st);
@@ -126,6 +128,17 @@ struct SolverView {
   size_t n;
 };
 int solver_view(hw_solver* s, SolverView* v);
+// Sub-domain solvers (hw_dd.cu): the planes a halo exchange moves (set 0: the 9 state planes of the current
+// state; set 1: those and the static planes b, dx b_x, dy b_y, b_x, b_y), the extended grid's Dev2D, and
+// the stream the solver launches on (swapped for graph capture; returns the previous one).
+int part_planes(hw_solver* s, int set, double** planes, int* nplanes);
+const Dev2D* part_dev(hw_solver* s);
+cudaStream_t solver_swap_stream(hw_solver* s, cudaStream_t st);
+int solver_cur(hw_solver* s);                  // which of the two state buffers holds the state
+cudaStream_t solver_stream(hw_solver* s);
+const hw_part_info* part_info(hw_solver* s);   // null unless a block solver
+// still water (h = 1, everything else 0) on the 2-node ring of 12 extended input planes (hw_dd.cu)
+void launch_fill_ring(double* const* planes12, int nxe, int nye, cudaStream_t st);
 int solver_set_state_planes(hw_solver* s, double* const* src);  // device copy into the current state
 void adjoint_release(hw_solver* s);  // frees a solver's adjoint working buffers; hw_destroy calls it
 

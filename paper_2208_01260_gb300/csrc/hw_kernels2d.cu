@@ -569,6 +569,11 @@ void launch_init2d(const Dev2D& d, const PhysIn& in, int* status, cudaStream_t s
   k_static2d<<<g, dim3(32, 8), 0, st>>>(d);
 }
 
+void launch_static2d(const Dev2D& d, cudaStream_t st) {
+  dim3 g((d.nx + 1 + 31) / 32, (d.ny + 1 + 7) / 8);
+  k_static2d<<<g, dim3(32, 8), 0, st>>>(d);
+}
+
 void launch_convert2d(const Dev2D& d, const Ptr9& src, const Ptr9& dst, int layout, int dir, cudaStream_t st) {
   const size_t n = (size_t)d.nx * d.ny;
   int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 16);

@@ -1,0 +1,229 @@
+"""Block decomposition of one 2D grid across processes (one process per GPU, or several blocks per process).
+
+The grid is split into px x py blocks (``hw_dd_partition``); block p belongs to rank ``p % world``. Each
+block is a solver on its nodes plus a ring of 2 halo nodes (``hw_part_create``). One SSP-RK3 stage
+(Sec. 2.2 eq. RK) of the 2D scheme (Sec. 3) is, on every rank:
+
+  1. the halo exchange of the 9 state planes: x faces, then y faces (whose strips span the ring, so the
+     corners follow); a block's face takes the neighbour's strip of the opposite face
+     (HW_HALO_NEIGHBOR, periodic included) or its own strip mirrored or repeated (walls, open ends);
+  2. each block's alpha keys (max(|u|+c), max(|v|+c) over its nodes and ring, as integer bit patterns),
+     the maximum over the rank's blocks, then over ranks (one all-reduce of 16 bytes): the global alpha
+     of Sec. 2.1 Step 1;
+  3. each block's stage with that alpha (stage 1 also takes the CFL step, Sec. 4).
+
+Messages of one exchange phase are posted in one batch, in a global order (receiving block, face) that
+every rank follows, so that the i-th message between two ranks is the same on both sides; strips that
+stay in the process are unpacked directly. The result equals the undecomposed solver's bit for bit.
+
+The transport is ``torch.distributed`` (NCCL between GPUs, gloo between CPU processes) or nothing for a
+single process. Blocks follow a small interface (``strip_size``, ``new_strip``, ``pack``, ``unpack``,
+``alpha_keys``, ``stage``, plus ``max_keys`` of the rank's rows); ``CudaBlock`` is the GPU block of this
+library, whose every step runs in its CUDA kernels.
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import (HW_FACE_E, HW_FACE_N, HW_FACE_S, HW_FACE_W, HW_HALO_NEIGHBOR, HW_LAYOUT_EQUILIBRIUM, hw_dd_max_keys,
+               hw_dd_partition, hw_destroy, hw_get_state, hw_grid, hw_halo_pack, hw_halo_strip_size, hw_halo_unpack,
+               hw_params, hw_part_alpha_keys, hw_part_create, hw_part_finish_init, hw_part_init, hw_part_stage)
+
+FACES_X = (HW_FACE_W, HW_FACE_E)
+FACES_Y = (HW_FACE_S, HW_FACE_N)
+SET_STATE, SET_INIT = 0, 1
+
+
+class Plan:
+    """Blocks of the grid and their owners."""
+
+    def __init__(self, grid: hw_grid, px: int, py: int, world: int = 1):
+        self.grid, self.px, self.py, self.world = grid, px, py, world
+        self.info = [hw_dd_partition(grid, px, py, p) for p in range(px * py)]
+
+    @property
+    def nparts(self) -> int:
+        return self.px * self.py
+
+    def owner(self, part: int) -> int:
+        return part % self.world
+
+    def local_parts(self, rank: int) -> List[int]:
+        return [p for p in range(self.nparts) if self.owner(p) == rank]
+
+    def messages(self, faces) -> List[tuple]:
+        """(receiving block, its face, sending block) of every NEIGHBOR face in a phase, in the global order."""
+        out = []
+        for p in range(self.nparts):
+            for f in faces:
+                if self.info[p].mode[f] == HW_HALO_NEIGHBOR:
+                    out.append((p, f, self.info[p].nbr[f]))
+        return out
+
+
+class Comm:
+    """Rank, world size and the two collectives the protocol needs (torch.distributed when world > 1)."""
+
+    def __init__(self, rank: int = 0, world: int = 1):
+        self.rank, self.world = rank, world
+
+    @classmethod
+    def from_torch(cls):
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            return cls(dist.get_rank(), dist.get_world_size())
+        return cls(0, 1)
+
+    def exchange(self, sends, recvs):
+        """sends: [(tensor, dst_rank, tag)], recvs: [(tensor, src_rank, tag)], both in the global order."""
+        if not sends and not recvs:
+            return
+        import torch.distributed as dist
+        # one batch per phase, posted in the global message order (each message is a send or a receive here;
+        # the tag is its position in that order, for transports that match by tag)
+        merged = [(tag, dist.isend, t, r) for t, r, tag in sends] + [(tag, dist.irecv, t, r) for t, r, tag in recvs]
+        merged.sort(key=lambda x: x[0])
+        ops = [dist.P2POp(op, t, peer, tag=tag) for tag, op, t, peer in merged]
+        for w in dist.batch_isend_irecv(ops):
+            w.wait()
+
+    def allreduce_max(self, t):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+
+
+def exchange(blocks: Dict[int, object], plan: Plan, set_: int, comm: Comm):
+    """One halo exchange of plane set `set_` for the rank's blocks (dict part -> block)."""
+    for faces in (FACES_X, FACES_Y):
+        packed = {}
+        for p, blk in blocks.items():
+            for f in faces:
+                buf = blk.new_strip(blk.strip_size(set_, f))
+                blk.pack(set_, f, buf)
+                packed[(p, f)] = buf
+        sends, recvs, received = [], [], {}
+        for order, (p, f, q) in enumerate(plan.messages(faces)):
+            mine_p, mine_q = plan.owner(p) == comm.rank, plan.owner(q) == comm.rank
+            if mine_q and not mine_p:
+                sends.append((packed[(q, f ^ 1)], plan.owner(p), order))
+            elif mine_p and not mine_q:
+                buf = blocks[p].new_strip(blocks[p].strip_size(set_, f))
+                recvs.append((buf, plan.owner(q), order))
+                received[(p, f)] = buf
+        comm.exchange(sends, recvs)
+        for p, blk in blocks.items():
+            for f in faces:
+                mode = plan.info[p].mode[f]
+                if mode == HW_HALO_NEIGHBOR:
+                    q = plan.info[p].nbr[f]
+                    src = received[(p, f)] if (p, f) in received else packed[(q, f ^ 1)]
+                else:
+                    src = packed[(p, f)]
+                blk.unpack(set_, f, mode, src)
+
+
+def global_keys(blocks: Dict[int, object], comm: Comm):
+    """The alpha keys of the rank's blocks, their maximum, then the maximum over ranks."""
+    items = sorted(blocks.items())
+    first = items[0][1]
+    rows = first.new_keys(len(items))
+    for r, (_, blk) in enumerate(items):
+        blk.alpha_keys(rows[r])
+    keys = first.new_keys(1)[0]
+    first.max_keys(rows, keys)
+    comm.allreduce_max(keys)
+    return keys
+
+
+def rk3_step(blocks: Dict[int, object], plan: Plan, comm: Comm, t_end: float = -1.0):
+    """One SSP-RK3 step of every block of the rank, dt = the CFL step at the step's start."""
+    for k in (1, 2, 3):
+        exchange(blocks, plan, SET_STATE, comm)
+        keys = global_keys(blocks, comm)
+        for _, blk in sorted(blocks.items()):
+            blk.stage(k, keys, t_end)
+
+
+def initialise(blocks: Dict[int, object], plan: Plan, comm: Comm, planes12_of):
+    """Load every block's own nodes (planes12_of(part) -> (12 arrays, ld)), exchange the state and static
+    planes once, then form the b-only source terms."""
+    for p, blk in sorted(blocks.items()):
+        arrays, ld = planes12_of(p)
+        blk.init(arrays, ld)
+    exchange(blocks, plan, SET_INIT, comm)
+    for _, blk in sorted(blocks.items()):
+        blk.finish_init()
+
+
+class CudaBlock:
+    """One block on this process's GPU (the library's block solver); strips and keys are CUDA tensors."""
+
+    def __init__(self, grid: hw_grid, params: hw_params, px: int, py: int, part: int, stream=None):
+        import torch
+        self.torch = torch
+        self.part = part
+        self.h = hw_part_create(grid, params, px, py, part, stream)
+        self.info = self.h.info
+        self.stream = stream
+
+    def close(self):
+        hw_destroy(self.h)
+
+    def init(self, planes12: Sequence, ld: int):
+        hw_part_init(self.h, planes12, ld)
+
+    def finish_init(self):
+        hw_part_finish_init(self.h)
+
+    def strip_size(self, set_: int, face: int) -> int:
+        return hw_halo_strip_size(self.h, set_, face)
+
+    def new_strip(self, n: int):
+        return self.torch.empty(n, dtype=self.torch.float64, device="cuda")
+
+    def new_keys(self, n: int):
+        return self.torch.zeros((n, 2), dtype=self.torch.int64, device="cuda")
+
+    def pack(self, set_: int, face: int, strip):
+        hw_halo_pack(self.h, set_, face, strip)
+
+    def unpack(self, set_: int, face: int, mode: int, strip):
+        hw_halo_unpack(self.h, set_, face, mode, strip)
+
+    def alpha_keys(self, row):
+        hw_part_alpha_keys(self.h, row)
+
+    def max_keys(self, rows, out):
+        hw_dd_max_keys(rows, out, self.stream)
+
+    def stage(self, k: int, keys, t_end: float = -1.0):
+        hw_part_stage(self.h, k, keys, t_end)
+
+    def state(self, layout: int = HW_LAYOUT_EQUILIBRIUM) -> List[np.ndarray]:
+        """The block's own nodes (9 planes, ny x nx each)."""
+        nxe, nye = self.info.nx + 4, self.info.ny + 4
+        ext = [np.empty((nye, nxe)) for _ in range(9)]
+        hw_get_state(self.h, ext, layout)
+        return [a[2:-2, 2:-2].copy() for a in ext]
+
+
+def window12(sc, info) -> tuple:
+    """The block's own nodes of a scenario's 12 input planes (host arrays, rows nx apart)."""
+    planes = [sc.h, sc.hu, sc.hv, sc.b] + list(sc.deriv)
+    out = [np.ascontiguousarray(a[info.j0:info.j0 + info.ny, info.i0:info.i0 + info.nx], dtype=np.float64)
+           for a in planes]
+    return out, info.nx
+
+
+def gather(plan: Plan, states: Dict[int, Sequence[np.ndarray]]) -> List[np.ndarray]:
+    """Global planes from the blocks' own nodes (host)."""
+    g = plan.grid
+    out = [np.empty((g.ny, g.nx)) for _ in range(9)]
+    for p, planes in states.items():
+        i = plan.info[p]
+        for q in range(9):
+            out[q][i.j0:i.j0 + i.ny, i.i0:i.i0 + i.nx] = planes[q]
+    return out
