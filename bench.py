@@ -398,6 +398,42 @@ def adjoint_cost(n=512, nsteps=400, snapshots=20):
     return out
 
 
+def decomposed_compare(steps, splits=((2, 2), (4, 2))):
+    """The benchmark workload split into blocks on this GPU (hw_dd_*: halo exchange between the blocks on
+    the device, alpha as the maximum over blocks, two steps per CUDA graph): point-updates/s per split next
+    to the undecomposed solver, and whether the states agree bit for bit."""
+    import torch
+    import paper_2208_01260_gb300 as hw
+    from paper_2208_01260_gb300 import scenarios as S
+    sc = S.bumps2d(NX, NY, strip=0.01)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(obj):
+        obj.advance(4)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        obj.advance(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+    s = hw.Solver.from_scenario(sc, hw.make_params())
+    ms_single = timed(s)
+    ref = s.state()
+    s.close()
+    out = {"steps": steps, "ms_per_step_single": ms_single, "unit": UNIT,
+           "value_single": NX * NY * STAGES / (ms_single * 1e-3), "splits": {}}
+    for px, py in splits:
+        d = hw.DecomposedSolver(sc, px, py)
+        ms = timed(d)
+        got = d.state()
+        d.close()
+        out["splits"]["%dx%d" % (px, py)] = {
+            "ms_per_step": ms, "value": NX * NY * STAGES / (ms * 1e-3), "over_single": ms_single / ms,
+            "bitwise_equal_to_single": all(np.array_equal(a, b) for a, b in zip(ref, got))}
+    return out
+
+
 def run_reference(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -445,6 +481,7 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=6, help="steps of the batched comparison (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=400, help="steps of the adjoint cost measurement (0 = skip)")
     ap.add_argument("--fp32-steps", type=int, default=200, help="steps of the single-precision variant (0 = skip)")
+    ap.add_argument("--decomp-steps", type=int, default=10, help="steps of the block-decomposition comparison (0 = skip)")
     ap.add_argument("--nx", type=int, default=2048, help="smaller grids for profiling captures only")
     ap.add_argument("--ny", type=int, default=2048)
     args = ap.parse_args()
@@ -608,13 +645,15 @@ def main():
             line[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     # (only in single-GPU runs: a scaling run measures the headline alone)
     if ws > 1:
-        args.batched_steps = args.adjoint_steps = args.fp32_steps = 0
+        args.batched_steps = args.adjoint_steps = args.fp32_steps = args.decomp_steps = 0
     if args.batched_steps > 0 and (NX, NY) == (2048, 2048):
         solver.close()
         extra("batched", lambda: batched_compare(args.batched_steps))
         # the regime the batched form is for: grids too small to fill the GPU one launch at a time
         extra("batched_small_grids", lambda: dict(batched_compare(args.batched_steps, n_inst=1024, fixed=(64, 64)),
                                                   workload="1024 grids of 64x64 (not config 4)"))
+    if args.decomp_steps > 0 and (NX, NY) == (2048, 2048):
+        extra("decomposed", lambda: decomposed_compare(args.decomp_steps))
     if args.adjoint_steps > 0 and (NX, NY) == (2048, 2048):
         extra("adjoint", lambda: adjoint_cost(nsteps=args.adjoint_steps))
     if args.fp32_steps > 0:
