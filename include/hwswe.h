@@ -180,15 +180,17 @@ int hw_batch_run(hw_batch* b, int nsteps, int use_graph);
 int hw_batch_get_state(hw_batch* b, int i, double* const* out, int layout, int ptr_kind);
 /* Simulated time and step count of every grid (t[n], steps[n]; either may be NULL). */
 int hw_batch_get_time(hw_batch* b, double* t, int* steps);
-/* Tile shapes of grid i: tx = threads per row of an x-tile (32, 64 or 128; each row covers tx - 3
- * interfaces and forms their tx node records, one per thread; 128/tx rows per tile), seg = interfaces
- * per y-segment (>= 1). Chosen by the autotuner; arithmetic is unaffected. */
-int hw_batch_set_tiles(hw_batch* b, int i, int tx, int seg);
-int hw_batch_get_tiles(hw_batch* b, int i, int* tx, int* seg);
+/* Tile shape of grid i. The sweeps run over flattened extended lines (each row, or each group of yc
+ * columns, with its 2 halo nodes on either side, one after the other): a tile of 192 threads forms 192
+ * node records and the interfaces whose stencils lie among them, so tiles run across line ends and no
+ * grid size leaves a ragged tile. An x-tile covers 192 consecutive extended nodes of the rows (189
+ * interfaces); a y-tile yc = 1, 2 or 4 adjacent columns of 192 / yc extended rows (yc (192 / yc - 3)
+ * interfaces). Chosen by the autotuner; arithmetic is unaffected. */
+int hw_batch_set_tiles(hw_batch* b, int i, int yc);
+int hw_batch_get_tiles(hw_batch* b, int i, int* yc);
 /* Autotuner measurement: average ms of the batched x-sweep and y-sweep over the grids ids[nids] with
- * trial tile shapes (tx, seg), over reps repetitions. Changes no state (interface planes are scratch). */
-int hw_batch_time_tiles(hw_batch* b, int nids, const int* ids, int tx, int seg, int reps, double* ms_x,
-                        double* ms_y);
+ * the trial y-tile width yc, over reps repetitions. Changes no state (interface planes are scratch). */
+int hw_batch_time_tiles(hw_batch* b, int nids, const int* ids, int yc, int reps, double* ms_x, double* ms_y);
 
 /* ---------------------------------------------------------------------------------------------
  * Discrete adjoint (2D, nonlinear weights and characteristic projection; limiter on or off).

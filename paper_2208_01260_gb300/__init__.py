@@ -528,9 +528,9 @@ def _batch_sigs():
         "hw_batch_run": [vp, i, i],
         "hw_batch_get_state": [vp, i, pp, i, i],
         "hw_batch_get_time": [vp, C.POINTER(d), C.POINTER(i)],
-        "hw_batch_set_tiles": [vp, i, i, i],
-        "hw_batch_get_tiles": [vp, i, C.POINTER(i), C.POINTER(i)],
-        "hw_batch_time_tiles": [vp, i, C.POINTER(i), i, i, i, C.POINTER(d), C.POINTER(d)],
+        "hw_batch_set_tiles": [vp, i, i],
+        "hw_batch_get_tiles": [vp, i, C.POINTER(i)],
+        "hw_batch_time_tiles": [vp, i, C.POINTER(i), i, i, C.POINTER(d), C.POINTER(d)],
     }.items():
         f = getattr(L, name)
         f.argtypes = args
@@ -585,21 +585,22 @@ def hw_batch_get_time(b: _BHandle):
     return np.array(t[:]), np.array(k[:])
 
 
-def hw_batch_set_tiles(b: _BHandle, i: int, tx: int, seg: int):
-    _check(_batch_sigs().hw_batch_set_tiles(b.ptr, int(i), int(tx), int(seg)), "hw_batch_set_tiles")
+def hw_batch_set_tiles(b: _BHandle, i: int, yc: int):
+    """y-tile width of grid i: 1, 2 or 4 columns per tile."""
+    _check(_batch_sigs().hw_batch_set_tiles(b.ptr, int(i), int(yc)), "hw_batch_set_tiles")
 
 
-def hw_batch_get_tiles(b: _BHandle, i: int):
-    tx, seg = C.c_int(), C.c_int()
-    _check(_batch_sigs().hw_batch_get_tiles(b.ptr, int(i), C.byref(tx), C.byref(seg)), "hw_batch_get_tiles")
-    return tx.value, seg.value
+def hw_batch_get_tiles(b: _BHandle, i: int) -> int:
+    yc = C.c_int()
+    _check(_batch_sigs().hw_batch_get_tiles(b.ptr, int(i), C.byref(yc)), "hw_batch_get_tiles")
+    return yc.value
 
 
-def hw_batch_time_tiles(b: _BHandle, ids: Sequence[int], tx: int, seg: int, reps: int = 3):
+def hw_batch_time_tiles(b: _BHandle, ids: Sequence[int], yc: int, reps: int = 3):
     arr = (C.c_int * len(ids))(*[int(i) for i in ids])
     mx, my = C.c_double(), C.c_double()
-    _check(_batch_sigs().hw_batch_time_tiles(b.ptr, len(ids), arr, int(tx), int(seg), int(reps), C.byref(mx),
-                                             C.byref(my)), "hw_batch_time_tiles")
+    _check(_batch_sigs().hw_batch_time_tiles(b.ptr, len(ids), arr, int(yc), int(reps), C.byref(mx), C.byref(my)),
+           "hw_batch_time_tiles")
     return mx.value, my.value
 
 

@@ -1,12 +1,15 @@
 """Tile-shape autotuner of the batched form.
 
-The batched kernels take two tile shapes per grid: the row width tx of an x-tile (32, 64 or 128
-threads, each row covering tx - 3 interfaces; 128/tx rows per tile) and the number of y-interfaces per
-y-segment. Neither changes the
-arithmetic. Grids are grouped in size classes (powers of two of nx for the x-tiles, of ny for the
-y-segments); for each class every candidate is timed on that class's grids with
-``hw_batch_time_tiles`` (events around the batched sweep launches) and the fastest is kept. Results
-are cached per device and class in a JSON file, so later batches reuse them without timing.
+The batched sweeps run over flattened extended lines (rows, or groups of yc adjacent columns, each with
+its two halo nodes on either side, one after the other) in tiles of 192 node records, so no grid size
+leaves a ragged tile; the x-tiles have one shape. What remains to choose is the y-tile width yc: 1, 2
+or 4 columns of 192 / yc extended rows. Wider tiles load more contiguous bytes per row; narrower ones
+form fewer halo records per interface. The choice never changes the arithmetic.
+
+Grids are grouped in size classes (powers of two of nx); for each class every candidate is timed on
+that class's grids with ``hw_batch_time_tiles`` (events around the batched sweep launches) and the
+fastest is kept. Results are cached per device and class in a JSON file, so later batches reuse them
+without timing.
 """
 from __future__ import annotations
 
@@ -15,8 +18,7 @@ import math
 import os
 from typing import Dict, Optional
 
-TX_CANDIDATES = (32, 64, 128)
-SEG_CANDIDATES = (16, 32, 64, 128, 256)
+YC_CANDIDATES = (1, 2, 4)
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cache.json")
 
 
@@ -41,40 +43,27 @@ def _load(path: str) -> Dict:
 
 
 def tune(batch, cache_path: Optional[str] = None, reps: int = 3, force: bool = False) -> Dict:
-    """Choose and apply tile shapes for every grid of ``batch`` (a BatchedSolver)."""
+    """Choose and apply the y-tile width of every grid of ``batch`` (a BatchedSolver)."""
     import paper_2208_01260_gb300 as hw
     path = cache_path or DEFAULT_CACHE
     cache = _load(path)
-    dev = cache.setdefault(_device_key(), {"tx": {}, "seg": {}})
-    grids = batch.grids
-    xcls: Dict[int, list] = {}
-    ycls: Dict[int, list] = {}
-    for i, g in enumerate(grids):
-        xcls.setdefault(size_class(g.nx), []).append(i)
-        ycls.setdefault(size_class(g.ny), []).append(i)
-    timings = {"tx": {}, "seg": {}}
-    for c, ids in sorted(xcls.items()):
+    dev = cache.setdefault(_device_key() + ":flat", {"yc": {}})
+    classes: Dict[int, list] = {}
+    for i, g in enumerate(batch.grids):
+        classes.setdefault(size_class(g.nx), []).append(i)
+    timings: Dict[str, Dict[int, float]] = {}
+    for c, ids in sorted(classes.items()):
         key = str(c)
-        if force or key not in dev["tx"]:
+        if force or key not in dev["yc"]:
             best = None
-            for tx in TX_CANDIDATES:
-                ms, _ = hw.hw_batch_time_tiles(batch.h, ids, tx, 64, reps)
-                timings["tx"].setdefault(key, {})[tx] = ms
+            for yc in YC_CANDIDATES:
+                _, ms = hw.hw_batch_time_tiles(batch.h, ids, yc, reps)
+                timings.setdefault(key, {})[yc] = ms
                 if best is None or ms < best[0]:
-                    best = (ms, tx)
-            dev["tx"][key] = best[1]
-    for c, ids in sorted(ycls.items()):
-        key = str(c)
-        if force or key not in dev["seg"]:
-            best = None
-            for seg in SEG_CANDIDATES:
-                _, ms = hw.hw_batch_time_tiles(batch.h, ids, 128, seg, reps)
-                timings["seg"].setdefault(key, {})[seg] = ms
-                if best is None or ms < best[0]:
-                    best = (ms, seg)
-            dev["seg"][key] = best[1]
-    for i, g in enumerate(grids):
-        hw.hw_batch_set_tiles(batch.h, i, dev["tx"][str(size_class(g.nx))], dev["seg"][str(size_class(g.ny))])
+                    best = (ms, yc)
+            dev["yc"][key] = best[1]
+    for i, g in enumerate(batch.grids):
+        hw.hw_batch_set_tiles(batch.h, i, dev["yc"][str(size_class(g.nx))])
     try:
         with open(path, "w") as f:
             json.dump(cache, f, indent=1, sort_keys=True)

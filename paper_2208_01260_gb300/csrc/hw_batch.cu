@@ -1,13 +1,15 @@
 // Batched form: many independent 2D grids of uneven sizes advance together, each with its own CFL
 // time step. All instances share pooled planes; every phase of an RK stage (alpha reduction, x-sweep,
-// y-sweep, node update) is ONE launch whose persistent blocks loop over a flattened list of tiles of
-// every instance, so the launch count per step does not depend on the number of instances and small
-// grids no longer leave the GPU idle. Two steps are captured in a CUDA graph. Tile shapes (interfaces
-// per x-tile, interfaces per y-segment) are per instance, chosen by the autotuner. The arithmetic is
-// the single-grid kernels' (hw_stencil2d.cuh), so each instance's result equals a single-grid
-// solver's to rounding (the compiler may contract multiply-adds differently in the two kernels),
-// with the same share of products on the integer pipes (bit-identical binary64, hw_fp64_int.h).
-// No block ever waits on another block.
+// y-sweep, node update) is ONE launch over a flattened list of work items of every instance (one block
+// per item; the alpha passes loop over theirs), so the launch count per step does not depend on the
+// number of instances and small grids no longer leave the GPU idle. Two steps are captured in a CUDA
+// graph. The sweeps use the single-grid tiles over flattened extended lines (hw_stencil2d.cuh), so no
+// grid size leaves a ragged tile; the y-tile width is per instance, chosen by the autotuner. The
+// arithmetic is the single-grid kernels', so each instance's result equals a single-grid solver's to
+// rounding (the compiler may contract multiply-adds differently in the two kernels), with the same
+// share of products on the integer pipes (each bit-identical to DMUL, hw_fp64_int.h). The kernels read
+// the pooled planes through the parameters' base pointers plus the instance's offsets, so that no
+// per-instance pointer takes a register. No block ever waits on another block.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -21,8 +23,7 @@ struct BInst {
   int nx, ny, bc_x, bc_y;
   double dx, dy, inv_dx, inv_dy, c_bx, c_by, c_gx, c_gy, c_mx, c_my;
   long long off_n, off_x, off_y;  // offsets of this grid in the pooled node / x-interface / y-interface planes
-  int tx, seg;                     // x-tile row width (32, 64 or 128 threads = tx - 3 interfaces and their
-                                   // tx node records; 128/tx rows per block), y segment
+  int yc;                          // columns per y-tile group (1, 2 or 4; TILE_T / yc extended rows per tile)
 };
 
 struct BatchDev {
@@ -40,7 +41,7 @@ struct BatchDev {
   double* sq[2];
   double* out[9];
   double* base[9];
-  unsigned long long* amax;  // 2 per instance
+  unsigned long long* amax;  // 3 per instance: alpha_x, alpha_y keys, the coarse pass's float maxima
   double* alpha;             // 2 per instance
   double* dt;                // 2 per instance: step, time after the step
   double* t;                 // 1 per instance
@@ -48,61 +49,84 @@ struct BatchDev {
   int* status;
 };
 
+// The instance's grid constants with the pooled planes' base pointers (they stay in the kernel parameters;
+// the kernels add the instance's offsets I.off_n, I.off_x, I.off_y to their indices).
 __device__ __forceinline__ void make_dev(const BatchDev& B, const BInst& I, Dev2D& d) {
   d.nx = I.nx; d.ny = I.ny; d.bc_x = I.bc_x; d.bc_y = I.bc_y;
   d.dx = I.dx; d.dy = I.dy; d.inv_dx = I.inv_dx; d.inv_dy = I.inv_dy;
   d.g = B.g; d.eps_w = B.eps_w; d.eps_lim = B.eps_lim;
   d.c_bx = I.c_bx; d.c_by = I.c_by; d.c_gx = I.c_gx; d.c_gy = I.c_gy; d.c_mx = I.c_mx; d.c_my = I.c_my;
 #pragma unroll
-  for (int q = 0; q < 9; ++q) d.S[q] = B.S[q] + I.off_n;
+  for (int q = 0; q < 9; ++q) d.S[q] = B.S[q];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) d.stat[q] = B.stat[q] + I.off_n;
+  for (int q = 0; q < 3; ++q) d.stat[q] = B.stat[q];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) d.bxy[q] = B.bxy[q] + I.off_n;
+  for (int q = 0; q < 2; ++q) d.bxy[q] = B.bxy[q];
 #pragma unroll
-  for (int q = 0; q < 12; ++q) { d.X[q] = B.X[q] + I.off_x; d.Y[q] = B.Y[q] + I.off_y; }
+  for (int q = 0; q < 12; ++q) { d.X[q] = B.X[q]; d.Y[q] = B.Y[q]; }
 #pragma unroll
-  for (int q = 0; q < 6; ++q) { d.qbx[q] = B.qbx[q] + I.off_x; d.qby[q] = B.qby[q] + I.off_y; }
+  for (int q = 0; q < 6; ++q) { d.qbx[q] = B.qbx[q]; d.qby[q] = B.qby[q]; }
 #pragma unroll
-  for (int q = 0; q < 2; ++q) { d.sv[q] = B.sv[q] + I.off_n; d.sq[q] = B.sq[q] + I.off_n; }
+  for (int q = 0; q < 2; ++q) { d.sv[q] = B.sv[q]; d.sq[q] = B.sq[q]; }
 }
 
-constexpr int BX_THREADS = 128;
-constexpr int BX_MAXN = BX_THREADS;     // node records per block: one per thread
-constexpr int BY_W = 32;
+constexpr int BN_T = 256;  // nodes per node-kernel item
 
-// ---- alpha per instance: items (inst, first node, count) ----
-__global__ void __launch_bounds__(256) k_balpha(BatchDev B, const int4* __restrict__ items, int nitems) {
+// ---- alpha per instance in two passes, as the single-grid reduction (a float estimate of every node,
+// the double value only near the float maximum): items (inst, first node, count) ----
+__global__ void __launch_bounds__(256) k_balpha_coarse(BatchDev B, const int4* __restrict__ items, int nitems) {
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int4 it = items[w];
     const BInst& I = B.inst[it.x];
-    const double* eta = B.S[0] + I.off_n;
-    const double* m = B.S[1] + I.off_n;
-    const double* wv = B.S[2] + I.off_n;
-    const double* b = B.stat[0] + I.off_n;
+    Dev2D d;
+    make_dev(B, I, d);
+    float mx = 0.0f, my = 0.0f;
+    int bad = 0;
+    const size_t base = (size_t)I.off_n;
+    for (int o = it.y + threadIdx.x; o < it.y + it.z; o += blockDim.x) {
+      float ax, ay;
+      bool exact, neg;
+      alpha_coarse(d, base + o, ax, ay, exact, neg);
+      if (exact) continue;
+      if (neg) { bad |= HW_STATUS_DEPTH; continue; }
+      mx = fmaxf(mx, ax);
+      my = fmaxf(my, ay);
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+      my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, s));
+    }
+    unsigned int* m32 = reinterpret_cast<unsigned int*>(B.amax + 3 * it.x + 2);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(m32, __float_as_uint(mx));
+      atomicMax(m32 + 1, __float_as_uint(my));
+    }
+    if (bad) atomicOr(B.status, bad);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_balpha_exact(BatchDev B, const int4* __restrict__ items, int nitems) {
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int4 it = items[w];
+    const BInst& I = B.inst[it.x];
+    Dev2D d;
+    make_dev(B, I, d);
+    const unsigned int* m32 = reinterpret_cast<const unsigned int*>(B.amax + 3 * it.x + 2);
     unsigned long long kx = 0, ky = 0;
     int bad = 0;
-    for (int o = it.y + threadIdx.x; o < it.y + it.z; o += blockDim.x) {
-      const double h = __ldg(eta + o) - __ldg(b + o);
-      if (!(h > 0.0) || !(h < 1e300)) { bad = 1; continue; }
-      const double rh = fast_rcp(h);
-      const double gh = B.g * h;
-      const double c = gh * fast_rsqrt(gh);
-      const double ax = dabs(__ldg(m + o) * rh) + c, ay = dabs(__ldg(wv + o) * rh) + c;
-      if (!(ax < 1e300) || !(ay < 1e300)) { bad = 1; continue; }
-      kx = max(kx, dkey(ax));
-      ky = max(ky, dkey(ay));
-    }
+    const size_t base = (size_t)I.off_n;
+    alpha_exact_range(d, m32, base + it.y + threadIdx.x, base + it.y + it.z, blockDim.x, kx, ky, bad);
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {
       kx = max(kx, __shfl_xor_sync(0xffffffffu, kx, s));
       ky = max(ky, __shfl_xor_sync(0xffffffffu, ky, s));
     }
     if ((threadIdx.x & 31) == 0) {
-      atomicMax(B.amax + 2 * it.x, kx);
-      atomicMax(B.amax + 2 * it.x + 1, ky);
+      if (kx) atomicMax(B.amax + 3 * it.x, kx);
+      if (ky) atomicMax(B.amax + 3 * it.x + 1, ky);
     }
-    if (bad) atomicOr(B.status, HW_STATUS_DEPTH);
+    if (bad) atomicOr(B.status, bad);
   }
 }
 
@@ -110,8 +134,8 @@ __global__ void __launch_bounds__(256) k_balpha(BatchDev B, const int4* __restri
 __global__ void k_bfinish(BatchDev B, int n, int with_dt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double ax = __longlong_as_double((long long)B.amax[2 * i]);
-  const double ay = __longlong_as_double((long long)B.amax[2 * i + 1]);
+  const double ax = __longlong_as_double((long long)B.amax[3 * i]);
+  const double ay = __longlong_as_double((long long)B.amax[3 * i + 1]);
   B.alpha[2 * i] = ax;
   B.alpha[2 * i + 1] = ay;
   if (with_dt) {
@@ -129,96 +153,45 @@ __global__ void k_btime(BatchDev B, int n) {
   if (B.dt[2 * i] > 0.0) ++B.nsteps[i];
 }
 
-// ---- x-sweep: items (inst, first row, first interface) ----
+// ---- x-sweep: items (inst, first extended node of the tile) over the flattened extended rows ----
 template <bool LINEAR, bool CHAR>
-__global__ void __launch_bounds__(BX_THREADS, 3) k_bsweep_x(BatchDev B, const int4* __restrict__ items, int nitems) {
-  __shared__ double sm[NREC * BX_MAXN];
-  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-    const int4 it = items[w];
-    const BInst I = B.inst[it.x];
+__global__ void __launch_bounds__(TILE_T, 2) k_bsweep_x(BatchDev B, const int4* __restrict__ items, int nitems) {
+  __shared__ double sm[NREC * TILE_T];
+  {
+    const int4 it = items[blockIdx.x];
+    const BInst& I = B.inst[it.x];
     Dev2D d;
     make_dev(B, I, d);
-    const int tx = I.tx, R = BX_THREADS / tx, NN = tx, stride = R * NN;  // tx - 3 interfaces per row
-    const int j0 = it.y, k0 = it.z;
-    const double ax = B.alpha[2 * it.x];
-    for (int t = threadIdx.x; t < stride; t += BX_THREADS) {
-      const int r = t / NN, c = t - r * NN;
-      const int j = j0 + r, i = k0 - 2 + c;
-      if (j >= d.ny || i > d.nx + 1) continue;
-      Node12 n;
-      load_node(d, i, j, n);
-      double rec[NREC];
-      node_record<0>(n, d.g, ax, rec);
-#pragma unroll
-      for (int f = 0; f < NREC; ++f) sm[f * stride + t] = rec[f];
-    }
-    __syncthreads();
-    const int r = threadIdx.x / tx, c = threadIdx.x - r * tx;
-    const int j = j0 + r, k = k0 + c;
-    if (c < tx - 3 && j < d.ny && k <= d.nx) {
-      const int t0 = r * NN + c;
-      const size_t o = (size_t)j * (d.nx + 1) + k;
-      double qb[6];
-#pragma unroll
-      for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qbx[q] + o);
-      double out[12];
-      interface_values<0, LINEAR, CHAR, true>(sm + t0, sm + t0 + 1, sm + t0 + 2, sm + t0 + 3, stride, qb, d.g, d.eps_w, out);
-#pragma unroll
-      for (int q = 0; q < 12; ++q) d.X[q][o] = out[q];
-    }
-    __syncthreads();
+    sweep_x_tile<LINEAR, CHAR, true>(d, B.alpha[2 * it.x], (unsigned)it.y, sm, (size_t)I.off_n, (size_t)I.off_x);
   }
 }
 
-// ---- y-sweep: items (inst, first column, first interface); each thread marches its column ----
+// ---- y-sweep: items (inst, first extended row of the tile) over the flattened column groups ----
 template <bool LINEAR, bool CHAR>
-__global__ void __launch_bounds__(BY_W, 12) k_bsweep_y(BatchDev B, const int4* __restrict__ items, int nitems) {
-  extern __shared__ double ring[];  // [4][NREC][BY_W]
-  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-    const int4 it = items[w];
-    const BInst I = B.inst[it.x];
+__global__ void __launch_bounds__(TILE_T, 2) k_bsweep_y(BatchDev B, const int4* __restrict__ items, int nitems) {
+  __shared__ double sm[NREC * TILE_T];
+  {
+    const int4 it = items[blockIdx.x];
+    const BInst& I = B.inst[it.x];
     Dev2D d;
     make_dev(B, I, d);
-    const int i = it.y + threadIdx.x;
-    if (i >= d.nx) continue;
-    const int k0 = it.z, seg = I.seg;
-    const double ay = B.alpha[2 * it.x + 1];
-    const int rend = min(k0 + seg, d.ny + 1);
-    for (int r = k0 - 2; r <= rend; ++r) {
-      Node12 n;
-      load_node(d, i, r, n);
-      double rec[NREC];
-      node_record<1>(n, d.g, ay, rec);
-      double* slot = ring + (size_t)(r & 3) * NREC * BY_W + threadIdx.x;
-#pragma unroll
-      for (int f = 0; f < NREC; ++f) slot[f * BY_W] = rec[f];
-      const int k = r - 1;
-      if (k >= k0 && k < k0 + seg && k <= d.ny) {
-        const double* s0 = ring + (size_t)((k - 2) & 3) * NREC * BY_W + threadIdx.x;
-        const double* s1 = ring + (size_t)((k - 1) & 3) * NREC * BY_W + threadIdx.x;
-        const double* s2 = ring + (size_t)((k) & 3) * NREC * BY_W + threadIdx.x;
-        const double* s3 = ring + (size_t)((k + 1) & 3) * NREC * BY_W + threadIdx.x;
-        const size_t o = (size_t)k * d.nx + i;
-        double qb[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qby[q] + o);
-        double out[12];
-        interface_values<1, LINEAR, CHAR, true>(s0, s1, s2, s3, BY_W, qb, d.g, d.eps_w, out);
-#pragma unroll
-        for (int q = 0; q < 12; ++q) d.Y[q][o] = out[q];
-      }
-    }
+    sweep_y_tile<LINEAR, CHAR, true>(d, B.alpha[2 * it.x + 1], (unsigned)it.y, I.yc, sm, (size_t)I.off_n,
+                                     (size_t)I.off_y);
   }
 }
 
-// ---- node update: items (inst, first column, first row) of 32 x 8 tiles ----
+// ---- node update: items (inst, first node) of BN_T consecutive nodes of one grid ----
+// Two blocks per SM: the instance's grid constants come from global memory and take registers that the
+// single-grid kernel keeps in its parameters (measured: 3 blocks per SM spill 0.75 KB per thread and run
+// no faster).
 template <bool LINEAR, bool CHAR>
-__global__ void __launch_bounds__(256, 2) k_bnode(BatchDev B, const int4* __restrict__ items, int nitems) {
-  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-    const int4 it = items[w];
-    const BInst I = B.inst[it.x];
-    const int i = it.y + threadIdx.x, j = it.z + threadIdx.y;
-    if (i >= I.nx || j >= I.ny) continue;
+__global__ void __launch_bounds__(BN_T, 2) k_bnode(BatchDev B, const int4* __restrict__ items, int nitems) {
+  {
+    const int4 it = items[blockIdx.x];
+    const BInst& I = B.inst[it.x];
+    const int o = it.y + threadIdx.x;
+    if (o >= I.nx * I.ny) return;
+    const int j = o / I.nx, i = o - j * I.nx;
     Dev2D d;
     make_dev(B, I, d);
     StageArgs sa;
@@ -227,11 +200,11 @@ __global__ void __launch_bounds__(256, 2) k_bnode(BatchDev B, const int4* __rest
     sa.dt = B.dt + 2 * it.x;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-      sa.out[q] = B.out[q] + I.off_n;
-      sa.base[q] = B.base[q] + I.off_n;
+      sa.out[q] = B.out[q];
+      sa.base[q] = B.base[q];
       sa.rhs_out[q] = nullptr;
     }
-    node_update<MODE_STAGE, LINEAR, CHAR, true>(d, sa, i, j);
+    node_update<MODE_STAGE, LINEAR, CHAR, true>(d, sa, i, j, (size_t)I.off_n, (size_t)I.off_x, (size_t)I.off_y);
   }
 }
 
@@ -267,7 +240,7 @@ struct hw_batch {
   // work lists
   int4* d_items[4] = {};  // alpha, x, y, node
   int nitems[4] = {};
-  int nb[4] = {1, 1, 1, 1};  // persistent grid size per phase (resident blocks on the device)
+  int nb[1] = {1};  // blocks of the alpha passes (resident blocks on the device; they loop over items)
   std::vector<bool> inited;
   bool dirty = false;  // tile shapes changed since the work lists were built
   cudaGraphExec_t graph = nullptr;
@@ -298,22 +271,20 @@ hw::Dev2D dev_of(hw_batch* b, int i, double** S) {
   return d;
 }
 
-int default_tx(int nx) { return nx + 1 > 96 ? 128 : (nx + 1 > 48 ? 64 : 32); }
-
-// Work lists for a subset of instances with their current tile shapes.
+// Work lists of a subset of instances: alpha (inst, first node, count), x-sweep tiles (inst, first
+// extended node), y-sweep tiles (inst, first extended row of a column group), node items (inst, first node).
 void build_items(const std::vector<hw::BInst>& inst, const std::vector<int>& ids, std::vector<int4> out[4]) {
   for (int p = 0; p < 4; ++p) out[p].clear();
   for (int i : ids) {
     const hw::BInst& I = inst[i];
     const int n = I.nx * I.ny;
     for (int o = 0; o < n; o += 4096) out[0].push_back(make_int4(i, o, std::min(4096, n - o), 0));
-    const int R = hw::BX_THREADS / I.tx;
-    for (int j = 0; j < I.ny; j += R)
-      for (int k = 0; k <= I.nx; k += I.tx - 3) out[1].push_back(make_int4(i, j, k, 0));
-    for (int c = 0; c < I.nx; c += hw::BY_W)
-      for (int k = 0; k <= I.ny; k += I.seg) out[2].push_back(make_int4(i, c, k, 0));
-    for (int j = 0; j < I.ny; j += 8)
-      for (int c = 0; c < I.nx; c += 32) out[3].push_back(make_int4(i, c, j, 0));
+    const long long tx = (long long)I.ny * (I.nx + 4);
+    for (long long e = 0; e < tx; e += hw::TILE_T - 3) out[1].push_back(make_int4(i, (int)e, 0, 0));
+    const int ifs = hw::TILE_T / I.yc - 3;
+    const long long ty = (long long)((I.nx + I.yc - 1) / I.yc) * (I.ny + 4);
+    for (long long e = 0; e < ty; e += ifs) out[2].push_back(make_int4(i, (int)e, 0, 0));
+    for (int o = 0; o < n; o += hw::BN_T) out[3].push_back(make_int4(i, o, 0, 0));
   }
 }
 
@@ -337,27 +308,17 @@ int persistent_blocks(const void* fn, int threads, size_t smem) {
   return sms * bps;
 }
 
-const size_t kRingBytes = (size_t)4 * hw::NREC * hw::BY_W * sizeof(double);
-
 template <bool L, bool C>
 void launch_phases(hw_batch* b, int which, int4* const* items, const int* counts, cudaStream_t st) {
-  // which: bit 0 x-sweep, bit 1 y-sweep, bit 2 node
-  if ((which & 1) && counts[1])
-    hw::k_bsweep_x<L, C><<<std::min(b->nb[1], counts[1]), hw::BX_THREADS, 0, st>>>(b->B, items[1], counts[1]);
-  if ((which & 2) && counts[2])
-    hw::k_bsweep_y<L, C><<<std::min(b->nb[2], counts[2]), hw::BY_W, kRingBytes, st>>>(b->B, items[2], counts[2]);
-  if ((which & 4) && counts[3])
-    hw::k_bnode<L, C><<<std::min(b->nb[3], counts[3]), dim3(32, 8), 0, st>>>(b->B, items[3], counts[3]);
+  // which: bit 0 x-sweep, bit 1 y-sweep, bit 2 node; one block per work item
+  if ((which & 1) && counts[1]) hw::k_bsweep_x<L, C><<<counts[1], hw::TILE_T, 0, st>>>(b->B, items[1], counts[1]);
+  if ((which & 2) && counts[2]) hw::k_bsweep_y<L, C><<<counts[2], hw::TILE_T, 0, st>>>(b->B, items[2], counts[2]);
+  if ((which & 4) && counts[3]) hw::k_bnode<L, C><<<counts[3], hw::BN_T, 0, st>>>(b->B, items[3], counts[3]);
 }
 
 template <bool L, bool C>
 int prime_blocks(hw_batch* b) {
-  if (cudaFuncSetAttribute(hw::k_bsweep_y<L, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes) != cudaSuccess)
-    return -1;
-  b->nb[0] = persistent_blocks((const void*)hw::k_balpha, 256, 0);
-  b->nb[1] = persistent_blocks((const void*)hw::k_bsweep_x<L, C>, hw::BX_THREADS, 0);
-  b->nb[2] = persistent_blocks((const void*)hw::k_bsweep_y<L, C>, hw::BY_W, kRingBytes);
-  b->nb[3] = persistent_blocks((const void*)hw::k_bnode<L, C>, 256, 0);
+  b->nb[0] = persistent_blocks((const void*)hw::k_balpha_exact, 256, 0);
   return 0;
 }
 
@@ -375,8 +336,10 @@ void bind(hw_batch* b) {
 
 void enqueue_alpha(hw_batch* b, int with_dt, cudaStream_t st) {
   bind(b);
-  cudaMemsetAsync(b->B.amax, 0, 2 * sizeof(unsigned long long) * b->n, st);
-  hw::k_balpha<<<std::min(b->nb[0], b->nitems[0]), 256, 0, st>>>(b->B, b->d_items[0], b->nitems[0]);
+  cudaMemsetAsync(b->B.amax, 0, 3 * sizeof(unsigned long long) * b->n, st);
+  const int na = std::min(b->nb[0], b->nitems[0]);
+  hw::k_balpha_coarse<<<na, 256, 0, st>>>(b->B, b->d_items[0], b->nitems[0]);
+  hw::k_balpha_exact<<<na, 256, 0, st>>>(b->B, b->d_items[0], b->nitems[0]);
   hw::k_bfinish<<<(b->n + 127) / 128, 128, 0, st>>>(b->B, b->n, with_dt);
 }
 
@@ -433,8 +396,7 @@ int hw_batch_create(int n, const hw_grid* grids, const hw_params* params, void* 
     I.c_bx = 0.5 / I.dx; I.c_by = 0.5 / I.dy; I.c_gx = 1.0 / (24.0 * I.dx); I.c_gy = 1.0 / (24.0 * I.dy);
     I.c_mx = 1.0 / (12.0 * I.dx); I.c_my = 1.0 / (12.0 * I.dy);
     I.off_n = (long long)b->tot_n; I.off_x = (long long)b->tot_x; I.off_y = (long long)b->tot_y;
-    I.tx = default_tx(g.nx);
-    I.seg = 64;
+    I.yc = 2;
     b->tot_n += (size_t)g.nx * g.ny;
     b->tot_x += (size_t)(g.nx + 1) * g.ny;
     b->tot_y += (size_t)g.nx * (g.ny + 1);
@@ -452,21 +414,21 @@ int hw_batch_create(int n, const hw_grid* grids, const hw_params* params, void* 
   for (int q = 0; q < 2; ++q) { A(&b->B.sv[q], b->tot_n); A(&b->B.sq[q], b->tot_n); }
   for (int q = 0; q < 12; ++q) A(&b->staging[q], b->max_n);
   double* misc = nullptr;
-  A(&misc, (size_t)8 * n + 8);
+  A(&misc, (size_t)9 * n + 8);
   if (rc == HW_OK) rc = balloc(b, (void**)&b->d_inst, sizeof(hw::BInst) * n);
   if (rc != HW_OK) { hw_batch_destroy(b); return rc; }
   b->B.amax = (unsigned long long*)misc;
-  b->B.alpha = misc + 2 * n;
-  b->B.dt = misc + 4 * n;
-  b->B.t = misc + 6 * n;
-  b->B.nsteps = (unsigned long long*)(misc + 7 * n);
-  b->B.status = (int*)(misc + 8 * n);
+  b->B.alpha = misc + 3 * n;
+  b->B.dt = misc + 5 * n;
+  b->B.t = misc + 7 * n;
+  b->B.nsteps = (unsigned long long*)(misc + 8 * n);
+  b->B.status = (int*)(misc + 9 * n);
   b->B.g = params->g; b->B.eps_w = params->eps_w; b->B.eps_lim = params->eps_lim; b->B.cfl = params->cfl;
   b->B.limiter = params->limiter;
   b->B.inst = b->d_inst;
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { b->cap_stream = nullptr; hw_batch_destroy(b); return bfail(HW_ERR_CUDA, cudaGetErrorString(e)); }
-  e = cudaMemsetAsync(misc, 0, ((size_t)8 * n + 8) * sizeof(double), b->stream);
+  e = cudaMemsetAsync(misc, 0, ((size_t)9 * n + 8) * sizeof(double), b->stream);
   if (e != cudaSuccess) { hw_batch_destroy(b); return bfail(HW_ERR_CUDA, cudaGetErrorString(e)); }
   {
     const bool lin = params->linear_weights != 0, chr = params->char_decomp != 0;
@@ -605,35 +567,31 @@ int hw_batch_get_time(hw_batch* b, double* t, int* steps) {
   return HW_OK;
 }
 
-int hw_batch_set_tiles(hw_batch* b, int i, int tx, int seg) {
+int hw_batch_set_tiles(hw_batch* b, int i, int yc) {
   if (!b || i < 0 || i >= b->n) return bfail(HW_ERR_ARG, "hw_batch_set_tiles: bad instance");
-  if (tx != 32 && tx != 64 && tx != 128) return bfail(HW_ERR_ARG, "hw_batch_set_tiles: tx must be 32, 64 or 128");
-  if (seg < 1) return bfail(HW_ERR_ARG, "hw_batch_set_tiles: seg must be >= 1");
-  b->inst[i].tx = tx;
-  b->inst[i].seg = std::min(seg, b->inst[i].ny + 1);
+  if (yc != 1 && yc != 2 && yc != 4) return bfail(HW_ERR_ARG, "hw_batch_set_tiles: yc must be 1, 2 or 4");
+  b->inst[i].yc = yc;
   b->dirty = true;  // work lists are rebuilt by the next run
   if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
   return HW_OK;
 }
 
-int hw_batch_get_tiles(hw_batch* b, int i, int* tx, int* seg) {
-  if (!b || i < 0 || i >= b->n || !tx || !seg) return bfail(HW_ERR_ARG, "hw_batch_get_tiles: bad argument");
-  *tx = b->inst[i].tx;
-  *seg = b->inst[i].seg;
+int hw_batch_get_tiles(hw_batch* b, int i, int* yc) {
+  if (!b || i < 0 || i >= b->n || !yc) return bfail(HW_ERR_ARG, "hw_batch_get_tiles: bad argument");
+  *yc = b->inst[i].yc;
   return HW_OK;
 }
 
-// Time the x- and y-sweeps of one stage over a subset of instances with trial tile shapes (the
+// Time the x- and y-sweeps of one stage over a subset of instances with a trial y-tile shape (the
 // autotuner's measurement). Writes only interface planes, which every stage recomputes.
-int hw_batch_time_tiles(hw_batch* b, int nids, const int* ids, int tx, int seg, int reps, double* ms_x, double* ms_y) {
+int hw_batch_time_tiles(hw_batch* b, int nids, const int* ids, int yc, int reps, double* ms_x, double* ms_y) {
   if (!b || nids < 1 || !ids || reps < 1) return bfail(HW_ERR_ARG, "hw_batch_time_tiles: bad argument");
-  if (tx != 32 && tx != 64 && tx != 128) return bfail(HW_ERR_ARG, "hw_batch_time_tiles: tx must be 32, 64 or 128");
+  if (yc != 1 && yc != 2 && yc != 4) return bfail(HW_ERR_ARG, "hw_batch_time_tiles: yc must be 1, 2 or 4");
   std::vector<hw::BInst> trial = b->inst;
   std::vector<int> sub(ids, ids + nids);
   for (int i : sub) {
     if (i < 0 || i >= b->n) return bfail(HW_ERR_ARG, "hw_batch_time_tiles: bad instance id");
-    trial[i].tx = tx;
-    trial[i].seg = std::max(1, std::min(seg, trial[i].ny + 1));
+    trial[i].yc = yc;
   }
   std::vector<int4> lists[4];
   build_items(trial, sub, lists);

@@ -14,15 +14,13 @@
 namespace hw {
 
 // ---------------------------------------------------------------------------------------------
-// x-sweep: one block of XS_T threads = XS_I = XS_T - 3 consecutive x-interfaces k (between nodes k-1
-// and k) of one row; each thread first forms one of the XS_N = XS_T node records the tile needs.
+// Sweeps: one tile of TILE_T threads per block over the flattened extended lines (hw_stencil2d.cuh),
+// TILE_T - 3 x-interfaces, or YS_C (TILE_T / YS_C - 3) y-interfaces, per block.
 // ---------------------------------------------------------------------------------------------
-constexpr int XS_T = 192;
-constexpr int XS_I = XS_T - 3;
-constexpr int XS_N = XS_T;
+constexpr int YS_C = 2;  // columns per y-tile group (measured at 2048^2: 2 beats 1 and 4)
 
 // The double kernels form their products (and the node kernel also its reciprocals) on the integer
-// pipes (hw_fp64_int.h: products bit-identical to DMUL): the FP64 pipe is their bound, the integer
+// pipes (hw_fp64_int.h: each product bit-identical to DMUL): the FP64 pipe is their bound, the integer
 // pipes idle. The node records stay on the FP64 pipe (moving them measured slower).
 template <class R>
 constexpr bool kIntMul = std::is_same<R, double>::value;
@@ -32,80 +30,18 @@ constexpr bool kIntMul = std::is_same<R, double>::value;
 template <class R>
 constexpr int kXsBlocks = std::is_same<R, double>::value ? 2 : 5;
 template <class R>
-constexpr int kYsBlocks = std::is_same<R, double>::value ? 12 : 32;
-template <class R>
 constexpr int kNodeBlocks = std::is_same<R, double>::value ? 3 : 5;
 
 template <bool LINEAR, bool CHAR, class R>
-__global__ void __launch_bounds__(XS_T, kXsBlocks<R>) k_sweep_x(Dev2DT<R> d, const R* __restrict__ alpha) {
-  __shared__ R sm[NREC * XS_N];
-  const int j = blockIdx.y;
-  const int k0 = blockIdx.x * XS_I;
-  const R ax = alpha[0];
-  for (int t = threadIdx.x; t < XS_N; t += XS_T) {
-    const int i = k0 - 2 + t;
-    if (i > d.nx + 1) break;
-    Node12T<R> n;
-    load_node(d, i, j, n);
-    R rec[NREC];
-    node_record<0>(n, R(d.g), ax, rec);
-#pragma unroll
-    for (int f = 0; f < NREC; ++f) sm[f * XS_N + t] = rec[f];
-  }
-  __syncthreads();
-  const int k = k0 + threadIdx.x;
-  if (threadIdx.x >= XS_I || k > d.nx) return;
-  const int t = threadIdx.x;
-  const size_t o = (size_t)j * (d.nx + 1) + k;
-  R qb[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qbx[q] + o);
-  R out[12];
-  interface_values<0, LINEAR, CHAR, kIntMul<R>>(sm + t, sm + t + 1, sm + t + 2, sm + t + 3, XS_N, qb, R(d.g), R(d.eps_w), out);
-#pragma unroll
-  for (int q = 0; q < 12; ++q) d.X[q][o] = out[q];
+__global__ void __launch_bounds__(TILE_T, kXsBlocks<R>) k_sweep_x(Dev2DT<R> d, const R* __restrict__ alpha) {
+  __shared__ R sm[NREC * TILE_T];
+  sweep_x_tile<LINEAR, CHAR, kIntMul<R>>(d, alpha[0], blockIdx.x * (TILE_T - 3), sm);
 }
 
-// ---------------------------------------------------------------------------------------------
-// y-sweep: each thread owns one column and marches down `seg` interfaces keeping the last four node
-// records in a private shared-memory ring (no block barrier, no recomputed halo across threads).
-// ---------------------------------------------------------------------------------------------
-constexpr int YS_W = 32;
-
 template <bool LINEAR, bool CHAR, class R>
-__global__ void __launch_bounds__(YS_W, kYsBlocks<R>) k_sweep_y(Dev2DT<R> d, const R* __restrict__ alpha, int seg) {
-  extern __shared__ __align__(16) unsigned char ring_raw[];
-  R* ring = reinterpret_cast<R*>(ring_raw);  // [4 slots][NREC][YS_W]
-  const int i = blockIdx.x * YS_W + threadIdx.x;
-  if (i >= d.nx) return;
-  const int k0 = blockIdx.y * seg;
-  const R ay = alpha[1];
-  const int rend = min(k0 + seg, d.ny + 1);
-  const int stride = YS_W;  // field stride inside one slot
-  for (int r = k0 - 2; r <= rend; ++r) {
-    Node12T<R> n;
-    load_node(d, i, r, n);
-    R rec[NREC];
-    node_record<1>(n, R(d.g), ay, rec);
-    R* slot = ring + (size_t)(r & 3) * NREC * YS_W + threadIdx.x;
-#pragma unroll
-    for (int f = 0; f < NREC; ++f) slot[f * stride] = rec[f];
-    const int k = r - 1;
-    if (k >= k0 && k < k0 + seg && k <= d.ny) {
-      const R* s0 = ring + (size_t)((k - 2) & 3) * NREC * YS_W + threadIdx.x;
-      const R* s1 = ring + (size_t)((k - 1) & 3) * NREC * YS_W + threadIdx.x;
-      const R* s2 = ring + (size_t)((k) & 3) * NREC * YS_W + threadIdx.x;
-      const R* s3 = ring + (size_t)((k + 1) & 3) * NREC * YS_W + threadIdx.x;
-      const size_t o = (size_t)k * d.nx + i;
-      R qb[6];
-#pragma unroll
-      for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qby[q] + o);
-      R out[12];
-      interface_values<1, LINEAR, CHAR, kIntMul<R>>(s0, s1, s2, s3, stride, qb, R(d.g), R(d.eps_w), out);
-#pragma unroll
-      for (int q = 0; q < 12; ++q) d.Y[q][o] = out[q];
-    }
-  }
+__global__ void __launch_bounds__(TILE_T, kXsBlocks<R>) k_sweep_y(Dev2DT<R> d, const R* __restrict__ alpha) {
+  __shared__ R sm[NREC * TILE_T];
+  sweep_y_tile<LINEAR, CHAR, kIntMul<R>>(d, alpha[1], blockIdx.x * (TILE_T / YS_C - 3), YS_C, sm);
 }
 
 template <int MODE, bool LINEAR, bool CHAR, class R>
@@ -117,48 +53,10 @@ __global__ void __launch_bounds__(256, kNodeBlocks<R>) k_node2d(Dev2DT<R> d, Sta
 }
 
 // ---------------------------------------------------------------------------------------------
-// alpha_x, alpha_y = max over nodes of |u| + c, |v| + c (exact max via ordered 64-bit keys),
-// plus a status flag for non-finite or non-positive depth.
-// In double, two passes keep the FP64 pipe out of most nodes: a coarse pass evaluates |u| + c in float
-// (from the depth formed in double, converted by integer operations) and reduces the float maxima M; an
-// exact pass re-evaluates every node in float and computes the double value only where the float one is
-// within a relative 1e-5 of M (or cannot be trusted: values outside float's range, NaN, infinity). The
-// float values are within about 1e-6 of the double ones, so the node attaining the double maximum is
-// always re-evaluated and the result is the exact double maximum (a re-evaluated node contributes to
-// both directions, which is harmless: no node's value exceeds a direction's maximum).
+// alpha_x, alpha_y = max over nodes of |u| + c, |v| + c, plus a status flag for non-finite or
+// non-positive depth: in double the two passes of hw_stencil2d.cuh (coarse float maxima, then the exact
+// double maximum near them), in single precision one pass.
 // ---------------------------------------------------------------------------------------------
-// double -> float by truncation with integer operations (the FP64 pipe stays free): relative error
-// below 2^-23 for values in float's normal range. Values below it become 0 (tiny is true); values
-// above it, infinities and NaN set huge.
-__device__ __forceinline__ float d2f_trunc(double x, bool& tiny, bool& huge) {
-  const long long b = __double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7ff);
-  tiny = e <= 1023 - 127;
-  huge = e >= 1023 + 128;
-  const unsigned int sign = (unsigned int)((unsigned long long)b >> 32) & 0x80000000u;
-  const unsigned int f = sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)((b >> 29) & 0x7fffff);
-  return tiny ? 0.0f : __uint_as_float(f);
-}
-
-// Float estimates of |u| + c and |v| + c at node o from the depth formed in double. exact: the node
-// needs the double evaluation regardless (a depth or momentum outside float's range, NaN, infinity);
-// neg: the depth is negative.
-__device__ __forceinline__ void alpha_coarse(const Dev2D& d, size_t o, float& ax, float& ay, bool& exact,
-                                             bool& neg) {
-  const double hd = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
-  bool t0, h0, t1, h1, t2, h2;
-  const float h = d2f_trunc(hd, t0, h0);
-  const float m = d2f_trunc(__ldg(d.S[1] + o), t1, h1);
-  const float w = d2f_trunc(__ldg(d.S[2] + o), t2, h2);
-  exact = t0 || h0 || h1 || h2;
-  neg = h < 0.0f;
-  const float rh = fast_rcp(h);
-  const float gh = (float)d.g * h;
-  const float c = gh * fast_rsqrt(gh);
-  ax = fabsf(m) * rh + c;
-  ay = fabsf(w) * rh + c;
-}
-
 __global__ void __launch_bounds__(256) k_alpha2d_coarse(Dev2D d, unsigned long long* amax, int* status) {
   const size_t n = (size_t)d.nx * d.ny;
   float mx = 0.0f, my = 0.0f;
@@ -189,24 +87,10 @@ __global__ void __launch_bounds__(256) k_alpha2d_coarse(Dev2D d, unsigned long l
 __global__ void __launch_bounds__(256) k_alpha2d_exact(Dev2D d, unsigned long long* amax, int* status) {
   const size_t n = (size_t)d.nx * d.ny;
   const unsigned int* m32 = reinterpret_cast<const unsigned int*>(amax + 2);
-  const float tx = __uint_as_float(m32[0]) * (1.0f - 1e-5f), ty = __uint_as_float(m32[1]) * (1.0f - 1e-5f);
   unsigned long long kx = 0, ky = 0;
   int bad = 0;
-  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
-    float fx, fy;
-    bool exact, neg;
-    alpha_coarse(d, o, fx, fy, exact, neg);
-    if (!exact && (neg || (fx < tx && fy < ty))) continue;
-    const double hd = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
-    if (!(hd > 0.0) || !(hd < 1e300)) { bad |= hd == hd ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE; continue; }
-    const double rh = fast_rcp(hd);
-    const double gh = d.g * hd;
-    const double c = gh * fast_rsqrt(gh);
-    const double ax = dabs(__ldg(d.S[1] + o) * rh) + c, ay = dabs(__ldg(d.S[2] + o) * rh) + c;
-    if (!(ax < 1e300) || !(ay < 1e300)) { bad |= HW_STATUS_NONFINITE; continue; }
-    kx = max(kx, dkey(ax));
-    ky = max(ky, dkey(ay));
-  }
+  alpha_exact_range(d, m32, (size_t)blockIdx.x * blockDim.x + threadIdx.x, n, (size_t)gridDim.x * blockDim.x, kx, ky,
+                    bad);
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) {
     kx = max(kx, __shfl_xor_sync(0xffffffffu, kx, s));
@@ -427,37 +311,15 @@ __global__ void k_static2d(Dev2D d) {
 // ---------------------------------------------------------------------------------------------
 template <bool L, bool C, class R>
 static void launch_sx(const Dev2DT<R>& d, const R* alpha, cudaStream_t st) {
-  dim3 gx((d.nx + 1 + XS_I - 1) / XS_I, d.ny);
-  k_sweep_x<L, C, R><<<gx, XS_T, 0, st>>>(d, alpha);
-}
-
-// Segment length of the y-sweep: one balanced wave of resident blocks when the grid allows it
-// (the blocks of a column segment all do the same work), at least 8 interfaces per segment.
-static int sweep_y_segment(int nx, int ny, int blocks_per_sm) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  const int cols = (nx + YS_W - 1) / YS_W;
-  const long resident = (long)sms * std::max(blocks_per_sm, 1);
-  long segs = std::max(1L, resident / cols);
-  int seg = (int)((ny + 1 + segs - 1) / segs);
-  return std::max(seg, std::min(8, ny + 1));
+  const unsigned long long total = (unsigned long long)d.ny * (d.nx + 4);
+  k_sweep_x<L, C, R><<<(unsigned)((total + TILE_T - 4) / (TILE_T - 3)), TILE_T, 0, st>>>(d, alpha);
 }
 
 template <bool L, bool C, class R>
 static void launch_sy(const Dev2DT<R>& d, const R* alpha, cudaStream_t st) {
-  const size_t smem = (size_t)4 * NREC * YS_W * sizeof(R);
-  static int bps = -1;
-  if (bps < 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_sweep_y<L, C, R>, YS_W, smem) != cudaSuccess) bps = 1;
-  }
-  const int seg = sweep_y_segment(d.nx, d.ny, bps);
-  dim3 gy((d.nx + YS_W - 1) / YS_W, (d.ny + 1 + seg - 1) / seg);
-  k_sweep_y<L, C, R><<<gy, YS_W, smem, st>>>(d, alpha, seg);
+  constexpr int IFS = TILE_T / YS_C - 3;
+  const unsigned long long total = (unsigned long long)((d.nx + YS_C - 1) / YS_C) * (d.ny + 4);
+  k_sweep_y<L, C, R><<<(unsigned)((total + IFS - 1) / IFS), TILE_T, 0, st>>>(d, alpha);
 }
 
 template <int MODE, bool L, bool C, class R>
@@ -466,15 +328,7 @@ static void launch_node(const Dev2DT<R>& d, const StageArgsT<R>& sa, cudaStream_
   k_node2d<MODE, L, C, R><<<g, dim3(32, 8), 0, st>>>(d, sa);
 }
 
-int set_kernel_attributes2d() {
-  const int smem = 4 * NREC * YS_W * (int)sizeof(double);
-  cudaError_t e = cudaSuccess;
-  e = cudaFuncSetAttribute(k_sweep_y<false, true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_y<true, true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_y<false, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_y<true, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  return e == cudaSuccess ? 0 : -1;
-}
+int set_kernel_attributes2d() { return 0; }
 
 void launch_alpha2d(const Dev2D& d, unsigned long long* amax, int* status, cudaStream_t st) {
   cudaMemsetAsync(amax, 0, 3 * sizeof(unsigned long long), st);

@@ -17,12 +17,13 @@ struct Node12T {
 };
 using Node12 = Node12T<double>;
 
+// base: offset of the grid's first node in the node planes (0 unless the planes pool several grids).
 template <class R>
-__device__ __forceinline__ void load_node(const Dev2DT<R>& d, int i, int j, Node12T<R>& n) {
+__device__ __forceinline__ void load_node(const Dev2DT<R>& d, int i, int j, Node12T<R>& n, size_t base = 0) {
   bool fx, fy;
   const int ii = map_index(i, d.nx, d.bc_x, fx);
   const int jj = map_index(j, d.ny, d.bc_y, fy);
-  const size_t o = (size_t)jj * d.nx + ii;
+  const size_t o = base + (size_t)jj * d.nx + ii;
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
     R x = __ldg(d.S[q] + o);
@@ -206,10 +207,11 @@ __device__ __forceinline__ void interface_values_m(const R* r0, const R* r1, con
 #undef RV
 }
 
-// One interface. IMUL: the products run on the integer pipes (hw_fp64_int.h, bit-identical to DMUL;
-// the reciprocals stay on the FP64 pipe: moving them raised spills); if any of them leaves the integer
-// fast path (subnormal, infinite or NaN data), the interface is recomputed on the FP64 pipe from the
-// same records.
+// One interface. IMUL: the products run on the integer pipes (hw_fp64_int.h: each product is
+// bit-identical to DMUL, but rounded on its own where the FP64 form may fuse it with an add into an fma,
+// so the results differ from the FP64-pipe form by rounding; the reciprocals stay on the FP64 pipe:
+// moving them raised spills); if any of them leaves the integer fast path (subnormal, infinite or NaN
+// data), the interface is recomputed on the FP64 pipe from the same records.
 template <int DIR, bool LINEAR, bool CHAR, bool IMUL = false, class R>
 __device__ __forceinline__ void interface_values(const R* r0, const R* r1, const R* r2,
                                                  const R* r3, int stride, const R qb[6], R g,
@@ -225,6 +227,157 @@ __device__ __forceinline__ void interface_values(const R* r0, const R* r1, const
     MulFP64 mf;
     interface_values_m<DIR, LINEAR, CHAR>(r0, r1, r2, r3, stride, qb, g, eps_w, out, mf);
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// alpha_x, alpha_y = max over nodes of |u| + c, |v| + c (exact max via ordered 64-bit keys) in two
+// passes that keep the FP64 pipe out of most nodes: a coarse pass evaluates |u| + c in float (from the
+// depth formed in double, converted by integer operations) and reduces the float maxima M; an exact pass
+// re-evaluates every node in float and computes the double value only where the float one is within a
+// relative 1e-5 of M (or cannot be trusted: values outside float's range, NaN, infinity). The float
+// values are within about 1e-6 of the double ones, so the node attaining the double maximum is always
+// re-evaluated and the result is the exact double maximum (a re-evaluated node contributes to both
+// directions, which is harmless: no node's value exceeds a direction's maximum).
+// ---------------------------------------------------------------------------------------------
+// double -> float by truncation with integer operations (the FP64 pipe stays free): relative error
+// below 2^-23 for values in float's normal range. Values below it become 0 (tiny is true); values
+// above it, infinities and NaN set huge.
+__device__ __forceinline__ float d2f_trunc(double x, bool& tiny, bool& huge) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  tiny = e <= 1023 - 127;
+  huge = e >= 1023 + 128;
+  const unsigned int sign = (unsigned int)((unsigned long long)b >> 32) & 0x80000000u;
+  const unsigned int f = sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)((b >> 29) & 0x7fffff);
+  return tiny ? 0.0f : __uint_as_float(f);
+}
+
+// Float estimates of |u| + c and |v| + c at node o from the depth formed in double. exact: the node
+// needs the double evaluation regardless (a depth or momentum outside float's range, NaN, infinity);
+// neg: the depth is negative.
+__device__ __forceinline__ void alpha_coarse(const Dev2D& d, size_t o, float& ax, float& ay, bool& exact,
+                                             bool& neg) {
+  const double hd = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
+  bool t0, h0, t1, h1, t2, h2;
+  const float h = d2f_trunc(hd, t0, h0);
+  const float m = d2f_trunc(__ldg(d.S[1] + o), t1, h1);
+  const float w = d2f_trunc(__ldg(d.S[2] + o), t2, h2);
+  exact = t0 || h0 || h1 || h2;
+  neg = h < 0.0f;
+  const float rh = fast_rcp(h);
+  const float gh = (float)d.g * h;
+  const float c = gh * fast_rsqrt(gh);
+  ax = fabsf(m) * rh + c;
+  ay = fabsf(w) * rh + c;
+}
+
+// The exact pass over nodes o = begin, begin + step, ... < end, with the coarse maxima m32[0..1]: keys of
+// the double maxima into kx, ky and status flags into bad.
+__device__ __forceinline__ void alpha_exact_range(const Dev2D& d, const unsigned int* m32, size_t begin, size_t end,
+                                                  size_t step, unsigned long long& kx, unsigned long long& ky,
+                                                  int& bad) {
+  const float tx = __uint_as_float(m32[0]) * (1.0f - 1e-5f), ty = __uint_as_float(m32[1]) * (1.0f - 1e-5f);
+  for (size_t o = begin; o < end; o += step) {
+    float fx, fy;
+    bool exact, neg;
+    alpha_coarse(d, o, fx, fy, exact, neg);
+    if (!exact && (neg || (fx < tx && fy < ty))) continue;
+    const double hd = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
+    if (!(hd > 0.0) || !(hd < 1e300)) { bad |= hd == hd ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE; continue; }
+    const double rh = fast_rcp(hd);
+    const double gh = d.g * hd;
+    const double c = gh * fast_rsqrt(gh);
+    const double ax = dabs(__ldg(d.S[1] + o) * rh) + c, ay = dabs(__ldg(d.S[2] + o) * rh) + c;
+    if (!(ax < 1e300) || !(ay < 1e300)) { bad |= HW_STATUS_NONFINITE; continue; }
+    kx = max(kx, dkey(ax));
+    ky = max(ky, dkey(ay));
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Sweep tiles over flattened extended lines (shared by the single-grid and the batched kernels).
+// x: extended node E = j (nx + 4) + e stands for node (e - 2, j), e = 0 .. nx + 3 (each row with two halo
+// nodes on either side, rows one after the other); the x-interface k of row j (between nodes k - 1 and k,
+// k = 0 .. nx) sits at E = j (nx + 4) + k and reads the records of E .. E + 3, all in its row.
+// y: the same over groups of yc adjacent columns: extended row E = g (ny + 4) + e of group g stands for
+// nodes (g yc + c, e - 2), c = 0 .. yc - 1.
+// A tile of TILE_T threads forms the node records of TILE_T consecutive extended nodes (x; yc columns of
+// TILE_T / yc extended rows in y), then, after one barrier, the interfaces whose four records lie in the
+// tile: tiles run across line ends, so no grid size leaves a ragged tile. All TILE_T threads must call;
+// sm holds NREC * TILE_T values. on / oi: offsets of the grid in pooled node / interface planes (the
+// batched form keeps the planes' base pointers in the kernel parameters and adds these, so that no
+// per-grid pointer occupies a register).
+// ---------------------------------------------------------------------------------------------
+constexpr int TILE_T = 192;
+
+template <bool LINEAR, bool CHAR, bool IMUL, class R>
+__device__ __forceinline__ void sweep_x_tile(const Dev2DT<R>& d, R ax, unsigned E0, R* sm, size_t on = 0,
+                                             size_t oi = 0) {
+  const unsigned W = d.nx + 4, total = (unsigned)d.ny * W;
+  const int t = threadIdx.x;
+  {
+    const unsigned E = E0 + t;
+    if (E < total) {
+      const unsigned j = E / W, e = E - j * W;
+      Node12T<R> n;
+      load_node(d, (int)e - 2, (int)j, n, on);
+      R rec[NREC];
+      node_record<0>(n, R(d.g), ax, rec);
+#pragma unroll
+      for (int f = 0; f < NREC; ++f) sm[f * TILE_T + t] = rec[f];
+    }
+  }
+  __syncthreads();
+  const unsigned E = E0 + t;
+  if (t >= TILE_T - 3 || E >= total) return;
+  const unsigned j = E / W, k = E - j * W;
+  if (k > (unsigned)d.nx) return;
+  const size_t o = oi + (size_t)j * (d.nx + 1) + k;
+  R qb[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qbx[q] + o);
+  R out[12];
+  interface_values<0, LINEAR, CHAR, IMUL>(sm + t, sm + t + 1, sm + t + 2, sm + t + 3, TILE_T, qb, R(d.g), R(d.eps_w), out);
+#pragma unroll
+  for (int q = 0; q < 12; ++q) d.X[q][o] = out[q];
+}
+
+template <bool LINEAR, bool CHAR, bool IMUL, class R>
+__device__ __forceinline__ void sweep_y_tile(const Dev2DT<R>& d, R ay, unsigned E0, int yc, R* sm, size_t on = 0,
+                                             size_t oi = 0) {
+  const int rows = TILE_T / yc, ifs = rows - 3;
+  const unsigned H = d.ny + 4, total = (unsigned)((d.nx + yc - 1) / yc) * H;
+  const int t = threadIdx.x, c = t % yc, r = t / yc;
+  {
+    const unsigned E = E0 + r;
+    if (r < rows && E < total) {
+      const unsigned g = E / H, e = E - g * H;
+      const int i = (int)g * yc + c;
+      if (i < d.nx) {
+        Node12T<R> n;
+        load_node(d, i, (int)e - 2, n, on);
+        R rec[NREC];
+        node_record<1>(n, R(d.g), ay, rec);
+#pragma unroll
+        for (int f = 0; f < NREC; ++f) sm[f * TILE_T + t] = rec[f];
+      }
+    }
+  }
+  __syncthreads();
+  const unsigned E = E0 + r;
+  if (r >= ifs || E >= total) return;
+  const unsigned g = E / H, k = E - g * H;
+  const int i = (int)g * yc + c;
+  if (k > (unsigned)d.ny || i >= d.nx) return;
+  const size_t o = oi + (size_t)k * d.nx + i;
+  R qb[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) qb[q] = __ldg(d.qby[q] + o);
+  R out[12];
+  const R* s0 = sm + t;
+  interface_values<1, LINEAR, CHAR, IMUL>(s0, s0 + yc, s0 + 2 * yc, s0 + 3 * yc, TILE_T, qb, R(d.g), R(d.eps_w), out);
+#pragma unroll
+  for (int q = 0; q < 12; ++q) d.Y[q][o] = out[q];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -267,11 +420,13 @@ __device__ __forceinline__ void limit_dir(const R Um[3], const R U0[3], const R 
 // RHS assembly, limiter and RK combination (or the bare RHS) at node (i, j) of one grid, products
 // formed by `mul`. With MulInt nothing is written when a product left the integer fast path
 // (mul.bad); the caller then recomputes the node with MulFP64 from the same (unchanged) inputs.
+// on, oxo, oyo: offsets of the grid in pooled node, x-interface and y-interface planes (0 for one grid).
 template <int MODE, bool LINEAR, bool CHAR, class R, class M>
-__device__ __forceinline__ void node_update_m(const Dev2DT<R>& d, const StageArgsT<R>& sa, int i, int j, M& mul) {
-  const size_t o = (size_t)j * d.nx + i;
-  const size_t ox = (size_t)j * (d.nx + 1) + i;  // left x-interface; right is ox + 1
-  const size_t oy = (size_t)j * d.nx + i;        // lower y-interface; upper is oy + nx
+__device__ __forceinline__ void node_update_m(const Dev2DT<R>& d, const StageArgsT<R>& sa, int i, int j, M& mul,
+                                              size_t on = 0, size_t oxo = 0, size_t oyo = 0) {
+  const size_t o = on + (size_t)j * d.nx + i;
+  const size_t ox = oxo + (size_t)j * (d.nx + 1) + i;  // left x-interface; right is ox + 1
+  const size_t oy = oyo + (size_t)j * d.nx + i;        // lower y-interface; upper is oy + nx
   R cur[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) cur[q] = __ldg(d.S[q] + o);
@@ -332,11 +487,11 @@ __device__ __forceinline__ void node_update_m(const Dev2DT<R>& d, const StageArg
     const R c = mul(gh, rs), ic2 = mul.k(R(0.5), rs);
     Node12T<R> nm, np;
     // x neighbours
-    load_node(d, i - 1, j, nm);
-    load_node(d, i + 1, j, np);
+    load_node(d, i - 1, j, nm, on);
+    load_node(d, i + 1, j, np, on);
     limit_dir<0, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 3, np.v + 3, u, v, c, ic2, gh, R(d.eps_lim), mod, mul);
-    load_node(d, i, j - 1, nm);
-    load_node(d, i, j + 1, np);
+    load_node(d, i, j - 1, nm, on);
+    load_node(d, i, j + 1, np, on);
     limit_dir<1, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 6, np.v + 6, u, v, c, ic2, gh, R(d.eps_lim), mod + 3, mul);
   } else {
 #pragma unroll
@@ -367,20 +522,23 @@ __device__ __forceinline__ void node_update_m(const Dev2DT<R>& d, const StageArg
   }
 }
 
-// The node update. IMUL: products on the integer pipes (bit-identical to DMUL); if any leaves the
-// integer fast path, the node is recomputed on the FP64 pipe.
+// The node update. IMUL: products on the integer pipes (each bit-identical to DMUL; results differ from
+// the fma-contracted FP64-pipe form by rounding); if any leaves the integer fast path, the node is
+// recomputed on the FP64 pipe, so an interface or node on that fallback rounds differently from its
+// neighbours, within the same tolerances (int_mul_fallback parity case).
 template <int MODE, bool LINEAR, bool CHAR, bool IMUL = false, class R>
-__device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT<R>& sa, int i, int j) {
+__device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT<R>& sa, int i, int j, size_t on = 0,
+                                            size_t oxo = 0, size_t oyo = 0) {
   if constexpr (IMUL && !LINEAR && std::is_same<R, double>::value) {
     MulInt mi;
-    node_update_m<MODE, LINEAR, CHAR>(d, sa, i, j, mi);
+    node_update_m<MODE, LINEAR, CHAR>(d, sa, i, j, mi, on, oxo, oyo);
     if (mi.bad) {
       MulFP64 mf;
-      node_update_m<MODE, LINEAR, CHAR>(d, sa, i, j, mf);
+      node_update_m<MODE, LINEAR, CHAR>(d, sa, i, j, mf, on, oxo, oyo);
     }
   } else {
     MulFP64 mf;
-    node_update_m<MODE, LINEAR, CHAR>(d, sa, i, j, mf);
+    node_update_m<MODE, LINEAR, CHAR>(d, sa, i, j, mf, on, oxo, oyo);
   }
 }
 

@@ -103,7 +103,7 @@ def test_tile_shapes_do_not_change_results(hw):
     a = hw.BatchedSolver(scs)
     c = hw.BatchedSolver(scs)
     for i, sc in enumerate(scs):
-        hw.hw_batch_set_tiles(c.h, i, [32, 64, 128][i % 3], [5, 16, 64, 300][i % 4])
+        hw.hw_batch_set_tiles(c.h, i, [1, 4, 2][i % 3])
     a.run(3, use_graph=False)
     c.run(3, use_graph=True)
     for i in range(len(scs)):
@@ -119,8 +119,7 @@ def test_autotuner_picks_valid_tiles(hw, tmp_path):
     res = b.autotune(cache_path=str(tmp_path / "tune.json"))
     assert (tmp_path / "tune.json").exists()
     for i, sc in enumerate(scs):
-        tx, seg = hw.hw_batch_get_tiles(b.h, i)
-        assert tx in autotune.TX_CANDIDATES and 1 <= seg <= sc.ny + 1
+        assert hw.hw_batch_get_tiles(b.h, i) in autotune.YC_CANDIDATES
     b.run(2)
     ref.run(2)
     for i in range(len(scs)):
