@@ -63,22 +63,22 @@ PEAK_FP64_OPS = SMS * DFMA_PER_SM_CLK * SM_GHZ * 1e9
 # 9 state, 3 static and 9 base planes and write 9 (limiter recomputed: 27 planes of 8 bytes on average).
 # The whole-step HBM fraction is taken against it.
 ALGO_BYTES_PER_NODE_STAGE = 216.0
-# DRAM bytes per unit from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum of one stage-3
-# launch at 2048x1024, the state and interface planes above L2), valid only for the kernel sources they
-# were taken on (sources_sha); scaled to a launch by its units (traffic is proportional to them).
+# DRAM bytes per unit from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum of one launch at
+# 2048x1024, the state and interface planes above L2; the node kernel at RK stage 3), valid only for the
+# kernel sources they were taken on (sources_sha); scaled to a launch by its units (traffic is proportional
+# to them).
 TRAFFIC = {
-    "sweep_x": {"bytes_per_unit": 223.6, "sha": "948dbe4e090f69d4"},
-    "sweep_y": {"bytes_per_unit": 232.8, "sha": "948dbe4e090f69d4"},
-    "node": {"bytes_per_unit": 529.4, "sha": "948dbe4e090f69d4"},
+    "sweep_x": {"bytes_per_unit": 223.3, "sha": "f6a27bdc01ffe577"},
+    "sweep_y": {"bytes_per_unit": 226.9, "sha": "f6a27bdc01ffe577"},
+    "node": {"bytes_per_unit": 532.5, "sha": "f6a27bdc01ffe577"},
 }
-# FP64-pipe instructions per unit (ncu: DFMA + DADD + DMUL thread instructions of one stage-3 launch at
-# 2048x1024 over its units). Part of the products run on the integer pipes (bit-identical binary64
-# multiplies), so these are below the algorithmic "ops" above; valid only for the kernel sources they
-# were taken on (sources_sha).
+# FP64-pipe instructions per unit (ncu: DFMA + DADD + DMUL thread instructions of the same launches over
+# their units). Part of the products run on the integer pipes (each bit-identical to DMUL), so these are
+# below the algorithmic "ops" above; valid only for the kernel sources they were taken on (sources_sha).
 FP64_PIPE_OPS = {
-    "sweep_x": {"ops_per_unit": 341.8, "sha": "948dbe4e090f69d4"},
-    "sweep_y": {"ops_per_unit": 343.3, "sha": "948dbe4e090f69d4"},
-    "node": {"ops_per_unit": 243.0, "sha": "948dbe4e090f69d4"},
+    "sweep_x": {"ops_per_unit": 341.9, "sha": "f6a27bdc01ffe577"},
+    "sweep_y": {"ops_per_unit": 342.8, "sha": "f6a27bdc01ffe577"},
+    "node": {"ops_per_unit": 243.0, "sha": "f6a27bdc01ffe577"},
 }
 STATE_BYTES = 9 * NX * NY * 8
 
