@@ -227,3 +227,18 @@ def gather(plan: Plan, states: Dict[int, Sequence[np.ndarray]]) -> List[np.ndarr
         for q in range(9):
             out[q][i.j0:i.j0 + i.ny, i.i0:i.i0 + i.nx] = planes[q]
     return out
+
+
+def partition_instances(points: Sequence[int], world: int) -> List[List[int]]:
+    """Instances of the batched form shared among `world` ranks with no communication: the largest first,
+    each to the rank with the fewest points so far (ties to the lower rank), so every rank's batch has
+    about the same work. Returns the instance indices of each rank, in increasing order."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    load = [0] * world
+    out: List[List[int]] = [[] for _ in range(world)]
+    for i in sorted(range(len(points)), key=lambda i: (-int(points[i]), i)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        out[r].append(i)
+        load[r] += int(points[i])
+    return [sorted(x) for x in out]

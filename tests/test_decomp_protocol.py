@@ -231,3 +231,19 @@ def test_protocol_two_ranks_equals_undecomposed_oracle(name):
     for rank, bad, nb in res:
         assert bad == [], (rank, bad)
         assert nb >= 1
+
+
+def test_batched_instances_partition_across_ranks():
+    """The batched form shares its instances among ranks with no communication: every instance on exactly
+    one rank, and no rank more than one largest instance above the average load."""
+    from paper_2208_01260_gb300 import decomp
+    from paper_2208_01260_gb300 import scenarios as S
+    nxs, nys = S.batch_sizes(512)
+    pts = [int(a) * int(b) for a, b in zip(nxs, nys)]
+    for world in (1, 2, 3, 8):
+        parts = decomp.partition_instances(pts, world)
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(len(pts)))
+        loads = [sum(pts[i] for i in p) for p in parts]
+        assert max(loads) - sum(pts) / world <= max(pts)
+    assert decomp.partition_instances([5, 5, 5, 5], 2) == [[0, 2], [1, 3]]
