@@ -315,6 +315,18 @@ int hw_dd_advance(hw_dd* d, int nsteps, double t_end, int use_graph, double* t_o
 int hw_dd_get_state(hw_dd* d, double* const* out, int layout, int ptr_kind);
 int hw_dd_destroy(hw_dd* d);
 
+/* Gauge misfit and its gradient for a run of the blocks (as hw_adjoint_run with HW_ADJ_TAPE, on the
+ * block decomposition's current state, with every stage of every step of every block kept in device
+ * memory): gauge_idx are nodes of the global grid (j nx + i); grad_state (9) and grad_static (3) are
+ * device planes of the global grid (overwritten). Each block reverses its own stages; between stages the
+ * transpose of the halo exchange adds the adjoints that reach a block's ring to the nodes the ring was
+ * copied from; the alpha adjoint (Sec. 2.1 Step 1) is summed over the blocks and applied once, at the
+ * global grid's first node attaining alpha. The loss equals hw_adjoint_run's bit for bit and the gradient
+ * to rounding (sums in another order). The blocks' states are unchanged. Synchronises the stream;
+ * HW_ERR_ARG, HW_ERR_NOMEM, HW_ERR_CUDA as hw_adjoint_run. */
+int hw_dd_adjoint_run(hw_dd* d, int nsteps, const double* dts, const int* gauge_idx, int ngauge,
+                      const double* eta_obs, double* loss_out, double* const* grad_state, double* const* grad_static);
+
 /* Allocation-free variant of the 1D right-hand side: the same numbers as hw_create + hw_init + hw_rhs on
  * a 1D grid (out: 4 planes d/dt (eta, m, eta_x, m_x)), with every array pointer on the device. The paper
  * has no counterpart; this call exists for callers that must not allocate device memory, such as code

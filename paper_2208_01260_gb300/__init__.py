@@ -38,7 +38,7 @@ __all__ = [
     "hw_batch_set_tiles", "hw_batch_get_tiles", "hw_batch_time_tiles",
     "hw_part_info", "hw_dd_partition", "hw_part_create", "hw_part_init", "hw_part_finish_init", "hw_halo_strip_size",
     "hw_halo_pack", "hw_halo_unpack", "hw_part_alpha_keys", "hw_part_stage", "hw_dd_create", "hw_dd_init",
-    "hw_dd_advance", "hw_dd_get_state", "hw_dd_destroy", "hw_dd_max_keys", "DecomposedSolver",
+    "hw_dd_advance", "hw_dd_get_state", "hw_dd_destroy", "hw_dd_max_keys", "hw_dd_adjoint_run", "DecomposedSolver",
 ]
 
 HW_OK = 0
@@ -366,6 +366,7 @@ def _dd_sigs():
         "hw_dd_advance": [vp, i, d, i, C.POINTER(d), C.POINTER(i)],
         "hw_dd_get_state": [vp, pp, i, i],
         "hw_dd_destroy": [vp],
+        "hw_dd_adjoint_run": [vp, i, C.POINTER(d), C.POINTER(i), i, C.POINTER(d), C.POINTER(d), pp, pp],
     }.items():
         f = getattr(L, name)
         f.argtypes = args
@@ -481,6 +482,22 @@ def hw_dd_get_state(d: _DDHandle, out: Sequence, layout: int = HW_LAYOUT_EQUILIB
     n = d.grid.nx * d.grid.ny
     _check(_dd_sigs().hw_dd_get_state(d.ptr, _pp([_ptr(a, n, True) for a in out]), int(layout), _kind(out)),
            "hw_dd_get_state")
+
+
+def hw_dd_adjoint_run(d: _DDHandle, dts, gauge_idx, eta_obs, grad_state: Sequence, grad_static: Sequence):
+    """Gauge misfit and its gradient over the blocks (whole-run tape); gradients are CUDA tensors of the
+    global grid. Returns the loss."""
+    dts = np.ascontiguousarray(dts, dtype=np.float64)
+    gi = np.ascontiguousarray(gauge_idx, dtype=np.int32)
+    ob = np.ascontiguousarray(eta_obs, dtype=np.float64)
+    n = d.grid.nx * d.grid.ny
+    loss = C.c_double()
+    _check(_dd_sigs().hw_dd_adjoint_run(d.ptr, len(dts), dts.ctypes.data_as(C.POINTER(C.c_double)),
+                                        gi.ctypes.data_as(C.POINTER(C.c_int)), len(gi),
+                                        ob.ctypes.data_as(C.POINTER(C.c_double)), C.byref(loss),
+                                        _pp([_ptr(a, n, True) for a in grad_state]),
+                                        _pp([_ptr(a, n, True) for a in grad_static])), "hw_dd_adjoint_run")
+    return loss.value
 
 
 class DecomposedSolver:

@@ -602,6 +602,67 @@ __global__ void k_loss_seed(const double* gval, const double* obs, const int* id
   if (g < ng) atomicAdd(leta + idx[g], 2.0 * (gval[g] - obs[g]));
 }
 
+// ---- block decomposition: gauges by (local node, global slot), alpha over the blocks ----
+__global__ void k_gather_eta_map(const double* eta, const int* idx, const int* slot, int n, double* out) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) out[slot[g]] = eta[idx[g]];
+}
+
+__global__ void k_loss_seed_map(const double* gval, const double* obs, const int* idx, const int* slot, int n,
+                                double* leta) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) atomicAdd(leta + idx[g], 2.0 * (gval[slot[g]] - obs[slot[g]]));
+}
+
+// out[d] = maximum over the rows of the blocks' alpha keys (rows[2 p + d])
+__global__ void k_keys_max(const unsigned long long* rows, int np, unsigned long long* out) {
+  const int d = threadIdx.x;
+  if (d >= 2) return;
+  unsigned long long m = 0;
+  for (int p = 0; p < np; ++p) m = max(m, rows[2 * p + d]);
+  out[d] = m;
+}
+
+// The first node of the global grid (index gj gnx + gi) attaining the stage's alpha, over the block's own
+// nodes (extended indices [2, nxl + 2) x [2, nyl + 2), block origin (i0, j0)); the minimum over the
+// blocks is the undecomposed grid's first maximising node.
+__global__ void __launch_bounds__(256) k_adj_alpha_find_block(AdjDev A, int nxl, int nyl, int i0, int j0, int gnx) {
+  const Dev2D& d = A.d;
+  const int n = nxl * nyl;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int li = t % nxl, lj = t / nxl;
+    const size_t o = (size_t)(lj + 2) * d.nx + (li + 2);
+    const double h = d.S[0][o] - d.stat[0][o];
+    const double rh = fast_rcp(h), gh = d.g * h, c = gh * fast_rsqrt(gh);
+    const double ax = dabs(d.S[1][o] * rh) + c, ay = dabs(d.S[2][o] * rh) + c;
+    const int gidx = (j0 + lj) * gnx + (i0 + li);
+    if (fabs(ax - A.alpha[0]) <= 4e-16 * A.alpha[0]) atomicMin(A.argmax, gidx);
+    if (fabs(ay - A.alpha[1]) <= 4e-16 * A.alpha[1]) atomicMin(A.argmax + 1, gidx);
+  }
+}
+
+// The alpha adjoint of all blocks (A.lalpha, summed) applied by the block that owns that node.
+__global__ void k_adj_alpha_apply_block(AdjDev A, int nxl, int nyl, int i0, int j0, int gnx) {
+  const Dev2D& d = A.d;
+  for (int dir = 0; dir < 2; ++dir) {
+    const int gidx = A.argmax[dir];
+    const double la = A.lalpha[dir];
+    if (gidx == INT_MAX || la == 0.0) continue;
+    const int gi = gidx % gnx - i0, gj = gidx / gnx - j0;
+    if (gi < 0 || gi >= nxl || gj < 0 || gj >= nyl) continue;
+    const size_t o = (size_t)(gj + 2) * d.nx + (gi + 2);
+    const double h = d.S[0][o] - d.stat[0][o];
+    const double rh = fast_rcp(h), gh = d.g * h, rs = fast_rsqrt(gh);
+    const double un = d.S[1 + dir][o] * rh;
+    const double sg = un < 0.0 ? -1.0 : 1.0;
+    const double lmom = la * sg * rh;
+    const double lh = la * (-sg * un * rh + 0.5 * d.g * rs);
+    atomicAdd(A.lin[0] + o, lh);
+    atomicAdd(A.lin[1 + dir] + o, lmom);
+    atomicAdd(A.lstat[0] + o, -lh);
+  }
+}
+
 }  // namespace hw
 
 // =============================================================================================
@@ -779,6 +840,56 @@ int forward_record(const hw::SolverView& v, AdjBuffers* B, const StepTape& T, do
   return HW_OK;
 }
 
+// The reverse of stage k of the recorded step T: its arguments (the adjoint of the stage output in lam[cur],
+// of its input written to lam[cur ^ 1]).
+hw::AdjDev stage_args(const hw::SolverView& v, AdjBuffers* B, const StepTape& T, double dt, int k, int cur) {
+  const double ak[4] = {0.0, 0.0, 0.75, 1.0 / 3.0}, bk[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
+  hw::Dev2D d = *v.d2;
+  for (int q = 0; q < 9; ++q) d.S[q] = T.in[k - 1][q];
+  hw::AdjDev A{};
+  A.d = d;
+  A.alpha = T.alpha + 2 * (k - 1);
+  A.k = k;
+  A.dt = dt;
+  A.a = ak[k];
+  A.b = bk[k];
+  A.limiter = v.params->limiter;
+  for (int q = 0; q < 9; ++q) {
+    A.lout[q] = B->lam[cur][q];
+    A.lin[q] = B->lam[cur ^ 1][q];
+    A.lbase[q] = B->lbase[q];
+    A.lR[q] = B->lR[q];
+  }
+  for (int q = 0; q < 6; ++q) { A.lmod[q] = B->lmod[q]; A.lqbx[q] = B->lqbx[q]; A.lqby[q] = B->lqby[q]; }
+  for (int f = 0; f < hw::NREC; ++f) { A.lrecx[f] = B->lrecx[f]; A.lrecy[f] = B->lrecy[f]; }
+  for (int q = 0; q < 3; ++q) { A.lstat[q] = B->lstat[q]; A.dbx[q] = T.dbx[k - 1][q]; A.dby[q] = T.dby[k - 1][q]; }
+  A.fax = T.fx[k - 1];
+  A.fay = T.fy[k - 1];
+  for (int q = 0; q < 2; ++q) { A.lsv[q] = B->lsv[q]; A.lsq[q] = B->lsq[q]; }
+  A.lalpha = B->lalpha;
+  A.argmax = B->argmax;
+  return A;
+}
+
+// Stage k's reverse up to alpha: the record adjoints cleared, then the node pre-pass, the sweeps, the
+// records and the limiter (the alpha adjoint accumulates in A.lalpha, which the caller clears).
+int reverse_stage_body(const hw::SolverView& v, AdjBuffers* B, const hw::AdjDev& A) {
+  int rc = HW_OK;
+  cudaStream_t st = v.stream;
+  const hw::Dev2D& d = A.d;
+  if ((rc = zero_planes(B->lrecx, hw::NREC, (size_t)(d.nx + 4) * d.ny, st))) return rc;
+  if ((rc = zero_planes(B->lrecy, hw::NREC, (size_t)d.nx * (d.ny + 4), st))) return rc;
+  const dim3 gn((d.nx + 31) / 32, (d.ny + 7) / 8), bn(32, 8);
+  hw::k_adj_node_pre<<<gn, bn, 0, st>>>(A);
+  hw::k_adj_sweep_x<<<dim3((d.nx + 1 + hw::AX_I - 1) / hw::AX_I, d.ny), hw::AX_T, 0, st>>>(A);
+  hw::k_adj_sweep_y<<<dim3((d.nx + 31) / 32, (d.ny + 1 + hw::AY_R - 1) / hw::AY_R), hw::AY_T, hw::AY_SMEM, st>>>(A);
+  const int nrec = (d.nx + 4) * d.ny + d.nx * (d.ny + 4);
+  hw::k_adj_records<<<(nrec + 255) / 256, 256, 0, st>>>(A);
+  if (A.limiter) hw::k_adj_limiter<<<gn, bn, 0, st>>>(A);
+  ACUDA(cudaGetLastError());
+  return HW_OK;
+}
+
 // Reverse of one recorded step: lam[cur] holds the adjoint of the step's output on entry and of its input
 // on return (in lam[*cur]); static adjoints accumulate.
 int reverse_recorded(const hw::SolverView& v, AdjBuffers* B, const StepTape& T, double dt, int* cur) {
@@ -787,43 +898,11 @@ int reverse_recorded(const hw::SolverView& v, AdjBuffers* B, const StepTape& T, 
   cudaStream_t st = v.stream;
   const size_t n = v.n;
   if ((rc = zero_planes(B->lbase, 9, n, st))) return rc;
-  hw::Dev2D d = *v.d2;
-  const double ak[4] = {0.0, 0.0, 0.75, 1.0 / 3.0}, bk[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
   for (int k = 3; k >= 1; --k) {
-    for (int q = 0; q < 9; ++q) d.S[q] = T.in[k - 1][q];
-    hw::AdjDev A{};
-    A.d = d;
-    A.alpha = T.alpha + 2 * (k - 1);
-    A.k = k;
-    A.dt = dt;
-    A.a = ak[k];
-    A.b = bk[k];
-    A.limiter = v.params->limiter;
-    for (int q = 0; q < 9; ++q) {
-      A.lout[q] = B->lam[*cur][q];
-      A.lin[q] = B->lam[*cur ^ 1][q];
-      A.lbase[q] = B->lbase[q];
-      A.lR[q] = B->lR[q];
-    }
-    for (int q = 0; q < 6; ++q) { A.lmod[q] = B->lmod[q]; A.lqbx[q] = B->lqbx[q]; A.lqby[q] = B->lqby[q]; }
-    for (int f = 0; f < hw::NREC; ++f) { A.lrecx[f] = B->lrecx[f]; A.lrecy[f] = B->lrecy[f]; }
-    for (int q = 0; q < 3; ++q) { A.lstat[q] = B->lstat[q]; A.dbx[q] = T.dbx[k - 1][q]; A.dby[q] = T.dby[k - 1][q]; }
-    A.fax = T.fx[k - 1];
-    A.fay = T.fy[k - 1];
-    for (int q = 0; q < 2; ++q) { A.lsv[q] = B->lsv[q]; A.lsq[q] = B->lsq[q]; }
-    A.lalpha = B->lalpha;
-    A.argmax = B->argmax;
-    if ((rc = zero_planes(B->lrecx, hw::NREC, (size_t)(d.nx + 4) * d.ny, st))) return rc;
-    if ((rc = zero_planes(B->lrecy, hw::NREC, (size_t)d.nx * (d.ny + 4), st))) return rc;
+    const hw::AdjDev A = stage_args(v, B, T, dt, k, *cur);
     ACUDA(cudaMemsetAsync(B->lalpha, 0, 2 * sizeof(double), st));
     ACUDA(cudaMemsetAsync(B->argmax, 0x7f, 2 * sizeof(int), st));
-    const dim3 gn((d.nx + 31) / 32, (d.ny + 7) / 8), bn(32, 8);
-    hw::k_adj_node_pre<<<gn, bn, 0, st>>>(A);
-    hw::k_adj_sweep_x<<<dim3((d.nx + 1 + hw::AX_I - 1) / hw::AX_I, d.ny), hw::AX_T, 0, st>>>(A);
-    hw::k_adj_sweep_y<<<dim3((d.nx + 31) / 32, (d.ny + 1 + hw::AY_R - 1) / hw::AY_R), hw::AY_T, hw::AY_SMEM, st>>>(A);
-    const int nrec = (d.nx + 4) * d.ny + d.nx * (d.ny + 4);
-    hw::k_adj_records<<<(nrec + 255) / 256, 256, 0, st>>>(A);
-    if (A.limiter) hw::k_adj_limiter<<<gn, bn, 0, st>>>(A);
+    if ((rc = reverse_stage_body(v, B, A))) return rc;
     hw::k_adj_alpha_find<<<std::min((int)((n + 255) / 256), 152 * 8), 256, 0, st>>>(A);
     hw::k_adj_alpha_apply<<<1, 1, 0, st>>>(A);
     ACUDA(cudaGetLastError());
@@ -1221,3 +1300,258 @@ int hw_adjoint_run(hw_solver* s, int nsteps, const double* dts, const int* gauge
 }
 
 }  // extern "C"
+
+// =============================================================================================
+// The adjoint of a run of a block decomposition (hw_dd_*): every block reverses its own stages on its
+// extended grid; between stages the transpose of the halo exchange adds the adjoints that landed on a
+// block's ring to the nodes the ring was copied from (and clears the ring); the alpha adjoint is summed
+// over the blocks and applied once, by the block owning the undecomposed grid's first maximising node.
+// =============================================================================================
+namespace {
+
+// state planes (eta, m, w, H1, M1, W1, H2, M2, W2) odd across x- and y-walls; static (b, b_x, b_y)
+constexpr unsigned kStateOddX = (1u << 1) | (1u << 3) | (1u << 5) | (1u << 7);
+constexpr unsigned kStateOddY = (1u << 2) | (1u << 5) | (1u << 6) | (1u << 7);
+constexpr unsigned kStatOddX = 1u << 1;
+constexpr unsigned kStatOddY = 1u << 2;
+
+struct DDBlock {
+  hw_solver* s = nullptr;
+  hw_part_info info{};
+  hw::SolverView v{};
+  AdjBuffers* B = nullptr;
+  double* tape = nullptr;
+  int* d_map = nullptr;  // [2][ng_p]: local extended node, global gauge slot
+  int ng = 0;
+};
+
+}  // namespace
+
+extern "C" int hw_dd_adjoint_run(hw_dd* dd, int nsteps, const double* dts, const int* gauge_idx, int ngauge,
+                                 const double* eta_obs, double* loss_out, double* const* grad_state,
+                                 double* const* grad_static) {
+  int np = 0;
+  hw_solver* const* parts = nullptr;
+  const hw_part_info* infos = nullptr;
+  cudaStream_t st = nullptr;
+  const hw_grid* grid = nullptr;
+  int rc = hw::dd_blocks(dd, &np, &parts, &infos, &st, &grid);
+  if (rc) return rc;
+  if (nsteps < 1 || !dts || !gauge_idx || ngauge < 1 || !eta_obs || !grad_state || !grad_static)
+    return afail(HW_ERR_ARG, "hw_dd_adjoint_run: bad argument");
+  const int gnx = grid->nx, gny = grid->ny;
+  for (int g = 0; g < ngauge; ++g)
+    if (gauge_idx[g] < 0 || gauge_idx[g] >= gnx * gny) return afail(HW_ERR_ARG, "hw_dd_adjoint_run: gauge out of range");
+  for (int q = 0; q < 9; ++q)
+    if (!grad_state[q]) return afail(HW_ERR_ARG, "hw_dd_adjoint_run: null gradient plane");
+  for (int q = 0; q < 3; ++q)
+    if (!grad_static[q]) return afail(HW_ERR_ARG, "hw_dd_adjoint_run: null gradient plane");
+  std::vector<DDBlock> bl(np);
+  for (int p = 0; p < np; ++p) {
+    bl[p].s = parts[p];
+    bl[p].info = infos[p];
+    if ((rc = check_adjoint_solver(parts[p], &bl[p].v))) return rc;
+    if ((rc = get_buffers(parts[p], bl[p].v, &bl[p].B))) return rc;
+  }
+  ACUDA(cudaFuncSetAttribute(hw::k_adj_sweep_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hw::AY_SMEM));
+  std::vector<RunTape> layout;
+  for (int p = 0; p < np; ++p) layout.emplace_back(bl[p].v, nsteps);
+  // gauges by owner block: local extended node and global slot
+  std::vector<std::vector<int>> loc(np), slot(np);
+  for (int g = 0; g < ngauge; ++g) {
+    const int gi = gauge_idx[g] % gnx, gj = gauge_idx[g] / gnx;
+    for (int p = 0; p < np; ++p) {
+      const hw_part_info& I = infos[p];
+      if (gi >= I.i0 && gi < I.i0 + I.nx && gj >= I.j0 && gj < I.j0 + I.ny) {
+        loc[p].push_back((gj - I.j0 + 2) * (I.nx + 4) + (gi - I.i0 + 2));
+        slot[p].push_back(g);
+        break;
+      }
+    }
+  }
+  double *d_gvals = nullptr, *d_obs = nullptr, *lal = nullptr, *tmp = nullptr;
+  unsigned long long* keys = nullptr;
+  size_t max_ext = 0;
+  for (int p = 0; p < np; ++p) max_ext = std::max(max_ext, bl[p].v.n);
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    for (DDBlock& b : bl) { cudaFree(b.tape); cudaFree(b.d_map); }
+    cudaFree(d_gvals); cudaFree(d_obs); cudaFree(lal); cudaFree(keys); cudaFree(tmp);
+  };
+  auto alloc = [&](void** q, size_t bytes, const char* what) {
+    if (rc != HW_OK) return;
+    if (cudaMalloc(q, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      rc = afail(HW_ERR_NOMEM, std::string("hw_dd_adjoint_run: allocation failed: ") + what);
+    }
+  };
+  alloc((void**)&d_gvals, (size_t)nsteps * ngauge * sizeof(double), "gauge values");
+  alloc((void**)&d_obs, (size_t)nsteps * ngauge * sizeof(double), "observations");
+  alloc((void**)&lal, 4 * sizeof(double), "alpha adjoint");  // [0..1] alpha adjoint, [2] first maximising nodes
+  alloc((void**)&keys, (2 * (size_t)np + 2) * sizeof(unsigned long long), "alpha keys");
+  alloc((void**)&tmp, 12 * max_ext * sizeof(double), "gradient scratch");
+  for (int p = 0; p < np; ++p) {
+    alloc((void**)&bl[p].tape, layout[p].bytes(), "tape");
+    bl[p].ng = (int)loc[p].size();
+    if (bl[p].ng) alloc((void**)&bl[p].d_map, 2 * bl[p].ng * sizeof(int), "gauge map");
+  }
+  auto check = [&](cudaError_t e, const char* what) {
+    if (rc == HW_OK && e != cudaSuccess) rc = afail(HW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  if (rc == HW_OK) {
+    check(cudaMemcpyAsync(d_obs, eta_obs, (size_t)nsteps * ngauge * sizeof(double), cudaMemcpyHostToDevice, st),
+          "hw_dd_adjoint_run: copy of observations");
+    for (int p = 0; p < np && rc == HW_OK; ++p) {
+      if (!bl[p].ng) continue;
+      std::vector<int> m(loc[p]);
+      m.insert(m.end(), slot[p].begin(), slot[p].end());
+      check(cudaMemcpyAsync(bl[p].d_map, m.data(), m.size() * sizeof(int), cudaMemcpyHostToDevice, st),
+            "hw_dd_adjoint_run: copy of the gauge map");
+      check(cudaStreamSynchronize(st), "hw_dd_adjoint_run: copy of the gauge map");
+    }
+    for (int p = 0; p < np && rc == HW_OK; ++p) {
+      const StepTape T0 = layout[p].step(bl[p].tape, 0);
+      for (int q = 0; q < 9 && rc == HW_OK; ++q)
+        check(cudaMemcpyAsync(T0.in[0][q], bl[p].v.state[q], bl[p].v.n * sizeof(double), cudaMemcpyDeviceToDevice, st),
+              "hw_dd_adjoint_run: copy of the initial state");
+    }
+  }
+  // forward pass, recorded: per stage the exchange, the blocks' alpha keys and their maximum, then the
+  // blocks' sweeps and node update into the tape
+  std::vector<double*> pl(9 * (size_t)np);
+  std::vector<double* const*> plp(np);
+  for (int p = 0; p < np; ++p) plp[p] = pl.data() + 9 * (size_t)p;
+  for (int j = 0; j < nsteps && rc == HW_OK; ++j) {
+    for (int p = 0; p < np && rc == HW_OK; ++p)
+      check(cudaMemcpyAsync(bl[p].v.dt, &dts[j], sizeof(double), cudaMemcpyHostToDevice, st), "hw_dd_adjoint_run: dt");
+    for (int k = 1; k <= 3 && rc == HW_OK; ++k) {
+      for (int p = 0; p < np; ++p) {
+        const StepTape T = layout[p].step(bl[p].tape, j);
+        for (int q = 0; q < 9; ++q) pl[9 * (size_t)p + q] = T.in[k - 1][q];
+      }
+      if ((rc = hw::dd_exchange_planes(dd, plp.data(), 9, kStateOddX, kStateOddY, st))) break;
+      for (int p = 0; p < np; ++p) {
+        const StepTape T = layout[p].step(bl[p].tape, j);
+        hw::Dev2D d = *bl[p].v.d2;
+        for (int q = 0; q < 9; ++q) d.S[q] = T.in[k - 1][q];
+        double* amax = bl[p].B->lalpha + 5;  // scratch of the reduction (3 slots)
+        hw::launch_alpha2d(d, (unsigned long long*)amax, (int*)(bl[p].B->lalpha + 2), st);
+        check(cudaMemcpyAsync(keys + 2 * p, amax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st),
+              "hw_dd_adjoint_run: alpha keys");
+      }
+      hw::k_keys_max<<<1, 32, 0, st>>>(keys, np, keys + 2 * np);
+      for (int p = 0; p < np; ++p) {
+        const StepTape T = layout[p].step(bl[p].tape, j);
+        hw::Dev2D d = *bl[p].v.d2;
+        for (int q = 0; q < 9; ++q) d.S[q] = T.in[k - 1][q];
+        for (int c = 0; c < 3; ++c) { d.X[3 + c] = T.dbx[k - 1][c]; d.Y[3 + c] = T.dby[k - 1][c]; }
+        d.X[0] = T.fx[k - 1];
+        d.Y[0] = T.fy[k - 1];
+        hw::launch_finish_alpha2d(d, keys + 2 * np, T.alpha + 2 * (k - 1), nullptr, bl[p].v.params->cfl, nullptr, -1.0,
+                                  st);
+        hw::launch_sweep_x2d(d, T.alpha + 2 * (k - 1), false, true, st);
+        hw::launch_sweep_y2d(d, T.alpha + 2 * (k - 1), false, true, st);
+        hw::StageArgs sa{};
+        sa.k = k;
+        sa.limiter = bl[p].v.params->limiter;
+        sa.dt = bl[p].v.dt;
+        for (int q = 0; q < 9; ++q) {
+          sa.out[q] = k < 3 ? T.in[k][q] : T.out[q];
+          sa.base[q] = bl[p].v.base[q];
+        }
+        hw::launch_node2d(d, sa, hw::MODE_STAGE, false, true, st);
+      }
+    }
+    for (int p = 0; p < np && rc == HW_OK; ++p)
+      if (bl[p].ng) {
+        const StepTape T = layout[p].step(bl[p].tape, j);
+        hw::k_gather_eta_map<<<(bl[p].ng + 127) / 128, 128, 0, st>>>(T.out[0], bl[p].d_map, bl[p].d_map + bl[p].ng,
+                                                                    bl[p].ng, d_gvals + (size_t)j * ngauge);
+      }
+  }
+  if (rc == HW_OK) check(cudaGetLastError(), "hw_dd_adjoint_run: forward pass");
+  if (rc == HW_OK && loss_out) {
+    std::vector<double> g((size_t)nsteps * ngauge);
+    check(cudaMemcpyAsync(g.data(), d_gvals, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+          "hw_dd_adjoint_run: copy of gauge values");
+    check(cudaStreamSynchronize(st), "hw_dd_adjoint_run: forward pass");
+    double L = 0.0;
+    for (size_t q = 0; q < g.size(); ++q) L += (g[q] - eta_obs[q]) * (g[q] - eta_obs[q]);
+    *loss_out = L;
+  }
+  // reverse pass
+  int cur = 0;
+  for (int p = 0; p < np && rc == HW_OK; ++p) rc = zero_planes(bl[p].B->lam[0], 9, bl[p].v.n, st);
+  for (int j = nsteps - 1; j >= 0 && rc == HW_OK; --j) {
+    for (int p = 0; p < np && rc == HW_OK; ++p) {
+      if (bl[p].ng)
+        hw::k_loss_seed_map<<<(bl[p].ng + 127) / 128, 128, 0, st>>>(d_gvals + (size_t)j * ngauge,
+                                                                   d_obs + (size_t)j * ngauge, bl[p].d_map,
+                                                                   bl[p].d_map + bl[p].ng, bl[p].ng,
+                                                                   bl[p].B->lam[cur][0]);
+      rc = zero_planes(bl[p].B->lbase, 9, bl[p].v.n, st);
+    }
+    for (int k = 3; k >= 1 && rc == HW_OK; --k) {
+      check(cudaMemsetAsync(lal, 0, 2 * sizeof(double), st), "hw_dd_adjoint_run: alpha adjoint");
+      check(cudaMemsetAsync(lal + 2, 0x7f, 2 * sizeof(int), st), "hw_dd_adjoint_run: alpha node");
+      std::vector<hw::AdjDev> A(np);
+      for (int p = 0; p < np && rc == HW_OK; ++p) {
+        A[p] = stage_args(bl[p].v, bl[p].B, layout[p].step(bl[p].tape, j), dts[j], k, cur);
+        A[p].lalpha = lal;
+        A[p].argmax = (int*)(lal + 2);
+        rc = reverse_stage_body(bl[p].v, bl[p].B, A[p]);
+      }
+      for (int p = 0; p < np && rc == HW_OK; ++p) {
+        const hw_part_info& I = bl[p].info;
+        hw::k_adj_alpha_find_block<<<std::min((I.nx * I.ny + 255) / 256, 152 * 8), 256, 0, st>>>(A[p], I.nx, I.ny, I.i0,
+                                                                                              I.j0, gnx);
+      }
+      for (int p = 0; p < np && rc == HW_OK; ++p) {
+        const hw_part_info& I = bl[p].info;
+        hw::k_adj_alpha_apply_block<<<1, 1, 0, st>>>(A[p], I.nx, I.ny, I.i0, I.j0, gnx);
+      }
+      if (rc == HW_OK) check(cudaGetLastError(), "hw_dd_adjoint_run: reverse stage");
+      for (int p = 0; p < np; ++p)
+        for (int q = 0; q < 9; ++q) pl[9 * (size_t)p + q] = bl[p].B->lam[cur ^ 1][q];
+      if (rc == HW_OK) rc = hw::dd_exchange_adjoint(dd, plp.data(), 9, kStateOddX, kStateOddY, st);
+      cur ^= 1;
+    }
+  }
+  // gradients: the state's in physical units, the static ones with their rings moved to the owners; the
+  // blocks' own nodes copied into the global planes (device)
+  for (int p = 0; p < np && rc == HW_OK; ++p) {
+    const hw_part_info& I = bl[p].info;
+    const int nxe = I.nx + 4;
+    const size_t n = bl[p].v.n;
+    const int blocks = std::min((int)((n + 255) / 256), 152 * 8);
+    hw::Ptr9 src{}, dst{};
+    for (int q = 0; q < 9; ++q) { src.p[q] = bl[p].B->lam[cur][q]; dst.p[q] = tmp + q * max_ext; }
+    hw::k_adj_convert<<<blocks, 256, 0, st>>>((int)n, bl[p].v.d2->dx, bl[p].v.d2->dy, src, dst, 0);
+    for (int q = 0; q < 9 && rc == HW_OK; ++q)
+      check(cudaMemcpy2DAsync(grad_state[q] + (size_t)I.j0 * gnx + I.i0, gnx * sizeof(double),
+                              tmp + q * max_ext + 2 * (size_t)nxe + 2, nxe * sizeof(double), I.nx * sizeof(double), I.ny,
+                              cudaMemcpyDeviceToDevice, st),
+            "hw_dd_adjoint_run: state gradient");
+  }
+  std::vector<double*> stat_planes(3 * (size_t)np);
+  std::vector<double* const*> sp(np);
+  for (int p = 0; p < np && rc == HW_OK; ++p) {
+    for (int q = 0; q < 3; ++q) stat_planes[3 * (size_t)p + q] = bl[p].B->lstatic_phys[q];
+    sp[p] = stat_planes.data() + 3 * (size_t)p;
+    rc = zero_planes(bl[p].B->lstatic_phys, 3, bl[p].v.n, st);
+    if (rc == HW_OK) rc = finish_static(bl[p].v, bl[p].B, bl[p].B->lstatic_phys);
+  }
+  if (rc == HW_OK) rc = hw::dd_exchange_adjoint(dd, sp.data(), 3, kStatOddX, kStatOddY, st);
+  for (int p = 0; p < np && rc == HW_OK; ++p) {
+    const hw_part_info& I = bl[p].info;
+    const int nxe = I.nx + 4;
+    for (int q = 0; q < 3 && rc == HW_OK; ++q)
+      check(cudaMemcpy2DAsync(grad_static[q] + (size_t)I.j0 * gnx + I.i0, gnx * sizeof(double),
+                              bl[p].B->lstatic_phys[q] + 2 * (size_t)nxe + 2, nxe * sizeof(double), I.nx * sizeof(double),
+                              I.ny, cudaMemcpyDeviceToDevice, st),
+            "hw_dd_adjoint_run: static gradient");
+  }
+  if (rc == HW_OK) check(cudaStreamSynchronize(st), "hw_dd_adjoint_run");
+  cleanup();
+  return rc;
+}

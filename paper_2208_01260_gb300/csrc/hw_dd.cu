@@ -64,23 +64,62 @@ __global__ void k_halo_pack(PlaneSet ps, int np, int nxe, int nye, int face, dou
   }
 }
 
-// mode NEIGHBOR: ring offset c <- strip offset c (the neighbour's nodes in increasing coordinate);
-// MIRROR: the ring node at distance d outside the wall <- the node at distance d - 1 inside it, i.e.
-// offset c <- 1 - c, negated for planes odd across this wall; REPLICATE: <- the boundary node.
+// The strip offset a ring offset c reads: NEIGHBOR c (the neighbour's nodes in increasing coordinate);
+// MIRROR 1 - c (the ring node at distance d outside the wall is the node at distance d - 1 inside it,
+// negated for planes odd across this wall); REPLICATE the boundary node.
+__device__ __forceinline__ int ring_source(int face, int mode, int c) {
+  if (mode == HW_HALO_MIRROR) return 1 - c;
+  if (mode == HW_HALO_REPLICATE) return (face == HW_FACE_W || face == HW_FACE_S) ? 0 : 1;
+  return c;
+}
+
 __global__ void k_halo_unpack(PlaneSet ps, int np, int nxe, int nye, int face, int mode, unsigned odd,
                               const double* __restrict__ strip) {
   const int len = face < 2 ? nye - 4 : nxe;
   const long long total = (long long)np * 2 * len;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(t % len), c = (int)((t / len) & 1), q = (int)(t / (2 * len));
-    int sc = c;
-    if (mode == HW_HALO_MIRROR) sc = 1 - c;
-    else if (mode == HW_HALO_REPLICATE) sc = (face == HW_FACE_W || face == HW_FACE_S) ? 0 : 1;
-    double v = strip[((long long)q * 2 + sc) * len + r];
+    double v = strip[((long long)q * 2 + ring_source(face, mode, c)) * len + r];
     if (mode == HW_HALO_MIRROR && ((odd >> q) & 1u)) v = -v;
     int i, j;
     ring_coords(face, nxe, nye, c, r, i, j);
     ps.p[q][(size_t)j * nxe + i] = v;
+  }
+}
+
+// Transpose of the exchange, for adjoints: the ring's values of a face (the adjoints of copies) move into
+// a strip in ring order and the ring is cleared ...
+__global__ void k_halo_adj_pack(PlaneSet ps, int np, int nxe, int nye, int face, double* __restrict__ strip) {
+  const int len = face < 2 ? nye - 4 : nxe;
+  const long long total = (long long)np * 2 * len;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t % len), c = (int)((t / len) & 1), q = (int)(t / (2 * len));
+    int i, j;
+    ring_coords(face, nxe, nye, c, r, i, j);
+    double* x = ps.p[q] + (size_t)j * nxe + i;
+    strip[t] = *x;
+    *x = 0.0;
+  }
+}
+
+// ... and are added to the nodes they were copied from: the neighbour's nodes next to the opposite face
+// (NEIGHBOR: called on the neighbour with that face), or the block's own nodes next to this face with the
+// mirror's signs (MIRROR) or summed into the boundary node (REPLICATE). One thread per strip position
+// and plane adds both ring offsets that read it, so no two threads write one node.
+__global__ void k_halo_adj_add(PlaneSet ps, int np, int nxe, int nye, int face, int mode, unsigned odd,
+                               const double* __restrict__ strip) {
+  const int len = face < 2 ? nye - 4 : nxe;
+  const long long total = (long long)np * 2 * len;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t % len), sc = (int)((t / len) & 1), q = (int)(t / (2 * len));
+    double v = 0.0;
+    for (int c = 0; c < 2; ++c)
+      if (ring_source(face, mode, c) == sc) v += strip[((long long)q * 2 + c) * len + r];
+    if (v == 0.0) continue;
+    if (mode == HW_HALO_MIRROR && ((odd >> q) & 1u)) v = -v;
+    int i, j;
+    strip_coords(face, nxe, nye, sc, r, i, j);
+    ps.p[q][(size_t)j * nxe + i] += v;
   }
 }
 
@@ -272,6 +311,12 @@ int dd_exchange(hw_dd* d, int set) {
   return HW_OK;
 }
 
+hw::PlaneSet plane_set(double* const* planes, int nplanes) {
+  hw::PlaneSet ps{};
+  for (int q = 0; q < nplanes; ++q) ps.p[q] = planes[q];
+  return ps;
+}
+
 // One SSP-RK3 step of every block (dt from the CFL step at the step's start, clipped to t_end).
 int dd_step(hw_dd* d, cudaStream_t st, double t_end) {
   for (int k = 1; k <= 3; ++k) {
@@ -289,6 +334,77 @@ void dd_set_stream(hw_dd* d, cudaStream_t st) {
 }
 
 }  // namespace
+
+namespace hw {
+
+int dd_blocks(hw_dd* d, int* np, hw_solver* const** parts, const hw_part_info** info, cudaStream_t* st,
+              const hw_grid** grid) {
+  if (!d) return set_last_error(HW_ERR_ARG, "null block decomposition");
+  *np = d->np;
+  *parts = d->parts.data();
+  *info = d->info.data();
+  *st = d->stream;
+  *grid = &d->grid;
+  return HW_OK;
+}
+
+int dd_exchange_planes(hw_dd* d, double* const* const* planes, int nplanes, unsigned oddx, unsigned oddy,
+                       cudaStream_t st) {
+  if (nplanes < 1 || nplanes > 14) return set_last_error(HW_ERR_ARG, "dd_exchange_planes: 1..14 planes");
+  for (int phase = 0; phase < 2; ++phase) {
+    for (int p = 0; p < d->np; ++p) {
+      const int nxe = d->info[p].nx + 4, nye = d->info[p].ny + 4;
+      for (int f = 2 * phase; f < 2 * phase + 2; ++f) {
+        const long long len = f < 2 ? nye - 4 : nxe;
+        k_halo_pack<<<blocks_for(nplanes * 2 * len), 256, 0, st>>>(plane_set(planes[p], nplanes), nplanes, nxe, nye,
+                                                                    f, d->strips[4 * p + f]);
+      }
+    }
+    for (int p = 0; p < d->np; ++p) {
+      const int nxe = d->info[p].nx + 4, nye = d->info[p].ny + 4;
+      for (int f = 2 * phase; f < 2 * phase + 2; ++f) {
+        const int mode = d->info[p].mode[f];
+        const int src = mode == HW_HALO_NEIGHBOR ? 4 * d->info[p].nbr[f] + (f ^ 1) : 4 * p + f;
+        const long long len = f < 2 ? nye - 4 : nxe;
+        k_halo_unpack<<<blocks_for(nplanes * 2 * len), 256, 0, st>>>(plane_set(planes[p], nplanes), nplanes, nxe, nye,
+                                                                      f, mode, f < 2 ? oddx : oddy, d->strips[src]);
+      }
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HW_OK : set_last_error(HW_ERR_CUDA, cudaGetErrorString(e));
+}
+
+int dd_exchange_adjoint(hw_dd* d, double* const* const* planes, int nplanes, unsigned oddx, unsigned oddy,
+                        cudaStream_t st) {
+  if (nplanes < 1 || nplanes > 14) return set_last_error(HW_ERR_ARG, "dd_exchange_adjoint: 1..14 planes");
+  for (int phase = 1; phase >= 0; --phase) {  // the reverse order of the exchange: y faces, then x faces
+    for (int p = 0; p < d->np; ++p) {
+      const int nxe = d->info[p].nx + 4, nye = d->info[p].ny + 4;
+      for (int f = 2 * phase; f < 2 * phase + 2; ++f) {
+        const long long len = f < 2 ? nye - 4 : nxe;
+        k_halo_adj_pack<<<blocks_for(nplanes * 2 * len), 256, 0, st>>>(plane_set(planes[p], nplanes), nplanes, nxe,
+                                                                        nye, f, d->strips[4 * p + f]);
+      }
+    }
+    for (int p = 0; p < d->np; ++p)
+      for (int f = 2 * phase; f < 2 * phase + 2; ++f) {
+        const int mode = d->info[p].mode[f];
+        // the ring of face f of block p was read from block q's nodes next to face g
+        const int q = mode == HW_HALO_NEIGHBOR ? d->info[p].nbr[f] : p;
+        const int g = mode == HW_HALO_NEIGHBOR ? (f ^ 1) : f;
+        const int nxe = d->info[q].nx + 4, nye = d->info[q].ny + 4;
+        const long long len = g < 2 ? nye - 4 : nxe;
+        k_halo_adj_add<<<blocks_for(nplanes * 2 * len), 256, 0, st>>>(plane_set(planes[q], nplanes), nplanes, nxe, nye,
+                                                                       g, mode, g < 2 ? oddx : oddy,
+                                                                       d->strips[4 * p + f]);
+      }
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HW_OK : set_last_error(HW_ERR_CUDA, cudaGetErrorString(e));
+}
+
+}  // namespace hw
 
 extern "C" {
 

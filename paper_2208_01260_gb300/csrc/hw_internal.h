@@ -139,6 +139,16 @@ cudaStream_t solver_stream(hw_solver* s);
 const hw_part_info* part_info(hw_solver* s);   // null unless a block solver
 // still water (h = 1, everything else 0) on the 2-node ring of 12 extended input planes (hw_dd.cu)
 void launch_fill_ring(double* const* planes12, int nxe, int nye, cudaStream_t st);
+// The blocks of a single-GPU block decomposition (hw_dd.cu), and its halo exchange on any set of
+// nplanes planes per block (planes[p][q], extended grids; oddx / oddy: bit q set for planes that change
+// sign across x- / y-walls), and the transpose of that exchange (for adjoints: the ring's values are
+// added to the nodes they were copied from and the ring is cleared). Stream-ordered on st.
+int dd_blocks(hw_dd* d, int* np, hw_solver* const** parts, const hw_part_info** info, cudaStream_t* st,
+              const hw_grid** grid);
+int dd_exchange_planes(hw_dd* d, double* const* const* planes, int nplanes, unsigned oddx, unsigned oddy,
+                       cudaStream_t st);
+int dd_exchange_adjoint(hw_dd* d, double* const* const* planes, int nplanes, unsigned oddx, unsigned oddy,
+                        cudaStream_t st);
 int solver_set_state_planes(hw_solver* s, double* const* src);  // device copy into the current state
 void adjoint_release(hw_solver* s);  // frees a solver's adjoint working buffers; hw_destroy calls it
 
