@@ -1327,9 +1327,9 @@ struct DDBlock {
 
 }  // namespace
 
-extern "C" int hw_dd_adjoint_run(hw_dd* dd, int nsteps, const double* dts, const int* gauge_idx, int ngauge,
-                                 const double* eta_obs, double* loss_out, double* const* grad_state,
-                                 double* const* grad_static) {
+namespace {
+int dd_adjoint_impl(hw_dd* dd, int nsteps, const double* dts, const int* gauge_idx, int ngauge, const double* eta_obs,
+                    double* loss_out, double* const* grad_state, double* const* grad_static) {
   int np = 0;
   hw_solver* const* parts = nullptr;
   const hw_part_info* infos = nullptr;
@@ -1553,5 +1553,30 @@ extern "C" int hw_dd_adjoint_run(hw_dd* dd, int nsteps, const double* dts, const
   }
   if (rc == HW_OK) check(cudaStreamSynchronize(st), "hw_dd_adjoint_run");
   cleanup();
+  return rc;
+}
+}  // namespace
+
+// The blocks' own streams are set aside for the run: its kernels interleave the blocks on the main stream.
+extern "C" int hw_dd_adjoint_run(hw_dd* dd, int nsteps, const double* dts, const int* gauge_idx, int ngauge,
+                                 const double* eta_obs, double* loss_out, double* const* grad_state,
+                                 double* const* grad_static) {
+  int np = 0;
+  hw_solver* const* parts = nullptr;
+  const hw_part_info* infos = nullptr;
+  cudaStream_t st = nullptr;
+  const hw_grid* grid = nullptr;
+  int rc = hw::dd_blocks(dd, &np, &parts, &infos, &st, &grid);
+  if (rc) return rc;
+  std::vector<cudaStream_t> own(np);
+  for (int p = 0; p < np; ++p) {
+    own[p] = hw::solver_stream(parts[p]);
+    ACUDA(cudaStreamSynchronize(own[p]));
+  }
+  ACUDA(cudaStreamSynchronize(st));
+  for (int p = 0; p < np; ++p) hw::solver_swap_stream(parts[p], st);
+  rc = dd_adjoint_impl(dd, nsteps, dts, gauge_idx, ngauge, eta_obs, loss_out, grad_state, grad_static);
+  cudaStreamSynchronize(st);
+  for (int p = 0; p < np; ++p) hw::solver_swap_stream(parts[p], own[p]);
   return rc;
 }

@@ -272,6 +272,11 @@ struct hw_dd {
   bool inited = false;
   cudaGraphExec_t graph = nullptr;
   double graph_t_end = -1.0;
+  // every block launches on its own stream, forked from and joined back to the main stream around the
+  // blocks' alpha and stage phases, so the blocks' kernels overlap (in a captured graph: parallel branches)
+  std::vector<cudaStream_t> pstream;
+  std::vector<cudaEvent_t> pevent;
+  cudaEvent_t fork_ev = nullptr;
 };
 
 namespace {
@@ -296,41 +301,53 @@ int dd_alloc(hw_dd* d, void** p, size_t bytes) {
   return HW_OK;
 }
 
-// One exchange of a plane set: x faces of every block, then y faces (corners).
-int dd_exchange(hw_dd* d, int set) {
-  for (int phase = 0; phase < 2; ++phase) {
-    for (int p = 0; p < d->np; ++p)
-      for (int f = 2 * phase; f < 2 * phase + 2; ++f) DD_OK(hw_halo_pack(d->parts[p], set, f, d->strips[4 * p + f]));
-    for (int p = 0; p < d->np; ++p)
-      for (int f = 2 * phase; f < 2 * phase + 2; ++f) {
-        const int mode = d->info[p].mode[f];
-        const int src = mode == HW_HALO_NEIGHBOR ? 4 * d->info[p].nbr[f] + (f ^ 1) : 4 * p + f;
-        DD_OK(hw_halo_unpack(d->parts[p], set, f, mode, d->strips[src]));
-      }
-  }
-  return HW_OK;
-}
-
 hw::PlaneSet plane_set(double* const* planes, int nplanes) {
   hw::PlaneSet ps{};
   for (int q = 0; q < nplanes; ++q) ps.p[q] = planes[q];
   return ps;
 }
 
-// One SSP-RK3 step of every block (dt from the CFL step at the step's start, clipped to t_end).
+int dd_exchange(hw_dd* d, int set, cudaStream_t st);
+
+// The blocks' streams wait for the main stream ...
+int dd_fork(hw_dd* d, cudaStream_t st) {
+  DD_CUDA(cudaEventRecord(d->fork_ev, st));
+  for (cudaStream_t ps : d->pstream) DD_CUDA(cudaStreamWaitEvent(ps, d->fork_ev, 0));
+  return HW_OK;
+}
+// ... and the main stream for every block's stream.
+int dd_join(hw_dd* d, cudaStream_t st) {
+  for (int p = 0; p < d->np; ++p) {
+    DD_CUDA(cudaEventRecord(d->pevent[p], d->pstream[p]));
+    DD_CUDA(cudaStreamWaitEvent(st, d->pevent[p], 0));
+  }
+  return HW_OK;
+}
+
+// One SSP-RK3 step of every block (dt from the CFL step at the step's start, clipped to t_end): per stage
+// the exchange on the main stream, the blocks' alpha keys on their streams, the maximum on the main
+// stream, the blocks' stages on their streams. On entry and on return every block's work is ordered
+// before the main stream's.
 int dd_step(hw_dd* d, cudaStream_t st, double t_end) {
   for (int k = 1; k <= 3; ++k) {
-    DD_OK(dd_exchange(d, 0));
+    DD_OK(dd_exchange(d, 0, st));
+    DD_OK(dd_fork(d, st));
     for (int p = 0; p < d->np; ++p) DD_OK(hw_part_alpha_keys(d->parts[p], d->keys + 2 * p));
+    DD_OK(dd_join(d, st));
     hw::k_max_keys<<<1, 32, 0, st>>>(d->keys, d->np, d->keys + 2 * d->np);
+    DD_OK(dd_fork(d, st));
     for (int p = 0; p < d->np; ++p) DD_OK(hw_part_stage(d->parts[p], k, d->keys + 2 * d->np, t_end));
+    DD_OK(dd_join(d, st));
   }
   DD_CUDA(cudaGetLastError());
   return HW_OK;
 }
 
-void dd_set_stream(hw_dd* d, cudaStream_t st) {
-  for (hw_solver* s : d->parts) hw::solver_swap_stream(s, st);
+// every block's stream drained after the main stream (before host reads through a block's stream)
+int dd_drain(hw_dd* d) {
+  DD_CUDA(cudaStreamSynchronize(d->stream));
+  for (cudaStream_t ps : d->pstream) DD_CUDA(cudaStreamSynchronize(ps));
+  return HW_OK;
 }
 
 }  // namespace
@@ -406,15 +423,32 @@ int dd_exchange_adjoint(hw_dd* d, double* const* const* planes, int nplanes, uns
 
 }  // namespace hw
 
+namespace {
+// One exchange of plane set 0 (state) or 1 (state and static planes) on the main stream.
+int dd_exchange(hw_dd* d, int set, cudaStream_t st) {
+  std::vector<double*> pl(14 * (size_t)d->np);
+  std::vector<double* const*> pp(d->np);
+  int nplanes = 0;
+  for (int p = 0; p < d->np; ++p) {
+    hw::part_planes(d->parts[p], set, pl.data() + 14 * (size_t)p, &nplanes);
+    pp[p] = pl.data() + 14 * (size_t)p;
+  }
+  return hw::dd_exchange_planes(d, pp.data(), nplanes, hw::kOddX, hw::kOddY, st);
+}
+}  // namespace
+
 extern "C" {
 
 int hw_dd_destroy(hw_dd* d) {
   if (!d) return HW_OK;
   if (d->graph) cudaGraphExecDestroy(d->graph);
-  for (hw_solver* s : d->parts) hw_destroy(s);
   if (d->stream) cudaStreamSynchronize(d->stream);
   else cudaDeviceSynchronize();
+  for (hw_solver* s : d->parts) hw_destroy(s);
   for (void* p : d->allocs) cudaFree(p);
+  for (cudaStream_t ps : d->pstream) cudaStreamDestroy(ps);
+  for (cudaEvent_t e : d->pevent) cudaEventDestroy(e);
+  if (d->fork_ev) cudaEventDestroy(d->fork_ev);
   if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
   delete d;
   return HW_OK;
@@ -435,8 +469,15 @@ int hw_dd_create(const hw_grid* grid, const hw_params* params, int px, int py, v
   int rc = HW_OK;
   size_t max_ext = 0;
   for (int p = 0; p < d->np && rc == HW_OK; ++p) {
+    cudaStream_t ps = nullptr;
+    cudaEvent_t pe = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+    if (e == cudaSuccess) d->pstream.push_back(ps);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pe, cudaEventDisableTiming);
+    if (e == cudaSuccess) d->pevent.push_back(pe);
+    if (e != cudaSuccess) { rc = dd_fail(HW_ERR_CUDA, cudaGetErrorString(e)); break; }
     hw_solver* s = nullptr;
-    rc = hw_part_create(grid, params, px, py, p, cuda_stream, &s);
+    rc = hw_part_create(grid, params, px, py, p, ps, &s);
     if (rc != HW_OK) break;
     d->parts.push_back(s);
     d->info.push_back(*hw::part_info(s));
@@ -461,6 +502,10 @@ int hw_dd_create(const hw_grid* grid, const hw_params* params, int px, int py, v
     cudaError_t e = cudaStreamCreateWithFlags(&d->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { d->cap_stream = nullptr; rc = dd_fail(HW_ERR_CUDA, cudaGetErrorString(e)); }
   }
+  if (rc == HW_OK) {
+    cudaError_t e = cudaEventCreateWithFlags(&d->fork_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) { d->fork_ev = nullptr; rc = dd_fail(HW_ERR_CUDA, cudaGetErrorString(e)); }
+  }
   if (rc != HW_OK) {
     hw_dd_destroy(d);
     return rc;
@@ -484,7 +529,8 @@ int hw_dd_init(hw_dd* d, const double* h, const double* hu, const double* hv, co
     if (rc == HW_ERR_DEPTH || rc == HW_ERR_NONFINITE) { if (first_err == HW_OK) first_err = rc; }
     else if (rc != HW_OK) return rc;
   }
-  DD_OK(dd_exchange(d, 1));
+  DD_OK(dd_exchange(d, 1, d->stream));
+  DD_CUDA(cudaStreamSynchronize(d->stream));
   for (int p = 0; p < d->np; ++p) DD_OK(hw_part_finish_init(d->parts[p]));
   d->inited = true;
   if (first_err != HW_OK) return dd_fail(first_err, "hw_dd_init: non-positive or non-finite depth in the input");
@@ -497,13 +543,13 @@ int hw_dd_advance(hw_dd* d, int nsteps, double t_end, int use_graph, double* t_o
   if (nsteps < 0) return dd_fail(HW_ERR_ARG, "hw_dd_advance: nsteps < 0");
   double t0 = 0.0, t = 0.0;
   long long n0 = 0, n1 = 0;
+  DD_OK(dd_drain(d));
   DD_OK(hw_get_time(d->parts[0], &t0, &n0));
   const bool has_end = t_end > 0.0;
   // a graph holds two steps (six stages: every block's state buffer returns to where it was)
   if (use_graph && (!d->graph || d->graph_t_end != t_end) && hw::solver_cur(d->parts[0]) == 0) {
     if (d->graph) { cudaGraphExecDestroy(d->graph); d->graph = nullptr; }
-    DD_CUDA(cudaStreamSynchronize(d->stream));
-    dd_set_stream(d, d->cap_stream);
+    DD_OK(dd_drain(d));
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(d->cap_stream, cudaStreamCaptureModeThreadLocal);
     int rc = HW_OK;
@@ -512,7 +558,6 @@ int hw_dd_advance(hw_dd* d, int nsteps, double t_end, int use_graph, double* t_o
       if (rc == HW_OK) rc = dd_step(d, d->cap_stream, t_end);
       e = cudaStreamEndCapture(d->cap_stream, &g);
     }
-    dd_set_stream(d, d->stream);
     if (rc != HW_OK) { if (g) cudaGraphDestroy(g); return rc; }
     if (e != cudaSuccess) return dd_fail(HW_ERR_CUDA, std::string("hw_dd_advance: capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&d->graph, g, 0);
@@ -537,8 +582,12 @@ int hw_dd_advance(hw_dd* d, int nsteps, double t_end, int use_graph, double* t_o
         done += 1;
       }
     }
-    if (has_end) DD_OK(hw_get_time(d->parts[0], &t, &n1));
+    if (has_end) {
+      DD_OK(dd_drain(d));
+      DD_OK(hw_get_time(d->parts[0], &t, &n1));
+    }
   }
+  DD_OK(dd_drain(d));
   int rc = HW_OK;
   for (hw_solver* s : d->parts) {
     int r = hw_sync(s);
@@ -557,16 +606,17 @@ int hw_dd_get_state(hw_dd* d, double* const* out, int layout, int ptr_kind) {
   for (int q = 0; q < 9; ++q)
     if (!out[q]) return dd_fail(HW_ERR_ARG, "hw_dd_get_state: null plane");
   const cudaMemcpyKind kind = ptr_kind == HW_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  DD_OK(dd_drain(d));
   for (int p = 0; p < d->np; ++p) {
     const hw_part_info& pi = d->info[p];
-    DD_OK(hw_get_state(d->parts[p], d->tmp, layout, HW_DEVICE));
+    DD_OK(hw_get_state(d->parts[p], d->tmp, layout, HW_DEVICE));  // on the block's stream
     const int nxe = pi.nx + 4;
     for (int q = 0; q < 9; ++q)
       DD_CUDA(cudaMemcpy2DAsync(out[q] + (size_t)pi.j0 * d->grid.nx + pi.i0, d->grid.nx * sizeof(double),
                                 d->tmp[q] + 2 * (size_t)nxe + 2, nxe * sizeof(double), pi.nx * sizeof(double), pi.ny,
-                                kind, d->stream));
+                                kind, d->pstream[p]));
+    DD_CUDA(cudaStreamSynchronize(d->pstream[p]));  // d->tmp is reused by the next block
   }
-  DD_CUDA(cudaStreamSynchronize(d->stream));
   return HW_OK;
 }
 

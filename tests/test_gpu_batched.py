@@ -68,6 +68,24 @@ def test_batched_matches_oracle(hw, orc, nsteps, use_graph):
     b.close()
 
 
+@pytest.mark.parametrize("pk", [{"char_decomp": 0}, {"limiter": 0}, {"linear_weights": 1}],
+                         ids=["no_char", "no_limiter", "linear_weights"])
+def test_batched_matches_oracle_other_parameters(hw, orc, pk):
+    """The batched kernels' other instantiations (no characteristic projection, no limiter, linear
+    weights) against the oracle with the same parameters, one step at the per-stage tolerance."""
+    scs = _mixed_batch()[:5]
+    b = hw.BatchedSolver(scs, hw.make_params(**pk))
+    b.run(1, use_graph=False)
+    for i, sc in enumerate(scs):
+        g = oracle_grid(orc, sc)
+        p = orc.make_params(eps_w=sc.eps_w, **pk)
+        cur, stat = oracle_state(orc, sc)
+        dt = orc.cfl_dt2d(g, p, cur, stat)
+        ref = orc.rk3_step2d(g, p, dt, cur, stat)
+        assert max(normwise(b.state(i), ref, stage_scales(ref, stat))) <= 1e-12, (i, pk)
+    b.close()
+
+
 def test_batched_equals_single_grid_solvers(hw):
     scs = _mixed_batch()
     b = hw.BatchedSolver(scs)

@@ -55,6 +55,21 @@ def test_decomposed_equals_undecomposed(hw, name, nx, ny, bcx, bcy, px, py):
     ref.close()
 
 
+@pytest.mark.parametrize("pk", [{"char_decomp": 0, "limiter": 0}, {"linear_weights": 1}], ids=["no_char_no_limiter", "linear"])
+def test_decomposed_equals_undecomposed_other_parameters(hw, pk):
+    """The other kernel instantiations through the blocks: still bitwise."""
+    sc = _scenario(90, 70, S.REFLECTIVE, S.PERIODIC, seed=65)
+    params = hw.make_params(**pk)
+    ref = hw.Solver.from_scenario(sc, params)
+    dd = hw.DecomposedSolver(sc, 3, 2, params)
+    ref.advance(5)
+    dd.advance(5)
+    for a, b in zip(ref.state(), dd.state()):
+        assert np.array_equal(a, b)
+    dd.close()
+    ref.close()
+
+
 def test_decomposed_end_time_and_depth_error(hw):
     sc = _scenario(96, 64, S.REFLECTIVE, S.PERIODIC, seed=62)
     ref = hw.Solver.from_scenario(sc, hw.make_params())
