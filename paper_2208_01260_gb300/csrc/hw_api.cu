@@ -173,6 +173,10 @@ int hw_create(const hw_grid* grid, const hw_params* params, void* cuda_stream, h
     return fail(HW_ERR_ARG, "hw_create: empty domain");
   if ((size_t)grid->nx * (size_t)grid->ny > ((size_t)1 << 31))
     return fail(HW_ERR_ARG, "hw_create: grid too large (more than 2^31 nodes)");
+  // the sweeps index their flattened extended lines, ny (nx + 4) and (nx / 2 + 1) (ny + 4) nodes, in 32 bits
+  if (grid->dim == 2 && ((size_t)grid->ny * ((size_t)grid->nx + 4) >= ((size_t)1 << 32) ||
+                         ((size_t)grid->nx / 2 + 1) * ((size_t)grid->ny + 4) >= ((size_t)1 << 32)))
+    return fail(HW_ERR_ARG, "hw_create: grid too elongated for the sweeps' 32-bit line indices");
   if (!(params->g > 0) || !(params->eps_w > 0) || !(params->eps_lim > 0) || !(params->cfl > 0))
     return fail(HW_ERR_ARG, "hw_create: g, cfl, eps_w and eps_lim must be positive");
   if (params->precision != HW_FP64 && params->precision != HW_FP32)
