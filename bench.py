@@ -431,7 +431,44 @@ def decomposed_compare(steps, splits=((2, 2), (4, 2))):
         out["splits"]["%dx%d" % (px, py)] = {
             "ms_per_step": ms, "value": NX * NY * STAGES / (ms * 1e-3), "over_single": ms_single / ms,
             "bitwise_equal_to_single": all(np.array_equal(a, b) for a, b in zip(ref, got))}
+    out["adjoint"] = decomposed_adjoint_compare()
     return out
+
+
+def decomposed_adjoint_compare(n=512, nsteps=100, px=2, py=2):
+    """The gauge-misfit gradient of the adjoint workload (512^2, 32 gauges) over 2 x 2 blocks against the
+    undecomposed adjoint, both on whole-run tapes: run times and the largest gradient difference."""
+    import torch
+    import paper_2208_01260_gb300 as hw
+    from paper_2208_01260_gb300 import adjoint as A
+    from paper_2208_01260_gb300 import scenarios as S
+    sc = S.adjoint_case(n)
+    gidx = S.gauges(n, n)
+    solver = hw.Solver.from_scenario(sc, hw.make_params())
+    dts = [solver.cfl_dt()] * nsteps
+    obs = np.full(nsteps * len(gidx), 1.0)
+    gs = torch.empty(9, n, n, dtype=torch.float64, device="cuda")
+    gb = torch.empty(3, n, n, dtype=torch.float64, device="cuda")
+    A.hw_adjoint_run(solver.h, dts[:2], gidx, obs[:2 * len(gidx)], A.HW_ADJ_TAPE, list(gs), list(gb))  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss, _ = A.hw_adjoint_run(solver.h, dts, gidx, obs, A.HW_ADJ_TAPE, list(gs), list(gb))
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    solver.close()
+    d = hw.DecomposedSolver(sc, px, py)
+    ds, db = torch.empty_like(gs), torch.empty_like(gb)
+    hw.hw_dd_adjoint_run(d.h, dts[:2], gidx, obs[:2 * len(gidx)], list(ds), list(db))  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss_dd = hw.hw_dd_adjoint_run(d.h, dts, gidx, obs, list(ds), list(db))
+    torch.cuda.synchronize()
+    t_dd = time.perf_counter() - t0
+    d.close()
+    scale = float(gs.abs().max())
+    return {"grid": [n, n], "steps": nsteps, "blocks": [px, py], "adjoint_run_s_single": t_single,
+            "adjoint_run_s_blocks": t_dd, "blocks_over_single": t_dd / t_single, "loss_equal": loss == loss_dd,
+            "max_grad_diff_over_largest": max(float((ds - gs).abs().max()), float((db - gb).abs().max())) / scale}
 
 
 def run_reference(args):

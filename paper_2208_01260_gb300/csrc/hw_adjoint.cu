@@ -1430,16 +1430,20 @@ int dd_adjoint_impl(hw_dd* dd, int nsteps, const double* dts, const int* gauge_i
         for (int q = 0; q < 9; ++q) pl[9 * (size_t)p + q] = T.in[k - 1][q];
       }
       if ((rc = hw::dd_exchange_planes(dd, plp.data(), 9, kStateOddX, kStateOddY, st))) break;
+      if ((rc = hw::dd_fork_blocks(dd, st))) break;
       for (int p = 0; p < np; ++p) {
         const StepTape T = layout[p].step(bl[p].tape, j);
         hw::Dev2D d = *bl[p].v.d2;
         for (int q = 0; q < 9; ++q) d.S[q] = T.in[k - 1][q];
         double* amax = bl[p].B->lalpha + 5;  // scratch of the reduction (3 slots)
-        hw::launch_alpha2d(d, (unsigned long long*)amax, (int*)(bl[p].B->lalpha + 2), st);
-        check(cudaMemcpyAsync(keys + 2 * p, amax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st),
+        hw::launch_alpha2d(d, (unsigned long long*)amax, (int*)(bl[p].B->lalpha + 2), bl[p].v.stream);
+        check(cudaMemcpyAsync(keys + 2 * p, amax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                              bl[p].v.stream),
               "hw_dd_adjoint_run: alpha keys");
       }
+      if ((rc = hw::dd_join_blocks(dd, st))) break;
       hw::k_keys_max<<<1, 32, 0, st>>>(keys, np, keys + 2 * np);
+      if ((rc = hw::dd_fork_blocks(dd, st))) break;
       for (int p = 0; p < np; ++p) {
         const StepTape T = layout[p].step(bl[p].tape, j);
         hw::Dev2D d = *bl[p].v.d2;
@@ -1447,10 +1451,11 @@ int dd_adjoint_impl(hw_dd* dd, int nsteps, const double* dts, const int* gauge_i
         for (int c = 0; c < 3; ++c) { d.X[3 + c] = T.dbx[k - 1][c]; d.Y[3 + c] = T.dby[k - 1][c]; }
         d.X[0] = T.fx[k - 1];
         d.Y[0] = T.fy[k - 1];
+        const cudaStream_t bs = bl[p].v.stream;
         hw::launch_finish_alpha2d(d, keys + 2 * np, T.alpha + 2 * (k - 1), nullptr, bl[p].v.params->cfl, nullptr, -1.0,
-                                  st);
-        hw::launch_sweep_x2d(d, T.alpha + 2 * (k - 1), false, true, st);
-        hw::launch_sweep_y2d(d, T.alpha + 2 * (k - 1), false, true, st);
+                                  bs);
+        hw::launch_sweep_x2d(d, T.alpha + 2 * (k - 1), false, true, bs);
+        hw::launch_sweep_y2d(d, T.alpha + 2 * (k - 1), false, true, bs);
         hw::StageArgs sa{};
         sa.k = k;
         sa.limiter = bl[p].v.params->limiter;
@@ -1459,8 +1464,9 @@ int dd_adjoint_impl(hw_dd* dd, int nsteps, const double* dts, const int* gauge_i
           sa.out[q] = k < 3 ? T.in[k][q] : T.out[q];
           sa.base[q] = bl[p].v.base[q];
         }
-        hw::launch_node2d(d, sa, hw::MODE_STAGE, false, true, st);
+        hw::launch_node2d(d, sa, hw::MODE_STAGE, false, true, bs);
       }
+      if ((rc = hw::dd_join_blocks(dd, st))) break;
     }
     for (int p = 0; p < np && rc == HW_OK; ++p)
       if (bl[p].ng) {
@@ -1495,12 +1501,14 @@ int dd_adjoint_impl(hw_dd* dd, int nsteps, const double* dts, const int* gauge_i
       check(cudaMemsetAsync(lal, 0, 2 * sizeof(double), st), "hw_dd_adjoint_run: alpha adjoint");
       check(cudaMemsetAsync(lal + 2, 0x7f, 2 * sizeof(int), st), "hw_dd_adjoint_run: alpha node");
       std::vector<hw::AdjDev> A(np);
+      if (rc == HW_OK) rc = hw::dd_fork_blocks(dd, st);
       for (int p = 0; p < np && rc == HW_OK; ++p) {
         A[p] = stage_args(bl[p].v, bl[p].B, layout[p].step(bl[p].tape, j), dts[j], k, cur);
         A[p].lalpha = lal;
         A[p].argmax = (int*)(lal + 2);
-        rc = reverse_stage_body(bl[p].v, bl[p].B, A[p]);
+        rc = reverse_stage_body(bl[p].v, bl[p].B, A[p]);  // on the block's stream
       }
+      if (rc == HW_OK) rc = hw::dd_join_blocks(dd, st);
       for (int p = 0; p < np && rc == HW_OK; ++p) {
         const hw_part_info& I = bl[p].info;
         hw::k_adj_alpha_find_block<<<std::min((I.nx * I.ny + 255) / 256, 152 * 8), 256, 0, st>>>(A[p], I.nx, I.ny, I.i0,
@@ -1535,12 +1543,14 @@ int dd_adjoint_impl(hw_dd* dd, int nsteps, const double* dts, const int* gauge_i
   }
   std::vector<double*> stat_planes(3 * (size_t)np);
   std::vector<double* const*> sp(np);
+  if (rc == HW_OK) rc = hw::dd_fork_blocks(dd, st);
   for (int p = 0; p < np && rc == HW_OK; ++p) {
     for (int q = 0; q < 3; ++q) stat_planes[3 * (size_t)p + q] = bl[p].B->lstatic_phys[q];
     sp[p] = stat_planes.data() + 3 * (size_t)p;
-    rc = zero_planes(bl[p].B->lstatic_phys, 3, bl[p].v.n, st);
+    rc = zero_planes(bl[p].B->lstatic_phys, 3, bl[p].v.n, bl[p].v.stream);
     if (rc == HW_OK) rc = finish_static(bl[p].v, bl[p].B, bl[p].B->lstatic_phys);
   }
+  if (rc == HW_OK) rc = hw::dd_join_blocks(dd, st);
   if (rc == HW_OK) rc = hw::dd_exchange_adjoint(dd, sp.data(), 3, kStatOddX, kStatOddY, st);
   for (int p = 0; p < np && rc == HW_OK; ++p) {
     const hw_part_info& I = bl[p].info;
@@ -1557,7 +1567,8 @@ int dd_adjoint_impl(hw_dd* dd, int nsteps, const double* dts, const int* gauge_i
 }
 }  // namespace
 
-// The blocks' own streams are set aside for the run: its kernels interleave the blocks on the main stream.
+// The main stream orders the run: the exchanges, the alpha reductions and the gauges run on it, each
+// block's stages on the block's own stream between a fork and a join.
 extern "C" int hw_dd_adjoint_run(hw_dd* dd, int nsteps, const double* dts, const int* gauge_idx, int ngauge,
                                  const double* eta_obs, double* loss_out, double* const* grad_state,
                                  double* const* grad_static) {
@@ -1568,15 +1579,10 @@ extern "C" int hw_dd_adjoint_run(hw_dd* dd, int nsteps, const double* dts, const
   const hw_grid* grid = nullptr;
   int rc = hw::dd_blocks(dd, &np, &parts, &infos, &st, &grid);
   if (rc) return rc;
-  std::vector<cudaStream_t> own(np);
-  for (int p = 0; p < np; ++p) {
-    own[p] = hw::solver_stream(parts[p]);
-    ACUDA(cudaStreamSynchronize(own[p]));
-  }
   ACUDA(cudaStreamSynchronize(st));
-  for (int p = 0; p < np; ++p) hw::solver_swap_stream(parts[p], st);
+  for (int p = 0; p < np; ++p) ACUDA(cudaStreamSynchronize(hw::solver_stream(parts[p])));
   rc = dd_adjoint_impl(dd, nsteps, dts, gauge_idx, ngauge, eta_obs, loss_out, grad_state, grad_static);
   cudaStreamSynchronize(st);
-  for (int p = 0; p < np; ++p) hw::solver_swap_stream(parts[p], own[p]);
+  for (int p = 0; p < np; ++p) cudaStreamSynchronize(hw::solver_stream(parts[p]));
   return rc;
 }

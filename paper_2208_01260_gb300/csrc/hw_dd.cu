@@ -354,6 +354,9 @@ int dd_drain(hw_dd* d) {
 
 namespace hw {
 
+int dd_fork_blocks(hw_dd* d, cudaStream_t st) { return dd_fork(d, st); }
+int dd_join_blocks(hw_dd* d, cudaStream_t st) { return dd_join(d, st); }
+
 int dd_blocks(hw_dd* d, int* np, hw_solver* const** parts, const hw_part_info** info, cudaStream_t* st,
               const hw_grid** grid) {
   if (!d) return set_last_error(HW_ERR_ARG, "null block decomposition");

@@ -149,6 +149,9 @@ int dd_exchange_planes(hw_dd* d, double* const* const* planes, int nplanes, unsi
                        cudaStream_t st);
 int dd_exchange_adjoint(hw_dd* d, double* const* const* planes, int nplanes, unsigned oddx, unsigned oddy,
                         cudaStream_t st);
+// every block's stream waits for st (fork); st waits for every block's stream (join)
+int dd_fork_blocks(hw_dd* d, cudaStream_t st);
+int dd_join_blocks(hw_dd* d, cudaStream_t st);
 int solver_set_state_planes(hw_solver* s, double* const* src);  // device copy into the current state
 void adjoint_release(hw_solver* s);  // frees a solver's adjoint working buffers; hw_destroy calls it
 
