@@ -235,8 +235,8 @@ def oracle_rate(seconds_budget=60.0):
 def batched_compare(steps, n_inst=512, fixed=None):
     """Config 4: n_inst grids with nx, ny log-uniform in [64, 1024] (or all of size `fixed`) on
     [0,1]^2, reflective, seeded bathymetry and surface hump, each at its own CFL dt. Aggregate
-    point-updates/s of the batched form (one launch per phase over all grids, CUDA graph) and of the
-    plain loop (one single-grid solver per instance advanced one step at a time: with the library's
+    point-updates/s of the batched form (one launch per phase over all grids, CUDA graph; then the same
+    batch with one cooperative launch per step) and of the plain loop (one single-grid solver per instance advanced one step at a time: with the library's
     cfl_dt() and rk3_step(dt), and, as a stronger baseline, with the device-side dt of hw_advance)."""
     import torch
     import paper_2208_01260_gb300 as hw
@@ -258,6 +258,19 @@ def batched_compare(steps, n_inst=512, fixed=None):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_b = e0.elapsed_time(e1)
+    # the same batch (same tiles, states carried on) with one cooperative launch per step
+    b.set_persistent(True)
+    b.run(4, use_graph=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.run(steps, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1)
+    blocks = hw.hw_batch_get_persistent(b.h)[1]
+    ph = hw.hw_batch_get_phase_times(b.h)  # the last timed step, per stage
+    phases = {name: sum(ph["stage%d_%s" % (k, name)] for k in (1, 2, 3)) / 3
+              for name in ("alpha_coarse", "alpha_exact", "alpha_dt", "sweeps", "node")}
     b.close()
     solvers = [hw.Solver.from_scenario(sc, hw.make_params()) for sc in scs]
 
@@ -282,6 +295,7 @@ def batched_compare(steps, n_inst=512, fixed=None):
     for s in solvers:
         s.close()
     vb = pts * STAGES * steps / (ms_b * 1e-3)
+    vpers = pts * STAGES * steps / (ms_p * 1e-3)
     vp = pts * STAGES * steps / (ms["api"] * 1e-3)
     vd = pts * STAGES * steps / (ms["device_dt"] * 1e-3)
     return {"instances": n_inst, "total_points": int(pts), "steps": steps, "value_batched": vb, "value_plain": vp,
@@ -290,6 +304,11 @@ def batched_compare(steps, n_inst=512, fixed=None):
             "value_plain_device_dt": vd, "ratio_vs_device_dt_loop": vb / vd,
             "ms_per_step_plain_device_dt": ms["device_dt"] / steps,
             "plain_device_dt": "per instance per step: hw_advance(1 step), dt found and applied on the device",
+            "value_batched_persistent": vpers, "ratio_persistent": vpers / vp,
+            "ms_per_step_batched_persistent": ms_p / steps,
+            "persistent_phase_ms_per_stage": phases,
+            "persistent": "one cooperative launch of %d blocks per step, phases separated by grid barriers "
+                          "(value_batched: 12 launches per step, one per phase)" % blocks,
             "unit": UNIT, "tiles": "autotuned per size class"}
 
 

@@ -191,6 +191,30 @@ int hw_batch_get_tiles(hw_batch* b, int i, int* yc);
 /* Autotuner measurement: average ms of the batched x-sweep and y-sweep over the grids ids[nids] with
  * the trial y-tile width yc, over reps repetitions. Changes no state (interface planes are scratch). */
 int hw_batch_time_tiles(hw_batch* b, int nids, const int* ids, int yc, int reps, double* ms_x, double* ms_y);
+/* Launch form of hw_batch_run (no counterpart in the paper). on = 0 (default): each phase of an RK stage
+ * is one launch over all grids (12 launches and 3 small key resets per step). on = 1: each step is ONE
+ * cooperative launch of as many blocks as the device holds at once (two small resets before it); its
+ * phases (the two alpha passes, the per-grid alpha and dt, both sweeps, the node update; three times) are
+ * separated by grid-wide barriers, and sweep tiles and node items are taken from counters. Each barrier
+ * wait is bounded (about 10 s): if one runs out, every block leaves the launch and hw_batch_run returns
+ * HW_ERR_TIMEOUT (the state is then undefined). The results equal the default form's to rounding.
+ * hw_batch_set_persistent returns HW_ERR_CUDA if the device cannot launch the step kernel cooperatively,
+ * HW_ERR_ARG for on other than 0 or 1; a switch drops the captured graph. hw_batch_get_persistent
+ * gives the form and the step kernel's block count (0 before the first switch to on = 1). */
+int hw_batch_set_persistent(hw_batch* b, int on);
+int hw_batch_get_persistent(hw_batch* b, int* on, int* blocks);
+/* Test of the persistent step's bounded barrier wait (after hw_batch_set_persistent(b, 1)): one launch in
+ * which block 0 leaves before the first grid barrier, with a 2 ms bound; the other blocks' waits run out
+ * and every block leaves. Returns HW_ERR_TIMEOUT when the bound worked (HW_OK would mean a barrier
+ * passed without block 0). The state, times and the context stay usable: the alpha keys, which every
+ * step resets, are the only memory written. HW_ERR_STATE before hw_batch_set_persistent(b, 1). */
+int hw_batch_test_barrier_timeout(hw_batch* b);
+/* Phase durations of the last persistent step launch, ms[15] in ms: for each RK stage the alpha coarse
+ * pass, the alpha exact pass, the per-grid alpha and dt, both sweeps, the node update (from the device's
+ * global timer read by block 0 as it leaves each grid barrier; the last phase ends with the last block).
+ * -1 for a phase the launch did not reach. Synchronises the stream. HW_ERR_STATE unless the batch is in
+ * the persistent form. */
+int hw_batch_get_phase_times(hw_batch* b, double* ms);
 
 /* ---------------------------------------------------------------------------------------------
  * Discrete adjoint (2D, nonlinear weights and characteristic projection; limiter on or off).

@@ -35,7 +35,8 @@ __all__ = [
     "hw_advance", "hw_get_state", "hw_set_state", "hw_get_base", "hw_sync", "hw_version", "Solver",
     "hw_set_profiling", "hw_get_profile", "hw_get_time", "hw_set_time", "hw_rhs1d_noalloc", "hw_selftest_fp64_int", "hw_measure_fp64_peak", "BatchedSolver", "hw_batch_create",
     "hw_batch_destroy", "hw_batch_init", "hw_batch_run", "hw_batch_get_state", "hw_batch_get_time",
-    "hw_batch_set_tiles", "hw_batch_get_tiles", "hw_batch_time_tiles",
+    "hw_batch_set_tiles", "hw_batch_get_tiles", "hw_batch_time_tiles", "hw_batch_set_persistent",
+    "hw_batch_get_persistent", "hw_batch_test_barrier_timeout", "hw_batch_get_phase_times",
     "hw_part_info", "hw_dd_partition", "hw_part_create", "hw_part_init", "hw_part_finish_init", "hw_halo_strip_size",
     "hw_halo_pack", "hw_halo_unpack", "hw_part_alpha_keys", "hw_part_stage", "hw_dd_create", "hw_dd_init",
     "hw_dd_advance", "hw_dd_get_state", "hw_dd_destroy", "hw_dd_max_keys", "hw_dd_adjoint_run", "DecomposedSolver",
@@ -548,6 +549,10 @@ def _batch_sigs():
         "hw_batch_set_tiles": [vp, i, i],
         "hw_batch_get_tiles": [vp, i, C.POINTER(i)],
         "hw_batch_time_tiles": [vp, i, C.POINTER(i), i, i, C.POINTER(d), C.POINTER(d)],
+        "hw_batch_set_persistent": [vp, i],
+        "hw_batch_get_persistent": [vp, C.POINTER(i), C.POINTER(i)],
+        "hw_batch_test_barrier_timeout": [vp],
+        "hw_batch_get_phase_times": [vp, C.POINTER(d)],
     }.items():
         f = getattr(L, name)
         f.argtypes = args
@@ -621,10 +626,41 @@ def hw_batch_time_tiles(b: _BHandle, ids: Sequence[int], yc: int, reps: int = 3)
     return mx.value, my.value
 
 
-class BatchedSolver:
-    """Many 2D grids advancing together (one launch per phase over all grids, CUDA graph)."""
+def hw_batch_set_persistent(b: _BHandle, on: bool):
+    """on: one cooperative launch per step (phases separated by bounded grid barriers); off: one launch per
+    phase (the default)."""
+    _check(_batch_sigs().hw_batch_set_persistent(b.ptr, int(bool(on))), "hw_batch_set_persistent")
 
-    def __init__(self, scenarios, params: Optional[hw_params] = None, stream=None):
+
+def hw_batch_get_persistent(b: _BHandle):
+    """(on, blocks): the launch form and the persistent step kernel's block count."""
+    on, blocks = C.c_int(), C.c_int()
+    _check(_batch_sigs().hw_batch_get_persistent(b.ptr, C.byref(on), C.byref(blocks)), "hw_batch_get_persistent")
+    return bool(on.value), blocks.value
+
+
+def hw_batch_test_barrier_timeout(b: _BHandle) -> int:
+    """One persistent step launch in which block 0 never reaches the first grid barrier (2 ms bound); returns
+    the C code: HW_ERR_TIMEOUT (-5) when the bounded wait worked."""
+    return int(_batch_sigs().hw_batch_test_barrier_timeout(b.ptr))
+
+
+BSTEP_PHASE_NAMES = [f"stage{k}_{p}" for k in (1, 2, 3) for p in ("alpha_coarse", "alpha_exact", "alpha_dt",
+                                                                   "sweeps", "node")]
+
+
+def hw_batch_get_phase_times(b: _BHandle) -> dict:
+    """Phase durations (ms) of the last persistent step launch, keyed by BSTEP_PHASE_NAMES."""
+    ms = (C.c_double * 15)()
+    _check(_batch_sigs().hw_batch_get_phase_times(b.ptr, ms), "hw_batch_get_phase_times")
+    return dict(zip(BSTEP_PHASE_NAMES, ms[:]))
+
+
+class BatchedSolver:
+    """Many 2D grids advancing together, with a CUDA graph of two steps: one launch per phase over all grids
+    (persistent=False), or one cooperative launch per step (persistent=True)."""
+
+    def __init__(self, scenarios, params: Optional[hw_params] = None, stream=None, persistent: bool = False):
         grids = [make_grid(s.nx, s.ny, s.x0, s.x1, s.y0, s.y1, s.bc_x, s.bc_y, dim=2) for s in scenarios]
         self.params = params or make_params()
         self.h = hw_batch_create(grids, self.params, stream)
@@ -632,6 +668,15 @@ class BatchedSolver:
         for i, s in enumerate(scenarios):
             arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in [s.h, s.hu, s.hv, s.b] + list(s.deriv)]
             hw_batch_init(self.h, i, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4:])
+        if persistent:
+            hw_batch_set_persistent(self.h, True)
+
+    def set_persistent(self, on: bool):
+        hw_batch_set_persistent(self.h, on)
+
+    @property
+    def persistent(self):
+        return hw_batch_get_persistent(self.h)[0]
 
     def close(self):
         hw_batch_destroy(self.h)

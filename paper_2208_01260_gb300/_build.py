@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libhwswe.so")
 SOURCES = ["hw_api.cu", "hw_kernels2d.cu", "hw_kernels1d.cu", "hw_noalloc.cu", "hw_batch.cu", "hw_adjoint.cu",
-           "hw_selftest.cu", "hw_peak.cu", "hw_dd.cu"]
+           "hw_selftest.cu", "hw_peak.cu", "hw_dd.cu", "hw_bstep.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

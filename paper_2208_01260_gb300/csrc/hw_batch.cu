@@ -9,66 +9,16 @@
 // rounding (the compiler may contract multiply-adds differently in the two kernels), with the same
 // share of products on the integer pipes (each bit-identical to DMUL, hw_fp64_int.h). The kernels read
 // the pooled planes through the parameters' base pointers plus the instance's offsets, so that no
-// per-instance pointer takes a register. No block ever waits on another block.
+// per-instance pointer takes a register. No block ever waits on another block. hw_batch_set_persistent
+// switches a batch to one cooperative launch per step instead (hw_bstep.cu).
 #include <algorithm>
 #include <string>
 #include <vector>
 
 #include "../../include/hwswe.h"
-#include "hw_stencil2d.cuh"
+#include "hw_batch.cuh"
 
 namespace hw {
-
-struct BInst {
-  int nx, ny, bc_x, bc_y;
-  double dx, dy, inv_dx, inv_dy, c_bx, c_by, c_gx, c_gy, c_mx, c_my;
-  long long off_n, off_x, off_y;  // offsets of this grid in the pooled node / x-interface / y-interface planes
-  int yc;                          // columns per y-tile group (1, 2 or 4; TILE_T / yc extended rows per tile)
-};
-
-struct BatchDev {
-  double g, eps_w, eps_lim, cfl;
-  int limiter, k;
-  const BInst* inst;
-  double* S[9];
-  double* stat[3];
-  double* bxy[2];
-  double* X[12];
-  double* Y[12];
-  double* qbx[6];
-  double* qby[6];
-  double* sv[2];
-  double* sq[2];
-  double* out[9];
-  double* base[9];
-  unsigned long long* amax;  // 3 per instance: alpha_x, alpha_y keys, the coarse pass's float maxima
-  double* alpha;             // 2 per instance
-  double* dt;                // 2 per instance: step, time after the step
-  double* t;                 // 1 per instance
-  unsigned long long* nsteps;
-  int* status;
-};
-
-// The instance's grid constants with the pooled planes' base pointers (they stay in the kernel parameters;
-// the kernels add the instance's offsets I.off_n, I.off_x, I.off_y to their indices).
-__device__ __forceinline__ void make_dev(const BatchDev& B, const BInst& I, Dev2D& d) {
-  d.nx = I.nx; d.ny = I.ny; d.bc_x = I.bc_x; d.bc_y = I.bc_y;
-  d.dx = I.dx; d.dy = I.dy; d.inv_dx = I.inv_dx; d.inv_dy = I.inv_dy;
-  d.g = B.g; d.eps_w = B.eps_w; d.eps_lim = B.eps_lim;
-  d.c_bx = I.c_bx; d.c_by = I.c_by; d.c_gx = I.c_gx; d.c_gy = I.c_gy; d.c_mx = I.c_mx; d.c_my = I.c_my;
-#pragma unroll
-  for (int q = 0; q < 9; ++q) d.S[q] = B.S[q];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) d.stat[q] = B.stat[q];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) d.bxy[q] = B.bxy[q];
-#pragma unroll
-  for (int q = 0; q < 12; ++q) { d.X[q] = B.X[q]; d.Y[q] = B.Y[q]; }
-#pragma unroll
-  for (int q = 0; q < 6; ++q) { d.qbx[q] = B.qbx[q]; d.qby[q] = B.qby[q]; }
-#pragma unroll
-  for (int q = 0; q < 2; ++q) { d.sv[q] = B.sv[q]; d.sq[q] = B.sq[q]; }
-}
 
 constexpr int BN_T = 256;  // nodes per node-kernel item
 
@@ -238,8 +188,12 @@ struct hw_batch {
   size_t max_n = 0;
   hw::BatchDev B{};
   // work lists
-  int4* d_items[4] = {};  // alpha, x, y, node
-  int nitems[4] = {};
+  int4* d_items[5] = {};  // alpha, x, y, node (BN_T nodes), node (TILE_T nodes, persistent step)
+  int nitems[5] = {};
+  // persistent step: one cooperative launch per step over bstep_blocks resident blocks
+  bool persistent = false;
+  int bstep_blocks = 0;
+  hw::StepSync* d_sync = nullptr;
   int nb[1] = {1};  // blocks of the alpha passes (resident blocks on the device; they loop over items)
   std::vector<bool> inited;
   bool dirty = false;  // tile shapes changed since the work lists were built
@@ -272,9 +226,10 @@ hw::Dev2D dev_of(hw_batch* b, int i, double** S) {
 }
 
 // Work lists of a subset of instances: alpha (inst, first node, count), x-sweep tiles (inst, first
-// extended node), y-sweep tiles (inst, first extended row of a column group), node items (inst, first node).
-void build_items(const std::vector<hw::BInst>& inst, const std::vector<int>& ids, std::vector<int4> out[4]) {
-  for (int p = 0; p < 4; ++p) out[p].clear();
+// extended node), y-sweep tiles (inst, first extended row of a column group), node items (inst, first node)
+// of BN_T nodes for the node kernel and of TILE_T nodes for the persistent step.
+void build_items(const std::vector<hw::BInst>& inst, const std::vector<int>& ids, std::vector<int4> out[5]) {
+  for (int p = 0; p < 5; ++p) out[p].clear();
   for (int i : ids) {
     const hw::BInst& I = inst[i];
     const int n = I.nx * I.ny;
@@ -285,11 +240,12 @@ void build_items(const std::vector<hw::BInst>& inst, const std::vector<int>& ids
     const long long ty = (long long)((I.nx + I.yc - 1) / I.yc) * (I.ny + 4);
     for (long long e = 0; e < ty; e += ifs) out[2].push_back(make_int4(i, (int)e, 0, 0));
     for (int o = 0; o < n; o += hw::BN_T) out[3].push_back(make_int4(i, o, 0, 0));
+    for (int o = 0; o < n; o += hw::TILE_T) out[4].push_back(make_int4(i, o, 0, 0));
   }
 }
 
-int upload_items(hw_batch* b, std::vector<int4> lists[4], int4** dst, int* counts) {
-  for (int p = 0; p < 4; ++p) {
+int upload_items(hw_batch* b, std::vector<int4> lists[5], int4** dst, int* counts) {
+  for (int p = 0; p < 5; ++p) {
     if (dst[p]) { cudaFree(dst[p]); dst[p] = nullptr; }
     counts[p] = (int)lists[p].size();
     if (counts[p] == 0) continue;
@@ -343,7 +299,35 @@ void enqueue_alpha(hw_batch* b, int with_dt, cudaStream_t st) {
   hw::k_bfinish<<<(b->n + 127) / 128, 128, 0, st>>>(b->B, b->n, with_dt);
 }
 
+// The persistent step: the keys and the barrier counters start at zero, then one cooperative launch.
+// drop_block >= 0 only in the test of the bounded barrier wait (that block leaves at once; short limits).
+void enqueue_bstep(hw_batch* b, cudaStream_t st, int drop_block = -1) {
+  hw::BatchDev B = b->B;
+  for (int q = 0; q < 9; ++q) {
+    B.S[q] = b->SA[q];
+    B.out[q] = b->SB[q];
+  }
+  hw::StepItems P{};
+  P.alpha = b->d_items[0]; P.n_alpha = b->nitems[0];
+  P.x = b->d_items[1]; P.n_x = b->nitems[1];
+  P.y = b->d_items[2]; P.n_y = b->nitems[2];
+  P.node = b->d_items[4]; P.n_node = b->nitems[4];
+  P.n_inst = b->n;
+  P.sync = b->d_sync;
+  P.limit_ns = drop_block < 0 ? hw::BSTEP_LIMIT_NS : 2000000ull;  // 2 ms in the test
+  P.limit_polls = drop_block < 0 ? hw::BSTEP_LIMIT_POLLS : (1u << 16);
+  P.drop_block = drop_block;
+  cudaMemsetAsync(b->B.amax, 0, 3 * sizeof(unsigned long long) * b->n, st);
+  cudaMemsetAsync(b->d_sync, 0, sizeof(hw::StepSync), st);
+  hw::launch_bstep(B, P, b->cur, b->bstep_blocks, b->params.linear_weights != 0, b->params.char_decomp != 0, st);
+  if (drop_block < 0) b->cur ^= 1;  // three stages: the step's result is in the other plane set
+}
+
 void enqueue_step(hw_batch* b, cudaStream_t st) {
+  if (b->persistent) {
+    enqueue_bstep(b, st);
+    return;
+  }
   for (int k = 1; k <= 3; ++k) {
     enqueue_alpha(b, k == 1, st);
     b->B.k = k;
@@ -357,7 +341,7 @@ void enqueue_step(hw_batch* b, cudaStream_t st) {
 int rebuild(hw_batch* b) {
   std::vector<int> ids(b->n);
   for (int i = 0; i < b->n; ++i) ids[i] = i;
-  std::vector<int4> lists[4];
+  std::vector<int4> lists[5];
   build_items(b->inst, ids, lists);
   BCUDA(cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(hw::BInst) * b->n, cudaMemcpyHostToDevice, b->stream));
   int rc = upload_items(b, lists, b->d_items, b->nitems);
@@ -416,6 +400,7 @@ int hw_batch_create(int n, const hw_grid* grids, const hw_params* params, void* 
   double* misc = nullptr;
   A(&misc, (size_t)9 * n + 8);
   if (rc == HW_OK) rc = balloc(b, (void**)&b->d_inst, sizeof(hw::BInst) * n);
+  if (rc == HW_OK) rc = balloc(b, (void**)&b->d_sync, sizeof(hw::StepSync));
   if (rc != HW_OK) { hw_batch_destroy(b); return rc; }
   b->B.amax = (unsigned long long*)misc;
   b->B.alpha = misc + 3 * n;
@@ -447,7 +432,7 @@ int hw_batch_destroy(hw_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->stream) cudaStreamSynchronize(b->stream);
   else cudaDeviceSynchronize();
-  for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < 5; ++p)
     if (b->d_items[p]) cudaFree(b->d_items[p]);
   for (void* p : b->allocs) cudaFree(p);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -527,8 +512,65 @@ int hw_batch_run(hw_batch* b, int nsteps, int use_graph) {
   BCUDA(cudaMemcpy(&st, b->B.status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st) {
     BCUDA(cudaMemset(b->B.status, 0, sizeof(int)));
+    if (st & hw::HW_STATUS_TIMEOUT)
+      return bfail(HW_ERR_TIMEOUT, "hw_batch_run: a grid barrier of the persistent step timed out");
     return bfail(HW_ERR_DEPTH, "hw_batch_run: non-positive or non-finite depth in some instance");
   }
+  return HW_OK;
+}
+
+int hw_batch_set_persistent(hw_batch* b, int on) {
+  if (!b || (on != 0 && on != 1)) return bfail(HW_ERR_ARG, "hw_batch_set_persistent: bad argument");
+  if (on && b->bstep_blocks == 0) {
+    b->bstep_blocks = hw::bstep_grid(b->params.linear_weights != 0, b->params.char_decomp != 0);
+    if (b->bstep_blocks == 0)
+      return bfail(HW_ERR_CUDA, "hw_batch_set_persistent: the device cannot launch the step kernel cooperatively");
+  }
+  if ((bool)on != b->persistent && b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->persistent = on != 0;
+  return HW_OK;
+}
+
+// One step launch with block 0 leaving before the first grid barrier: the other blocks' waits run out
+// after 2 ms (or 2^16 polls) and every block leaves. The keys are the only memory written.
+int hw_batch_test_barrier_timeout(hw_batch* b) {
+  if (!b) return bfail(HW_ERR_ARG, "hw_batch_test_barrier_timeout: null batch");
+  if (b->bstep_blocks < 2) return bfail(HW_ERR_STATE, "hw_batch_test_barrier_timeout: call hw_batch_set_persistent(b, 1) first");
+  for (int i = 0; i < b->n; ++i)
+    if (!b->inited[i]) return bfail(HW_ERR_STATE, "hw_batch_test_barrier_timeout: every instance must be initialised");
+  if (b->dirty) {
+    int rc = rebuild(b);
+    if (rc != HW_OK) return rc;
+    b->dirty = false;
+  }
+  enqueue_bstep(b, b->stream, 0);
+  BCUDA(cudaGetLastError());
+  BCUDA(cudaStreamSynchronize(b->stream));
+  int st = 0;
+  BCUDA(cudaMemcpy(&st, b->B.status, sizeof(int), cudaMemcpyDeviceToHost));
+  BCUDA(cudaMemset(b->B.status, 0, sizeof(int)));
+  if (st & hw::HW_STATUS_TIMEOUT) return bfail(HW_ERR_TIMEOUT, "hw_batch_test_barrier_timeout: the barrier wait ran out");
+  return HW_OK;
+}
+
+int hw_batch_get_phase_times(hw_batch* b, double* ms) {
+  if (!b || !ms) return bfail(HW_ERR_ARG, "hw_batch_get_phase_times: bad argument");
+  if (!b->persistent) return bfail(HW_ERR_STATE, "hw_batch_get_phase_times: the batch is not in the persistent form");
+  hw::StepSync s{};
+  BCUDA(cudaStreamSynchronize(b->stream));
+  BCUDA(cudaMemcpy(&s, b->d_sync, sizeof(s), cudaMemcpyDeviceToHost));
+  for (int p = 0; p < hw::BSTEP_PHASES; ++p)
+    ms[p] = (s.t[p + 1] >= s.t[p] && s.t[p] != 0) ? (double)(s.t[p + 1] - s.t[p]) * 1e-6 : -1.0;
+  return HW_OK;
+}
+
+int hw_batch_get_persistent(hw_batch* b, int* on, int* blocks) {
+  if (!b) return bfail(HW_ERR_ARG, "hw_batch_get_persistent: null batch");
+  if (on) *on = b->persistent ? 1 : 0;
+  if (blocks) *blocks = b->bstep_blocks;
   return HW_OK;
 }
 
@@ -593,10 +635,10 @@ int hw_batch_time_tiles(hw_batch* b, int nids, const int* ids, int yc, int reps,
     if (i < 0 || i >= b->n) return bfail(HW_ERR_ARG, "hw_batch_time_tiles: bad instance id");
     trial[i].yc = yc;
   }
-  std::vector<int4> lists[4];
+  std::vector<int4> lists[5];
   build_items(trial, sub, lists);
-  int4* items[4] = {};
-  int counts[4] = {};
+  int4* items[5] = {};
+  int counts[5] = {};
   BCUDA(cudaMemcpyAsync(b->d_inst, trial.data(), sizeof(hw::BInst) * b->n, cudaMemcpyHostToDevice, b->stream));
   int rc = upload_items(b, lists, items, counts);
   if (rc) return rc;
@@ -619,7 +661,7 @@ int hw_batch_time_tiles(hw_batch* b, int nids, const int* ids, int yc, int reps,
     ty_ms += c;
   }
   cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
-  for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < 5; ++p)
     if (items[p]) cudaFree(items[p]);
   BCUDA(cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(hw::BInst) * b->n, cudaMemcpyHostToDevice, b->stream));
   BCUDA(cudaStreamSynchronize(b->stream));

@@ -17,8 +17,18 @@ struct Node12T {
 };
 using Node12 = Node12T<double>;
 
+// Load of a plane that changes between launches. COH = false: through the read-only data path (valid
+// while no block of the running kernel writes the plane). COH = true: an ordinary global load, for a
+// kernel whose later phases read what its earlier phases wrote (a persistent kernel with grid
+// barriers); the read-only path is not kept coherent with such writes.
+template <bool COH, class T>
+__device__ __forceinline__ T ldp(const T* p) {
+  if constexpr (COH) return *p;
+  else return __ldg(p);
+}
+
 // base: offset of the grid's first node in the node planes (0 unless the planes pool several grids).
-template <class R>
+template <bool COH = false, class R>
 __device__ __forceinline__ void load_node(const Dev2DT<R>& d, int i, int j, Node12T<R>& n, size_t base = 0) {
   bool fx, fy;
   const int ii = map_index(i, d.nx, d.bc_x, fx);
@@ -26,7 +36,7 @@ __device__ __forceinline__ void load_node(const Dev2DT<R>& d, int i, int j, Node
   const size_t o = base + (size_t)jj * d.nx + ii;
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
-    R x = __ldg(d.S[q] + o);
+    R x = ldp<COH>(d.S[q] + o);
     if (fx) x *= R(par_x2d(q));
     if (fy) x *= R(par_y2d(q));
     n.v[q] = x;
@@ -255,13 +265,14 @@ __device__ __forceinline__ float d2f_trunc(double x, bool& tiny, bool& huge) {
 // Float estimates of |u| + c and |v| + c at node o from the depth formed in double. exact: the node
 // needs the double evaluation regardless (a depth or momentum outside float's range, NaN, infinity);
 // neg: the depth is negative.
+template <bool COH = false>
 __device__ __forceinline__ void alpha_coarse(const Dev2D& d, size_t o, float& ax, float& ay, bool& exact,
                                              bool& neg) {
-  const double hd = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
+  const double hd = ldp<COH>(d.S[0] + o) - __ldg(d.stat[0] + o);
   bool t0, h0, t1, h1, t2, h2;
   const float h = d2f_trunc(hd, t0, h0);
-  const float m = d2f_trunc(__ldg(d.S[1] + o), t1, h1);
-  const float w = d2f_trunc(__ldg(d.S[2] + o), t2, h2);
+  const float m = d2f_trunc(ldp<COH>(d.S[1] + o), t1, h1);
+  const float w = d2f_trunc(ldp<COH>(d.S[2] + o), t2, h2);
   exact = t0 || h0 || h1 || h2;
   neg = h < 0.0f;
   const float rh = fast_rcp(h);
@@ -273,6 +284,35 @@ __device__ __forceinline__ void alpha_coarse(const Dev2D& d, size_t o, float& ax
 
 // The exact pass over nodes o = begin, begin + step, ... < end, with the coarse maxima m32[0..1]: keys of
 // the double maxima into kx, ky and status flags into bad.
+// The double evaluation of the exact pass at node o: keys of |u| + c and |v| + c into kx, ky (maxima),
+// status flags into bad.
+template <bool COH = false>
+__device__ __forceinline__ void alpha_exact_node(const Dev2D& d, size_t o, unsigned long long& kx,
+                                                 unsigned long long& ky, int& bad) {
+  const double hd = ldp<COH>(d.S[0] + o) - __ldg(d.stat[0] + o);
+  if (!(hd > 0.0) || !(hd < 1e300)) {
+    bad |= hd == hd ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE;
+    return;
+  }
+  const double rh = fast_rcp(hd);
+  const double gh = d.g * hd;
+  const double c = gh * fast_rsqrt(gh);
+  const double ax = dabs(ldp<COH>(d.S[1] + o) * rh) + c, ay = dabs(ldp<COH>(d.S[2] + o) * rh) + c;
+  if (!(ax < 1e300) || !(ay < 1e300)) {
+    bad |= HW_STATUS_NONFINITE;
+    return;
+  }
+  kx = max(kx, dkey(ax));
+  ky = max(ky, dkey(ay));
+}
+
+// Whether the exact pass evaluates a node, from its coarse estimates and the thresholds tx, ty (the coarse
+// maxima lowered by the estimates' error bound).
+__device__ __forceinline__ bool alpha_needs_exact(float fx, float fy, bool exact, bool neg, float tx, float ty) {
+  return exact || (!neg && !(fx < tx && fy < ty));
+}
+
+template <bool COH = false>
 __device__ __forceinline__ void alpha_exact_range(const Dev2D& d, const unsigned int* m32, size_t begin, size_t end,
                                                   size_t step, unsigned long long& kx, unsigned long long& ky,
                                                   int& bad) {
@@ -280,17 +320,8 @@ __device__ __forceinline__ void alpha_exact_range(const Dev2D& d, const unsigned
   for (size_t o = begin; o < end; o += step) {
     float fx, fy;
     bool exact, neg;
-    alpha_coarse(d, o, fx, fy, exact, neg);
-    if (!exact && (neg || (fx < tx && fy < ty))) continue;
-    const double hd = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
-    if (!(hd > 0.0) || !(hd < 1e300)) { bad |= hd == hd ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE; continue; }
-    const double rh = fast_rcp(hd);
-    const double gh = d.g * hd;
-    const double c = gh * fast_rsqrt(gh);
-    const double ax = dabs(__ldg(d.S[1] + o) * rh) + c, ay = dabs(__ldg(d.S[2] + o) * rh) + c;
-    if (!(ax < 1e300) || !(ay < 1e300)) { bad |= HW_STATUS_NONFINITE; continue; }
-    kx = max(kx, dkey(ax));
-    ky = max(ky, dkey(ay));
+    alpha_coarse<COH>(d, o, fx, fy, exact, neg);
+    if (alpha_needs_exact(fx, fy, exact, neg, tx, ty)) alpha_exact_node<COH>(d, o, kx, ky, bad);
   }
 }
 
@@ -306,11 +337,11 @@ __device__ __forceinline__ void alpha_exact_range(const Dev2D& d, const unsigned
 // tile: tiles run across line ends, so no grid size leaves a ragged tile. All TILE_T threads must call;
 // sm holds NREC * TILE_T values. on / oi: offsets of the grid in pooled node / interface planes (the
 // batched form keeps the planes' base pointers in the kernel parameters and adds these, so that no
-// per-grid pointer occupies a register).
+// per-grid pointer occupies a register). COH: state loads as in ldp.
 // ---------------------------------------------------------------------------------------------
 constexpr int TILE_T = 192;
 
-template <bool LINEAR, bool CHAR, bool IMUL, class R>
+template <bool LINEAR, bool CHAR, bool IMUL, bool COH = false, class R>
 __device__ __forceinline__ void sweep_x_tile(const Dev2DT<R>& d, R ax, unsigned E0, R* sm, size_t on = 0,
                                              size_t oi = 0) {
   const unsigned W = d.nx + 4, total = (unsigned)d.ny * W;
@@ -320,7 +351,7 @@ __device__ __forceinline__ void sweep_x_tile(const Dev2DT<R>& d, R ax, unsigned 
     if (E < total) {
       const unsigned j = E / W, e = E - j * W;
       Node12T<R> n;
-      load_node(d, (int)e - 2, (int)j, n, on);
+      load_node<COH>(d, (int)e - 2, (int)j, n, on);
       R rec[NREC];
       node_record<0>(n, R(d.g), ax, rec);
 #pragma unroll
@@ -342,7 +373,7 @@ __device__ __forceinline__ void sweep_x_tile(const Dev2DT<R>& d, R ax, unsigned 
   for (int q = 0; q < 12; ++q) d.X[q][o] = out[q];
 }
 
-template <bool LINEAR, bool CHAR, bool IMUL, class R>
+template <bool LINEAR, bool CHAR, bool IMUL, bool COH = false, class R>
 __device__ __forceinline__ void sweep_y_tile(const Dev2DT<R>& d, R ay, unsigned E0, int yc, R* sm, size_t on = 0,
                                              size_t oi = 0) {
   const int rows = TILE_T / yc, ifs = rows - 3;
@@ -355,7 +386,7 @@ __device__ __forceinline__ void sweep_y_tile(const Dev2DT<R>& d, R ay, unsigned 
       const int i = (int)g * yc + c;
       if (i < d.nx) {
         Node12T<R> n;
-        load_node(d, i, (int)e - 2, n, on);
+        load_node<COH>(d, i, (int)e - 2, n, on);
         R rec[NREC];
         node_record<1>(n, R(d.g), ay, rec);
 #pragma unroll
@@ -421,7 +452,8 @@ __device__ __forceinline__ void limit_dir(const R Um[3], const R U0[3], const R 
 // formed by `mul`. With MulInt nothing is written when a product left the integer fast path
 // (mul.bad); the caller then recomputes the node with MulFP64 from the same (unchanged) inputs.
 // on, oxo, oyo: offsets of the grid in pooled node, x-interface and y-interface planes (0 for one grid).
-template <int MODE, bool LINEAR, bool CHAR, class R, class M>
+// COH: loads of the state, interface and base planes as in ldp.
+template <int MODE, bool LINEAR, bool CHAR, bool COH, class R, class M>
 __device__ __forceinline__ void node_update_m(const Dev2DT<R>& d, const StageArgsT<R>& sa, int i, int j, M& mul,
                                               size_t on = 0, size_t oxo = 0, size_t oyo = 0) {
   const size_t o = on + (size_t)j * d.nx + i;
@@ -429,7 +461,7 @@ __device__ __forceinline__ void node_update_m(const Dev2DT<R>& d, const StageArg
   const size_t oy = oyo + (size_t)j * d.nx + i;        // lower y-interface; upper is oy + nx
   R cur[9];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) cur[q] = __ldg(d.S[q] + o);
+  for (int q = 0; q < 9; ++q) cur[q] = ldp<COH>(d.S[q] + o);
   if (MODE == MODE_STAGE && !(*sa.dt > 0.0)) {
     // a step of size 0 (e.g. clipped at the end time) leaves the state unchanged
 #pragma unroll
@@ -446,14 +478,14 @@ __device__ __forceinline__ void node_update_m(const Dev2DT<R>& d, const StageArg
   R Rv[9];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const R dFx = __ldg(d.X[c] + ox + 1) - __ldg(d.X[c] + ox);
-    const R dFy = __ldg(d.Y[c] + oy + d.nx) - __ldg(d.Y[c] + oy);
-    const R dbx = __ldg(d.X[3 + c] + ox + 1) - __ldg(d.X[3 + c] + ox);
-    const R dby = __ldg(d.Y[3 + c] + oy + d.nx) - __ldg(d.Y[3 + c] + oy);
-    const R dGx = __ldg(d.X[6 + c] + ox + 1) - __ldg(d.X[6 + c] + ox);
-    const R dGy = __ldg(d.Y[6 + c] + oy + d.nx) - __ldg(d.Y[6 + c] + oy);
-    const R dMx = __ldg(d.X[9 + c] + ox + 1) - __ldg(d.X[9 + c] + ox);
-    const R dMy = __ldg(d.Y[9 + c] + oy + d.nx) - __ldg(d.Y[9 + c] + oy);
+    const R dFx = ldp<COH>(d.X[c] + ox + 1) - ldp<COH>(d.X[c] + ox);
+    const R dFy = ldp<COH>(d.Y[c] + oy + d.nx) - ldp<COH>(d.Y[c] + oy);
+    const R dbx = ldp<COH>(d.X[3 + c] + ox + 1) - ldp<COH>(d.X[3 + c] + ox);
+    const R dby = ldp<COH>(d.Y[3 + c] + oy + d.nx) - ldp<COH>(d.Y[3 + c] + oy);
+    const R dGx = ldp<COH>(d.X[6 + c] + ox + 1) - ldp<COH>(d.X[6 + c] + ox);
+    const R dGy = ldp<COH>(d.Y[6 + c] + oy + d.nx) - ldp<COH>(d.Y[6 + c] + oy);
+    const R dMx = ldp<COH>(d.X[9 + c] + ox + 1) - ldp<COH>(d.X[9 + c] + ox);
+    const R dMy = ldp<COH>(d.Y[9 + c] + oy + d.nx) - ldp<COH>(d.Y[9 + c] + oy);
     const R db = fma(c_bx, dbx, mul(c_by, dby));  // [b~]_x/dx + [b-]_y/dy
     Rv[c] = fma(-ge, db, fma(-c_bx, dFx, -mul(c_by, dFy)));
     R rv = fma(-c_gx, dGx, -mul(c_my, dMy));
@@ -487,11 +519,11 @@ __device__ __forceinline__ void node_update_m(const Dev2DT<R>& d, const StageArg
     const R c = mul(gh, rs), ic2 = mul.k(R(0.5), rs);
     Node12T<R> nm, np;
     // x neighbours
-    load_node(d, i - 1, j, nm, on);
-    load_node(d, i + 1, j, np, on);
+    load_node<COH>(d, i - 1, j, nm, on);
+    load_node<COH>(d, i + 1, j, np, on);
     limit_dir<0, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 3, np.v + 3, u, v, c, ic2, gh, R(d.eps_lim), mod, mul);
-    load_node(d, i, j - 1, nm, on);
-    load_node(d, i, j + 1, np, on);
+    load_node<COH>(d, i, j - 1, nm, on);
+    load_node<COH>(d, i, j + 1, np, on);
     limit_dir<1, LINEAR, CHAR>(nm.v, cur, np.v, nm.v + 6, np.v + 6, u, v, c, ic2, gh, R(d.eps_lim), mod + 3, mul);
   } else {
 #pragma unroll
@@ -514,7 +546,7 @@ __device__ __forceinline__ void node_update_m(const Dev2DT<R>& d, const StageArg
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
       const R cq = q < 3 ? cur[q] : mod[q - 3];
-      res[q] = fma(a, __ldg(sa.base[q] + o), mul(b, fma(dt, Rv[q], cq)));
+      res[q] = fma(a, ldp<COH>(sa.base[q] + o), mul(b, fma(dt, Rv[q], cq)));
     }
     if (mul.bad) return;
 #pragma unroll
@@ -526,19 +558,19 @@ __device__ __forceinline__ void node_update_m(const Dev2DT<R>& d, const StageArg
 // the fma-contracted FP64-pipe form by rounding); if any leaves the integer fast path, the node is
 // recomputed on the FP64 pipe, so an interface or node on that fallback rounds differently from its
 // neighbours, within the same tolerances (int_mul_fallback parity case).
-template <int MODE, bool LINEAR, bool CHAR, bool IMUL = false, class R>
+template <int MODE, bool LINEAR, bool CHAR, bool IMUL = false, bool COH = false, class R>
 __device__ __forceinline__ void node_update(const Dev2DT<R>& d, const StageArgsT<R>& sa, int i, int j, size_t on = 0,
                                             size_t oxo = 0, size_t oyo = 0) {
   if constexpr (IMUL && !LINEAR && std::is_same<R, double>::value) {
     MulInt mi;
-    node_update_m<MODE, LINEAR, CHAR>(d, sa, i, j, mi, on, oxo, oyo);
+    node_update_m<MODE, LINEAR, CHAR, COH>(d, sa, i, j, mi, on, oxo, oyo);
     if (mi.bad) {
       MulFP64 mf;
-      node_update_m<MODE, LINEAR, CHAR>(d, sa, i, j, mf, on, oxo, oyo);
+      node_update_m<MODE, LINEAR, CHAR, COH>(d, sa, i, j, mf, on, oxo, oyo);
     }
   } else {
     MulFP64 mf;
-    node_update_m<MODE, LINEAR, CHAR>(d, sa, i, j, mf, on, oxo, oyo);
+    node_update_m<MODE, LINEAR, CHAR, COH>(d, sa, i, j, mf, on, oxo, oyo);
   }
 }
 
