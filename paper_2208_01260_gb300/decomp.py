@@ -17,7 +17,11 @@ every rank follows, so that the i-th message between two ranks is the same on bo
 stay in the process are unpacked directly. The result equals the undecomposed solver's bit for bit.
 
 The transport is ``torch.distributed`` (NCCL between GPUs, gloo between CPU processes) or nothing for a
-single process. Blocks follow a small interface (``strip_size``, ``new_strip``, ``pack``, ``unpack``,
+single process. Failures are detected on the host, between launches: a rank whose step fails (a block's
+error, a collective that failed or outlived ``Comm.timeout_s``) writes the reason under ``ABORT_KEY`` in
+the process group's store and raises ``DecompFailure``; every rank reads that key before each stage's
+exchange, and its own collectives are bounded by the same timeout, so the others raise ``DecompFailure``
+before their next launch or at their next collective instead of waiting for ever. Blocks follow a small interface (``strip_size``, ``new_strip``, ``pack``, ``unpack``,
 ``alpha_keys``, ``stage``, plus ``max_keys`` of the rank's rows); ``CudaBlock`` is the GPU block of this
 library, whose every step runs in its CUDA kernels.
 """
@@ -30,6 +34,13 @@ import numpy as np
 from . import (HW_FACE_E, HW_FACE_N, HW_FACE_S, HW_FACE_W, HW_HALO_NEIGHBOR, HW_LAYOUT_EQUILIBRIUM, hw_dd_max_keys,
                hw_dd_partition, hw_destroy, hw_get_state, hw_grid, hw_halo_pack, hw_halo_strip_size, hw_halo_unpack,
                hw_params, hw_part_alpha_keys, hw_part_create, hw_part_finish_init, hw_part_init, hw_part_stage)
+
+ABORT_KEY = "hw_dd_abort"
+
+
+class DecompFailure(RuntimeError):
+    """A rank of the decomposition failed (this one or a peer); the step did not complete."""
+
 
 FACES_X = (HW_FACE_W, HW_FACE_E)
 FACES_Y = (HW_FACE_S, HW_FACE_N)
@@ -64,17 +75,35 @@ class Plan:
 
 
 class Comm:
-    """Rank, world size and the two collectives the protocol needs (torch.distributed when world > 1)."""
+    """Rank, world size, the two collectives the protocol needs (torch.distributed when world > 1), each wait
+    bounded by timeout_s, and the failure flag in the store (store: a torch.distributed Store, or None)."""
 
-    def __init__(self, rank: int = 0, world: int = 1):
-        self.rank, self.world = rank, world
+    def __init__(self, rank: int = 0, world: int = 1, store=None, timeout_s: Optional[float] = None):
+        self.rank, self.world, self.store, self.timeout_s = rank, world, store, timeout_s
 
     @classmethod
-    def from_torch(cls):
+    def from_torch(cls, timeout_s: Optional[float] = None):
+        """The default process group's rank, size and store (None when the group keeps its store private)."""
         import torch.distributed as dist
         if dist.is_available() and dist.is_initialized():
-            return cls(dist.get_rank(), dist.get_world_size())
+            store = None
+            try:
+                from torch.distributed.distributed_c10d import _get_default_store
+                store = _get_default_store()
+            except Exception:  # noqa: BLE001
+                store = None
+            return cls(dist.get_rank(), dist.get_world_size(), store, timeout_s)
         return cls(0, 1)
+
+    def _wait(self, work, what):
+        from datetime import timedelta
+        try:
+            if self.timeout_s is None:
+                work.wait()
+            else:
+                work.wait(timedelta(seconds=self.timeout_s))
+        except Exception as e:  # noqa: BLE001
+            raise self.fail("%s: %s: %s" % (what, type(e).__name__, e)) from e
 
     def exchange(self, sends, recvs):
         """sends: [(tensor, dst_rank, tag)], recvs: [(tensor, src_rank, tag)], both in the global order."""
@@ -86,13 +115,46 @@ class Comm:
         merged = [(tag, dist.isend, t, r) for t, r, tag in sends] + [(tag, dist.irecv, t, r) for t, r, tag in recvs]
         merged.sort(key=lambda x: x[0])
         ops = [dist.P2POp(op, t, peer, tag=tag) for tag, op, t, peer in merged]
-        for w in dist.batch_isend_irecv(ops):
-            w.wait()
+        try:
+            works = dist.batch_isend_irecv(ops)
+        except Exception as e:  # noqa: BLE001
+            raise self.fail("halo exchange: %s: %s" % (type(e).__name__, e)) from e
+        for w in works:
+            self._wait(w, "halo exchange")
 
     def allreduce_max(self, t):
         if self.world > 1:
             import torch.distributed as dist
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            try:
+                work = dist.all_reduce(t, op=dist.ReduceOp.MAX, async_op=True)
+            except Exception as e:  # noqa: BLE001
+                raise self.fail("alpha all-reduce: %s: %s" % (type(e).__name__, e)) from e
+            self._wait(work, "alpha all-reduce")
+
+    def check_peers(self):
+        """Raise DecompFailure if any rank has reported a failure (a read of the store, no wait)."""
+        if self.store is None or self.world == 1:
+            return
+        try:
+            if self.store.check([ABORT_KEY]):
+                raise DecompFailure(self.store.get(ABORT_KEY).decode())
+        except DecompFailure:
+            raise
+        except Exception as e:  # noqa: BLE001  (the store itself is gone: its host rank ended)
+            raise DecompFailure("rank %d: store unreachable: %s" % (self.rank, e)) from e
+
+    def fail(self, why: str) -> DecompFailure:
+        """Report this rank's failure in the store (first report kept) and return the exception to raise."""
+        msg = "rank %d: %s" % (self.rank, why)
+        if self.store is not None and self.world > 1:
+            try:
+                self.store.compare_set(ABORT_KEY, "", msg)
+                first = self.store.get(ABORT_KEY).decode()
+                if first != msg:
+                    msg = "%s (first failure reported: %s)" % (msg, first)
+            except Exception:  # noqa: BLE001
+                pass
+        return DecompFailure(msg)
 
 
 def exchange(blocks: Dict[int, object], plan: Plan, set_: int, comm: Comm):
@@ -139,12 +201,19 @@ def global_keys(blocks: Dict[int, object], comm: Comm):
 
 
 def rk3_step(blocks: Dict[int, object], plan: Plan, comm: Comm, t_end: float = -1.0):
-    """One SSP-RK3 step of every block of the rank, dt = the CFL step at the step's start."""
+    """One SSP-RK3 step of every block of the rank, dt = the CFL step at the step's start. Raises
+    DecompFailure (after reporting it) if a block's stage fails here or a peer has reported a failure."""
     for k in (1, 2, 3):
+        comm.check_peers()
         exchange(blocks, plan, SET_STATE, comm)
         keys = global_keys(blocks, comm)
-        for _, blk in sorted(blocks.items()):
-            blk.stage(k, keys, t_end)
+        for p, blk in sorted(blocks.items()):
+            try:
+                blk.stage(k, keys, t_end)
+            except DecompFailure:
+                raise
+            except Exception as e:  # noqa: BLE001
+                raise comm.fail("block %d, stage %d: %s: %s" % (p, k, type(e).__name__, e)) from e
 
 
 def initialise(blocks: Dict[int, object], plan: Plan, comm: Comm, planes12_of):

@@ -1,6 +1,8 @@
 """The block decomposition on the CPU: the partition (host-only C call) and the halo/alpha protocol of
 ``paper_2208_01260_gb300.decomp`` across gloo ranks, each block advanced by the CPU oracle, against the
-oracle's undecomposed run, bit for bit.
+oracle's undecomposed run, bit for bit; and the protocol's failure detection (a rank whose block raises, a
+rank that leaves without a word, a dropped halo message): every rank ends with DecompFailure within a few
+collective timeouts instead of waiting for ever.
 
 The blocks here are test doubles: each holds its block plus the 2-node ring in host arrays, packs and
 unpacks strips with numpy by the rules hwswe.h states for hw_halo_pack / hw_halo_unpack, takes alpha from
@@ -12,6 +14,7 @@ the extended grids' spacings equal the global one exactly, as the GPU block solv
 import os
 import socket
 import sys
+import time
 
 import numpy as np
 import pytest
@@ -231,6 +234,107 @@ def test_protocol_two_ranks_equals_undecomposed_oracle(name):
     for rank, bad, nb in res:
         assert bad == [], (rank, bad)
         assert nb >= 1
+
+
+class FailingBlock(OracleBlock):
+    """An oracle block whose stage raises at its fail_at-th call (a host-side fault of one block)."""
+
+    def __init__(self, *a, fail_at=None, **k):
+        super().__init__(*a, **k)
+        self.fail_at, self.nstage = fail_at, 0
+
+    def stage(self, k, keys, t_end):
+        self.nstage += 1
+        if self.nstage == self.fail_at:
+            raise RuntimeError("injected block failure")
+        super().stage(k, keys, t_end)
+
+
+def _dropping_comm(decomp, base, drop_call):
+    """A Comm whose drop_call-th exchange leaves out its first send (a message lost on the way)."""
+    class Dropping(decomp.Comm):
+        calls = 0
+
+        def exchange(self, sends, recvs):
+            Dropping.calls += 1
+            if Dropping.calls == drop_call and sends:
+                sends = sends[1:]
+            super().exchange(sends, recvs)
+    return Dropping(base.rank, base.world, base.store, base.timeout_s)
+
+
+def _failing_rank(rank, ws, port, mode, q):
+    from datetime import timedelta
+    result = None
+    try:
+        os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+        sys.path.insert(0, ROOT)
+        import torch.distributed as dist
+        import oracle as orc
+        import paper_2208_01260_gb300 as hw
+        from paper_2208_01260_gb300 import decomp
+        dist.init_process_group("gloo", rank=rank, world_size=ws, timeout=timedelta(seconds=30))
+        sc, grid, px, py = _case("refl_per")
+        params = orc.make_params(eps_w=sc.eps_w)
+        plan = decomp.Plan(grid, px, py, ws)
+        comm = decomp.Comm.from_torch(timeout_s=3.0)
+        assert comm.store is not None
+        if mode == "drop" and rank == 1:
+            comm = _dropping_comm(decomp, comm, drop_call=9)  # initialisation x, y; 2 per stage: step 2, stage 1, x faces
+        fail_at = 4 if (mode == "raise" and rank == 1) else None  # step 2, stage 1
+        blocks = {p: FailingBlock(orc, hw, grid, params, px, py, p, fail_at=fail_at) for p in plan.local_parts(rank)}
+        decomp.initialise(blocks, plan, comm, lambda p: decomp.window12(sc, plan.info[p]))
+        t0 = time.time()
+        try:
+            for step in range(4):
+                if mode == "leave" and rank == 1 and step == 1:
+                    q.put((rank, "left", 0.0))
+                    q.close()
+                    q.join_thread()
+                    os._exit(0)  # gone between steps, nothing reported
+                decomp.rk3_step(blocks, plan, comm)
+            result = (rank, "completed", time.time() - t0)
+        except decomp.DecompFailure as e:
+            result = (rank, "DecompFailure: %s" % e, time.time() - t0)
+    except Exception as e:  # noqa: BLE001
+        result = (rank, "error: %r" % e, 0.0)
+    q.put(result)
+    q.close()
+    q.join_thread()
+    os._exit(0)  # leave without tearing down a process group that may have work pending
+
+
+@pytest.mark.parametrize("mode", ["raise", "leave", "drop"])
+def test_protocol_failures_end_every_rank(mode):
+    """raise: rank 1's block raises at step 2; rank 1 reports it in the store and raises DecompFailure,
+    and rank 0 ends its next collective with DecompFailure naming rank 1's failure. leave: rank 1 exits
+    between steps without a word; rank 0's next collective fails within its 3 s bound. drop: rank 1 loses
+    one halo message of step 2; rank 0's receive runs out, rank 1's all-reduce runs out or it reads rank
+    0's report. No rank runs on, and none waits longer than a few timeouts."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_rank, args=(r, 2, port, mode, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        res = dict((r, (msg, dt)) for r, msg, dt in (q.get(timeout=120) for _ in range(2)))
+    finally:
+        for p in procs:
+            p.join(30)
+            if p.exitcode is None:
+                p.kill()
+    if mode == "raise":
+        assert res[1][0].startswith("DecompFailure: rank 1: block") and "injected block failure" in res[1][0], res
+        assert res[0][0].startswith("DecompFailure") and "rank 1: block" in res[0][0], res
+    elif mode == "leave":
+        assert res[1][0] == "left", res
+        assert res[0][0].startswith("DecompFailure: rank 0:"), res
+    else:
+        assert res[0][0].startswith("DecompFailure: rank 0: halo exchange"), res
+        assert res[1][0].startswith("DecompFailure"), res
+    for r, (msg, dt) in res.items():
+        assert dt < 20.0, (r, msg, dt)
 
 
 def test_batched_instances_partition_across_ranks():
