@@ -97,18 +97,29 @@ __global__ void __launch_bounds__(256, kNodeBlocks<R>) k_node2d(Dev2DT<R> d, Sta
 // non-positive depth: in double the two passes of hw_stencil2d.cuh (coarse float maxima, then the exact
 // double maximum near them), in single precision one pass.
 // ---------------------------------------------------------------------------------------------
+// Each thread takes kAlphaU nodes a stride apart per iteration, their loads issued together (the passes
+// are bound by memory latency at one node per thread in flight).
+constexpr int kAlphaU = 4;
+
 __global__ void __launch_bounds__(256) k_alpha2d_coarse(Dev2D d, unsigned long long* amax, int* status) {
-  const size_t n = (size_t)d.nx * d.ny;
+  const size_t n = (size_t)d.nx * d.ny, stride = (size_t)gridDim.x * blockDim.x;
   float mx = 0.0f, my = 0.0f;
   int bad = 0;
-  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
-    float ax, ay;
-    bool exact, neg;
-    alpha_coarse(d, o, ax, ay, exact, neg);
-    if (exact) continue;  // the exact pass evaluates (and, if need be, flags) this node
-    if (neg) { bad |= HW_STATUS_DEPTH; continue; }
-    mx = fmaxf(mx, ax);
-    my = fmaxf(my, ay);
+  for (size_t o0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o0 < n; o0 += kAlphaU * stride) {
+    float ax[kAlphaU], ay[kAlphaU];
+    bool exact[kAlphaU], neg[kAlphaU];
+#pragma unroll
+    for (int u = 0; u < kAlphaU; ++u) {
+      exact[u] = true;  // past the end: skipped
+      if (o0 + u * stride < n) alpha_coarse(d, o0 + u * stride, ax[u], ay[u], exact[u], neg[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kAlphaU; ++u) {
+      if (exact[u]) continue;  // the exact pass evaluates (and, if need be, flags) this node
+      if (neg[u]) { bad |= HW_STATUS_DEPTH; continue; }
+      mx = fmaxf(mx, ax[u]);
+      my = fmaxf(my, ay[u]);
+    }
   }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) {
@@ -124,13 +135,26 @@ __global__ void __launch_bounds__(256) k_alpha2d_coarse(Dev2D d, unsigned long l
   if (bad) atomicOr(status, bad);
 }
 
+// The nodes alpha_exact_range would evaluate, kAlphaU at a time.
 __global__ void __launch_bounds__(256) k_alpha2d_exact(Dev2D d, unsigned long long* amax, int* status) {
-  const size_t n = (size_t)d.nx * d.ny;
+  const size_t n = (size_t)d.nx * d.ny, stride = (size_t)gridDim.x * blockDim.x;
   const unsigned int* m32 = reinterpret_cast<const unsigned int*>(amax + 2);
+  const float tx = __uint_as_float(m32[0]) * (1.0f - 1e-5f), ty = __uint_as_float(m32[1]) * (1.0f - 1e-5f);
   unsigned long long kx = 0, ky = 0;
   int bad = 0;
-  alpha_exact_range(d, m32, (size_t)blockIdx.x * blockDim.x + threadIdx.x, n, (size_t)gridDim.x * blockDim.x, kx, ky,
-                    bad);
+  for (size_t o0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o0 < n; o0 += kAlphaU * stride) {
+    float fx[kAlphaU], fy[kAlphaU];
+    bool exact[kAlphaU], neg[kAlphaU], in[kAlphaU];
+#pragma unroll
+    for (int u = 0; u < kAlphaU; ++u) {
+      in[u] = o0 + u * stride < n;
+      if (in[u]) alpha_coarse(d, o0 + u * stride, fx[u], fy[u], exact[u], neg[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kAlphaU; ++u)
+      if (in[u] && alpha_needs_exact(fx[u], fy[u], exact[u], neg[u], tx, ty))
+        alpha_exact_node(d, o0 + u * stride, kx, ky, bad);
+  }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) {
     kx = max(kx, __shfl_xor_sync(0xffffffffu, kx, s));
