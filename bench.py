@@ -68,17 +68,17 @@ ALGO_BYTES_PER_NODE_STAGE = 216.0
 # kernel sources they were taken on (sources_sha); scaled to a launch by its units (traffic is proportional
 # to them).
 TRAFFIC = {
-    "sweep_x": {"bytes_per_unit": 223.3, "sha": "6c3808f6f4b7d83f"},
-    "sweep_y": {"bytes_per_unit": 227.0, "sha": "6c3808f6f4b7d83f"},
-    "node": {"bytes_per_unit": 531.9, "sha": "6c3808f6f4b7d83f"},
+    "sweep_x": {"bytes_per_unit": 223.3, "sha": "9f87d6a751d6f588"},
+    "sweep_y": {"bytes_per_unit": 226.8, "sha": "9f87d6a751d6f588"},
+    "node": {"bytes_per_unit": 530.6, "sha": "9f87d6a751d6f588"},
 }
 # FP64-pipe instructions per unit (ncu: DFMA + DADD + DMUL thread instructions of the same launches over
 # their units). Part of the products run on the integer pipes (each bit-identical to DMUL), so these are
 # below the algorithmic "ops" above; valid only for the kernel sources they were taken on (sources_sha).
 FP64_PIPE_OPS = {
-    "sweep_x": {"ops_per_unit": 341.9, "sha": "6c3808f6f4b7d83f"},
-    "sweep_y": {"ops_per_unit": 342.8, "sha": "6c3808f6f4b7d83f"},
-    "node": {"ops_per_unit": 243.0, "sha": "6c3808f6f4b7d83f"},
+    "sweep_x": {"ops_per_unit": 341.9, "sha": "9f87d6a751d6f588"},
+    "sweep_y": {"ops_per_unit": 342.8, "sha": "9f87d6a751d6f588"},
+    "node": {"ops_per_unit": 243.0, "sha": "9f87d6a751d6f588"},
 }
 STATE_BYTES = 9 * NX * NY * 8
 
