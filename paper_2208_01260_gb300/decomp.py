@@ -78,8 +78,10 @@ class Comm:
     """Rank, world size, the two collectives the protocol needs (torch.distributed when world > 1), each wait
     bounded by timeout_s, and the failure flag in the store (store: a torch.distributed Store, or None)."""
 
-    def __init__(self, rank: int = 0, world: int = 1, store=None, timeout_s: Optional[float] = None):
+    def __init__(self, rank: int = 0, world: int = 1, store=None, timeout_s: Optional[float] = None,
+                 host_staging: bool = False):
         self.rank, self.world, self.store, self.timeout_s = rank, world, store, timeout_s
+        self.host_staging = host_staging  # CUDA tensors travel through host copies (gloo between GPU ranks)
 
     @classmethod
     def from_torch(cls, timeout_s: Optional[float] = None):
@@ -92,7 +94,8 @@ class Comm:
                 store = _get_default_store()
             except Exception:  # noqa: BLE001
                 store = None
-            return cls(dist.get_rank(), dist.get_world_size(), store, timeout_s)
+            return cls(dist.get_rank(), dist.get_world_size(), store, timeout_s,
+                       host_staging=dist.get_backend() == "gloo")
         return cls(0, 1)
 
     def _wait(self, work, what):
@@ -110,6 +113,17 @@ class Comm:
         if not sends and not recvs:
             return
         import torch.distributed as dist
+        staged = []
+        if self.host_staging:
+            sends = [(t.cpu() if t.is_cuda else t, r, tag) for t, r, tag in sends]
+            host_recvs = []
+            for t, r, tag in recvs:
+                if t.is_cuda:
+                    h = t.new_empty(t.shape, device="cpu")
+                    staged.append((t, h))
+                    t = h
+                host_recvs.append((t, r, tag))
+            recvs = host_recvs
         # one batch per phase, posted in the global message order (each message is a send or a receive here;
         # the tag is its position in that order, for transports that match by tag)
         merged = [(tag, dist.isend, t, r) for t, r, tag in sends] + [(tag, dist.irecv, t, r) for t, r, tag in recvs]
@@ -121,15 +135,20 @@ class Comm:
             raise self.fail("halo exchange: %s: %s" % (type(e).__name__, e)) from e
         for w in works:
             self._wait(w, "halo exchange")
+        for dev, host in staged:
+            dev.copy_(host)
 
     def allreduce_max(self, t):
         if self.world > 1:
             import torch.distributed as dist
+            buf = t.cpu() if (self.host_staging and t.is_cuda) else t
             try:
-                work = dist.all_reduce(t, op=dist.ReduceOp.MAX, async_op=True)
+                work = dist.all_reduce(buf, op=dist.ReduceOp.MAX, async_op=True)
             except Exception as e:  # noqa: BLE001
                 raise self.fail("alpha all-reduce: %s: %s" % (type(e).__name__, e)) from e
             self._wait(work, "alpha all-reduce")
+            if buf is not t:
+                t.copy_(buf)
 
     def check_peers(self):
         """Raise DecompFailure if any rank has reported a failure (a read of the store, no wait)."""
