@@ -16,12 +16,14 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/hwswe.h"
 #include "hw_adjoint.cuh"
+#include "hw_halo.h"
 #include "hw_internal.h"
 
 namespace hw {
@@ -708,12 +710,16 @@ struct AdjBuffers {
 std::mutex g_adj_mu;
 std::vector<AdjBuffers*> g_adj;  // one per live solver that used the adjoint (released by hw_destroy)
 
-int adj_alloc(AdjBuffers* B, double** p, size_t cnt) {
+// Zeroed on the solver's stream: the static adjoints accumulate into their buffers from the first use on
+// (each use clears them when it is done), so they must start at zero, not at whatever the memory held.
+int adj_alloc(AdjBuffers* B, double** p, size_t cnt, cudaStream_t st) {
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, cnt * sizeof(double));
   if (e != cudaSuccess) return afail(HW_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   B->allocs.push_back(q);
   *p = (double*)q;
+  e = cudaMemsetAsync(q, 0, cnt * sizeof(double), st);
+  if (e != cudaSuccess) return afail(HW_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   return HW_OK;
 }
 
@@ -733,7 +739,7 @@ int get_buffers(hw_solver* s, const hw::SolverView& v, AdjBuffers** out) {
   B->ny = v.d2->ny;
   const size_t n = v.n, nxi = (size_t)(B->nx + 1) * B->ny, nyi = (size_t)B->nx * (B->ny + 1);
   int rc = HW_OK;
-  auto A = [&](double** p, size_t c) { if (rc == HW_OK) rc = adj_alloc(B, p, c); };
+  auto A = [&](double** p, size_t c) { if (rc == HW_OK) rc = adj_alloc(B, p, c, v.stream); };
   for (int k = 0; k < 3; ++k)
     for (int q = 0; q < 9; ++q) A(&B->stage_in[k][q], n);
   for (int q = 0; q < 9; ++q) { A(&B->stage_out[q], n); A(&B->lam[0][q], n); A(&B->lam[1][q], n); A(&B->lbase[q], n); A(&B->lR[q], n); }
@@ -1586,3 +1592,330 @@ extern "C" int hw_dd_adjoint_run(hw_dd* dd, int nsteps, const double* dts, const
   for (int p = 0; p < np; ++p) cudaStreamSynchronize(hw::solver_stream(parts[p]));
   return rc;
 }
+
+// =============================================================================================
+// Per-block adjoint (hw_part_adj_*): the steps of dd_adjoint_impl for one block solver, so that blocks
+// owned by different processes run the same adjoint with the exchanges, the alpha keys, the gauge values
+// and the alpha adjoint carried between them by the caller (paper_2208_01260_gb300/decomp.py).
+// =============================================================================================
+struct hw_part_adj {
+  hw_solver* s = nullptr;
+  hw_part_info info{};
+  hw::SolverView v{};
+  AdjBuffers* B = nullptr;
+  RunTape* layout = nullptr;
+  double* tape = nullptr;
+  int nsteps = 0, ngauge = 0, nloc = 0, gnx = 0;
+  int* d_map = nullptr;     // [2][nloc]: local extended node, global gauge slot
+  double* d_gvals = nullptr;  // [nsteps][ngauge]: this block's gauges (zeros elsewhere)
+  double* d_gall = nullptr;   // [nsteps][ngauge]: all gauges (set_misfit)
+  double* d_obs = nullptr;
+  double* lal = nullptr;      // [2] alpha adjoint, then [2] ints: first maximising node
+  double* tmp = nullptr;      // 9 planes: state gradient in physical units
+  double* keys = nullptr;     // 3 key slots of the alpha reduction
+  int cur = 0;
+  bool reverse = false;
+  hw::AdjDev last{};
+  bool have_last = false;
+};
+
+namespace {
+int pa_check(hw_part_adj* a, const char* fn) {
+  if (!a || !a->s) return afail(HW_ERR_ARG, std::string(fn) + ": null context");
+  return HW_OK;
+}
+int pa_stage(hw_part_adj* a, int j, int k, const char* fn) {
+  int rc = pa_check(a, fn);
+  if (rc) return rc;
+  if (j < 0 || j >= a->nsteps || k < 1 || k > 3) return afail(HW_ERR_ARG, std::string(fn) + ": step or stage out of range");
+  return HW_OK;
+}
+int pa_face(int face, const char* fn) {
+  if (face < HW_FACE_W || face > HW_FACE_N) return afail(HW_ERR_ARG, std::string(fn) + ": bad face");
+  return HW_OK;
+}
+__global__ void k_set_int2(int* p, int a, int b) {
+  p[0] = a;
+  p[1] = b;
+}
+void pa_free(hw_part_adj* a) {
+  if (a->v.stream) cudaStreamSynchronize(a->v.stream);
+  cudaFree(a->tape); cudaFree(a->d_map); cudaFree(a->d_gvals); cudaFree(a->d_gall); cudaFree(a->d_obs);
+  cudaFree(a->lal); cudaFree(a->tmp); cudaFree(a->keys);
+  delete a->layout;
+  delete a;
+}
+}  // namespace
+
+extern "C" {
+
+int hw_part_adj_create(hw_solver* s, int nsteps, int ngauge, int nloc, const int* gauge_slot, const int* gauge_node,
+                       int global_nx, hw_part_adj** out) {
+  if (!out) return afail(HW_ERR_ARG, "hw_part_adj_create: null output");
+  *out = nullptr;
+  const hw_part_info* I = hw::part_info(s);
+  if (!I) return afail(HW_ERR_ARG, "hw_part_adj_create: not a block solver");
+  if (nsteps < 1 || ngauge < 1 || nloc < 0 || nloc > ngauge || (nloc > 0 && (!gauge_slot || !gauge_node)) || global_nx < 1)
+    return afail(HW_ERR_ARG, "hw_part_adj_create: bad argument");
+  hw_part_adj* a = new hw_part_adj();
+  a->s = s;
+  a->info = *I;
+  int rc = check_adjoint_solver(s, &a->v);
+  if (rc == HW_OK) rc = get_buffers(s, a->v, &a->B);
+  if (rc) { delete a; return rc; }
+  a->nsteps = nsteps; a->ngauge = ngauge; a->nloc = nloc; a->gnx = global_nx;
+  std::vector<int> map(2 * (size_t)nloc);
+  for (int g = 0; g < nloc; ++g) {
+    const int gi = gauge_node[g] % global_nx - I->i0, gj = gauge_node[g] / global_nx - I->j0;
+    if (gauge_node[g] < 0 || gi < 0 || gi >= I->nx || gj < 0 || gj >= I->ny || gauge_slot[g] < 0 || gauge_slot[g] >= ngauge) {
+      delete a;
+      return afail(HW_ERR_ARG, "hw_part_adj_create: gauge not on the block's own nodes, or slot out of range");
+    }
+    map[g] = (gj + 2) * (I->nx + 4) + (gi + 2);
+    map[nloc + g] = gauge_slot[g];
+  }
+  a->layout = new RunTape(a->v, nsteps);
+  auto alloc = [&](void** q, size_t bytes) {
+    if (rc != HW_OK) return;
+    if (cudaMalloc(q, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      rc = afail(HW_ERR_NOMEM, "hw_part_adj_create: allocation failed");
+    }
+  };
+  alloc((void**)&a->tape, a->layout->bytes());
+  if (nloc) alloc((void**)&a->d_map, map.size() * sizeof(int));
+  const size_t gb = (size_t)nsteps * ngauge * sizeof(double);
+  alloc((void**)&a->d_gvals, gb);
+  alloc((void**)&a->d_gall, gb);
+  alloc((void**)&a->d_obs, gb);
+  alloc((void**)&a->lal, 4 * sizeof(double));
+  alloc((void**)&a->tmp, 9 * a->v.n * sizeof(double));
+  alloc((void**)&a->keys, 4 * sizeof(double));
+  if (rc) { pa_free(a); return rc; }
+  cudaStream_t st = a->v.stream;
+  cudaError_t e = cudaFuncSetAttribute(hw::k_adj_sweep_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hw::AY_SMEM);
+  if (e == cudaSuccess && nloc) e = cudaMemcpyAsync(a->d_map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a->d_gvals, 0, gb, st);
+  const StepTape T0 = a->layout->step(a->tape, 0);
+  for (int q = 0; q < 9 && e == cudaSuccess; ++q)
+    e = cudaMemcpyAsync(T0.in[0][q], a->v.state[q], a->v.n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { pa_free(a); return afail(HW_ERR_CUDA, std::string("hw_part_adj_create: ") + cudaGetErrorString(e)); }
+  *out = a;
+  return HW_OK;
+}
+
+int hw_part_adj_destroy(hw_part_adj* a) {
+  if (a) pa_free(a);
+  return HW_OK;
+}
+
+int hw_part_adj_strip_size(hw_part_adj* a, int what, int face, long long* count) {
+  int rc = pa_check(a, "hw_part_adj_strip_size");
+  if (!rc) rc = pa_face(face, "hw_part_adj_strip_size");
+  if (rc) return rc;
+  if ((what != 0 && what != 1) || !count) return afail(HW_ERR_ARG, "hw_part_adj_strip_size: bad argument");
+  const long long len = face < 2 ? a->info.ny : a->info.nx + 4;
+  *count = (what == 0 ? 9 : 3) * 2 * len;
+  return HW_OK;
+}
+
+int hw_part_adj_pack(hw_part_adj* a, int j, int k, int face, double* strip) {
+  int rc = pa_stage(a, j, k, "hw_part_adj_pack");
+  if (!rc) rc = pa_face(face, "hw_part_adj_pack");
+  if (rc) return rc;
+  if (!strip) return afail(HW_ERR_ARG, "hw_part_adj_pack: null strip");
+  const StepTape T = a->layout->step(a->tape, j);
+  return hw::halo_pack_planes(T.in[k - 1], 9, a->info.nx + 4, a->info.ny + 4, face, strip, a->v.stream);
+}
+
+int hw_part_adj_unpack(hw_part_adj* a, int j, int k, int face, int mode, const double* strip) {
+  int rc = pa_stage(a, j, k, "hw_part_adj_unpack");
+  if (!rc) rc = pa_face(face, "hw_part_adj_unpack");
+  if (rc) return rc;
+  if (!strip || mode < HW_HALO_NEIGHBOR || mode > HW_HALO_REPLICATE) return afail(HW_ERR_ARG, "hw_part_adj_unpack: bad argument");
+  const StepTape T = a->layout->step(a->tape, j);
+  return hw::halo_unpack_planes(T.in[k - 1], 9, a->info.nx + 4, a->info.ny + 4, face, mode,
+                                face < 2 ? kStateOddX : kStateOddY, strip, a->v.stream);
+}
+
+int hw_part_adj_alpha_keys(hw_part_adj* a, int j, int k, unsigned long long* keys) {
+  int rc = pa_stage(a, j, k, "hw_part_adj_alpha_keys");
+  if (rc) return rc;
+  if (!keys) return afail(HW_ERR_ARG, "hw_part_adj_alpha_keys: null keys");
+  const StepTape T = a->layout->step(a->tape, j);
+  hw::Dev2D d = *a->v.d2;
+  for (int q = 0; q < 9; ++q) d.S[q] = T.in[k - 1][q];
+  hw::launch_alpha2d(d, (unsigned long long*)a->keys, (int*)(a->B->lalpha + 2), a->v.stream);
+  ACUDA(cudaMemcpyAsync(keys, a->keys, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, a->v.stream));
+  return HW_OK;
+}
+
+int hw_part_adj_forward_stage(hw_part_adj* a, int j, int k, double dt, const unsigned long long* keys) {
+  int rc = pa_stage(a, j, k, "hw_part_adj_forward_stage");
+  if (rc) return rc;
+  if (!keys || !(dt >= 0.0) || !(dt < 1e300)) return afail(HW_ERR_ARG, "hw_part_adj_forward_stage: bad argument");
+  const hw::SolverView& v = a->v;
+  cudaStream_t st = v.stream;
+  const StepTape T = a->layout->step(a->tape, j);
+  if (k == 1) ACUDA(cudaMemcpyAsync(v.dt, &dt, sizeof(double), cudaMemcpyHostToDevice, st));
+  hw::Dev2D d = *v.d2;
+  for (int q = 0; q < 9; ++q) d.S[q] = T.in[k - 1][q];
+  for (int c = 0; c < 3; ++c) { d.X[3 + c] = T.dbx[k - 1][c]; d.Y[3 + c] = T.dby[k - 1][c]; }
+  d.X[0] = T.fx[k - 1];
+  d.Y[0] = T.fy[k - 1];
+  hw::launch_finish_alpha2d(d, keys, T.alpha + 2 * (k - 1), nullptr, v.params->cfl, nullptr, -1.0, st);
+  hw::launch_sweep_x2d(d, T.alpha + 2 * (k - 1), false, true, st);
+  hw::launch_sweep_y2d(d, T.alpha + 2 * (k - 1), false, true, st);
+  hw::StageArgs sa{};
+  sa.k = k;
+  sa.limiter = v.params->limiter;
+  sa.dt = v.dt;
+  for (int q = 0; q < 9; ++q) {
+    sa.out[q] = k < 3 ? T.in[k][q] : T.out[q];
+    sa.base[q] = v.base[q];
+  }
+  hw::launch_node2d(d, sa, hw::MODE_STAGE, false, true, st);
+  if (k == 3 && a->nloc)
+    hw::k_gather_eta_map<<<(a->nloc + 127) / 128, 128, 0, st>>>(T.out[0], a->d_map, a->d_map + a->nloc, a->nloc,
+                                                              a->d_gvals + (size_t)j * a->ngauge);
+  ACUDA(cudaGetLastError());
+  return HW_OK;
+}
+
+int hw_part_adj_gauges(hw_part_adj* a, double* gvals) {
+  int rc = pa_check(a, "hw_part_adj_gauges");
+  if (rc) return rc;
+  if (!gvals) return afail(HW_ERR_ARG, "hw_part_adj_gauges: null output");
+  ACUDA(cudaMemcpyAsync(gvals, a->d_gvals, (size_t)a->nsteps * a->ngauge * sizeof(double), cudaMemcpyDeviceToHost,
+                        a->v.stream));
+  ACUDA(cudaStreamSynchronize(a->v.stream));
+  return HW_OK;
+}
+
+int hw_part_adj_set_misfit(hw_part_adj* a, const double* gvals, const double* eta_obs) {
+  int rc = pa_check(a, "hw_part_adj_set_misfit");
+  if (rc) return rc;
+  if (!gvals || !eta_obs) return afail(HW_ERR_ARG, "hw_part_adj_set_misfit: null argument");
+  const size_t gb = (size_t)a->nsteps * a->ngauge * sizeof(double);
+  cudaStream_t st = a->v.stream;
+  ACUDA(cudaMemcpyAsync(a->d_gall, gvals, gb, cudaMemcpyHostToDevice, st));
+  ACUDA(cudaMemcpyAsync(a->d_obs, eta_obs, gb, cudaMemcpyHostToDevice, st));
+  ACUDA(cudaStreamSynchronize(st));
+  a->cur = 0;
+  rc = zero_planes(a->B->lam[0], 9, a->v.n, st);
+  a->reverse = rc == HW_OK;
+  a->have_last = false;
+  return rc;
+}
+
+int hw_part_adj_reverse_stage(hw_part_adj* a, int j, int k, double dt, double* lalpha, int* argmax) {
+  int rc = pa_stage(a, j, k, "hw_part_adj_reverse_stage");
+  if (rc) return rc;
+  if (!a->reverse) return afail(HW_ERR_STATE, "hw_part_adj_reverse_stage: call hw_part_adj_set_misfit first");
+  if (!lalpha || !argmax) return afail(HW_ERR_ARG, "hw_part_adj_reverse_stage: null output");
+  const hw::SolverView& v = a->v;
+  cudaStream_t st = v.stream;
+  if (k == 3) {  // the step's misfit seeds the adjoint of its output; the base adjoint starts at zero
+    if (a->nloc)
+      hw::k_loss_seed_map<<<(a->nloc + 127) / 128, 128, 0, st>>>(a->d_gall + (size_t)j * a->ngauge,
+                                                                 a->d_obs + (size_t)j * a->ngauge, a->d_map,
+                                                                 a->d_map + a->nloc, a->nloc, a->B->lam[a->cur][0]);
+    if ((rc = zero_planes(a->B->lbase, 9, v.n, st))) return rc;
+  }
+  hw::AdjDev A = stage_args(v, a->B, a->layout->step(a->tape, j), dt, k, a->cur);
+  A.lalpha = a->lal;
+  A.argmax = (int*)(a->lal + 2);
+  ACUDA(cudaMemsetAsync(a->lal, 0, 2 * sizeof(double), st));
+  k_set_int2<<<1, 1, 0, st>>>(A.argmax, INT_MAX, INT_MAX);
+  if ((rc = reverse_stage_body(v, a->B, A))) return rc;
+  const hw_part_info& I = a->info;
+  hw::k_adj_alpha_find_block<<<std::min((I.nx * I.ny + 255) / 256, 152 * 8), 256, 0, st>>>(A, I.nx, I.ny, I.i0, I.j0,
+                                                                                        a->gnx);
+  ACUDA(cudaGetLastError());
+  double h[4];
+  ACUDA(cudaMemcpyAsync(h, a->lal, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  ACUDA(cudaStreamSynchronize(st));
+  lalpha[0] = h[0];
+  lalpha[1] = h[1];
+  std::memcpy(argmax, h + 2, 2 * sizeof(int));
+  a->last = A;
+  a->have_last = true;
+  return HW_OK;
+}
+
+int hw_part_adj_alpha_apply(hw_part_adj* a, const double* lalpha, const int* argmax) {
+  int rc = pa_check(a, "hw_part_adj_alpha_apply");
+  if (rc) return rc;
+  if (!a->have_last) return afail(HW_ERR_STATE, "hw_part_adj_alpha_apply: no reverse stage to complete");
+  if (!lalpha || !argmax) return afail(HW_ERR_ARG, "hw_part_adj_alpha_apply: null argument");
+  cudaStream_t st = a->v.stream;
+  double h[4] = {lalpha[0], lalpha[1], 0.0, 0.0};
+  std::memcpy(h + 2, argmax, 2 * sizeof(int));
+  ACUDA(cudaMemcpyAsync(a->lal, h, 4 * sizeof(double), cudaMemcpyHostToDevice, st));
+  const hw_part_info& I = a->info;
+  hw::k_adj_alpha_apply_block<<<1, 1, 0, st>>>(a->last, I.nx, I.ny, I.i0, I.j0, a->gnx);
+  ACUDA(cudaGetLastError());
+  ACUDA(cudaStreamSynchronize(st));  // h is read by the copy
+  a->cur ^= 1;  // the adjoint of the stage's input is now current
+  a->have_last = false;
+  return HW_OK;
+}
+
+int hw_part_adj_rpack(hw_part_adj* a, int what, int face, double* strip) {
+  int rc = pa_check(a, "hw_part_adj_rpack");
+  if (!rc) rc = pa_face(face, "hw_part_adj_rpack");
+  if (rc) return rc;
+  if ((what != 0 && what != 1) || !strip) return afail(HW_ERR_ARG, "hw_part_adj_rpack: bad argument");
+  double* const* planes = what == 0 ? a->B->lam[a->cur] : a->B->lstatic_phys;
+  return hw::halo_adj_pack_planes(planes, what == 0 ? 9 : 3, a->info.nx + 4, a->info.ny + 4, face, strip, a->v.stream);
+}
+
+int hw_part_adj_radd(hw_part_adj* a, int what, int face, int mode, const double* strip) {
+  int rc = pa_check(a, "hw_part_adj_radd");
+  if (!rc) rc = pa_face(face, "hw_part_adj_radd");
+  if (rc) return rc;
+  if ((what != 0 && what != 1) || !strip || mode < HW_HALO_NEIGHBOR || mode > HW_HALO_REPLICATE)
+    return afail(HW_ERR_ARG, "hw_part_adj_radd: bad argument");
+  double* const* planes = what == 0 ? a->B->lam[a->cur] : a->B->lstatic_phys;
+  const unsigned odd = what == 0 ? (face < 2 ? kStateOddX : kStateOddY) : (face < 2 ? kStatOddX : kStatOddY);
+  return hw::halo_adj_add_planes(planes, what == 0 ? 9 : 3, a->info.nx + 4, a->info.ny + 4, face, mode, odd, strip,
+                                 a->v.stream);
+}
+
+int hw_part_adj_finish_static(hw_part_adj* a) {
+  int rc = pa_check(a, "hw_part_adj_finish_static");
+  if (rc) return rc;
+  if ((rc = zero_planes(a->B->lstatic_phys, 3, a->v.n, a->v.stream))) return rc;
+  return finish_static(a->v, a->B, a->B->lstatic_phys);
+}
+
+int hw_part_adj_gradients(hw_part_adj* a, double* const* grad_state, double* const* grad_static, int ld, int ptr_kind) {
+  int rc = pa_check(a, "hw_part_adj_gradients");
+  if (rc) return rc;
+  if (!grad_state || !grad_static || ld < a->info.nx || (ptr_kind != HW_HOST && ptr_kind != HW_DEVICE))
+    return afail(HW_ERR_ARG, "hw_part_adj_gradients: bad argument");
+  for (int q = 0; q < 9; ++q)
+    if (!grad_state[q]) return afail(HW_ERR_ARG, "hw_part_adj_gradients: null plane");
+  for (int q = 0; q < 3; ++q)
+    if (!grad_static[q]) return afail(HW_ERR_ARG, "hw_part_adj_gradients: null plane");
+  const hw::SolverView& v = a->v;
+  cudaStream_t st = v.stream;
+  const size_t n = v.n;
+  const int nxe = a->info.nx + 4;
+  hw::Ptr9 src{}, dst{};
+  for (int q = 0; q < 9; ++q) { src.p[q] = a->B->lam[a->cur][q]; dst.p[q] = a->tmp + q * n; }
+  hw::k_adj_convert<<<std::min((int)((n + 255) / 256), 152 * 8), 256, 0, st>>>((int)n, v.d2->dx, v.d2->dy, src, dst, 0);
+  ACUDA(cudaGetLastError());
+  const cudaMemcpyKind kind = ptr_kind == HW_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  for (int q = 0; q < 12; ++q) {
+    const double* from = (q < 9 ? a->tmp + q * n : a->B->lstatic_phys[q - 9]) + 2 * (size_t)nxe + 2;
+    double* to = q < 9 ? grad_state[q] : grad_static[q - 9];
+    ACUDA(cudaMemcpy2DAsync(to, ld * sizeof(double), from, nxe * sizeof(double), a->info.nx * sizeof(double),
+                            a->info.ny, kind, st));
+  }
+  ACUDA(cudaStreamSynchronize(st));
+  return HW_OK;
+}
+
+}  // extern "C"
