@@ -351,6 +351,51 @@ int hw_dd_destroy(hw_dd* d);
 int hw_dd_adjoint_run(hw_dd* d, int nsteps, const double* dts, const int* gauge_idx, int ngauge,
                       const double* eta_obs, double* loss_out, double* const* grad_state, double* const* grad_static);
 
+/* The same adjoint one block at a time, for blocks owned by different processes (no counterpart in the
+ * paper): the caller carries the exchanges, alpha keys, gauge values and the alpha adjoint between the
+ * blocks (paper_2208_01260_gb300/decomp.py, adjoint_run). On block solver s (hw_part_create, initialised,
+ * nonlinear weights and characteristic projection), in order:
+ *   forward, for each step j = 0 .. nsteps-1 and stage k = 1, 2, 3: the exchange of the stage input
+ *     (hw_part_adj_pack / _unpack, with the same modes, pairing and order as hw_halo_pack / _unpack),
+ *     hw_part_adj_alpha_keys, the maximum of all blocks' keys, hw_part_adj_forward_stage with it;
+ *   hw_part_adj_gauges, summed over all blocks (each slot holds one block's value, zeros elsewhere),
+ *     and hw_part_adj_set_misfit with the full arrays (it also gives the loss);
+ *   reverse, for j = nsteps-1 .. 0 and k = 3, 2, 1: hw_part_adj_reverse_stage, the sum over all blocks
+ *     of their alpha adjoints and the minimum of their nodes, hw_part_adj_alpha_apply with those, then
+ *     the transposed exchange of what = 0 (y faces first, then x faces): every block's ring strip of each
+ *     face by hw_part_adj_rpack (which clears the ring), added by hw_part_adj_radd on the block it was
+ *     copied from: the NEIGHBOR's opposite face, or the block's own face for MIRROR / REPLICATE;
+ *   hw_part_adj_finish_static, the transposed exchange of what = 1, hw_part_adj_gradients.
+ * Everything runs on the block solver's stream. Memory: the block's whole-run tape (every stage of every
+ * step), as hw_dd_adjoint_run. Errors: HW_ERR_ARG (bad step, stage, face, mode or pointer; gauge not on
+ * the block's own nodes), HW_ERR_STATE (reverse before set_misfit, apply without a reverse stage),
+ * HW_ERR_NOMEM, HW_ERR_CUDA. */
+typedef struct hw_part_adj hw_part_adj;
+/* nloc of the ngauge gauges lie on the block's own nodes: gauge_node their global nodes (j global_nx + i),
+ * gauge_slot their positions in the global list. The tape starts from the block's current state. */
+int hw_part_adj_create(hw_solver* s, int nsteps, int ngauge, int nloc, const int* gauge_slot, const int* gauge_node,
+                       int global_nx, hw_part_adj** out);
+int hw_part_adj_destroy(hw_part_adj* a);
+/* doubles of a strip of face: what = 0, the 9 state planes (stage input or its adjoint); 1, the 3 static */
+int hw_part_adj_strip_size(hw_part_adj* a, int what, int face, long long* count);
+int hw_part_adj_pack(hw_part_adj* a, int j, int k, int face, double* strip);                  /* device strip */
+int hw_part_adj_unpack(hw_part_adj* a, int j, int k, int face, int mode, const double* strip);
+int hw_part_adj_alpha_keys(hw_part_adj* a, int j, int k, unsigned long long* keys);           /* device keys[2] */
+int hw_part_adj_forward_stage(hw_part_adj* a, int j, int k, double dt, const unsigned long long* keys);
+int hw_part_adj_gauges(hw_part_adj* a, double* gvals);                  /* host [nsteps][ngauge]; syncs */
+/* host, full arrays; loss_out (optional): the misfit, summed as hw_adjoint_run and hw_dd_adjoint_run do */
+int hw_part_adj_set_misfit(hw_part_adj* a, const double* gvals, const double* eta_obs, double* loss_out);
+/* lalpha[2] (host): the block's share of the alpha adjoint; argmax[2] (host): its first node (global
+ * index) attaining each alpha, INT_MAX if none. Stage 3 first adds the step's misfit. Syncs. */
+int hw_part_adj_reverse_stage(hw_part_adj* a, int j, int k, double dt, double* lalpha, int* argmax);
+int hw_part_adj_alpha_apply(hw_part_adj* a, const double* lalpha, const int* argmax);        /* host */
+int hw_part_adj_rpack(hw_part_adj* a, int what, int face, double* strip);                     /* device */
+int hw_part_adj_radd(hw_part_adj* a, int what, int face, int mode, const double* strip);
+int hw_part_adj_finish_static(hw_part_adj* a);
+/* The block's own nodes of the state gradient (9, physical units as hw_adjoint_run) and the static one
+ * (3), rows ld apart, HW_HOST or HW_DEVICE; syncs. */
+int hw_part_adj_gradients(hw_part_adj* a, double* const* grad_state, double* const* grad_static, int ld, int ptr_kind);
+
 /* Allocation-free variant of the 1D right-hand side: the same numbers as hw_create + hw_init + hw_rhs on
  * a 1D grid (out: 4 planes d/dt (eta, m, eta_x, m_x)), with every array pointer on the device. The paper
  * has no counterpart; this call exists for callers that must not allocate device memory, such as code

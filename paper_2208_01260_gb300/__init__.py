@@ -39,7 +39,7 @@ __all__ = [
     "hw_batch_get_persistent", "hw_batch_test_barrier_timeout", "hw_batch_get_phase_times",
     "hw_part_info", "hw_dd_partition", "hw_part_create", "hw_part_init", "hw_part_finish_init", "hw_halo_strip_size",
     "hw_halo_pack", "hw_halo_unpack", "hw_part_alpha_keys", "hw_part_stage", "hw_dd_create", "hw_dd_init",
-    "hw_dd_advance", "hw_dd_get_state", "hw_dd_destroy", "hw_dd_max_keys", "hw_dd_adjoint_run", "DecomposedSolver",
+    "hw_dd_advance", "hw_dd_get_state", "hw_dd_destroy", "hw_dd_max_keys", "hw_dd_adjoint_run", "DecomposedSolver", "PartAdjoint",
 ]
 
 HW_OK = 0
@@ -368,6 +368,21 @@ def _dd_sigs():
         "hw_dd_get_state": [vp, pp, i, i],
         "hw_dd_destroy": [vp],
         "hw_dd_adjoint_run": [vp, i, C.POINTER(d), C.POINTER(i), i, C.POINTER(d), C.POINTER(d), pp, pp],
+        "hw_part_adj_create": [vp, i, i, i, C.POINTER(i), C.POINTER(i), i, C.POINTER(vp)],
+        "hw_part_adj_destroy": [vp],
+        "hw_part_adj_strip_size": [vp, i, i, C.POINTER(ll)],
+        "hw_part_adj_pack": [vp, i, i, i, vp],
+        "hw_part_adj_unpack": [vp, i, i, i, i, vp],
+        "hw_part_adj_alpha_keys": [vp, i, i, vp],
+        "hw_part_adj_forward_stage": [vp, i, i, d, vp],
+        "hw_part_adj_gauges": [vp, C.POINTER(d)],
+        "hw_part_adj_set_misfit": [vp, C.POINTER(d), C.POINTER(d), C.POINTER(d)],
+        "hw_part_adj_reverse_stage": [vp, i, i, d, C.POINTER(d), C.POINTER(i)],
+        "hw_part_adj_alpha_apply": [vp, C.POINTER(d), C.POINTER(i)],
+        "hw_part_adj_rpack": [vp, i, i, vp],
+        "hw_part_adj_radd": [vp, i, i, i, vp],
+        "hw_part_adj_finish_static": [vp],
+        "hw_part_adj_gradients": [vp, pp, pp, i, i],
     }.items():
         f = getattr(L, name)
         f.argtypes = args
@@ -417,6 +432,101 @@ def hw_part_init(h: _Handle, planes12: Sequence, ld: int):
 
 def hw_part_finish_init(h: _Handle):
     _check(_dd_sigs().hw_part_finish_init(h.ptr), "hw_part_finish_init")
+
+
+class PartAdjoint:
+    """The per-block adjoint context (hw_part_adj_*) of block solver `h` for a run of nsteps with the
+    gauges of the global list that lie on the block's own nodes (slots and global node indices)."""
+
+    def __init__(self, h: _Handle, nsteps: int, ngauge: int, slots: Sequence[int], nodes: Sequence[int], global_nx: int):
+        L = _dd_sigs()
+        n = len(slots)
+        sl = (C.c_int * max(n, 1))(*[int(x) for x in slots])
+        nd = (C.c_int * max(n, 1))(*[int(x) for x in nodes])
+        out = C.c_void_p()
+        _check(L.hw_part_adj_create(h.ptr, int(nsteps), int(ngauge), n, sl, nd, int(global_nx), C.byref(out)),
+               "hw_part_adj_create")
+        self.ptr, self.h, self.nsteps, self.ngauge = out, h, nsteps, ngauge
+
+    def close(self):
+        if self.ptr:
+            _dd_sigs().hw_part_adj_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def strip_size(self, what: int, face: int) -> int:
+        n = C.c_longlong()
+        _check(_dd_sigs().hw_part_adj_strip_size(self.ptr, int(what), int(face), C.byref(n)), "hw_part_adj_strip_size")
+        return n.value
+
+    def pack(self, j: int, k: int, face: int, strip):
+        _check(_dd_sigs().hw_part_adj_pack(self.ptr, int(j), int(k), int(face), _dev_ptr(strip)), "hw_part_adj_pack")
+
+    def unpack(self, j: int, k: int, face: int, mode: int, strip):
+        _check(_dd_sigs().hw_part_adj_unpack(self.ptr, int(j), int(k), int(face), int(mode), _dev_ptr(strip)),
+               "hw_part_adj_unpack")
+
+    def alpha_keys(self, j: int, k: int, keys):
+        _check(_dd_sigs().hw_part_adj_alpha_keys(self.ptr, int(j), int(k), _dev_ptr(keys)), "hw_part_adj_alpha_keys")
+
+    def forward_stage(self, j: int, k: int, dt: float, keys):
+        _check(_dd_sigs().hw_part_adj_forward_stage(self.ptr, int(j), int(k), float(dt), _dev_ptr(keys)),
+               "hw_part_adj_forward_stage")
+
+    def gauges(self) -> np.ndarray:
+        out = np.zeros(self.nsteps * self.ngauge)
+        _check(_dd_sigs().hw_part_adj_gauges(self.ptr, out.ctypes.data_as(C.POINTER(C.c_double))), "hw_part_adj_gauges")
+        return out
+
+    def set_misfit(self, gvals, obs) -> float:
+        """Starts the reverse pass; returns the loss (summed as the library's other adjoint entry points)."""
+        g = np.ascontiguousarray(gvals, dtype=np.float64).ravel()
+        o = np.ascontiguousarray(obs, dtype=np.float64).ravel()
+        if g.size != self.nsteps * self.ngauge or o.size != g.size:
+            raise ValueError("gauge values and observations need nsteps x ngauge entries")
+        D = C.POINTER(C.c_double)
+        loss = C.c_double()
+        _check(_dd_sigs().hw_part_adj_set_misfit(self.ptr, g.ctypes.data_as(D), o.ctypes.data_as(D), C.byref(loss)),
+               "hw_part_adj_set_misfit")
+        return loss.value
+
+    def reverse_stage(self, j: int, k: int, dt: float):
+        """(alpha adjoint share [2], first maximising global nodes [2])."""
+        la = (C.c_double * 2)()
+        am = (C.c_int * 2)()
+        _check(_dd_sigs().hw_part_adj_reverse_stage(self.ptr, int(j), int(k), float(dt), la, am),
+               "hw_part_adj_reverse_stage")
+        return [la[0], la[1]], [am[0], am[1]]
+
+    def alpha_apply(self, lalpha, argmax):
+        la = (C.c_double * 2)(*[float(x) for x in lalpha])
+        am = (C.c_int * 2)(*[int(x) for x in argmax])
+        _check(_dd_sigs().hw_part_adj_alpha_apply(self.ptr, la, am), "hw_part_adj_alpha_apply")
+
+    def rpack(self, what: int, face: int, strip):
+        _check(_dd_sigs().hw_part_adj_rpack(self.ptr, int(what), int(face), _dev_ptr(strip)), "hw_part_adj_rpack")
+
+    def radd(self, what: int, face: int, mode: int, strip):
+        _check(_dd_sigs().hw_part_adj_radd(self.ptr, int(what), int(face), int(mode), _dev_ptr(strip)),
+               "hw_part_adj_radd")
+
+    def finish_static(self):
+        _check(_dd_sigs().hw_part_adj_finish_static(self.ptr), "hw_part_adj_finish_static")
+
+    def gradients(self):
+        """The block's own nodes of the state gradient (9 planes) and the static one (3), host arrays."""
+        info = self.h.info
+        gs = [np.empty((info.ny, info.nx)) for _ in range(9)]
+        gb = [np.empty((info.ny, info.nx)) for _ in range(3)]
+        _check(_dd_sigs().hw_part_adj_gradients(self.ptr, _pp([C.c_void_p(a.ctypes.data) for a in gs]),
+                                                 _pp([C.c_void_p(a.ctypes.data) for a in gb]), info.nx, HW_HOST),
+               "hw_part_adj_gradients")
+        return gs, gb
 
 
 def hw_halo_strip_size(h: _Handle, set_: int, face: int) -> int:

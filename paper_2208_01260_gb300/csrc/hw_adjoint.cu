@@ -782,6 +782,14 @@ void hw::adjoint_release(hw_solver* s) {
 
 namespace {
 
+// The gauge misfit sum over (step, gauge) of (eta - obs)^2, in that order: one function, so that every
+// entry point (single grid, blocks on one GPU, blocks over processes) rounds it alike.
+double misfit_loss(const double* g, const double* obs, size_t n) {
+  double L = 0.0;
+  for (size_t q = 0; q < n; ++q) L += (g[q] - obs[q]) * (g[q] - obs[q]);
+  return L;
+}
+
 int zero_planes(double* const* p, int count, size_t n, cudaStream_t st) {
   for (int q = 0; q < count; ++q) ACUDA(cudaMemsetAsync(p[q], 0, n * sizeof(double), st));
   return HW_OK;
@@ -1153,9 +1161,7 @@ int hw_gauge_loss(hw_solver* s, int nsteps, const double* dts, const int* gauge_
   if (rc == HW_OK) {
     ACUDA(cudaMemcpyAsync(g.data(), d_g, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     ACUDA(cudaStreamSynchronize(st));
-    double L = 0.0;
-    for (size_t q = 0; q < g.size(); ++q) L += (g[q] - eta_obs[q]) * (g[q] - eta_obs[q]);
-    *loss_out = L;
+    *loss_out = misfit_loss(g.data(), eta_obs, g.size());
     if (eta_gauges) std::copy(g.begin(), g.end(), eta_gauges);
     double* src[9];
     for (int q = 0; q < 9; ++q) src[q] = d_save + (size_t)q * v.n;
@@ -1274,9 +1280,7 @@ int hw_adjoint_run(hw_solver* s, int nsteps, const double* dts, const int* gauge
     check(cudaMemcpyAsync(g.data(), R.d_gvals, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
           "hw_adjoint_run: copy of gauge values");
     check(cudaStreamSynchronize(st), "hw_adjoint_run: forward pass");
-    double L = 0.0;
-    for (size_t q = 0; q < g.size(); ++q) L += (g[q] - eta_obs[q]) * (g[q] - eta_obs[q]);
-    *loss_out = L;
+    *loss_out = misfit_loss(g.data(), eta_obs, g.size());
   }
   // reverse pass
   if (rc == HW_OK) rc = zero_planes(B->lam[0], 9, v.n, st);
@@ -1487,9 +1491,7 @@ int dd_adjoint_impl(hw_dd* dd, int nsteps, const double* dts, const int* gauge_i
     check(cudaMemcpyAsync(g.data(), d_gvals, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
           "hw_dd_adjoint_run: copy of gauge values");
     check(cudaStreamSynchronize(st), "hw_dd_adjoint_run: forward pass");
-    double L = 0.0;
-    for (size_t q = 0; q < g.size(); ++q) L += (g[q] - eta_obs[q]) * (g[q] - eta_obs[q]);
-    *loss_out = L;
+    *loss_out = misfit_loss(g.data(), eta_obs, g.size());
   }
   // reverse pass
   int cur = 0;
@@ -1793,10 +1795,11 @@ int hw_part_adj_gauges(hw_part_adj* a, double* gvals) {
   return HW_OK;
 }
 
-int hw_part_adj_set_misfit(hw_part_adj* a, const double* gvals, const double* eta_obs) {
+int hw_part_adj_set_misfit(hw_part_adj* a, const double* gvals, const double* eta_obs, double* loss_out) {
   int rc = pa_check(a, "hw_part_adj_set_misfit");
   if (rc) return rc;
   if (!gvals || !eta_obs) return afail(HW_ERR_ARG, "hw_part_adj_set_misfit: null argument");
+  if (loss_out) *loss_out = misfit_loss(gvals, eta_obs, (size_t)a->nsteps * a->ngauge);
   const size_t gb = (size_t)a->nsteps * a->ngauge * sizeof(double);
   cudaStream_t st = a->v.stream;
   ACUDA(cudaMemcpyAsync(a->d_gall, gvals, gb, cudaMemcpyHostToDevice, st));

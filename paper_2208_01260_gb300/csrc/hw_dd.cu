@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/hwswe.h"
+#include "hw_halo.h"
 #include "hw_internal.h"
 
 namespace hw {
@@ -424,6 +425,35 @@ int dd_exchange_adjoint(hw_dd* d, double* const* const* planes, int nplanes, uns
   return e == cudaSuccess ? HW_OK : set_last_error(HW_ERR_CUDA, cudaGetErrorString(e));
 }
 
+}  // namespace hw
+
+namespace hw {
+static int halo_launch_done() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HW_OK : set_last_error(HW_ERR_CUDA, cudaGetErrorString(e));
+}
+int halo_pack_planes(double* const* planes, int np, int nxe, int nye, int face, double* strip, cudaStream_t st) {
+  const long long len = face < 2 ? nye - 4 : nxe;
+  k_halo_pack<<<blocks_for(np * 2 * len), 256, 0, st>>>(plane_set(planes, np), np, nxe, nye, face, strip);
+  return halo_launch_done();
+}
+int halo_unpack_planes(double* const* planes, int np, int nxe, int nye, int face, int mode, unsigned odd,
+                       const double* strip, cudaStream_t st) {
+  const long long len = face < 2 ? nye - 4 : nxe;
+  k_halo_unpack<<<blocks_for(np * 2 * len), 256, 0, st>>>(plane_set(planes, np), np, nxe, nye, face, mode, odd, strip);
+  return halo_launch_done();
+}
+int halo_adj_pack_planes(double* const* planes, int np, int nxe, int nye, int face, double* strip, cudaStream_t st) {
+  const long long len = face < 2 ? nye - 4 : nxe;
+  k_halo_adj_pack<<<blocks_for(np * 2 * len), 256, 0, st>>>(plane_set(planes, np), np, nxe, nye, face, strip);
+  return halo_launch_done();
+}
+int halo_adj_add_planes(double* const* planes, int np, int nxe, int nye, int face, int mode, unsigned odd,
+                        const double* strip, cudaStream_t st) {
+  const long long len = face < 2 ? nye - 4 : nxe;
+  k_halo_adj_add<<<blocks_for(np * 2 * len), 256, 0, st>>>(plane_set(planes, np), np, nxe, nye, face, mode, odd, strip);
+  return halo_launch_done();
+}
 }  // namespace hw
 
 namespace {

@@ -31,9 +31,10 @@ from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 
-from . import (HW_FACE_E, HW_FACE_N, HW_FACE_S, HW_FACE_W, HW_HALO_NEIGHBOR, HW_LAYOUT_EQUILIBRIUM, hw_dd_max_keys,
-               hw_dd_partition, hw_destroy, hw_get_state, hw_grid, hw_halo_pack, hw_halo_strip_size, hw_halo_unpack,
-               hw_params, hw_part_alpha_keys, hw_part_create, hw_part_finish_init, hw_part_init, hw_part_stage)
+from . import (HW_FACE_E, HW_FACE_N, HW_FACE_S, HW_FACE_W, HW_HALO_NEIGHBOR, HW_LAYOUT_EQUILIBRIUM, PartAdjoint,
+               hw_dd_max_keys, hw_dd_partition, hw_destroy, hw_get_state, hw_grid, hw_halo_pack, hw_halo_strip_size,
+               hw_halo_unpack, hw_params, hw_part_alpha_keys, hw_part_create, hw_part_finish_init, hw_part_init,
+               hw_part_stage)
 
 ABORT_KEY = "hw_dd_abort"
 
@@ -137,6 +138,21 @@ class Comm:
             self._wait(w, "halo exchange")
         for dev, host in staged:
             dev.copy_(host)
+
+    def allreduce(self, t, op: str, what: str):
+        """All-reduce of tensor t in place across ranks (op: "max", "min" or "sum"; what names it in errors)."""
+        if self.world == 1:
+            return
+        import torch.distributed as dist
+        rop = {"max": dist.ReduceOp.MAX, "min": dist.ReduceOp.MIN, "sum": dist.ReduceOp.SUM}[op]
+        buf = t.cpu() if (self.host_staging and t.is_cuda) else t
+        try:
+            work = dist.all_reduce(buf, op=rop, async_op=True)
+        except Exception as e:  # noqa: BLE001
+            raise self.fail("%s: %s: %s" % (what, type(e).__name__, e)) from e
+        self._wait(work, what)
+        if buf is not t:
+            t.copy_(buf)
 
     def allreduce_max(self, t):
         if self.world > 1:
@@ -330,3 +346,181 @@ def partition_instances(points: Sequence[int], world: int) -> List[List[int]]:
         out[r].append(i)
         load[r] += int(points[i])
     return [sorted(x) for x in out]
+
+
+# ------------------------------------------------------------------------------------------------
+# The adjoint over the blocks of several processes (the per-block calls hw_part_adj_* of hwswe.h): the
+# forward run recorded on every block's tape with the exchanges and the alpha all-reduce of rk3_step,
+# the gauge values summed over the blocks, then every stage reversed: the blocks' alpha-adjoint shares
+# summed and their first maximising nodes reduced to the global one (applied once, by its owner), and
+# the transposed exchange moving ring adjoints back to the nodes they were copied from, y faces first.
+# ------------------------------------------------------------------------------------------------
+INT_MAX = 2 ** 31 - 1
+
+
+def gauges_on(plan: Plan, part: int, gauge_idx: Sequence[int]):
+    """(slots, global nodes) of the gauges on block `part`'s own nodes."""
+    i, gnx = plan.info[part], plan.grid.nx
+    slots, nodes = [], []
+    for slot, g in enumerate(gauge_idx):
+        gi, gj = int(g) % gnx, int(g) // gnx
+        if i.i0 <= gi < i.i0 + i.nx and i.j0 <= gj < i.j0 + i.ny:
+            slots.append(slot)
+            nodes.append(int(g))
+    return slots, nodes
+
+
+class CudaBlockAdjoint:
+    """The per-block adjoint context of a CudaBlock (strips and keys as CUDA tensors)."""
+
+    def __init__(self, block: "CudaBlock", nsteps: int, ngauge: int, slots, nodes, global_nx: int):
+        self.block = block
+        self.a = PartAdjoint(block.h, nsteps, ngauge, slots, nodes, global_nx)
+
+    def close(self):
+        self.a.close()
+
+    def new_strip(self, n):
+        return self.block.new_strip(n)
+
+    def new_keys(self, n):
+        return self.block.new_keys(n)
+
+    def max_keys(self, rows, out):
+        self.block.max_keys(rows, out)
+
+    def __getattr__(self, name):  # strip_size, pack, unpack, alpha_keys, forward_stage, ... of PartAdjoint
+        return getattr(self.a, name)
+
+
+def _exchange_stage_input(ctxs, plan: Plan, comm: Comm, j: int, k: int):
+    """The forward exchange of the tapes' stage-k inputs of step j (as exchange(), plane set of 9)."""
+    for faces in (FACES_X, FACES_Y):
+        packed = {}
+        for p, c in ctxs.items():
+            for f in faces:
+                buf = c.new_strip(c.strip_size(0, f))
+                c.pack(j, k, f, buf)
+                packed[(p, f)] = buf
+        sends, recvs, received = [], [], {}
+        for order, (p, f, q) in enumerate(plan.messages(faces)):
+            mine_p, mine_q = plan.owner(p) == comm.rank, plan.owner(q) == comm.rank
+            if mine_q and not mine_p:
+                sends.append((packed[(q, f ^ 1)], plan.owner(p), order))
+            elif mine_p and not mine_q:
+                buf = ctxs[p].new_strip(ctxs[p].strip_size(0, f))
+                recvs.append((buf, plan.owner(q), order))
+                received[(p, f)] = buf
+        comm.exchange(sends, recvs)
+        for p, c in ctxs.items():
+            for f in faces:
+                mode = plan.info[p].mode[f]
+                if mode == HW_HALO_NEIGHBOR:
+                    q = plan.info[p].nbr[f]
+                    src = received[(p, f)] if (p, f) in received else packed[(q, f ^ 1)]
+                else:
+                    src = packed[(p, f)]
+                c.unpack(j, k, f, mode, src)
+
+
+def exchange_adjoint(ctxs, plan: Plan, comm: Comm, what: int):
+    """The transpose of one exchange on the adjoint planes `what` (0: state, 1: static): y faces, then x
+    faces; each block's ring strip of a face (cleared) is added to the nodes it was copied from."""
+    for faces in (FACES_Y, FACES_X):
+        packed = {}
+        for p, c in ctxs.items():
+            for f in faces:
+                buf = c.new_strip(c.strip_size(what, f))
+                c.rpack(what, f, buf)
+                packed[(p, f)] = buf
+        # the forward message (p receives face f from q) runs backwards: p's ring strip goes to q
+        sends, recvs, received = [], [], {}
+        for order, (p, f, q) in enumerate(plan.messages(faces)):
+            mine_p, mine_q = plan.owner(p) == comm.rank, plan.owner(q) == comm.rank
+            if mine_p and not mine_q:
+                sends.append((packed[(p, f)], plan.owner(q), order))
+            elif mine_q and not mine_p:
+                buf = ctxs[q].new_strip(ctxs[q].strip_size(what, f ^ 1))
+                recvs.append((buf, plan.owner(p), order))
+                received[(p, f)] = buf
+        comm.exchange(sends, recvs)
+        for p, c in sorted(ctxs.items()):
+            for f in faces:
+                mode = plan.info[p].mode[f]
+                if mode != HW_HALO_NEIGHBOR:
+                    c.radd(what, f, mode, packed[(p, f)])
+                elif plan.owner(plan.info[p].nbr[f]) == comm.rank:
+                    ctxs[plan.info[p].nbr[f]].radd(what, f ^ 1, mode, packed[(p, f)])
+        for (p, f), buf in sorted(received.items()):
+            ctxs[plan.info[p].nbr[f]].radd(what, f ^ 1, HW_HALO_NEIGHBOR, buf)
+
+
+def _stage_keys(ctxs, comm: Comm, j: int, k: int):
+    items = sorted(ctxs.items())
+    first = items[0][1]
+    rows = first.new_keys(len(items))
+    for r, (_, c) in enumerate(items):
+        c.alpha_keys(j, k, rows[r])
+    keys = first.new_keys(1)[0]
+    first.max_keys(rows, keys)
+    comm.allreduce_max(keys)
+    return keys
+
+
+def adjoint_run(blocks: Dict[int, object], plan: Plan, comm: Comm, dts: Sequence[float], gauge_idx: Sequence[int],
+                eta_obs, make_ctx=None):
+    """Gauge misfit sum_j sum_g (eta_g - obs)^2 of a run of len(dts) steps from the blocks' current states and
+    its gradient, as hw_dd_adjoint_run but with the blocks spread over ranks. Returns (loss, {part: (9 state
+    gradient planes, 3 static ones)}) for the rank's blocks (own nodes, physical units). make_ctx(part, block,
+    nsteps, ngauge, slots, nodes, global_nx) builds a block's context (default: CudaBlockAdjoint)."""
+    import torch
+    nsteps, ngauge = len(dts), len(gauge_idx)
+    obs = np.ascontiguousarray(eta_obs, dtype=np.float64).reshape(nsteps * ngauge)
+    make_ctx = make_ctx or (lambda p, b, n, ng, sl, nd, gnx: CudaBlockAdjoint(b, n, ng, sl, nd, gnx))
+    ctxs = {}
+    for p, b in sorted(blocks.items()):
+        slots, nodes = gauges_on(plan, p, gauge_idx)
+        ctxs[p] = make_ctx(p, b, nsteps, ngauge, slots, nodes, plan.grid.nx)
+    try:
+        for j in range(nsteps):
+            for k in (1, 2, 3):
+                comm.check_peers()
+                _exchange_stage_input(ctxs, plan, comm, j, k)
+                keys = _stage_keys(ctxs, comm, j, k)
+                for _, c in sorted(ctxs.items()):
+                    c.forward_stage(j, k, dts[j], keys)
+        gv = torch.zeros(nsteps * ngauge, dtype=torch.float64)
+        for _, c in sorted(ctxs.items()):
+            gv += torch.from_numpy(c.gauges())  # each slot is one block's value, zeros elsewhere: exact
+        comm.allreduce(gv, "sum", "gauge values")
+        g = gv.numpy()
+        loss = None
+        for _, c in sorted(ctxs.items()):
+            loss = c.set_misfit(g, obs)  # the library sums the misfit as its other adjoint entry points do
+        for j in reversed(range(nsteps)):
+            for k in (3, 2, 1):
+                comm.check_peers()
+                la = torch.zeros(2, dtype=torch.float64)
+                am = torch.full((2,), INT_MAX, dtype=torch.int64)
+                for _, c in sorted(ctxs.items()):
+                    l, a = c.reverse_stage(j, k, dts[j])
+                    la += torch.tensor(l, dtype=torch.float64)
+                    am = torch.minimum(am, torch.tensor(a, dtype=torch.int64))
+                comm.allreduce(la, "sum", "alpha adjoint")
+                comm.allreduce(am, "min", "alpha node")
+                for _, c in sorted(ctxs.items()):
+                    c.alpha_apply(la.tolist(), am.tolist())
+                exchange_adjoint(ctxs, plan, comm, 0)
+        for _, c in sorted(ctxs.items()):
+            c.finish_static()
+        exchange_adjoint(ctxs, plan, comm, 1)
+        grads = {p: c.gradients() for p, c in sorted(ctxs.items())}
+    except DecompFailure:
+        raise
+    except Exception as e:  # noqa: BLE001
+        raise comm.fail("adjoint: %s: %s" % (type(e).__name__, e)) from e
+    finally:
+        for c in ctxs.values():
+            if hasattr(c, "close"):
+                c.close()
+    return loss, grads

@@ -337,6 +337,114 @@ def test_protocol_failures_end_every_rank(mode):
         assert dt < 20.0, (r, msg, dt)
 
 
+class RingBlock:
+    """A numpy block for the exchange and its transpose: 9 extended planes x (forward) and y (adjoint),
+    strips packed, unpacked, packed-and-cleared and added by the rules hwswe.h states for hw_halo_pack /
+    hw_halo_unpack and hw_part_adj_rpack / hw_part_adj_radd."""
+
+    def __init__(self, info, rng):
+        import torch
+        self.torch, self.info = torch, info
+        self.nxe, self.nye = info.nx + 4, info.ny + 4
+        self.x = [np.zeros((self.nye, self.nxe)) for _ in range(9)]
+        for a in self.x:
+            a[2:-2, 2:-2] = rng.integers(-8, 9, size=(info.ny, info.nx))
+        self.y = [rng.integers(-8, 9, size=(self.nye, self.nxe)).astype(np.float64) for _ in range(9)]
+
+    def new_strip(self, n):
+        return self.torch.zeros(n, dtype=self.torch.float64)
+
+    def strip_size(self, what, face):
+        return 9 * 2 * (self.info.ny if face < 2 else self.nxe)
+
+    def _own(self, face, c):
+        ny, nx = self.info.ny, self.info.nx
+        return {0: (slice(2, 2 + ny), 2 + c), 1: (slice(2, 2 + ny), nx + c),
+                2: (2 + c, slice(None)), 3: (ny + c, slice(None))}[face]
+
+    def _ring(self, face, c):
+        ny, nx = self.info.ny, self.info.nx
+        return {0: (slice(2, 2 + ny), c), 1: (slice(2, 2 + ny), nx + 2 + c),
+                2: (c, slice(None)), 3: (ny + 2 + c, slice(None))}[face]
+
+    @staticmethod
+    def _source(face, mode, c):  # the strip offset a ring offset c is copied from
+        return c if mode == 0 else (1 - c if mode == 1 else (0 if face in (0, 2) else 1))
+
+    def pack(self, j, k, face, strip):
+        strip.numpy()[:] = np.concatenate([a[self._own(face, c)] for a in self.x for c in (0, 1)])
+
+    def unpack(self, j, k, face, mode, strip):
+        s = strip.numpy().reshape(9, 2, -1)
+        odd = ODD_X if face < 2 else ODD_Y
+        for q, a in enumerate(self.x):
+            for c in (0, 1):
+                v = s[q, self._source(face, mode, c)]
+                a[self._ring(face, c)] = -v if (mode == 1 and q in odd) else v
+
+    def rpack(self, what, face, strip):
+        strip.numpy()[:] = np.concatenate([a[self._ring(face, c)] for a in self.y for c in (0, 1)])
+        for a in self.y:
+            for c in (0, 1):
+                a[self._ring(face, c)] = 0.0
+
+    def radd(self, what, face, mode, strip):
+        s = strip.numpy().reshape(9, 2, -1)
+        odd = ODD_X if face < 2 else ODD_Y
+        for q, a in enumerate(self.y):
+            for c in (0, 1):
+                v = s[q, c]
+                a[self._own(face, self._source(face, mode, c))] += -v if (mode == 1 and q in odd) else v
+
+
+def _transpose_rank(rank, ws, port, name, q):
+    try:
+        os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+        sys.path.insert(0, ROOT)
+        import torch
+        import torch.distributed as dist
+        from paper_2208_01260_gb300 import decomp
+        dist.init_process_group("gloo", rank=rank, world_size=ws)
+        _, grid, px, py = _case(name)
+        plan = decomp.Plan(grid, px, py, ws)
+        comm = decomp.Comm.from_torch(timeout_s=30.0)
+        blocks = {p: RingBlock(plan.info[p], np.random.default_rng(100 + p)) for p in plan.local_parts(rank)}
+        decomp._exchange_stage_input(blocks, plan, comm, 0, 1)  # x: own nodes -> extended (E x)
+        lhs = sum(float((a * c).sum()) for b in blocks.values() for a, c in zip(b.x, b.y))  # <E x, y>
+        decomp.exchange_adjoint(blocks, plan, comm, 0)  # y -> E^T y on the own nodes, rings cleared
+        rhs = sum(float((a[2:-2, 2:-2] * c[2:-2, 2:-2]).sum()) for b in blocks.values() for a, c in zip(b.x, b.y))
+        ring_left = sum(float(np.abs(c).sum() - np.abs(c[2:-2, 2:-2]).sum()) for b in blocks.values() for c in b.y)
+        t = torch.tensor([lhs, rhs, ring_left], dtype=torch.float64)
+        dist.all_reduce(t)
+        q.put((rank, t.tolist()))
+        dist.destroy_process_group()
+    except Exception as e:  # noqa: BLE001
+        q.put((rank, "error: %r" % e))
+
+
+@pytest.mark.parametrize("name", ["refl_per", "per_out", "out_refl", "per_per_4"])
+def test_adjoint_exchange_is_the_transpose(name):
+    """The transposed exchange of the multi-process adjoint (decomp.exchange_adjoint: y faces, then x faces,
+    ring strips sent back to the blocks they came from and added there, with the mirror's signs and the
+    open end's repeated node) against the forward exchange on two gloo ranks: <E x, y> = <x, E^T y> summed
+    over all blocks, exactly (small integers), and every ring left at zero; for walls, periodic wrap across
+    ranks, open ends and corners."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_transpose_rank, args=(r, 2, port, name, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=300) for _ in range(2)]
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    for rank, v in res:
+        assert not isinstance(v, str), v
+        lhs, rhs, rest = v
+        assert lhs == rhs and rest == 0.0, (name, lhs, rhs, rest)
+
+
 def test_batched_instances_partition_across_ranks():
     """The batched form shares its instances among ranks with no communication: every instance on exactly
     one rank, and no rank more than one largest instance above the average load."""

@@ -250,3 +250,122 @@ def test_protocol_two_processes_on_the_gpu(hw):
     for qq, (a, b) in enumerate(zip(ref.state(), got)):
         assert np.array_equal(a, b), (qq, float(np.abs(a - b).max()))
     ref.close()
+
+
+def _adjoint_problem(hw, sc, nsteps, ng, seed):
+    rng = np.random.default_rng(seed)
+    ref = hw.Solver.from_scenario(sc, hw.make_params())
+    dts = [ref.cfl_dt()] * nsteps
+    ref.close()
+    gidx = rng.choice(sc.nx * sc.ny, ng, replace=False).astype(np.int32)
+    obs = 1.0 + 0.002 * rng.normal(size=nsteps * ng)
+    return dts, gidx, obs
+
+
+def _undecomposed_adjoint(hw, sc, dts, gidx, obs):
+    import torch
+    from paper_2208_01260_gb300 import adjoint as A
+    ref = hw.Solver.from_scenario(sc, hw.make_params())
+    gs = torch.empty(9, sc.ny, sc.nx, dtype=torch.float64, device="cuda")
+    gb = torch.empty(3, sc.ny, sc.nx, dtype=torch.float64, device="cuda")
+    loss, _ = A.hw_adjoint_run(ref.h, dts, gidx, obs, A.HW_ADJ_TAPE, [gs[q] for q in range(9)], [gb[q] for q in range(3)])
+    ref.close()
+    return loss, gs.cpu().numpy(), gb.cpu().numpy()
+
+
+def _check_adjoint_grads(plan, grads, ref_s, ref_b):
+    scale = float(np.abs(ref_s).max())
+    for p, (gs, gb) in grads.items():
+        i = plan.info[p]
+        win = (slice(i.j0, i.j0 + i.ny), slice(i.i0, i.i0 + i.nx))
+        for q in range(9):
+            assert np.abs(gs[q] - ref_s[q][win]).max() <= 1e-10 * scale, (p, q)
+        for q in range(3):
+            assert np.abs(gb[q] - ref_b[q][win]).max() <= 1e-10 * scale, (p, 9 + q)
+
+
+def test_adjoint_protocol_in_one_process(hw):
+    """The multi-process adjoint (decomp.adjoint_run over hw_part_adj_*) with all 2 x 2 blocks in this process
+    against the undecomposed adjoint on its whole-run tape: the loss bit for bit, the gradients to 1e-10 of the
+    largest state-gradient entry (the alpha adjoint's shares summed in another order)."""
+    from paper_2208_01260_gb300 import decomp
+    sc = _scenario(96, 66, S.REFLECTIVE, S.PERIODIC, seed=64)
+    dts, gidx, obs = _adjoint_problem(hw, sc, 5, 9, 8)
+    g = hw.make_grid(sc.nx, sc.ny, sc.x0, sc.x1, sc.y0, sc.y1, sc.bc_x, sc.bc_y, dim=2)
+    params = hw.make_params()
+    plan = decomp.Plan(g, 2, 2, 1)
+    comm = decomp.Comm(0, 1)
+    blocks = {p: decomp.CudaBlock(g, params, 2, 2, p) for p in plan.local_parts(0)}
+    decomp.initialise(blocks, plan, comm, lambda p: decomp.window12(sc, plan.info[p]))
+    loss, grads = decomp.adjoint_run(blocks, plan, comm, dts, gidx, obs)
+    for b in blocks.values():
+        b.close()
+    ref_loss, ref_s, ref_b = _undecomposed_adjoint(hw, sc, dts, gidx, obs)
+    assert loss == ref_loss
+    _check_adjoint_grads(plan, grads, ref_s, ref_b)
+
+
+def _gpu_adjoint_rank(rank, ws, port, q):
+    try:
+        os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        sys.path.insert(0, root)
+        from datetime import timedelta
+        import torch
+        import torch.distributed as dist
+        import paper_2208_01260_gb300 as hw
+        from paper_2208_01260_gb300 import decomp
+        torch.cuda.set_device(0)
+        dist.init_process_group("gloo", rank=rank, world_size=ws, timeout=timedelta(seconds=120))
+        sc = _scenario(96, 66, S.PERIODIC, S.REFLECTIVE, seed=67)
+        dts, gidx, obs = _adjoint_problem(hw, sc, 4, 8, 9)
+        g = hw.make_grid(sc.nx, sc.ny, sc.x0, sc.x1, sc.y0, sc.y1, sc.bc_x, sc.bc_y, dim=2)
+        params = hw.make_params()
+        plan = decomp.Plan(g, 2, 2, ws)
+        comm = decomp.Comm.from_torch(timeout_s=60.0)
+        blocks = {p: decomp.CudaBlock(g, params, 2, 2, p) for p in plan.local_parts(rank)}
+        decomp.initialise(blocks, plan, comm, lambda p: decomp.window12(sc, plan.info[p]))
+        loss, grads = decomp.adjoint_run(blocks, plan, comm, dts, gidx, obs)
+        q.put((rank, loss, grads))
+        for b in blocks.values():
+            b.close()
+        dist.destroy_process_group()
+    except Exception as e:  # noqa: BLE001
+        q.put((rank, "error: %r" % e, None))
+
+
+def test_adjoint_protocol_two_processes_on_the_gpu(hw):
+    """The multi-process adjoint across two processes on this GPU (2 x 2 blocks, two per rank; strips, keys,
+    gauge values and alpha adjoints through gloo): both ranks find the undecomposed adjoint's loss bit for bit
+    and their blocks' gradients within 1e-10 of the largest state-gradient entry, with periodic wrap across
+    ranks along x and walls along y."""
+    import torch.multiprocessing as mp
+    from paper_2208_01260_gb300 import decomp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    procs = [ctx.Process(target=_gpu_adjoint_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        res = [q.get(timeout=600) for _ in range(2)]
+    finally:
+        for p in procs:
+            p.join(60)
+            if p.exitcode is None:
+                p.kill()
+    for r in res:
+        assert not isinstance(r[1], str), r[1]
+    sc = _scenario(96, 66, S.PERIODIC, S.REFLECTIVE, seed=67)
+    dts, gidx, obs = _adjoint_problem(hw, sc, 4, 8, 9)
+    ref_loss, ref_s, ref_b = _undecomposed_adjoint(hw, sc, dts, gidx, obs)
+    g = hw.make_grid(sc.nx, sc.ny, sc.x0, sc.x1, sc.y0, sc.y1, sc.bc_x, sc.bc_y, dim=2)
+    plan = decomp.Plan(g, 2, 2, 2)
+    parts = []
+    for rank, loss, grads in res:
+        assert loss == ref_loss, (rank, loss, ref_loss)
+        _check_adjoint_grads(plan, grads, ref_s, ref_b)
+        parts += list(grads)
+    assert sorted(parts) == [0, 1, 2, 3]
