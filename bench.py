@@ -678,9 +678,27 @@ def main():
         solver.advance(1, use_graph=False)
         hw.hw_get_state(solver.h, hout, hw.HW_LAYOUT_PHYSICAL)
     torch.cuda.synchronize()
-    e2e_v, e2e_s, _ = job_rate(NX * NY * STAGES * ke, time.perf_counter() - t0, ws)
+    e2e_serial, _, _ = job_rate(NX * NY * STAGES * ke, time.perf_counter() - t0, ws)
+    # the same jobs (state up, one step, state down) through pipeline.JobPipeline: two solvers on their
+    # own streams and host threads, so one job's copies run during the other's step
+    from paper_2208_01260_gb300.pipeline import JobPipeline
+    pipe = JobPipeline(sc, hw.make_params(), lanes=2)
+    outs = [[torch.empty(NY, NX, dtype=torch.float64).pin_memory().numpy() for _ in range(9)] for _ in range(2)]
+    pipe.run([hin] * 2, outs)  # warm-up
+    kp = max(4, ke)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pipe.run([hin] * kp, [outs[i % 2] for i in range(kp)])
+    torch.cuda.synchronize()
+    e2e_v, _, _ = job_rate(NX * NY * STAGES * kp, time.perf_counter() - t0, ws)
+    pipe.close()
     e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": STATE_BYTES,
-           "d2h_bytes_per_step": STATE_BYTES, "steps": ke}
+           "d2h_bytes_per_step": STATE_BYTES, "steps": kp,
+           "how": "independent jobs (the 9-plane state uploaded from pinned host memory, one RK3 step, the state "
+                  "downloaded), two solvers on their own streams and host threads (pipeline.JobPipeline)",
+           "serial": {"value": e2e_serial, "steps": ke,
+                      "how": "one solver: upload, step, download, one job after the other"}}
 
     solver.sync()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

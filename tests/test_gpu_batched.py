@@ -145,6 +145,31 @@ def test_autotuner_picks_valid_tiles(hw, tmp_path):
             assert np.array_equal(x, y)
 
 
+def test_config4_full_batch_against_oracle(hw, orc, tmp_path):
+    """The benchmark's batched workload at its full size (512 instances, nx and ny log-uniform in [64, 1024],
+    58 M points) in the configuration bench.py times (autotuned tiles, two steps from a captured graph): the
+    three smallest instances and the largest against the oracle's two SSP-RK3 steps at their own CFL steps,
+    every node (relative L1 1e-9, normwise 1e-11), and the times against the oracle's; every instance has
+    taken two steps."""
+    nxs, nys = S.batch_sizes(512)
+    scs = [S.batch_scenario(i, int(nxs[i]), int(nys[i])) for i in range(512)]
+    pts = nxs.astype(np.int64) * nys
+    b = hw.BatchedSolver(scs)
+    b.autotune(cache_path=str(tmp_path / "tune.json"))
+    b.run(2, use_graph=True)
+    t, steps = b.times()
+    assert list(steps) == [2] * 512
+    order = np.argsort(pts, kind="stable")
+    for i in list(order[:3]) + [int(order[-1])]:
+        sc = scs[i]
+        ref, stat, tref = _oracle_run(orc, sc, 2)
+        got = b.state(int(i))
+        assert abs(t[i] - tref) <= 1e-13 * tref, (i, t[i], tref)
+        assert max(rel_l1(got, ref)) <= 1e-9, (i, rel_l1(got, ref))
+        assert max(normwise(got, ref, stage_scales(ref, stat))) <= 1e-11, i
+    b.close()
+
+
 def test_batch_rejects_bad_grids_and_depth(hw):
     with pytest.raises(hw.HwError):
         hw.hw_batch_create([hw.make_grid(64, 1, dim=1)], hw.make_params())
