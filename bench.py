@@ -535,6 +535,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--batched-steps", type=int, default=6, help="steps of the batched comparison (0 = skip)")
+    ap.add_argument("--batched-instances", type=int, default=512,
+                    help="instances of the batched comparison (512: the benchmark workload; fewer for a small "
+                         "case to profile)")
     ap.add_argument("--adjoint-steps", type=int, default=400, help="steps of the adjoint cost measurement (0 = skip)")
     ap.add_argument("--fp32-steps", type=int, default=200, help="steps of the single-precision variant (0 = skip)")
     ap.add_argument("--decomp-steps", type=int, default=10, help="steps of the block-decomposition comparison (0 = skip)")
@@ -722,7 +725,10 @@ def main():
         args.batched_steps = args.adjoint_steps = args.fp32_steps = args.decomp_steps = 0
     if args.batched_steps > 0 and (NX, NY) == (2048, 2048):
         solver.close()
-        extra("batched", lambda: batched_compare(args.batched_steps))
+        extra("batched", lambda: dict(batched_compare(args.batched_steps, n_inst=args.batched_instances),
+                                      **({} if args.batched_instances == 512 else
+                                         {"workload": "%d grids drawn as the benchmark's (sizes log-uniform in [64, 1024]; not config 4)"
+                                                      % args.batched_instances})))
         # the regime the batched form is for: grids too small to fill the GPU one launch at a time
         extra("batched_small_grids", lambda: dict(batched_compare(args.batched_steps, n_inst=1024, fixed=(64, 64)),
                                                   workload="1024 grids of 64x64 (not config 4)"))
