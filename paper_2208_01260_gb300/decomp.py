@@ -52,6 +52,8 @@ class Plan:
     """Blocks of the grid and their owners."""
 
     def __init__(self, grid: hw_grid, px: int, py: int, world: int = 1):
+        if world < 1 or px * py < world:
+            raise ValueError("every rank needs a block: px * py = %d < world = %d" % (px * py, world))
         self.grid, self.px, self.py, self.world = grid, px, py, world
         self.info = [hw_dd_partition(grid, px, py, p) for p in range(px * py)]
 

@@ -31,6 +31,15 @@ def _grid(hw, nx, ny, bcx, bcy):
     return hw.make_grid(nx, ny, 0.0, nx / 64.0, 0.0, ny / 64.0, bcx, bcy, dim=2)
 
 
+def test_plan_needs_a_block_per_rank():
+    import paper_2208_01260_gb300 as hw
+    from paper_2208_01260_gb300 import decomp
+    g = _grid(hw, 64, 32, PER, PER)
+    with pytest.raises(ValueError):
+        decomp.Plan(g, 1, 2, 3)
+    assert decomp.Plan(g, 1, 2, 2).local_parts(1) == [1]
+
+
 def test_partition_covers_grid_and_pairs_neighbours():
     import paper_2208_01260_gb300 as hw
     for (nx, ny, px, py, bcx, bcy) in [(48, 40, 3, 2, PER, REF), (50, 33, 4, 3, OUT, PER), (9, 4, 2, 2, REF, OUT),
