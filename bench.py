@@ -63,18 +63,18 @@ PEAK_FP64_OPS = SMS * DFMA_PER_SM_CLK * SM_GHZ * 1e9
 # 9 state, 3 static and 9 base planes and write 9 (limiter recomputed: 27 planes of 8 bytes on average).
 # The whole-step HBM fraction is taken against it.
 ALGO_BYTES_PER_NODE_STAGE = 216.0
-# DRAM bytes per unit from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum of one launch at
-# 2048x1024, the state and interface planes above L2; the node kernel at RK stage 3), valid only for the
-# kernel sources they were taken on (sources_sha); scaled to a launch by its units (traffic is proportional
-# to them).
+# DRAM bytes per unit from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
+# benchmark at 2048^2, a one-pass capture; the node kernel at RK stage 3), valid only for the kernel sources
+# they were taken on (sources_sha); times the units of a launch.
 TRAFFIC = {
-    "sweep_x": {"bytes_per_unit": 223.3, "sha": "9f87d6a751d6f588"},
-    "sweep_y": {"bytes_per_unit": 226.8, "sha": "9f87d6a751d6f588"},
-    "node": {"bytes_per_unit": 530.6, "sha": "9f87d6a751d6f588"},
+    "sweep_x": {"bytes_per_unit": 231.5, "sha": "9f87d6a751d6f588"},
+    "sweep_y": {"bytes_per_unit": 235.5, "sha": "9f87d6a751d6f588"},
+    "node": {"bytes_per_unit": 535.2, "sha": "9f87d6a751d6f588"},
 }
-# FP64-pipe instructions per unit (ncu: DFMA + DADD + DMUL thread instructions of the same launches over
-# their units). Part of the products run on the integer pipes (each bit-identical to DMUL), so these are
-# below the algorithmic "ops" above; valid only for the kernel sources they were taken on (sources_sha).
+# FP64-pipe instructions per unit (ncu --set full at 2048x1024: DFMA + DADD + DMUL thread instructions of
+# one launch over its units; the count per unit does not depend on the grid size). Part of the products
+# run on the integer pipes (each bit-identical to DMUL), so these are below the algorithmic "ops" above;
+# valid only for the kernel sources they were taken on (sources_sha).
 FP64_PIPE_OPS = {
     "sweep_x": {"ops_per_unit": 341.9, "sha": "9f87d6a751d6f588"},
     "sweep_y": {"ops_per_unit": 342.8, "sha": "9f87d6a751d6f588"},
