@@ -369,3 +369,47 @@ def test_adjoint_protocol_two_processes_on_the_gpu(hw):
         _check_adjoint_grads(plan, grads, ref_s, ref_b)
         parts += list(grads)
     assert sorted(parts) == [0, 1, 2, 3]
+
+
+def test_part_adjoint_argument_and_order_errors(hw):
+    """hw_part_adj_*: a gauge off the block's own nodes, step, stage, face, mode and plane-set arguments out
+    of range (HW_ERR_ARG), the reverse before hw_part_adj_set_misfit and an alpha application without a
+    reverse stage (HW_ERR_STATE); a context on a solver that is not a block is refused."""
+    import torch
+    from paper_2208_01260_gb300 import decomp
+    sc = _scenario(64, 48, S.REFLECTIVE, S.REFLECTIVE, seed=68)
+    g = hw.make_grid(sc.nx, sc.ny, sc.x0, sc.x1, sc.y0, sc.y1, sc.bc_x, sc.bc_y, dim=2)
+    params = hw.make_params()
+    plan = decomp.Plan(g, 2, 1, 1)
+    comm = decomp.Comm(0, 1)
+    blocks = {p: decomp.CudaBlock(g, params, 2, 1, p) for p in plan.local_parts(0)}
+    decomp.initialise(blocks, plan, comm, lambda p: decomp.window12(sc, plan.info[p]))
+    blk = blocks[0]
+    with pytest.raises(hw.HwError) as e:  # node (40, 5) lies on block 1
+        hw.PartAdjoint(blk.h, 2, 1, [0], [5 * sc.nx + 40], sc.nx)
+    assert e.value.code == -1
+    a = hw.PartAdjoint(blk.h, 2, 1, [0], [5 * sc.nx + 3], sc.nx)
+    strip = torch.zeros(a.strip_size(0, hw.HW_FACE_E), dtype=torch.float64, device="cuda")
+    keys = torch.zeros(2, dtype=torch.int64, device="cuda")
+    for call in (lambda: a.pack(2, 1, hw.HW_FACE_E, strip), lambda: a.pack(0, 4, hw.HW_FACE_E, strip),
+                 lambda: a.pack(0, 1, 7, strip), lambda: a.unpack(0, 1, hw.HW_FACE_E, 9, strip),
+                 lambda: a.rpack(2, hw.HW_FACE_E, strip), lambda: a.forward_stage(0, 1, -1.0, keys),
+                 lambda: a.strip_size(3, hw.HW_FACE_E)):
+        with pytest.raises(hw.HwError) as e:
+            call()
+        assert e.value.code == -1
+    with pytest.raises(hw.HwError) as e:
+        a.reverse_stage(1, 3, 1e-3)
+    assert e.value.code == -6
+    a.set_misfit(np.zeros(2), np.zeros(2))
+    with pytest.raises(hw.HwError) as e:
+        a.alpha_apply([0.0, 0.0], [0, 0])
+    assert e.value.code == -6
+    a.close()
+    s = hw.Solver.from_scenario(sc, params)
+    with pytest.raises(hw.HwError) as e:
+        hw.PartAdjoint(s.h, 2, 1, [0], [3], sc.nx)
+    assert e.value.code == -1
+    s.close()
+    for b in blocks.values():
+        b.close()
