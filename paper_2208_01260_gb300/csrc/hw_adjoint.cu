@@ -705,6 +705,7 @@ struct AdjBuffers {
   double* lalpha = nullptr;
   int* argmax = nullptr;
   double* lstatic_phys[3] = {};
+  unsigned long long* amax = nullptr;  // the forward alpha reduction's keys and scratch (kAlpha2dScratch)
 };
 
 std::mutex g_adj_mu;
@@ -755,6 +756,7 @@ int get_buffers(hw_solver* s, const hw::SolverView& v, AdjBuffers** out) {
   for (int q = 0; q < 2; ++q) { A(&B->lsv[q], n); A(&B->lsq[q], n); }
   double* misc = nullptr;
   A(&misc, 8);
+  A(reinterpret_cast<double**>(&B->amax), hw::kAlpha2dScratch);
   if (rc != HW_OK) {
     for (void* p : B->allocs) cudaFree(p);
     delete B;
@@ -834,9 +836,8 @@ int forward_record(const hw::SolverView& v, AdjBuffers* B, const StepTape& T, do
     for (int c = 0; c < 3; ++c) { d.X[3 + c] = T.dbx[k - 1][c]; d.Y[3 + c] = T.dby[k - 1][c]; }
     d.X[0] = T.fx[k - 1];
     d.Y[0] = T.fy[k - 1];
-    double* amax = B->lalpha + 5;  // scratch for the reduction keys (3 slots)
-    hw::launch_alpha2d(d, (unsigned long long*)amax, (int*)(B->lalpha + 2), st);
-    hw::launch_finish_alpha2d(d, (const unsigned long long*)amax, T.alpha + 2 * (k - 1), nullptr, v.params->cfl,
+    hw::launch_alpha2d(d, B->amax, (int*)(B->lalpha + 2), st);
+    hw::launch_finish_alpha2d(d, B->amax, T.alpha + 2 * (k - 1), nullptr, v.params->cfl,
                               nullptr, -1.0, st);
     hw::launch_sweep_x2d(d, T.alpha + 2 * (k - 1), lin, chr, st);
     hw::launch_sweep_y2d(d, T.alpha + 2 * (k - 1), lin, chr, st);
@@ -1445,9 +1446,8 @@ int dd_adjoint_impl(hw_dd* dd, int nsteps, const double* dts, const int* gauge_i
         const StepTape T = layout[p].step(bl[p].tape, j);
         hw::Dev2D d = *bl[p].v.d2;
         for (int q = 0; q < 9; ++q) d.S[q] = T.in[k - 1][q];
-        double* amax = bl[p].B->lalpha + 5;  // scratch of the reduction (3 slots)
-        hw::launch_alpha2d(d, (unsigned long long*)amax, (int*)(bl[p].B->lalpha + 2), bl[p].v.stream);
-        check(cudaMemcpyAsync(keys + 2 * p, amax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+        hw::launch_alpha2d(d, bl[p].B->amax, (int*)(bl[p].B->lalpha + 2), bl[p].v.stream);
+        check(cudaMemcpyAsync(keys + 2 * p, bl[p].B->amax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
                               bl[p].v.stream),
               "hw_dd_adjoint_run: alpha keys");
       }
@@ -1614,7 +1614,7 @@ struct hw_part_adj {
   double* d_obs = nullptr;
   double* lal = nullptr;      // [2] alpha adjoint, then [2] ints: first maximising node
   double* tmp = nullptr;      // 9 planes: state gradient in physical units
-  double* keys = nullptr;     // 3 key slots of the alpha reduction
+  double* keys = nullptr;     // the alpha reduction's keys and scratch (kAlpha2dScratch slots)
   int cur = 0;
   bool reverse = false;
   hw::AdjDev last{};
@@ -1692,7 +1692,7 @@ int hw_part_adj_create(hw_solver* s, int nsteps, int ngauge, int nloc, const int
   alloc((void**)&a->d_obs, gb);
   alloc((void**)&a->lal, 4 * sizeof(double));
   alloc((void**)&a->tmp, 9 * a->v.n * sizeof(double));
-  alloc((void**)&a->keys, 4 * sizeof(double));
+  alloc((void**)&a->keys, hw::kAlpha2dScratch * sizeof(double));
   if (rc) { pa_free(a); return rc; }
   cudaStream_t st = a->v.stream;
   cudaError_t e = cudaFuncSetAttribute(hw::k_adj_sweep_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hw::AY_SMEM);

@@ -198,8 +198,9 @@ int hw_create(const hw_grid* grid, const hw_params* params, void* cuda_stream, h
   for (int q = 0; q < 12; ++q) A(&s->staging[q], s->n);
   double* misc = nullptr;
   A(&misc, 16);
+  // the alpha reduction's keys and scratch (launch_alpha2d: kAlpha2dScratch 8-byte slots)
+  A(reinterpret_cast<double**>(&s->amax), hw::kAlpha2dScratch);
   if (rc != HW_OK) { hw_destroy(s); return rc; }
-  s->amax = (unsigned long long*)misc;  // 3 slots: alpha_x, alpha_y keys and the coarse pass's maxima
   s->alpha = misc + 3;
   s->dt = misc + 5;  // dt[0] = step, dt[1] = time after the step (written by the CFL kernel)
   s->t = misc + 7;

@@ -81,7 +81,11 @@ struct PhysIn1D {
 
 // launchers (hw_kernels2d.cu)
 int set_kernel_attributes2d();
-// amax: 3 device slots (the alpha_x and alpha_y keys, and scratch of the reduction); cleared here.
+// amax (double grids): kAlpha2dScratch device slots: the alpha_x and alpha_y keys, then scratch of the
+// reduction (its float maxima, then one slot per tile); the first three are cleared here. The float
+// variant's reduction uses the first three.
+constexpr int kAlpha2dTiles = 152 * 8;
+constexpr int kAlpha2dScratch = 3 + kAlpha2dTiles;
 void launch_alpha2d(const Dev2D& d, unsigned long long* amax, int* status, cudaStream_t st);
 void launch_finish_alpha2d(const Dev2D& d, const unsigned long long* amax, double* alpha, double* dt_out,
                            double cfl, const double* t_now, double t_end, cudaStream_t st);

@@ -97,25 +97,39 @@ __global__ void __launch_bounds__(256, kNodeBlocks<R>) k_node2d(Dev2DT<R> d, Sta
 // non-positive depth: in double the two passes of hw_stencil2d.cuh (coarse float maxima, then the exact
 // double maximum near them), in single precision one pass.
 // ---------------------------------------------------------------------------------------------
-// Each thread takes kAlphaU nodes a stride apart per iteration, their loads issued together (the passes
-// are bound by memory latency at one node per thread in flight).
+// Each block reduces one contiguous tile of nodes; each thread keeps kAlphaU nodes' loads in flight. The
+// coarse pass records every tile's float maxima (bit 31 set when a node of the tile needs the exact
+// evaluation regardless), so the exact pass skips the tiles that cannot hold a maximum: it evaluates the
+// same nodes, by the same rule, as a pass over all nodes would.
 constexpr int kAlphaU = 4;
+constexpr unsigned kTileExact = 0x80000000u;
+
+__device__ __forceinline__ void alpha_tile(size_t n, size_t& begin, size_t& end) {
+  const size_t per = (n + gridDim.x - 1) / gridDim.x;
+  begin = min(n, (size_t)blockIdx.x * per);
+  end = min(n, begin + per);
+}
 
 __global__ void __launch_bounds__(256) k_alpha2d_coarse(Dev2D d, unsigned long long* amax, int* status) {
-  const size_t n = (size_t)d.nx * d.ny, stride = (size_t)gridDim.x * blockDim.x;
+  __shared__ float s_m[2][8];
+  __shared__ int s_ex[8];
+  size_t begin, end;
+  alpha_tile((size_t)d.nx * d.ny, begin, end);
   float mx = 0.0f, my = 0.0f;
-  int bad = 0;
-  for (size_t o0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o0 < n; o0 += kAlphaU * stride) {
+  int bad = 0, ex = 0;
+  for (size_t o0 = begin + threadIdx.x; o0 < end; o0 += kAlphaU * blockDim.x) {
     float ax[kAlphaU], ay[kAlphaU];
     bool exact[kAlphaU], neg[kAlphaU];
 #pragma unroll
     for (int u = 0; u < kAlphaU; ++u) {
-      exact[u] = true;  // past the end: skipped
-      if (o0 + u * stride < n) alpha_coarse(d, o0 + u * stride, ax[u], ay[u], exact[u], neg[u]);
+      exact[u] = false;
+      neg[u] = true;  // past the end: skipped
+      if (o0 + u * blockDim.x < end) alpha_coarse(d, o0 + u * blockDim.x, ax[u], ay[u], exact[u], neg[u]);
     }
 #pragma unroll
     for (int u = 0; u < kAlphaU; ++u) {
-      if (exact[u]) continue;  // the exact pass evaluates (and, if need be, flags) this node
+      if (o0 + u * blockDim.x >= end) continue;
+      if (exact[u]) { ex = 1; continue; }  // the exact pass evaluates (and, if need be, flags) this node
       if (neg[u]) { bad |= HW_STATUS_DEPTH; continue; }
       mx = fmaxf(mx, ax[u]);
       my = fmaxf(my, ay[u]);
@@ -126,34 +140,48 @@ __global__ void __launch_bounds__(256) k_alpha2d_coarse(Dev2D d, unsigned long l
     mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
     my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, s));
   }
-  // non-negative floats order as their bit patterns; both maxima share the third 64-bit slot
-  unsigned int* m32 = reinterpret_cast<unsigned int*>(amax + 2);
-  if ((threadIdx.x & 31) == 0) {
+  ex = __any_sync(0xffffffffu, ex);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { s_m[0][w] = mx; s_m[1][w] = my; s_ex[w] = ex; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      mx = fmaxf(mx, s_m[0][k]);
+      my = fmaxf(my, s_m[1][k]);
+      ex |= s_ex[k];
+    }
+    // non-negative floats order as their bit patterns; both maxima share the third 64-bit slot
+    unsigned int* m32 = reinterpret_cast<unsigned int*>(amax + 2);
     atomicMax(m32, __float_as_uint(mx));
     atomicMax(m32 + 1, __float_as_uint(my));
+    const unsigned f = ex ? kTileExact : 0u;
+    reinterpret_cast<uint2*>(amax + 3)[blockIdx.x] = make_uint2(__float_as_uint(mx) | f, __float_as_uint(my) | f);
   }
   if (bad) atomicOr(status, bad);
 }
 
-// The nodes alpha_exact_range would evaluate, kAlphaU at a time.
+// The nodes alpha_exact_range would evaluate, in the tiles whose coarse maxima reach the thresholds.
 __global__ void __launch_bounds__(256) k_alpha2d_exact(Dev2D d, unsigned long long* amax, int* status) {
-  const size_t n = (size_t)d.nx * d.ny, stride = (size_t)gridDim.x * blockDim.x;
   const unsigned int* m32 = reinterpret_cast<const unsigned int*>(amax + 2);
   const float tx = __uint_as_float(m32[0]) * (1.0f - 1e-5f), ty = __uint_as_float(m32[1]) * (1.0f - 1e-5f);
+  const uint2 tile = reinterpret_cast<const uint2*>(amax + 3)[blockIdx.x];
+  if (!((tile.x | tile.y) & kTileExact) && __uint_as_float(tile.x) < tx && __uint_as_float(tile.y) < ty) return;
+  size_t begin, end;
+  alpha_tile((size_t)d.nx * d.ny, begin, end);
   unsigned long long kx = 0, ky = 0;
   int bad = 0;
-  for (size_t o0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o0 < n; o0 += kAlphaU * stride) {
+  for (size_t o0 = begin + threadIdx.x; o0 < end; o0 += kAlphaU * blockDim.x) {
     float fx[kAlphaU], fy[kAlphaU];
     bool exact[kAlphaU], neg[kAlphaU], in[kAlphaU];
 #pragma unroll
     for (int u = 0; u < kAlphaU; ++u) {
-      in[u] = o0 + u * stride < n;
-      if (in[u]) alpha_coarse(d, o0 + u * stride, fx[u], fy[u], exact[u], neg[u]);
+      in[u] = o0 + u * blockDim.x < end;
+      if (in[u]) alpha_coarse(d, o0 + u * blockDim.x, fx[u], fy[u], exact[u], neg[u]);
     }
 #pragma unroll
     for (int u = 0; u < kAlphaU; ++u)
       if (in[u] && alpha_needs_exact(fx[u], fy[u], exact[u], neg[u], tx, ty))
-        alpha_exact_node(d, o0 + u * stride, kx, ky, bad);
+        alpha_exact_node(d, o0 + u * blockDim.x, kx, ky, bad);
   }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) {
@@ -423,7 +451,7 @@ int set_kernel_attributes2d() { return 0; }
 void launch_alpha2d(const Dev2D& d, unsigned long long* amax, int* status, cudaStream_t st) {
   cudaMemsetAsync(amax, 0, 3 * sizeof(unsigned long long), st);
   const size_t n = (size_t)d.nx * d.ny;
-  int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 8);
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)kAlpha2dTiles);  // tiles: amax[3 ..]
   k_alpha2d_coarse<<<blocks, 256, 0, st>>>(d, amax, status);
   k_alpha2d_exact<<<blocks, 256, 0, st>>>(d, amax, status);
 }
