@@ -67,18 +67,18 @@ ALGO_BYTES_PER_NODE_STAGE = 216.0
 # benchmark at 2048^2, a one-pass capture; the node kernel at RK stage 3), valid only for the kernel sources
 # they were taken on (sources_sha); times the units of a launch.
 TRAFFIC = {
-    "sweep_x": {"bytes_per_unit": 231.5, "sha": "9f87d6a751d6f588"},
-    "sweep_y": {"bytes_per_unit": 235.5, "sha": "9f87d6a751d6f588"},
-    "node": {"bytes_per_unit": 535.2, "sha": "9f87d6a751d6f588"},
+    "sweep_x": {"bytes_per_unit": 231.4, "sha": "7cd94204e63c4974"},
+    "sweep_y": {"bytes_per_unit": 235.7, "sha": "7cd94204e63c4974"},
+    "node": {"bytes_per_unit": 534.9, "sha": "7cd94204e63c4974"},
 }
 # FP64-pipe instructions per unit (ncu --set full at 2048x1024: DFMA + DADD + DMUL thread instructions of
 # one launch over its units; the count per unit does not depend on the grid size). Part of the products
 # run on the integer pipes (each bit-identical to DMUL), so these are below the algorithmic "ops" above;
 # valid only for the kernel sources they were taken on (sources_sha).
 FP64_PIPE_OPS = {
-    "sweep_x": {"ops_per_unit": 341.9, "sha": "9f87d6a751d6f588"},
-    "sweep_y": {"ops_per_unit": 342.8, "sha": "9f87d6a751d6f588"},
-    "node": {"ops_per_unit": 243.0, "sha": "9f87d6a751d6f588"},
+    "sweep_x": {"ops_per_unit": 341.9, "sha": "7cd94204e63c4974"},
+    "sweep_y": {"ops_per_unit": 342.8, "sha": "7cd94204e63c4974"},
+    "node": {"ops_per_unit": 243.0, "sha": "7cd94204e63c4974"},
 }
 STATE_BYTES = 9 * NX * NY * 8
 
