@@ -9,10 +9,10 @@
 // Alpha passes stride over their items; sweep tiles and node items are taken by blocks one at a time from
 // counters, so a phase ends within one item of its last block; consecutive sweep tiles alternate between
 // two shared-memory buffers, so a tile costs one block barrier as in the per-phase kernels. The tile and
-// node code is the per-phase
-// kernels' (hw_batch.cu) with state, interface and base planes read by ordinary loads (they are written
-// by earlier phases of the same launch). Results equal the per-phase form's to rounding (the compiler
-// may contract multiply-adds differently in the two kernels).
+// node code is the per-phase kernels' (hw_batch.cu) with state, interface and base planes read by
+// ordinary loads (they are written by earlier phases of the same launch). Results equal the per-phase
+// form's bit for bit in every case tested (the same source; the compiler could in principle contract
+// multiply-adds differently in the two kernels).
 //
 // Every barrier wait is bounded: a block whose wait runs out (P.limit_ns on the global timer, or
 // P.limit_polls polls) sets HW_STATUS_TIMEOUT and the abort flag; every other block leaves at its next
@@ -38,10 +38,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid-wide barrier number ++phase (all threads of every block call it). Arrival is a release add by one thread after the block's barrier, the
-// wait an acquire load followed by the block's barrier, so every write made by any block before the grid
-// barrier is visible to every thread after it. Returns false if the block must leave the kernel (its own
-// wait ran out, or another block's did).
+// Grid-wide barrier number ++phase (all threads of every block call it). Arrival is a release add by one
+// thread after the block's barrier, the wait an acquire load followed by the block's barrier, so every
+// write made by any block before the grid barrier is visible to every thread after it. Returns false if
+// the block must leave the kernel (its own wait ran out, or another block's did).
 __device__ __forceinline__ bool grid_barrier(const StepItems& P, unsigned int& phase, int* status, int* s_flag) {
   StepSync* const s = P.sync;
   ++phase;
