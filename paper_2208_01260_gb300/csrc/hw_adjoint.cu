@@ -1144,15 +1144,28 @@ int hw_gauge_loss(hw_solver* s, int nsteps, const double* dts, const int* gauge_
   for (int g = 0; g < ngauge; ++g)
     if (gauge_idx[g] < 0 || (size_t)gauge_idx[g] >= v.n) return afail(HW_ERR_ARG, "hw_gauge_loss: gauge out of range");
   cudaStream_t st = v.stream;
-  std::vector<double> start(9 * v.n);
   double *d_save = nullptr, *d_g = nullptr;
   int* d_idx = nullptr;
-  ACUDA(cudaMalloc(&d_save, 9 * v.n * sizeof(double)));
-  ACUDA(cudaMalloc(&d_g, (size_t)nsteps * ngauge * sizeof(double)));
-  ACUDA(cudaMalloc(&d_idx, ngauge * sizeof(int)));
-  ACUDA(cudaMemcpyAsync(d_idx, gauge_idx, ngauge * sizeof(int), cudaMemcpyHostToDevice, st));
-  for (int q = 0; q < 9; ++q)
-    ACUDA(cudaMemcpyAsync(d_save + (size_t)q * v.n, v.state[q], v.n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // every exit after the first allocation frees the working buffers
+  auto check = [&](cudaError_t e, const char* what) {
+    if (rc == HW_OK && e != cudaSuccess) rc = afail(HW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  auto alloc = [&](void** p, size_t bytes, const char* what) {
+    if (rc != HW_OK) return;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      rc = afail(HW_ERR_NOMEM, std::string("hw_gauge_loss: allocation failed: ") + what);
+    }
+  };
+  alloc((void**)&d_save, 9 * v.n * sizeof(double), "saved state");
+  alloc((void**)&d_g, (size_t)nsteps * ngauge * sizeof(double), "gauge values");
+  alloc((void**)&d_idx, ngauge * sizeof(int), "gauge indices");
+  if (rc == HW_OK) {
+    check(cudaMemcpyAsync(d_idx, gauge_idx, ngauge * sizeof(int), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    for (int q = 0; q < 9; ++q)
+      check(cudaMemcpyAsync(d_save + (size_t)q * v.n, v.state[q], v.n * sizeof(double), cudaMemcpyDeviceToDevice, st),
+            "cudaMemcpyAsync");
+  }
   for (int j = 0; j < nsteps && rc == HW_OK; ++j) {
     rc = hw_rk3_step(s, dts[j]);
     hw::solver_view(s, &v);
@@ -1160,8 +1173,10 @@ int hw_gauge_loss(hw_solver* s, int nsteps, const double* dts, const int* gauge_
   }
   std::vector<double> g((size_t)nsteps * ngauge);
   if (rc == HW_OK) {
-    ACUDA(cudaMemcpyAsync(g.data(), d_g, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    ACUDA(cudaStreamSynchronize(st));
+    check(cudaMemcpyAsync(g.data(), d_g, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    check(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  }
+  if (rc == HW_OK) {
     *loss_out = misfit_loss(g.data(), eta_obs, g.size());
     if (eta_gauges) std::copy(g.begin(), g.end(), eta_gauges);
     double* src[9];
