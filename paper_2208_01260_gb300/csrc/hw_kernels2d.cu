@@ -195,22 +195,39 @@ __global__ void __launch_bounds__(256) k_alpha2d_exact(Dev2D d, unsigned long lo
   if (bad) atomicOr(status, bad);
 }
 
-// Single precision: the maximum in float, widened to a double key once per warp.
+// Single precision: the maximum in float, widened to a double key once per warp. Each thread keeps the
+// loads of kAlphaU nodes in flight (the pass is bound by memory latency otherwise).
 __global__ void __launch_bounds__(256) k_alpha2d_f32(Dev2DT<float> d, unsigned long long* amax, int* status) {
   int bad = 0;
-  const size_t n = (size_t)d.nx * d.ny;
+  const size_t n = (size_t)d.nx * d.ny, step = (size_t)gridDim.x * blockDim.x;
   float mx = 0.0f, my = 0.0f;
-  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
-    const float h = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
-    if (!(h > 0.0f) || !(h < 3e38f)) { bad |= h == h ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE; continue; }
-    const float rh = fast_rcp(h);
-    const float gh = d.g * h;
-    const float c = gh * fast_rsqrt(gh);
-    const float u = __ldg(d.S[1] + o) * rh, v = __ldg(d.S[2] + o) * rh;
-    const float ax = fabsf(u) + c, ay = fabsf(v) + c;
-    if (!(ax < 3e38f) || !(ay < 3e38f)) { bad |= HW_STATUS_NONFINITE; continue; }
-    mx = fmaxf(mx, ax);
-    my = fmaxf(my, ay);
+  for (size_t o0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o0 < n; o0 += kAlphaU * step) {
+    float hn[kAlphaU], mn[kAlphaU], wn[kAlphaU];
+#pragma unroll
+    for (int q = 0; q < kAlphaU; ++q) {
+      const size_t o = o0 + q * step;
+      hn[q] = 1.0f;
+      mn[q] = wn[q] = 0.0f;
+      if (o < n) {
+        hn[q] = __ldg(d.S[0] + o) - __ldg(d.stat[0] + o);
+        mn[q] = __ldg(d.S[1] + o);
+        wn[q] = __ldg(d.S[2] + o);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kAlphaU; ++q) {
+      if (o0 + q * step >= n) continue;
+      const float h = hn[q];
+      if (!(h > 0.0f) || !(h < 3e38f)) { bad |= h == h ? HW_STATUS_DEPTH : HW_STATUS_NONFINITE; continue; }
+      const float rh = fast_rcp(h);
+      const float gh = d.g * h;
+      const float c = gh * fast_rsqrt(gh);
+      const float u = mn[q] * rh, v = wn[q] * rh;
+      const float ax = fabsf(u) + c, ay = fabsf(v) + c;
+      if (!(ax < 3e38f) || !(ay < 3e38f)) { bad |= HW_STATUS_NONFINITE; continue; }
+      mx = fmaxf(mx, ax);
+      my = fmaxf(my, ay);
+    }
   }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) {
