@@ -118,9 +118,11 @@ int hw_rk3_step(hw_solver* s, double dt);
 int hw_rk3_stage(hw_solver* s, int k, double dt);
 
 /* nsteps RK3 steps with dt = CFL step computed on the device at the start of each step, clipped so
- * that the last step ends at t_end if t_end > 0 (stops early once t_end is reached). The steps run
- * from a captured CUDA graph when use_graph != 0. On return *t_out (may be NULL) holds the simulated
- * time advanced and *steps_out (may be NULL) the steps taken; synchronises the stream. */
+ * that the last step ends at t_end if t_end > 0 (stops early once t_end is reached: the host reads the
+ * time back after chunks of about half the steps left, and steps launched past t_end have size 0 and
+ * leave the state unchanged). The steps run from a captured CUDA graph when use_graph != 0. On return
+ * *t_out (may be NULL) holds the simulated time advanced and *steps_out (may be NULL) the steps taken
+ * (those of size 0 not counted); synchronises the stream. */
 int hw_advance(hw_solver* s, int nsteps, double t_end, int use_graph, double* t_out, int* steps_out);
 
 /* Read / write the state (the variables of Sec. 2 / Sec. 3: the physical layout h, hu, hv and their
