@@ -232,6 +232,63 @@ def oracle_rate(seconds_budget=60.0):
     return NX * NY * stages / elapsed, desc, threads, elapsed
 
 
+ONEDIM_RUNS = (("config1_n200_t0.2", "perturbed1d", 0.2), ("ex41_n1600_t0.1", "accuracy1d", 0.1))
+
+
+def _onedim_scenario(kind):
+    from paper_2208_01260_gb300 import scenarios as S
+    return S.perturbed1d() if kind == "perturbed1d" else S.accuracy1d(1600)
+
+
+def onedim(reps=5):
+    """The 1D scheme (Sec. 2.1-2.2) on the paper's 1D grid sizes: config 1 (N = 200, reflective, two bumps,
+    the 1e-3 pulse, epsilon 1e-10, CFL 0.6 to t = 0.2) and the accuracy sweep's largest grid (N = 1600,
+    periodic, Ex. 4.1 data, CFL steps to t = 0.1). Each run goes from the initial state to t_end through
+    hw_advance from its CUDA graph; host wall time around the call (it returns when the run is done),
+    median of `reps` runs after one untimed run. Grids of a few hundred nodes leave the GPU launch-bound."""
+    import torch
+    import paper_2208_01260_gb300 as hw
+    out = {}
+    for name, kind, t_end in ONEDIM_RUNS:
+        sc = _onedim_scenario(kind)
+        s = hw.Solver.from_scenario(sc, hw.make_params(eps_w=sc.eps_w))
+        st0 = s.state()
+        times = []
+        for r in range(reps + 1):
+            hw.hw_set_state(s.h, st0, hw.HW_LAYOUT_EQUILIBRIUM)
+            hw.hw_set_time(s.h, 0.0, 0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            t, n = s.advance(10 ** 6, t_end=t_end)
+            el = time.perf_counter() - t0
+            if r:
+                times.append(el)
+        s.close()
+        el = statistics.median(times)
+        out[name] = {"nx": sc.nx, "steps": n, "t_end": t, "run_ms": el * 1e3, "ms_per_step": el * 1e3 / n,
+                     "value": sc.nx * STAGES * n / el, "unit": UNIT}
+    out["how"] = ("whole run from the initial state to t_end through hw_advance (CUDA graph of two steps), host "
+                  "wall time, median of %d runs" % reps)
+    return out
+
+
+def oracle_onedim():
+    """The oracle on the runs of onedim(), one host core each (a 1D grid is one row: one OpenMP thread)."""
+    import oracle
+    out = {}
+    for name, kind, t_end in ONEDIM_RUNS:
+        sc = _onedim_scenario(kind)
+        g = oracle.make_grid(sc.nx, 1, sc.x0, sc.x1, bc_x=sc.bc_x)
+        p = oracle.make_params(eps_w=sc.eps_w)
+        st, stat = oracle.to_state1d(sc.h, sc.hu, sc.b, sc.deriv)
+        t0 = time.perf_counter()
+        _, t, n = oracle.run1d(g, p, st, stat, t_end)
+        el = time.perf_counter() - t0
+        out[name] = {"nx": sc.nx, "steps": n, "run_ms": el * 1e3, "value": sc.nx * STAGES * n / el, "unit": UNIT,
+                     "cores": 1}
+    return out
+
+
 def batched_compare(steps, n_inst=512, fixed=None):
     """Config 4: n_inst grids with nx, ny log-uniform in [64, 1024] (or all of size `fixed`) on
     [0,1]^2, reflective, seeded bathymetry and surface hump, each at its own CFL dt. Aggregate
@@ -541,6 +598,7 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=400, help="steps of the adjoint cost measurement (0 = skip)")
     ap.add_argument("--fp32-steps", type=int, default=200, help="steps of the single-precision variant (0 = skip)")
     ap.add_argument("--decomp-steps", type=int, default=10, help="steps of the block-decomposition comparison (0 = skip)")
+    ap.add_argument("--onedim-reps", type=int, default=5, help="timed runs of each 1D run (0 = skip)")
     ap.add_argument("--nx", type=int, default=2048, help="smaller grids for profiling captures only")
     ap.add_argument("--ny", type=int, default=2048)
     args = ap.parse_args()
@@ -728,7 +786,7 @@ def main():
             line[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     # (only in single-GPU runs: a scaling run measures the headline alone)
     if ws > 1:
-        args.batched_steps = args.adjoint_steps = args.fp32_steps = args.decomp_steps = 0
+        args.batched_steps = args.adjoint_steps = args.fp32_steps = args.decomp_steps = args.onedim_reps = 0
     if args.batched_steps > 0 and (NX, NY) == (2048, 2048):
         solver.close()
         extra("batched", lambda: dict(batched_compare(args.batched_steps, n_inst=args.batched_instances),
@@ -744,10 +802,15 @@ def main():
         extra("adjoint", lambda: adjoint_cost(nsteps=args.adjoint_steps))
     if args.fp32_steps > 0:
         extra("fp32", lambda: fp32_variant(args.fp32_steps))
+    if args.onedim_reps > 0:
+        extra("onedim", lambda: onedim(args.onedim_reps))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         def cpu():
             rate, desc, threads, el = oracle_rate()
-            return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc, "seconds": el}
+            out = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc, "seconds": el}
+            if args.onedim_reps > 0:
+                out["onedim"] = oracle_onedim()
+            return out
         extra("cpu_baseline", cpu)
     if rank == 0:
         print(json.dumps(line), flush=True)
