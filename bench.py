@@ -740,30 +740,38 @@ def main():
         hw.hw_get_state(solver.h, hout, hw.HW_LAYOUT_PHYSICAL)
     torch.cuda.synchronize()
     e2e_serial, _, _ = job_rate(NX * NY * STAGES * ke, time.perf_counter() - t0, ws)
-    # the same jobs (state up, one step, state down) through pipeline.JobPipeline: two solvers on their
-    # own streams and host threads, so one job's copies run during the other's step
-    from paper_2208_01260_gb300.pipeline import JobPipeline
-    pipe = JobPipeline(sc, hw.make_params(), lanes=2)
+    # the same jobs (state up, one step, state down) through the pipelines of pipeline.py: two solvers on
+    # their own streams and host threads (JobPipeline, the figure), and one solver whose copies run on an
+    # upload and a download stream during the neighbouring jobs' steps (StagedPipeline)
+    from paper_2208_01260_gb300.pipeline import JobPipeline, StagedPipeline
     outs = [[torch.empty(NY, NX, dtype=torch.float64).pin_memory().numpy() for _ in range(9)] for _ in range(2)]
-    pipe.run([hin] * 2, outs)  # warm-up
     kp = max(4, ke)
-    # three timed runs of kp jobs each; the median run is the figure (the host threads that feed the two
-    # lanes share the machine's cores, so a single run of a quarter second can catch a stall)
-    runs = []
-    for _ in range(3):
-        barrier(ws)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pipe.run([hin] * kp, [outs[i % 2] for i in range(kp)])
-        torch.cuda.synchronize()
-        runs.append(job_rate(NX * NY * STAGES * kp, time.perf_counter() - t0, ws)[0])
+
+    def pipeline_runs(pipe):
+        pipe.run([hin] * 2, outs)  # warm-up
+        # three timed runs of kp jobs each; the median run is the figure
+        runs = []
+        for _ in range(3):
+            barrier(ws)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pipe.run([hin] * kp, [outs[i % 2] for i in range(kp)])
+            torch.cuda.synchronize()
+            runs.append(job_rate(NX * NY * STAGES * kp, time.perf_counter() - t0, ws)[0])
+        pipe.close()
+        return runs
+    runs = pipeline_runs(JobPipeline(sc, hw.make_params(), lanes=2))
+    runs2 = pipeline_runs(StagedPipeline(sc, hw.make_params()))
     e2e_v = statistics.median(runs)
-    pipe.close()
     e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": STATE_BYTES,
            "d2h_bytes_per_step": STATE_BYTES, "steps": kp, "runs": runs,
            "how": "independent jobs (the 9-plane state uploaded from pinned host memory, one RK3 step, the state "
                   "downloaded), two solvers on their own streams and host threads (pipeline.JobPipeline); "
                   "median of three timed runs of `steps` jobs",
+           "staged": {"value": statistics.median(runs2), "runs": runs2, "steps": kp,
+                      "how": "the same jobs through one solver whose uploads and downloads run on their own streams "
+                             "through two device staging sets each way, while the neighbouring jobs step "
+                             "(pipeline.StagedPipeline: half the device memory)"},
            "serial": {"value": e2e_serial, "steps": ke,
                       "how": "one solver: upload, step, download, one job after the other"}}
 
