@@ -11,6 +11,13 @@
 #include "../../include/hwswe.h"
 #include "hw_internal.h"
 
+namespace hw {
+// 1D alpha's reduction with its finish in one launch (hw_kernels1d.cu): slot[0..1] are zero between
+// launches (cleared by each launch's last block); same alpha and step as the separate launches.
+void launch_alpha_finish1d(const Dev1D& d, unsigned long long* slot, int* status, double* alpha, double* dt_out,
+                           double cfl, const double* t_now, double t_end, cudaStream_t st);
+}  // namespace hw
+
 namespace {
 
 // NVTX range for the duration of one API call (a no-op unless a profiler is attached).
@@ -253,6 +260,7 @@ int hw_create(const hw_grid* grid, const hw_params* params, void* cuda_stream, h
   cudaError_t e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { s->cap_stream = nullptr; hw_destroy(s); return fail(HW_ERR_CUDA, cudaGetErrorString(e)); }
   e = cudaMemsetAsync(misc, 0, 16 * sizeof(double), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->amax + 2, 0, 2 * sizeof(unsigned long long), s->stream);  // 1D alpha slots
   if (e != cudaSuccess) { hw_destroy(s); return fail(HW_ERR_CUDA, cudaGetErrorString(e)); }
   bind_state(s, s->SA);
   *out = s;
@@ -360,11 +368,10 @@ static void enqueue_alpha(hw_solver* s, bool with_dt, double t_end) {
       hw::launch_finish_alpha2d(s->d2, s->amax, s->alpha, with_dt ? s->dt : nullptr, s->params.cfl,
                                 with_dt ? s->t : nullptr, t_end, s->stream);
     } else {
-      hw::launch_alpha1d(s->d1, s->amax, s->status, s->stream);
-      hw::launch_finish_alpha1d(s->d1, s->amax, s->alpha, with_dt ? s->dt : nullptr, s->params.cfl,
+      hw::launch_alpha_finish1d(s->d1, s->amax + 2, s->status, s->alpha, with_dt ? s->dt : nullptr, s->params.cfl,
                                 with_dt ? s->t : nullptr, t_end, s->stream);
     }
-  }, s->is2d() && !s->fp32 ? 3 : 2);  // reduction (two passes in 2D double) and finish
+  }, s->is2d() ? (s->fp32 ? 2 : 3) : 1);  // reduction (two passes in 2D double) and finish; one launch in 1D
 }
 
 // One stage: sweeps on the current state (alpha already in s->alpha), node kernel into the other
